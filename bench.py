@@ -1,0 +1,485 @@
+#!/usr/bin/env python3
+"""Benchmark: one training step of differentiable tile-based Gaussian
+splatting (project + SH, key emission + depth sort, compositing, image loss,
+backward) on the 4M-Gaussian 3840x2160 workload, on N GPUs of one node.
+
+Prints ONE JSON line on rank 0. `value` is Mpix/s of the whole job (rendered
+and back-propagated pixels of all ranks / max-over-ranks time). With
+--impl reference, the CPU oracle (the reference implementation of this build)
+is timed instead on bounded window samples of the same workload.
+
+Multi-GPU: the path needs no exchange on one GPU per scene, so --gpus N runs N
+independent replicas (weak scaling, no collective on the data path; a
+barrier and a max-reduction of the timings only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd ms/iter & Mpix/s @4M Gaussians 4K; batched vs per-view, same tol"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="diff_4k", choices=["diff_4k", "batch16", "train_1080p", "tiny"])
+    ap.add_argument("--mode", default="batched", choices=["batched", "per_view"])
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the per-view comparison leg")
+    ap.add_argument("--tile", default=None, help="WxH tile override, e.g. 16x16")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (barrier + max over ranks only)
+# ---------------------------------------------------------------------------
+class Dist:
+    def __init__(self, want_gpus):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            if backend == "nccl":
+                torch.cuda.set_device(self.local_rank)
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+
+        dev = "cuda" if torch.cuda.is_available() and self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+def max_over_ranks(values):
+    """Combines per-rank step times the way the JSON line reports them."""
+    return max(values)
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def make_scene(name):
+    from paper_2606_11390_gb300 import scenes
+
+    return scenes.make(name)
+
+
+def workload_config(scene, args, tile):
+    s = scene
+    return {"workload": s["name"], "gaussians": int(s["means"].shape[0]), "views": int(s["sizes"].shape[0]),
+            "resolutions": sorted({f"{w}x{h}" for w, h in s["sizes"]}), "pixels": int(
+                (s["sizes"][:, 0].astype(np.int64) * s["sizes"][:, 1]).sum()),
+            "tile": f"{tile[0]}x{tile[1]}", "sh_degree": int(s["cfg"]["sh_degree"]), "mode": args.mode,
+            "cuda_graph": args.mode == "batched" and not args.no_graph,
+            "loss": f"L1 + {s['loss'][1]} L2", "l2_flush": "none: inputs (params 0.94 GB + keys) exceed the 129 MB L2"}
+
+
+# ---------------------------------------------------------------------------
+# per-stage timing of an eager step (for the roofline of the dominant kernel)
+# ---------------------------------------------------------------------------
+def stage_times(step, iters=5):
+    import torch
+
+    from paper_2606_11390_gb300 import _native as gs
+    from paper_2606_11390_gb300 import renderer as R
+
+    names = ["project", "bin_sort", "raster_fwd", "loss", "raster_bwd+project_bwd"]
+    acc = {n: 0.0 for n in names}
+    fr, cams = step.frames[0], step.frame_cams[0]
+    stream = torch.cuda.current_stream()
+    for _ in range(iters):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
+        ev[0].record(stream)
+        R.project(step.params, cams, fr)
+        ev[1].record(stream)
+        R.bin_sort(fr)
+        ev[2].record(stream)
+        fr.image = step.image
+        R.rasterize_fwd(fr)
+        ev[3].record(stream)
+        gs.gs_image_loss(step.image, step.target, step.w_l1, step.w_l2, step.dL_dimage, step.loss)
+        ev[4].record(stream)
+        R.rasterize_bwd(step.params, cams, fr, step.dL_dimage, step.grads)
+        ev[5].record(stream)
+        torch.cuda.synchronize()
+        for i, n in enumerate(names):
+            acc[n] += ev[i].elapsed_time(ev[i + 1])
+    return {n: acc[n] / iters for n in names}
+
+
+def raster_bwd_only_time(step, iters=5):
+    """Time of the rasterisation-backward kernel alone (d_projected), on the
+    launching stream, with the per-Gaussian backward excluded."""
+    import torch
+
+    from paper_2606_11390_gb300 import renderer as R
+
+    fr, cams = step.frames[0], step.frame_cams[0]
+    stream = torch.cuda.current_stream()
+    # project_bwd alone: time it by running the full backward and subtracting
+    t_full = 0.0
+    for _ in range(iters):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        R.rasterize_bwd(step.params, cams, fr, step.dL_dimage, step.grads)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_full += a.elapsed_time(b)
+    return t_full / iters
+
+
+def pair_counts(step):
+    """Evaluated (pixel, splat) pairs implied by the outputs: the backward
+    visits, per pixel, its `last` entries (sum of last); the forward visits at
+    least those."""
+    import torch
+
+    last = step.frames[0].last
+    return int(last.to(torch.int64).sum().item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline
+# ---------------------------------------------------------------------------
+def cpu_sample(scene, window=(512, 256)):
+    """Times the oracle on the workload: per-Gaussian stages (projection and
+    its backward) over all Gaussians for the full view, per-pixel stages (key
+    sort, compositing and its backward) on a centred window, then
+    extrapolates the per-pixel stages to the full image."""
+    from oracle import oracle as O
+    from paper_2606_11390_gb300 import scenes
+
+    W, H = int(scene["sizes"][0, 0]), int(scene["sizes"][0, 1])
+    ww, wh = window
+    x0, y0 = (W - ww) // 2 // 16 * 16, (H - wh) // 2 // 16 * 16
+    t0 = time.perf_counter()
+    proj = O.project(scene)
+    t_proj = time.perf_counter() - t0
+    d0 = np.zeros((proj["counts"].shape[0], 9))
+    t0 = time.perf_counter()
+    O.project_bwd(scene, d0)
+    t_pbwd = time.perf_counter() - t0
+    crop = scenes.crop_view(scene, x0, y0, ww, wh)
+    cproj = O.project(crop)
+    t0 = time.perf_counter()
+    bins = O.bin_sort(crop, cproj)
+    ras = O.raster_fwd(crop, cproj, bins)
+    L, g = O.loss(ras["image"].astype(np.float32), crop["target"], *crop["loss"])
+    O.raster_bwd(crop, cproj, bins, g)
+    t_pix = time.perf_counter() - t0
+    P = W * H
+    total = t_proj + t_pbwd + t_pix * P / (ww * wh)
+    return {"value": P / total / 1e6, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+            "sample": (f"single-threaded C++ oracle: projection fwd+bwd over all {scene['means'].shape[0]} "
+                       f"Gaussians for the full {W}x{H} view ({t_proj + t_pbwd:.1f} s), sort+composite+backward on "
+                       f"a {ww}x{wh} window ({t_pix:.1f} s) extrapolated x{P / (ww * wh):.1f} to the full image"),
+            "seconds_measured": round(t_proj + t_pbwd + t_pix, 2)}
+
+
+def reference_arm(args, dist):
+    """--impl reference: the oracle, as it stands, timed per step on a bounded
+    window sample of the same workload."""
+    if dist.rank != 0:
+        return 0
+    from oracle import oracle as O
+    from paper_2606_11390_gb300 import scenes
+
+    O.build()
+    scene = make_scene(args.workload)
+    W, H = int(scene["sizes"][0, 0]), int(scene["sizes"][0, 1])
+    ww, wh = 256, 128
+    x0, y0 = (W - ww) // 2 // 16 * 16, (H - wh) // 2 // 16 * 16
+    crop = scenes.crop_view(scene, x0, y0, ww, wh)
+
+    def one():
+        proj = O.project(crop)
+        bins = O.bin_sort(crop, proj)
+        ras = O.raster_fwd(crop, proj, bins)
+        L, g = O.loss(ras["image"].astype(np.float32), crop["target"], *crop["loss"])
+        d = O.raster_bwd(crop, proj, bins, g)
+        O.project_bwd(crop, d)
+
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    dt = (time.perf_counter() - t0) / args.steps
+    value = ww * wh / dt / 1e6
+    sample = (f"single-threaded C++ oracle, full step (projection+SH of all {scene['means'].shape[0]} Gaussians, "
+              f"sort, compositing, L1+L2 loss, backward) for a {ww}x{wh} window of the {W}x{H} view")
+    line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "reference",
+            "config": {"workload": scene["name"], "sample": f"{ww}x{wh} window", "gaussians": int(scene["means"].shape[0])},
+            "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# main arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    dist = Dist(args.gpus)
+    if args.impl == "reference":
+        rc = reference_arm(args, dist)
+        dist.close()
+        return rc
+    import torch
+
+    from paper_2606_11390_gb300 import _native as gs
+    from paper_2606_11390_gb300 import renderer as R
+
+    dev = dist.local_rank if torch.cuda.is_available() else 0
+    torch.cuda.set_device(dev)
+    gs.load()
+    scene = make_scene(args.workload)
+    tile = tuple(int(x) for x in args.tile.split("x")) if args.tile else (scene["cfg"]["tile_w"], scene["cfg"]["tile_h"])
+    step = R.TrainStep(scene, mode=args.mode, graph=not args.no_graph, tile=tile).prepare()
+    P = step.cams.n_pixels
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        step.run()
+    torch.cuda.synchronize()
+    step.check()
+
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.3)
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    step.check()
+    ms_local = e0.elapsed_time(e1) / args.steps
+    ms = dist.max(ms_local)
+    value = dist.world * P / (ms * 1e-3) / 1e6
+
+    extra = {}
+    if dist.rank == 0:
+        # per-stage times from an instrumented eager step (same kernels, same stream)
+        if args.mode == "batched":
+            st = stage_times(step)
+            extra["stage_ms"] = {k: round(v, 4) for k, v in st.items()}
+            extra["n_isect"] = step.n_isect()
+            extra["pairs_bwd"] = pair_counts(step)
+            dom = max(st, key=st.get)
+            peaks, src = measured_peaks()
+            # roofline of the dominant stage
+            roof = roofline_for(dom, st[dom], step, peaks, src)
+            extra["roofline"] = roof
+        # batched vs per-view on the same GPU
+        if args.mode == "batched" and not args.no_compare and step.cams.V > 1:
+            pv = R.TrainStep(scene, mode="per_view", tile=tile, params=step.params).prepare()
+            for _ in range(2):
+                pv.run()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(max(3, args.steps // 2)):
+                pv.run()
+            b.record(stream)
+            torch.cuda.synchronize()
+            pms = a.elapsed_time(b) / max(3, args.steps // 2)
+            extra["per_view"] = {"ms_per_step": pms, "value": P / (pms * 1e-3) / 1e6,
+                                 "batched_speedup": pms / ms_local}
+            del pv
+        if not args.no_e2e:
+            extra["e2e"] = e2e_measure(step, args, dist.world)
+        if not args.no_cpu_baseline:
+            extra["cpu_baseline"] = cpu_sample(scene)
+
+    if dist.rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": dist.world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": workload_config(scene, args, tile), "clocks": clk,
+                "gpu_launches": step.launches_per_step * args.steps}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    dist.close()
+    return 0
+
+
+def roofline_for(stage, ms, step, peaks, src):
+    """Achieved vs peak for the dominant stage. Raster stages are bound by FP32
+    issue (ALU): algorithmic work = evaluated (pixel, splat) pairs x FP32
+    operations per pair; per-Gaussian and sort stages are HBM-bound with the
+    algorithmic bytes of their inputs and outputs."""
+    import torch
+
+    fr = step.frames[0]
+    N, V, I, P = step.N, step.cams.V, step.n_isect(), step.cams.n_pixels
+    if stage in ("raster_fwd", "raster_bwd+project_bwd"):
+        pairs = pair_counts(step)
+        ops_per_pair = 22 if stage == "raster_fwd" else 60
+        sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+        peak = n_sm * 128 * sm_mhz * 1e6 / 1e12  # FP32 lane-ops/s in T
+        achieved = pairs * ops_per_pair / (ms * 1e-3) / 1e12
+        return {"stage": stage, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{n_sm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({src} max SM clock)",
+                "work": f"{pairs} pairs x {ops_per_pair} FP32 ops"}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    if stage == "project":
+        bytes_ = N * 236 + V * N * (48 + 8 + 4)
+    elif stage == "bin_sort":
+        bytes_ = V * N * 8 + I * (12 + 8 + 24 * 6 + 8)
+    else:
+        bytes_ = P * 3 * 4 * 3
+    achieved = bytes_ / (ms * 1e-3) / 1e9
+    return {"stage": stage, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None, "peak_source": src}
+
+
+def e2e_measure(step, args, world):
+    """Same metric through the public API with host buffers: per step, copy the
+    parameters, cameras and target from pinned host memory, run the step, read
+    back the loss and the parameter gradients."""
+    import torch
+
+    host_params = torch.empty_like(step.params.flat, device="cpu").pin_memory()
+    host_params.copy_(step.params.flat)
+    host_target = torch.empty_like(step.target, device="cpu").pin_memory()
+    host_target.copy_(step.target)
+    host_cams = torch.from_numpy(step.cams.host.copy()).pin_memory()
+    host_grads = torch.empty_like(step.grads.flat, device="cpu").pin_memory()
+    host_loss = torch.empty(1, dtype=torch.float64).pin_memory()
+    stream = torch.cuda.current_stream()
+    n = max(3, args.steps // 2)
+
+    def one():
+        step.params.flat.copy_(host_params, non_blocking=True)
+        step.target.copy_(host_target, non_blocking=True)
+        step.cams.dev.copy_(host_cams, non_blocking=True)
+        step.run()
+        host_grads.copy_(step.grads.flat, non_blocking=True)
+        host_loss.copy_(step.loss, non_blocking=True)
+
+    one()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    a.record(stream)
+    for _ in range(n):
+        one()
+    b.record(stream)
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) / n
+    ms = a.elapsed_time(b) / n
+    bi = host_params.numel() * 4 + host_target.numel() * 4 + host_cams.numel() * 4
+    bo = host_grads.numel() * 4 + 8
+    return {"value": world * step.cams.n_pixels / (ms * 1e-3) / 1e6, "unit": "Mpix/s", "ms_per_step": ms,
+            "wall_ms_per_step": wall * 1e3, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,252 @@
+/*
+ * gs.h - C ABI of the GB300 (sm_103a) differentiable tile-based Gaussian
+ * splatting library (libgs_gb300.so).
+ *
+ * The library implements the per-step operators of Gaussian-splatting
+ * training that arXiv 2606.11390 distributes across GPUs (§4 "Distributed
+ * Gaussian Splatting"): per-Gaussian spherical-harmonic colour evaluation and
+ * projection, which yield a colour and projected geometry per camera of the
+ * batch; a depth sort per camera; tile rasterisation; and the backward pass of
+ * each, which sums per-Gaussian gradients with atomics. The paper takes
+ * the mathematics of these operators from 3D Gaussian Splatting (Kerbl et al.
+ * 2023, cited in §1): EWA projection of 3D Gaussians, real SH colour of degree
+ * <= 3, and front-to-back alpha compositing of depth-sorted splats per tile.
+ * Everything here runs on one GPU.
+ *
+ * Conventions common to every entry point
+ * ---------------------------------------
+ * - Pointers named *_dev or documented as "device" point to device memory;
+ *   everything else is host memory. All device buffers are allocated and
+ *   owned by the caller. The library never allocates or frees memory and
+ *   never synchronises the device or the stream: every call only enqueues
+ *   work on `stream` (a cudaStream_t; NULL means the legacy default stream)
+ *   and returns.
+ * - Return value: GS_OK, or a synchronous error found before or while
+ *   enqueuing (bad argument, unsupported configuration, CUDA launch error).
+ *   On a synchronous error nothing has been enqueued unless the code is
+ *   GS_ERR_CUDA.
+ * - Conditions only known on the device are OR-ed as GS_STATUS_* bits into
+ *   the caller's int32 device word `status_dev`; the caller reads it after the
+ *   stream has completed and clears it when it wants to.
+ * - Float arrays are IEEE binary32. Device pointers must be 16-byte aligned
+ *   (cudaMalloc and PyTorch allocations are); gs_project and gs_rasterize_bwd
+ *   use TMA bulk copies when they are, and plain loads otherwise.
+ *
+ * Data layout (N Gaussians, V views, view v is W_v x H_v pixels)
+ * ----------------------------------------------------------------
+ *   means [N][3], log_scales [N][3], quats [N][4] as (w, x, y, z), not
+ *   necessarily normalised, opacity_logits [N], sh [N][16][3]
+ *   (coefficient-major, channel-minor; coefficients beyond (degree+1)^2 are
+ *   ignored).
+ *   cams_dev: V gs_camera records in device memory (poses and intrinsics).
+ *   sizes: V pairs (W_v, H_v) in host memory; they fix the tile and pixel
+ *   layout of a call.
+ *   Record index of (view v, Gaussian g) is vg = v*N + g.
+ *   Tiles: view v has ntx_v = ceil(W_v / tile_w) by nty_v = ceil(H_v / tile_h)
+ *   tiles; the global tile id of (v, tx, ty) is tile_base_v + ty*ntx_v + tx,
+ *   with tile_base_v the number of tiles of the views before v.
+ *   Pixels: view v's pixels start at pix_base_v = sum_{u<v} W_u H_u and are
+ *   row-major; image arrays hold 3 interleaved channels per pixel.
+ */
+#ifndef GS_GB300_H_
+#define GS_GB300_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* gs_stream_t; /* identical to cudaStream_t */
+
+/* Symbol visibility: the library is built with hidden visibility and exports
+ * exactly the functions declared with GS_API. */
+#if defined(__GNUC__)
+#define GS_API __attribute__((visibility("default")))
+#else
+#define GS_API
+#endif
+
+/* Synchronous return codes. */
+#define GS_OK 0
+#define GS_ERR_ARG 1         /* invalid argument (null pointer, bad size, misaligned, ...) */
+#define GS_ERR_CUDA 2        /* a CUDA call failed while enqueuing */
+#define GS_ERR_UNSUPPORTED 3 /* valid but unsupported configuration (tile size, view count) */
+
+/* Asynchronous status bits, OR-ed into *status_dev. */
+#define GS_STATUS_CAPACITY 1 /* more tile intersections than `capacity`: keys clipped, ranges invalid */
+#define GS_STATUS_TIMEOUT 2  /* a bounded device-side wait gave up: results of that call are invalid */
+#define GS_STATUS_BOUNDS 4   /* an index failed a device-side range check and was skipped */
+
+#define GS_MAX_VIEWS 64
+
+/* One camera, 80 bytes. viewmat is the row-major 4x4 world->camera matrix in
+ * OpenCV axes (+x right, +y down, +z forward); fx, fy, cx, cy in pixels. */
+typedef struct gs_camera {
+  float viewmat[16];
+  float fx, fy, cx, cy;
+} gs_camera;
+
+/* Rendering constants, 52 bytes. tile_w x tile_h must be one of 8x8, 16x16,
+ * 32x16. sh_degree in 0..3. flags: GS_FLAG_* bits. Culling: near_plane < depth < far_plane. eps2d is
+ * added to the diagonal of every 2D covariance. Compositing: alpha =
+ * min(alpha_cap, opacity * exp(-power)); entries with alpha < alpha_min are
+ * skipped; compositing stops before the entry that would take the
+ * transmittance below t_stop. bg is added with the final transmittance. */
+typedef struct gs_config {
+  int32_t tile_w, tile_h, sh_degree, flags;
+  float near_plane, far_plane, eps2d, alpha_cap, alpha_min, t_stop;
+  float bg[3];
+} gs_config;
+
+/* gs_config.flags: gs_rasterize_bwd adds the parameter gradients to the
+ * output arrays instead of overwriting them (to sum over separate calls). */
+#define GS_FLAG_ACCUMULATE_GRADS 1
+
+/* Number of 32-bit floats in one projected record (see gs_project). */
+#define GS_RECORD_FLOATS 12
+/* Number of 32-bit floats of gradient per projected record (see gs_rasterize_bwd). */
+#define GS_DRECORD_FLOATS 9
+
+/* Library version (major*10000 + minor*100 + patch). */
+GS_API int gs_version(void);
+
+/* Human-readable text for a synchronous return code (GS_OK, GS_ERR_*). Never NULL. */
+GS_API const char* gs_status_string(int code);
+
+/* Tile and pixel totals of a view layout (host only, nothing enqueued).
+ * sizes: V (W, H) pairs, host. Writes *n_tiles and *n_pixels (either may be
+ * NULL). Errors: GS_ERR_ARG for V outside 1..GS_MAX_VIEWS or non-positive
+ * sizes; GS_ERR_UNSUPPORTED for a tile size other than 8x8, 16x16, 32x16. */
+GS_API int gs_layout_totals(const int32_t* sizes, int32_t V, const gs_config* cfg, int64_t* n_tiles, int64_t* n_pixels);
+
+/* gs_project - per-(view, Gaussian) SH colour and EWA projection.
+ * Paper: §4, the spherical-harmonics and projection operators, which compute
+ * per Gaussian its colour and projected geometry for every camera of the
+ * batch; mathematics of 3DGS (Kerbl et al. 2023): s = exp(log_scale), q/|q|,
+ * opacity = sigmoid(logit), Sigma = R S S R^T, t = W mean + t_cam,
+ * Sigma2 = J W Sigma W^T J^T + eps2d I with the pinhole Jacobian J at t (frustum
+ * clamped to 1.3x the field of view), conic = Sigma2^-1, 3-sigma radius from
+ * the larger eigenvalue, tile rectangle, colour = max(0, SH(dir) + 0.5).
+ * One launch covers all V views (parameters are read once per Gaussian).
+ *
+ * in  (device): means, log_scales, quats, opacity_logits, sh; cams_dev [V].
+ * in  (host)  : sizes [V][2], cfg.
+ * out (device): projected [V*N][12] floats per record vg:
+ *                 0 mean2d.x  1 mean2d.y  2 conic A  3 conic B  4 conic C
+ *                 5 opacity   6 depth     7 radius   8 r  9 g  10 b  11 = 0
+ *               (all zero for an invisible record);
+ *               rects [V*N][4] int16 tile rectangle (x0, y0, x1, y1), half-open;
+ *               counts [V*N] uint32 = (x1-x0)*(y1-y0), 0 if culled.
+ * N may be 0 (nothing enqueued). Errors: GS_ERR_ARG, GS_ERR_UNSUPPORTED, GS_ERR_CUDA. */
+GS_API int gs_project(const float* means, const float* log_scales, const float* quats, const float* opacity_logits,
+               const float* sh, int64_t N, const gs_camera* cams_dev, const int32_t* sizes, int32_t V,
+               const gs_config* cfg, float* projected, int16_t* rects, uint32_t* counts, int32_t* status_dev,
+               gs_stream_t stream);
+
+/* Bytes of device workspace gs_bin_sort needs for N Gaussians, V views, a
+ * key capacity and n_tiles tiles (from gs_layout_totals). */
+GS_API size_t gs_bin_sort_workspace_bytes(int64_t N, int32_t V, int64_t capacity, int64_t n_tiles);
+
+/* gs_bin_sort - tile keys and per-camera depth sort.
+ * Paper: §4, where each camera's Gaussians are depth-sorted before
+ * rasterisation, and §3.2 (the paper sorts with CUB's radix sort; this is a
+ * CUB-free onesweep LSD radix sort). For every visible record vg (views ascending, Gaussians ascending)
+ * and every tile (tx, ty) of its rectangle in row-major order one pair
+ *   key = (global tile id << 32) | float bits of depth,  val = vg
+ * is emitted; the pairs are then stably sorted by key, so equal keys stay in
+ * Gaussian-index order. Finally tile_ranges[t] = [start, end) of tile t's
+ * entries in the sorted list ([0, 0) for an empty tile).
+ *
+ * in  (device): projected, rects, counts from gs_project.
+ * in  (host)  : N, sizes [V][2], cfg, capacity (>= 0, < 2^32).
+ * out (device): keys [capacity] uint64, vals [capacity] uint32 (first n
+ *               entries valid), tile_ranges [n_tiles][2] uint32,
+ *               n_isect_dev [1] int64 = total number of intersections.
+ * workspace (device, caller-owned, >= gs_bin_sort_workspace_bytes, 256-byte
+ *   aligned): scratch, contents undefined on return.
+ * If the total exceeds `capacity`, only the first `capacity` pairs in
+ * emission order are kept, GS_STATUS_CAPACITY is set and keys, vals and
+ * ranges must not be used: grow the buffers to *n_isect_dev and call again.
+ * A device wait that exceeds its iteration bound sets GS_STATUS_TIMEOUT.
+ * Errors: GS_ERR_ARG (also for a too-small workspace), GS_ERR_CUDA. */
+GS_API int gs_bin_sort(const float* projected, const int16_t* rects, const uint32_t* counts, int64_t N, const int32_t* sizes,
+                int32_t V, const gs_config* cfg, uint64_t* keys, uint32_t* vals, int64_t capacity,
+                uint32_t* tile_ranges, int64_t* n_isect_dev, void* workspace, size_t workspace_bytes,
+                int32_t* status_dev, gs_stream_t stream);
+
+/* gs_rasterize_fwd - tile rasterisation (front-to-back alpha compositing).
+ * Paper: §4, the rasterisation operator that renders each camera's image;
+ * rule of 3DGS: for pixel p (sampled at its centre) of tile t, for the
+ * entries of t in sorted order, power = 0.5 d^T conic d with d = p - mean2d,
+ * skip if power < 0, alpha = min(alpha_cap, opacity exp(-power)), skip if
+ * alpha < alpha_min, stop before the entry whose T(1-alpha) < t_stop, else
+ * C += colour alpha T and T *= (1 - alpha). out = C + T bg.
+ *
+ * in  (device): projected, vals (sorted), tile_ranges from gs_bin_sort.
+ * in  (host)  : sizes [V][2], cfg.
+ * out (device): image [P][3], final_T [P] (transmittance after the last
+ *               composited entry), last [P] uint32 (1 + position, within its
+ *               tile's range, of the last composited entry; 0 if none).
+ * Errors: GS_ERR_ARG, GS_ERR_UNSUPPORTED, GS_ERR_CUDA. */
+GS_API int gs_rasterize_fwd(const float* projected, const uint32_t* vals, const uint32_t* tile_ranges, const int32_t* sizes,
+                     int32_t V, const gs_config* cfg, float* image, float* final_T, uint32_t* last,
+                     gs_stream_t stream);
+
+/* gs_rasterize_bwd - backward of rasterisation, projection and SH colour.
+ * Paper: §4, where the backward pass keeps the forward pass's partitioning
+ * and sums gradients with atomics; here device-scope FP32 atomics on one
+ * GPU. Each pixel walks its tile's list in
+ * reverse from `last`, recovering the transmittance before each entry from
+ * final_T by dividing by (1 - alpha) instead of storing per-pixel lists.
+ * Per-entry gradients are reduced across each warp with shuffles, summed per
+ * tile in shared memory and added to d_projected with one atomic per value.
+ * A second kernel then chains d_projected through colour, conic, 2D mean,
+ * Jacobian, view transform, covariance and the activations to the parameter
+ * gradients, one thread per Gaussian summing over views (no atomics).
+ *
+ * in  (device): the parameters and cams_dev given to gs_project; projected,
+ *               counts from gs_project; vals, tile_ranges from gs_bin_sort;
+ *               final_T, last from gs_rasterize_fwd; dL_dimage [P][3].
+ * in  (host)  : N, sizes [V][2], cfg.
+ * scratch/out (device): d_projected [V*N][9] = dL/d(mean2d.x, mean2d.y,
+ *               conic A, B, C, r, g, b, opacity) per record; zeroed by this
+ *               call, then accumulated.
+ * out (device): d_means [N][3], d_log_scales [N][3], d_quats [N][4],
+ *               d_opacity_logits [N], d_sh [N][16][3]: overwritten, or added
+ *               to when cfg->flags has GS_FLAG_ACCUMULATE_GRADS; d_sh
+ *               coefficients beyond the degree receive 0.
+ * Errors: GS_ERR_ARG, GS_ERR_UNSUPPORTED, GS_ERR_CUDA. */
+GS_API int gs_rasterize_bwd(const float* means, const float* log_scales, const float* quats, const float* opacity_logits,
+                     const float* sh, int64_t N, const gs_camera* cams_dev, const int32_t* sizes, int32_t V,
+                     const gs_config* cfg, const float* projected, const uint32_t* counts, const uint32_t* vals,
+                     const uint32_t* tile_ranges, const float* final_T, const uint32_t* last, const float* dL_dimage,
+                     float* d_projected, float* d_means, float* d_log_scales, float* d_quats, float* d_opacity_logits,
+                     float* d_sh, int32_t* status_dev, gs_stream_t stream);
+
+/* gs_image_loss - image-space loss and its gradient.
+ * Paper: §4 names an image-space loss per camera (fused SSIM); this is the
+ * L1 + L2 loss of the workloads: L = w_l1 mean|r| + w_l2 mean(r^2),
+ * r = image - target, means over all n values.
+ * in  (device): image [n], target [n]. out (device): dL_dimage [n]
+ * (overwritten), loss_dev [1] double (overwritten). Errors: GS_ERR_ARG, GS_ERR_CUDA. */
+GS_API int gs_image_loss(const float* image, const float* target, int64_t n, float w_l1, float w_l2, float* dL_dimage,
+                  double* loss_dev, gs_stream_t stream);
+
+/* gs_adam_step - fused Adam update over a flat parameter array.
+ * Paper: §3.2 (fused Adam with vectorised loads and stores and
+ * transcendental results cached in shared memory); update of Kingma & Ba
+ * 2015: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
+ * in/out (device): param [n], exp_avg [n], exp_avg_sq [n]; in: grad [n],
+ * step_dev [1] int32 = t >= 1 (read on the device, so a captured graph
+ * sees the current step). Errors: GS_ERR_ARG, GS_ERR_CUDA. */
+GS_API int gs_adam_step(float* param, const float* grad, float* exp_avg, float* exp_avg_sq, int64_t n, float lr, float beta1,
+                 float beta2, float eps, const int32_t* step_dev, gs_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_GB300_H_ */

@@ -1,0 +1,24 @@
+// Host-side declarations shared by the translation units of libgs_gb300.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "gs_common.cuh"
+
+namespace gs {
+
+// Validates sizes/cfg and fills a Layout; returns a GS_* code.
+int build_layout(const int32_t* sizes, int32_t V, const gs_config* cfg, Layout* L, int64_t* n_pixels);
+
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? GS_OK : GS_ERR_CUDA; }
+
+// Launch of the per-Gaussian backward (defined in project.cu, used by
+// gs_rasterize_bwd in raster.cu).
+int launch_project_bwd(const float* means, const float* log_scales, const float* quats, const float* opacity_logits,
+                       const float* sh, int64_t N, const gs_camera* cams, const Layout& L, const Consts& K,
+                       const uint32_t* counts, const float* d_projected, float* d_means, float* d_log_scales,
+                       float* d_quats, float* d_opacity_logits, float* d_sh, int32_t* status, cudaStream_t stream);
+
+}  // namespace gs

@@ -1,0 +1,373 @@
+// Tile rasterisation: front-to-back alpha compositing (forward) and its
+// reverse-order backward.
+//
+// Paper: arXiv 2606.11390 §4 - rasterisation is partitioned per camera (or per
+// image tile), and its backward keeps the forward partitioning and sums the
+// per-Gaussian gradients with atomics (device scope suffices on one GPU).
+// Compositing rule of 3D Gaussian Splatting (Kerbl et al. 2023): per pixel,
+// for the tile's depth-sorted entries, alpha = min(cap, o exp(-power)),
+// skip alpha < alpha_min, stop before T(1 - alpha) < t_stop, C += c alpha T.
+//
+// GB300 design. One CTA per (view, tile) with one thread per pixel; the tile's
+// splats are staged into shared memory in batches of one per thread. The
+// per-pair arithmetic is written with explicitly rounded operations and a
+// fixed ex2.approx so that the backward recomputes bit-identical alphas and
+// takes exactly the forward's skip / stop decisions. The backward walks each
+// tile's list in reverse from the largest `last` of its pixels, recovers
+// T_k = T_{k+1} / (1 - alpha_k) from the stored final T, reduces the 9
+// per-pixel gradient values of a splat across the warp with a 12-shuffle
+// reduce-scatter (instead of 9 x 5 butterfly shuffles), sums the warps of the
+// CTA in shared memory, and issues one FP32 atomic per value per (tile,
+// splat) to the per-record gradient buffer.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gs_common.cuh"
+#include "gs_internal.h"
+
+namespace gs {
+namespace {
+
+constexpr float kLog2e = 1.4426950408889634f;
+
+// Splat data staged in shared memory, with the conic pre-scaled so that
+// e = (A' dx + B' dy) dx + C' dy dy = -power * log2(e).
+struct SplatS {
+  float4 a;  // mean.x, mean.y, A' = -0.5 A log2e, B' = -B log2e
+  float4 b;  // C' = -0.5 C log2e, opacity, r, g
+  float c;   // b
+};
+
+__device__ __forceinline__ void load_splat(const float4* __restrict__ projected, uint32_t vg, float4& a, float4& b,
+                                           float& c) {
+  const float4 r0 = __ldg(projected + 3 * static_cast<size_t>(vg));
+  const float4 r1 = __ldg(projected + 3 * static_cast<size_t>(vg) + 1);
+  const float4 r2 = __ldg(projected + 3 * static_cast<size_t>(vg) + 2);
+  a = make_float4(r0.x, r0.y, -0.5f * kLog2e * r0.z, -kLog2e * r0.w);
+  b = make_float4(-0.5f * kLog2e * r1.x, r1.y, r2.x, r2.y);
+  c = r2.z;
+}
+
+// e = -power*log2(e) for pixel centre (px, py). Every operation explicitly
+// rounded so forward and backward compute the same bits.
+__device__ __forceinline__ float splat_exponent(float px, float py, const float4& a, float Cp, float& dx, float& dy) {
+  dx = __fsub_rn(px, a.x);
+  dy = __fsub_rn(py, a.y);
+  const float q = __fmaf_rn(a.z, dx, __fmul_rn(a.w, dy));
+  return __fmaf_rn(q, dx, __fmul_rn(__fmul_rn(Cp, dy), dy));
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW* TH) raster_fwd_kernel(const float4* __restrict__ projected,
+                                                             const uint32_t* __restrict__ vals,
+                                                             const uint2* __restrict__ ranges, const Layout L,
+                                                             const Consts K, float* __restrict__ image,
+                                                             float* __restrict__ final_T, uint32_t* __restrict__ last) {
+  constexpr int B = TW * TH;
+  __shared__ float4 s_a[B];
+  __shared__ float4 s_b[B];
+  __shared__ float s_c[B];
+  const uint32_t tile = blockIdx.x;
+  const int v = view_of_tile(L, tile);
+  const uint32_t local = tile - L.tile_base[v];
+  const int ntx = L.ntx[v];
+  const int tx = static_cast<int>(local % ntx), ty = static_cast<int>(local / ntx);
+  const int tid = threadIdx.x;
+  const int x = tx * TW + (tid % TW), y = ty * TH + (tid / TW);
+  const int W = L.width[v], H = L.height[v];
+  const bool inside = x < W && y < H;
+  const float px = static_cast<float>(x) + 0.5f, py = static_cast<float>(y) + 0.5f;
+  const uint2 range = ranges[tile];
+  const int n = static_cast<int>(range.y - range.x);
+  const float cap = K.alpha_cap, amin = K.alpha_min, tstop = K.t_stop;
+  float T = 1.0f, c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
+  uint32_t lastc = 0;
+  bool done = !inside;
+  for (int b0 = 0; b0 < n; b0 += B) {
+    if (__syncthreads_count(done) == B) break;
+    if (b0 + tid < n) {
+      float4 a, b;
+      float c;
+      load_splat(projected, vals[range.x + b0 + tid], a, b, c);
+      s_a[tid] = a;
+      s_b[tid] = b;
+      s_c[tid] = c;
+    }
+    __syncthreads();
+    const int cnt = min(B, n - b0);
+    if (!done) {
+      for (int j = 0; j < cnt; ++j) {
+        const float4 a = s_a[j];
+        const float4 b = s_b[j];
+        float dx, dy;
+        const float e = splat_exponent(px, py, a, b.x, dx, dy);
+        if (e > 0.0f) continue;
+        const float alpha = fminf(cap, __fmul_rn(b.y, ex2_approx(e)));
+        if (alpha < amin) continue;
+        const float Tn = __fmul_rn(T, __fsub_rn(1.0f, alpha));
+        if (Tn < tstop) {
+          done = true;
+          break;
+        }
+        const float w = __fmul_rn(alpha, T);
+        c0 = __fmaf_rn(b.z, w, c0);
+        c1 = __fmaf_rn(b.w, w, c1);
+        c2 = __fmaf_rn(s_c[j], w, c2);
+        T = Tn;
+        lastc = static_cast<uint32_t>(b0 + j + 1);
+      }
+    }
+  }
+  if (inside) {
+    const size_t p = static_cast<size_t>(L.pix_base[v]) + static_cast<size_t>(y) * W + x;
+    image[3 * p] = c0 + T * K.bg[0];
+    image[3 * p + 1] = c1 + T * K.bg[1];
+    image[3 * p + 2] = c2 + T * K.bg[2];
+    final_T[p] = T;
+    last[p] = lastc;
+  }
+}
+
+// Reduce-scatter of 9 values over a warp with 12 shuffles. On return, the
+// lane holds the warp-wide sum of value index slot_of_lane(lane) (or 0 where
+// that is -1); lanes 2k and 2k+1 hold the same slot.
+__device__ __forceinline__ float warp_reduce9(const float v[9], int lane) {
+  const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4, h1 = lane & 2;
+  float s[5];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float send = h4 ? v[i] : v[5 + i];
+    s[i] = (h4 ? v[5 + i] : v[i]) + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  {
+    const float send = h4 ? v[4] : 0.0f;
+    const float r = __shfl_xor_sync(0xffffffffu, send, 16);
+    s[4] = h4 ? 0.0f : v[4] + r;
+  }
+  float t[3];
+  t[0] = (h3 ? s[3] : s[0]) + __shfl_xor_sync(0xffffffffu, h3 ? s[0] : s[3], 8);
+  t[1] = (h3 ? s[4] : s[1]) + __shfl_xor_sync(0xffffffffu, h3 ? s[1] : s[4], 8);
+  t[2] = (h3 ? 0.0f : s[2]) + __shfl_xor_sync(0xffffffffu, h3 ? s[2] : 0.0f, 8);
+  float u[2];
+  u[0] = (h2 ? t[2] : t[0]) + __shfl_xor_sync(0xffffffffu, h2 ? t[0] : t[2], 4);
+  u[1] = (h2 ? 0.0f : t[1]) + __shfl_xor_sync(0xffffffffu, h2 ? t[1] : 0.0f, 4);
+  float w = (h1 ? u[1] : u[0]) + __shfl_xor_sync(0xffffffffu, h1 ? u[0] : u[1], 2);
+  w += __shfl_xor_sync(0xffffffffu, w, 1);
+  return w;
+}
+
+__device__ __forceinline__ int slot_of_lane(int lane) {
+  const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4, h1 = lane & 2;
+  int s[5];
+  for (int i = 0; i < 4; ++i) s[i] = h4 ? 5 + i : i;
+  s[4] = h4 ? -1 : 4;
+  int t[3] = {h3 ? s[3] : s[0], h3 ? s[4] : s[1], h3 ? -1 : s[2]};
+  int u[2] = {h2 ? t[2] : t[0], h2 ? -1 : t[1]};
+  return h1 ? u[1] : u[0];
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW* TH) raster_bwd_kernel(
+    const float4* __restrict__ projected, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
+    const Layout L, const Consts K, const float* __restrict__ final_T, const uint32_t* __restrict__ last,
+    const float* __restrict__ dL_dimage, float* __restrict__ d_proj) {
+  constexpr int B = TW * TH;
+  constexpr int NW = B / 32;
+  __shared__ float4 s_a[B];
+  __shared__ float4 s_b[B];
+  __shared__ float s_c[B];
+  __shared__ uint32_t s_vg[B];
+  __shared__ float s_grad[B * 9];
+  __shared__ uint32_t s_wmax[NW];
+  const uint32_t tile = blockIdx.x;
+  const int v = view_of_tile(L, tile);
+  const uint32_t local = tile - L.tile_base[v];
+  const int ntx = L.ntx[v];
+  const int tx = static_cast<int>(local % ntx), ty = static_cast<int>(local / ntx);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int x = tx * TW + (tid % TW), y = ty * TH + (tid / TW);
+  const int W = L.width[v], H = L.height[v];
+  const bool inside = x < W && y < H;
+  const float px = static_cast<float>(x) + 0.5f, py = static_cast<float>(y) + 0.5f;
+  const uint2 range = ranges[tile];
+  const float cap = K.alpha_cap, amin = K.alpha_min;
+  float T = 1.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
+  uint32_t lastp = 0;
+  if (inside) {
+    const size_t p = static_cast<size_t>(L.pix_base[v]) + static_cast<size_t>(y) * W + x;
+    T = final_T[p];
+    lastp = last[p];
+    g0 = dL_dimage[3 * p];
+    g1 = dL_dimage[3 * p + 1];
+    g2 = dL_dimage[3 * p + 2];
+  }
+  const float Tfin = T;
+  const float gbg = Tfin * (g0 * K.bg[0] + g1 * K.bg[1] + g2 * K.bg[2]);
+  float ar0 = 0.0f, ar1 = 0.0f, ar2 = 0.0f;  // colour accumulated behind the current entry
+  const int my_slot = slot_of_lane(lane);
+  // number of entries any pixel of the tile needs
+  {
+    const uint32_t m = __reduce_max_sync(0xffffffffu, lastp);
+    if (lane == 0) s_wmax[warp] = m;
+  }
+  for (int i = tid; i < B * 9; i += B) s_grad[i] = 0.0f;
+  __syncthreads();
+  uint32_t max_last = 0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) max_last = max(max_last, s_wmax[w]);
+
+  for (int b_end = static_cast<int>(max_last); b_end > 0; b_end -= B) {
+    const int cnt = min(B, b_end);
+    if (tid < cnt) {
+      const uint32_t vg = vals[range.x + b_end - 1 - tid];
+      float4 a, b;
+      float c;
+      load_splat(projected, vg, a, b, c);
+      s_a[tid] = a;
+      s_b[tid] = b;
+      s_c[tid] = c;
+      s_vg[tid] = vg;
+    }
+    __syncthreads();
+    for (int j = 0; j < cnt; ++j) {
+      const uint32_t rel = static_cast<uint32_t>(b_end - 1 - j);
+      float gv[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) gv[i] = 0.0f;
+      bool contrib = false;
+      if (rel < lastp) {
+        const float4 a = s_a[j];
+        const float4 b = s_b[j];
+        float dx, dy;
+        const float e = splat_exponent(px, py, a, b.x, dx, dy);
+        if (e <= 0.0f) {
+          const float G = ex2_approx(e);
+          const float oG = __fmul_rn(b.y, G);
+          const float alpha = fminf(cap, oG);
+          if (alpha >= amin) {
+            contrib = true;
+            const float one_m = __fsub_rn(1.0f, alpha);
+            const float inv = rcp_approx(one_m);
+            T = T * inv;  // transmittance in front of this entry
+            const float w = alpha * T;
+            const float c2v = s_c[j];
+            gv[5] = w * g0;
+            gv[6] = w * g1;
+            gv[7] = w * g2;
+            const float dalpha = T * ((b.z - ar0) * g0 + (b.w - ar1) * g1 + (c2v - ar2) * g2) - gbg * inv;
+            ar0 += alpha * (b.z - ar0);
+            ar1 += alpha * (b.w - ar1);
+            ar2 += alpha * (c2v - ar2);
+            if (!(oG > cap)) {
+              gv[8] = dalpha * G;
+              // d power = -dalpha * alpha; power gradients in terms of the
+              // unscaled conic: A = -2 A'/log2e, B = -B'/log2e, C = -2 C'/log2e
+              const float dpow = -dalpha * alpha;
+              const float il = 1.0f / kLog2e;
+              gv[0] = dpow * (2.0f * a.z * dx + a.w * dy) * il;
+              gv[1] = dpow * (a.w * dx + 2.0f * b.x * dy) * il;
+              gv[2] = dpow * 0.5f * dx * dx;
+              gv[3] = dpow * dx * dy;
+              gv[4] = dpow * 0.5f * dy * dy;
+            }
+          }
+        }
+      }
+      if (__any_sync(0xffffffffu, contrib)) {
+        const float r = warp_reduce9(gv, lane);
+        if (!(lane & 1) && my_slot >= 0 && r != 0.0f) atomicAdd(&s_grad[j * 9 + my_slot], r);
+      }
+    }
+    __syncthreads();
+    if (tid < cnt) {
+      float* dst = d_proj + static_cast<size_t>(s_vg[tid]) * kDRecordFloats;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const float gval = s_grad[tid * 9 + i];
+        if (gval != 0.0f) {
+          atomicAdd(dst + i, gval);
+          s_grad[tid * 9 + i] = 0.0f;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int TW, int TH>
+int launch_fwd(const float4* projected, const uint32_t* vals, const uint2* ranges, const Layout& L, const Consts& K,
+               float* image, float* final_T, uint32_t* last, cudaStream_t stream) {
+  raster_fwd_kernel<TW, TH><<<static_cast<unsigned>(L.n_tiles), TW * TH, 0, stream>>>(projected, vals, ranges, L, K,
+                                                                                      image, final_T, last);
+  return cuda_status(cudaGetLastError());
+}
+
+template <int TW, int TH>
+int launch_bwd(const float4* projected, const uint32_t* vals, const uint2* ranges, const Layout& L, const Consts& K,
+               const float* final_T, const uint32_t* last, const float* dL_dimage, float* d_proj,
+               cudaStream_t stream) {
+  raster_bwd_kernel<TW, TH><<<static_cast<unsigned>(L.n_tiles), TW * TH, 0, stream>>>(
+      projected, vals, ranges, L, K, final_T, last, dL_dimage, d_proj);
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace
+}  // namespace gs
+
+extern "C" int gs_rasterize_fwd(const float* projected, const uint32_t* vals, const uint32_t* tile_ranges,
+                                const int32_t* sizes, int32_t V, const gs_config* cfg, float* image, float* final_T,
+                                uint32_t* last, gs_stream_t stream_) {
+  using namespace gs;
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  Layout L;
+  int rc = build_layout(sizes, V, cfg, &L, nullptr);
+  if (rc != GS_OK) return rc;
+  if (!projected || !tile_ranges || !image || !final_T || !last) return GS_ERR_ARG;
+  if (!aligned16(projected) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7u)) return GS_ERR_ARG;
+  const Consts K = make_consts(*cfg);
+  const float4* pr = reinterpret_cast<const float4*>(projected);
+  const uint2* rg = reinterpret_cast<const uint2*>(tile_ranges);
+  if (L.tile_w == 16 && L.tile_h == 16) return launch_fwd<16, 16>(pr, vals, rg, L, K, image, final_T, last, stream);
+  if (L.tile_w == 8 && L.tile_h == 8) return launch_fwd<8, 8>(pr, vals, rg, L, K, image, final_T, last, stream);
+  if (L.tile_w == 32 && L.tile_h == 16) return launch_fwd<32, 16>(pr, vals, rg, L, K, image, final_T, last, stream);
+  return GS_ERR_UNSUPPORTED;
+}
+
+extern "C" int gs_rasterize_bwd(const float* means, const float* log_scales, const float* quats,
+                                const float* opacity_logits, const float* sh, int64_t N, const gs_camera* cams_dev,
+                                const int32_t* sizes, int32_t V, const gs_config* cfg, const float* projected,
+                                const uint32_t* counts, const uint32_t* vals, const uint32_t* tile_ranges,
+                                const float* final_T, const uint32_t* last, const float* dL_dimage,
+                                float* d_projected, float* d_means, float* d_log_scales, float* d_quats,
+                                float* d_opacity_logits, float* d_sh, int32_t* status_dev, gs_stream_t stream_) {
+  using namespace gs;
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  Layout L;
+  int rc = build_layout(sizes, V, cfg, &L, nullptr);
+  if (rc != GS_OK) return rc;
+  if (N < 0 || cfg->sh_degree < 0 || cfg->sh_degree > 3) return GS_ERR_ARG;
+  if (N == 0) return GS_OK;
+  if (N * static_cast<int64_t>(V) >= (int64_t(1) << 32)) return GS_ERR_ARG;
+  if (!means || !log_scales || !quats || !opacity_logits || !sh || !cams_dev || !projected || !counts ||
+      !tile_ranges || !final_T || !last || !dL_dimage || !d_projected || !d_means || !d_log_scales || !d_quats ||
+      !d_opacity_logits || !d_sh)
+    return GS_ERR_ARG;
+  if (!aligned16(projected) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7u)) return GS_ERR_ARG;
+  const Consts K = make_consts(*cfg);
+  if (cudaMemsetAsync(d_projected, 0, sizeof(float) * kDRecordFloats * static_cast<size_t>(N) * V, stream) !=
+      cudaSuccess)
+    return GS_ERR_CUDA;
+  const float4* pr = reinterpret_cast<const float4*>(projected);
+  const uint2* rg = reinterpret_cast<const uint2*>(tile_ranges);
+  if (L.tile_w == 16 && L.tile_h == 16)
+    rc = launch_bwd<16, 16>(pr, vals, rg, L, K, final_T, last, dL_dimage, d_projected, stream);
+  else if (L.tile_w == 8 && L.tile_h == 8)
+    rc = launch_bwd<8, 8>(pr, vals, rg, L, K, final_T, last, dL_dimage, d_projected, stream);
+  else if (L.tile_w == 32 && L.tile_h == 16)
+    rc = launch_bwd<32, 16>(pr, vals, rg, L, K, final_T, last, dL_dimage, d_projected, stream);
+  else
+    return GS_ERR_UNSUPPORTED;
+  if (rc != GS_OK) return rc;
+  return launch_project_bwd(means, log_scales, quats, opacity_logits, sh, N, cams_dev, L, K, counts, d_projected,
+                            d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, status_dev, stream);
+}

@@ -1,0 +1,350 @@
+"""Runtime around the C ABI: device-resident scenes, per-call buffers, the
+autograd Function, and the training-step runner (per-view or batched, the
+latter captured in a CUDA graph).
+
+PyTorch supplies device memory and streams only; every stage of the step runs
+in libgs_gb300 kernels (see include/gs.h).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+from . import _native as gs
+
+PARAM_NAMES = ("means", "log_scales", "quats", "opacity_logits", "sh")
+PARAM_WIDTH = {"means": 3, "log_scales": 3, "quats": 4, "opacity_logits": 1, "sh": 48}
+FLOATS_PER_GAUSSIAN = sum(PARAM_WIDTH.values())  # 59
+
+
+def _round_up(x, m):
+    return (x + m - 1) // m * m
+
+
+class FlatParams:
+    """The five parameter arrays of N Gaussians as views into one flat float32
+    device buffer. Each segment starts on a 16-byte boundary (N is padded to a
+    multiple of 4), so kernels can stage them with TMA bulk copies and a single
+    fused Adam launch covers all of them."""
+
+    def __init__(self, N: int, device="cuda", buf: torch.Tensor | None = None):
+        self.N = N
+        self.Np = _round_up(max(N, 1), 4)
+        self.numel = FLOATS_PER_GAUSSIAN * self.Np
+        self.flat = buf if buf is not None else torch.zeros(self.numel, dtype=torch.float32, device=device)
+        assert self.flat.numel() == self.numel
+        self.views = {}
+        off = 0
+        for name in PARAM_NAMES:
+            w = PARAM_WIDTH[name]
+            seg = self.flat[off:off + w * N]
+            shape = (N, 16, 3) if name == "sh" else ((N,) if w == 1 else (N, w))
+            self.views[name] = seg.view(shape)
+            off += w * self.Np
+
+    def __getitem__(self, k):
+        return self.views[k]
+
+    def like(self):
+        return FlatParams(self.N, self.flat.device)
+
+    def load_from(self, scene: dict):
+        for name in PARAM_NAMES:
+            src = torch.from_numpy(np.ascontiguousarray(scene[name], np.float32))
+            self.views[name].copy_(src.view(self.views[name].shape))
+        return self
+
+
+class Cameras:
+    """Cameras of one batch: poses/intrinsics on the device (gs_camera records,
+    20 floats each) and the (W, H) layout on the host."""
+
+    def __init__(self, cams: np.ndarray, sizes: np.ndarray, device="cuda"):
+        cams = np.ascontiguousarray(cams, np.float32).reshape(-1, 20)
+        self.sizes = np.ascontiguousarray(sizes, np.int32).reshape(-1, 2)
+        assert cams.shape[0] == self.sizes.shape[0]
+        self.V = cams.shape[0]
+        self.host = cams
+        self.dev = torch.from_numpy(cams).to(device)
+        self.n_pixels = int((self.sizes[:, 0].astype(np.int64) * self.sizes[:, 1]).sum())
+        self.pix_base = np.concatenate([[0], np.cumsum(self.sizes[:, 0].astype(np.int64) * self.sizes[:, 1])])
+
+    def view(self, v: int) -> "Cameras":
+        c = Cameras.__new__(Cameras)
+        c.sizes = self.sizes[v:v + 1]
+        c.V = 1
+        c.host = self.host[v:v + 1]
+        c.dev = self.dev[v:v + 1]
+        c.n_pixels = int(c.sizes[0, 0]) * int(c.sizes[0, 1])
+        c.pix_base = np.array([0, c.n_pixels])
+        return c
+
+
+class Frame:
+    """Device buffers of one rendering call for N Gaussians and a camera
+    layout, with a key capacity that grows on demand."""
+
+    def __init__(self, N: int, cams: Cameras, cfg: dict, capacity: int | None = None, device="cuda"):
+        self.N, self.cams, self.cfg = N, cams, dict(cfg)
+        self.device = device
+        V = cams.V
+        self.n_tiles, self.n_pixels = gs.gs_layout_totals(cams.sizes, cfg)
+        i32 = dict(dtype=torch.int32, device=device)
+        f32 = dict(dtype=torch.float32, device=device)
+        self.projected = torch.zeros(V * N * gs.RECORD_FLOATS, **f32)
+        self.rects = torch.zeros(V * N * 4, dtype=torch.int16, device=device)
+        self.counts = torch.zeros(V * N, **i32)
+        self.tile_ranges = torch.zeros(self.n_tiles * 2, **i32)
+        self.n_isect = torch.zeros(1, dtype=torch.int64, device=device)
+        self.status = torch.zeros(1, **i32)
+        self.image = torch.zeros(self.n_pixels * 3, **f32)
+        self.final_T = torch.zeros(self.n_pixels, **f32)
+        self.last = torch.zeros(self.n_pixels, **i32)
+        self.dL_dimage = torch.zeros(self.n_pixels * 3, **f32)
+        self.loss = torch.zeros(1, dtype=torch.float64, device=device)
+        self.d_projected = torch.zeros(V * N * gs.DRECORD_FLOATS, **f32)
+        self.capacity = 0
+        self.set_capacity(capacity if capacity is not None else max(1024, 8 * V * N))
+
+    def set_capacity(self, capacity: int):
+        capacity = int(capacity)
+        if capacity == self.capacity:
+            return
+        self.capacity = capacity
+        self.keys = torch.zeros(max(capacity, 1), dtype=torch.int64, device=self.device)
+        self.vals = torch.zeros(max(capacity, 1), dtype=torch.int32, device=self.device)
+        ws = gs.gs_bin_sort_workspace_bytes(self.N, self.cams.V, capacity, self.n_tiles)
+        self.workspace = torch.zeros(ws, dtype=torch.uint8, device=self.device)
+
+    def read_status(self) -> int:
+        return int(self.status.item())
+
+    def clear_status(self):
+        self.status.zero_()
+
+
+def project(params: FlatParams, cams: Cameras, frame: Frame, stream=None):
+    gs.gs_project(params["means"], params["log_scales"], params["quats"], params["opacity_logits"], params["sh"],
+                  cams.dev, cams.sizes, frame.cfg, frame.projected, frame.rects, frame.counts, frame.status, stream)
+
+
+def bin_sort(frame: Frame, stream=None):
+    gs.gs_bin_sort(frame.projected, frame.rects, frame.counts, frame.N, frame.cams.sizes, frame.cfg, frame.keys,
+                   frame.vals, frame.capacity, frame.tile_ranges, frame.n_isect, frame.workspace, frame.status, stream)
+
+
+def rasterize_fwd(frame: Frame, stream=None):
+    gs.gs_rasterize_fwd(frame.projected, frame.vals, frame.tile_ranges, frame.cams.sizes, frame.cfg, frame.image,
+                        frame.final_T, frame.last, stream)
+
+
+def rasterize_bwd(params: FlatParams, cams: Cameras, frame: Frame, dL_dimage, grads: FlatParams, stream=None,
+                  accumulate=False):
+    cfg = dict(frame.cfg, flags=gs.GS_FLAG_ACCUMULATE_GRADS if accumulate else 0)
+    gs.gs_rasterize_bwd(params["means"], params["log_scales"], params["quats"], params["opacity_logits"],
+                        params["sh"], cams.dev, cams.sizes, cfg, frame.projected, frame.counts, frame.vals,
+                        frame.tile_ranges, frame.final_T, frame.last, dL_dimage, frame.d_projected, grads["means"],
+                        grads["log_scales"], grads["quats"], grads["opacity_logits"], grads["sh"], frame.status,
+                        stream)
+
+
+def render(params: FlatParams, cams: Cameras, frame: Frame, max_retries: int = 3):
+    """project -> bin_sort -> rasterize_fwd, growing the key capacity (host
+    check after the sort) until every intersection fits."""
+    project(params, cams, frame)
+    for _ in range(max_retries + 1):
+        frame.clear_status()
+        bin_sort(frame)
+        st = frame.read_status()
+        if st & gs.GS_STATUS_TIMEOUT:
+            raise gs.GSError("gs_bin_sort: device wait timed out")
+        if not (st & gs.GS_STATUS_CAPACITY):
+            break
+        need = int(frame.n_isect.item())
+        frame.set_capacity(int(need * 1.25) + 1024)
+    else:
+        raise gs.GSError("gs_bin_sort: capacity retries exhausted")
+    rasterize_fwd(frame)
+    return frame
+
+
+class GaussianRasterize(torch.autograd.Function):
+    """image[P, 3] = render(means, log_scales, quats, opacity_logits, sh).
+
+    The forward keeps only what the backward needs: the projected records, the
+    sorted list and tile ranges, and per pixel the final transmittance and the
+    last-contributor count (no per-pixel lists). The backward calls
+    gs_rasterize_bwd, which recomputes transmittance in reverse."""
+
+    @staticmethod
+    def forward(ctx, means, log_scales, quats, opacity_logits, sh, cams: Cameras, frame: Frame):
+        N = means.shape[0]
+        params = _PackedView(means, log_scales, quats, opacity_logits, sh, N)
+        render(params, cams, frame)
+        ctx.frame, ctx.cams = frame, cams
+        ctx.save_for_backward(means, log_scales, quats, opacity_logits, sh)
+        return frame.image.view(-1, 3).clone()
+
+    @staticmethod
+    def backward(ctx, grad_image):
+        means, log_scales, quats, opacity_logits, sh = ctx.saved_tensors
+        frame, cams = ctx.frame, ctx.cams
+        N = means.shape[0]
+        params = _PackedView(means, log_scales, quats, opacity_logits, sh, N)
+        grads = FlatParams(N, means.device)
+        rasterize_bwd(params, cams, frame, grad_image.contiguous().view(-1), grads)
+        return (grads["means"], grads["log_scales"], grads["quats"], grads["opacity_logits"], grads["sh"], None,
+                None)
+
+
+class _PackedView:
+    """Parameter tensors in the form the binding functions index by name;
+    each must be contiguous float32 on the device."""
+
+    def __init__(self, means, log_scales, quats, opacity_logits, sh, N):
+        self.N = N
+        self.views = {}
+        for name, t in zip(PARAM_NAMES, (means, log_scales, quats, opacity_logits, sh)):
+            if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+                raise ValueError(f"{name}: expected a contiguous float32 CUDA tensor")
+            self.views[name] = t.detach()
+
+    def __getitem__(self, k):
+        return self.views[k]
+
+
+def rasterize(means, log_scales, quats, opacity_logits, sh, cams: Cameras, frame: Frame):
+    """Differentiable render of all views of `cams`; returns image [P, 3]."""
+    return GaussianRasterize.apply(means, log_scales, quats, opacity_logits, sh, cams, frame)
+
+
+class TrainStep:
+    """One training step (forward, image loss, backward, optionally Adam) over
+    a batch of views, entirely in libgs_gb300 kernels.
+
+    mode="batched": one launch per stage for all views; after `prepare()` the
+    whole step is captured into a CUDA graph and `run()` is one graph replay.
+    mode="per_view": every stage launched separately per view (the plain path
+    a per-camera training loop would take), without graph capture.
+    """
+
+    def __init__(self, scene: dict, mode="batched", adam=False, lr=1e-3, betas=(0.9, 0.999), eps=1e-15,
+                 tile=None, device="cuda", graph=True, params: FlatParams | None = None):
+        self.mode, self.adam_on, self.graph_on = mode, adam, graph and mode == "batched"
+        self.lr, self.betas, self.eps = lr, betas, eps
+        self.cfg = dict(scene["cfg"])
+        if tile is not None:
+            self.cfg["tile_w"], self.cfg["tile_h"] = tile
+        self.N = int(scene["means"].shape[0])
+        self.params = params if params is not None else FlatParams(self.N, device).load_from(scene)
+        self.grads = self.params.like()
+        self.cams = Cameras(scene["cams"], scene["sizes"], device)
+        self.target = torch.from_numpy(np.ascontiguousarray(scene["target"], np.float32).reshape(-1)).to(device)
+        self.w_l1, self.w_l2 = scene["loss"]
+        if mode == "batched":
+            self.frame_cams = [self.cams]
+        else:
+            self.frame_cams = [self.cams.view(v) for v in range(self.cams.V)]
+        self.frames = [Frame(self.N, c, self.cfg, device=device) for c in self.frame_cams]
+        self.image = torch.zeros(self.cams.n_pixels * 3, dtype=torch.float32, device=device)
+        self.dL_dimage = torch.zeros_like(self.image)
+        self.loss = torch.zeros(1, dtype=torch.float64, device=device)
+        self.step_count = torch.zeros(1, dtype=torch.int32, device=device)
+        if adam:
+            self.exp_avg = torch.zeros_like(self.params.flat)
+            self.exp_avg_sq = torch.zeros_like(self.params.flat)
+        self.graph = None
+        self.launches_per_step = None
+
+    # -- stage launches ------------------------------------------------------
+    def _enqueue(self, stream=None):
+        """Enqueues one full step; returns the number of library kernels launched."""
+        n = 0
+        pv = self.mode == "per_view"
+        for v, (fr, cams) in enumerate(zip(self.frames, self.frame_cams)):
+            project(self.params, cams, fr, stream)
+            bin_sort(fr, stream)
+            # the frame's image is its slice of the packed image
+            a, b = int(self.cams.pix_base[v]) * 3, int(self.cams.pix_base[v + 1 if pv else -1]) * 3
+            fr.image = self.image[a:b]
+            rasterize_fwd(fr, stream)
+            n += 1 + self._sort_launches(fr) + 1
+        gs.gs_image_loss(self.image, self.target, self.w_l1, self.w_l2, self.dL_dimage, self.loss, stream)
+        n += 1
+        for v, (fr, cams) in enumerate(zip(self.frames, self.frame_cams)):
+            a, b = int(self.cams.pix_base[v]) * 3, int(self.cams.pix_base[v + 1 if pv else -1]) * 3
+            rasterize_bwd(self.params, cams, fr, self.dL_dimage[a:b], self.grads, stream, accumulate=pv and v > 0)
+            n += 2
+        if self.adam_on:
+            gs.gs_adam_step(self.params.flat, self.grads.flat, self.exp_avg, self.exp_avg_sq, self.lr, self.betas[0],
+                            self.betas[1], self.eps, self.step_count, stream)
+            n += 1
+        return n
+
+    @staticmethod
+    def _sort_launches(fr: Frame) -> int:
+        bits = max(1, math.ceil(math.log2(max(fr.n_tiles, 2))))
+        passes = 4 + (bits + 7) // 8
+        return 1 + 1 + 1 + 1 + passes + 1  # scan, emit, histogram, hist scan, passes, ranges
+
+    def prepare(self, warmup_checks=2):
+        """Sizes the key capacity from an eager run, then (batched mode)
+        captures the step into a CUDA graph."""
+        for fr in self.frames:
+            fr.clear_status()
+        for _ in range(warmup_checks + 3):
+            if self.adam_on:
+                self.step_count.fill_(1)
+            self._enqueue()
+            torch.cuda.synchronize()
+            grew = False
+            for fr in self.frames:
+                st = fr.read_status()
+                if st & gs.GS_STATUS_TIMEOUT:
+                    raise gs.GSError("device wait timed out")
+                if st & gs.GS_STATUS_CAPACITY:
+                    fr.set_capacity(int(int(fr.n_isect.item()) * 1.15) + 4096)
+                    grew = True
+                fr.clear_status()
+            if not grew:
+                break
+        else:
+            raise gs.GSError("could not size the key capacity")
+        self.launches_per_step = self._enqueue()  # counted on an eager step
+        torch.cuda.synchronize()
+        if self.graph_on:
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s):
+                self._enqueue(s)  # warm the capture stream
+            torch.cuda.current_stream().wait_stream(s)
+            torch.cuda.synchronize()
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph):
+                self._enqueue(torch.cuda.current_stream())
+            torch.cuda.synchronize()
+        return self
+
+    def run(self):
+        """Enqueues one step (graph replay in batched mode)."""
+        if self.adam_on:
+            self._bump_step()
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self._enqueue()
+
+    def _bump_step(self):
+        self.step_count.add_(1)
+
+    def check(self):
+        """Host check of the device status words (call after a sync)."""
+        for fr in self.frames:
+            st = fr.read_status()
+            if st:
+                raise gs.GSError(f"device status {st}: capacity/timeout/bounds")
+
+    def n_isect(self) -> int:
+        return int(sum(int(fr.n_isect.item()) for fr in self.frames))

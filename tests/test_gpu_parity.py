@@ -1,0 +1,182 @@
+"""GPU vs oracle parity through the C ABI (libgs_gb300.so).
+
+Bars: bit-exact tile counts, rectangles, depths, sorted keys/values and tile
+ranges; images within 1e-5 absolute; gradients within 1e-3 relative (see
+gpu_util.grad_close). Pixels whose compositing involved a decision within
+1e-4 (relative) of a threshold (alpha cutoff, alpha cap, transmittance stop)
+can legitimately go either way between two correct float implementations;
+the oracle flags them, they are checked at 1e-2 and their share is bounded.
+"""
+import numpy as np
+import pytest
+
+from paper_2606_11390_gb300 import scenes
+
+from gpu_util import grad_close, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_11390_gb300 import _native
+
+    _native.load()
+
+
+def _scenes():
+    yield "tiny_cfg", scenes.tiny()
+    yield "ragged_2view", scenes.random_small(101, N=1000, width=173, height=91, n_views=2, spread=1.5)
+    s = scenes.random_small(102, N=777, width=97, height=131, n_views=3, tile=8, log_scale_mu=-2.2)
+    yield "tile8_3view", s
+    s = scenes.random_small(103, N=513, width=150, height=70, n_views=1, log_scale_mu=-1.5)
+    s["cfg"] = scenes.make_cfg(tile_w=32, tile_h=16, bg=(0.2, 0.5, 0.9))
+    yield "tile32x16_bg", s
+    yield "sh_deg1", scenes.random_small(104, N=300, width=64, height=64, sh_degree=1)
+
+
+SCENES = list(_scenes())
+IDS = [n for n, _ in SCENES]
+
+
+def _check_forward(s, g, o_proj, o_bins, o_ras):
+    # integers and the strictly rounded projection path: bit-exact
+    np.testing.assert_array_equal(g["counts"], o_proj["counts"])
+    np.testing.assert_array_equal(g["rects"], o_proj["rects"])
+    vis = o_proj["counts"] > 0
+    for k, name in ((0, "mean2d.x"), (1, "mean2d.y"), (2, "A"), (3, "B"), (4, "C"), (6, "depth"), (7, "radius")):
+        np.testing.assert_array_equal(g["projected"][vis, k], o_proj["projected"][vis, k], err_msg=name)
+    np.testing.assert_allclose(g["projected"][vis, 5], o_proj["projected"][vis, 5], rtol=2e-6, err_msg="opacity")
+    np.testing.assert_allclose(g["projected"][vis, 8:11], o_proj["projected"][vis, 8:11], atol=2e-6, err_msg="rgb")
+    assert not g["projected"][~vis].any()
+    # keys / values / ranges: bit-exact
+    assert g["n_isect"] == o_bins["n_isect"]
+    np.testing.assert_array_equal(g["keys"], o_bins["keys"])
+    np.testing.assert_array_equal(g["vals"], o_bins["vals"])
+    np.testing.assert_array_equal(g["ranges"], o_bins["ranges"])
+    # images
+    marg = o_ras["marginal_pix"].astype(bool)
+    assert marg.mean() < 0.01, marg.mean()
+    np.testing.assert_allclose(g["image"][~marg], o_ras["image"][~marg], atol=1e-5, rtol=0)
+    np.testing.assert_allclose(g["image"][marg], o_ras["image"][marg], atol=1e-2, rtol=0)
+    np.testing.assert_allclose(g["final_T"][~marg], o_ras["final_T"][~marg], atol=1e-5, rtol=0)
+    np.testing.assert_array_equal(g["last"][~marg], o_ras["last"][~marg])
+
+
+@pytest.mark.parametrize("name,s", SCENES, ids=IDS)
+def test_forward_parity(oracle, name, s):
+    o_proj, o_bins, o_ras = oracle.forward(s, "f32")
+    g = run_gpu(s)
+    assert g["status"] == 0
+    _check_forward(s, g, o_proj, o_bins, o_ras)
+
+
+@pytest.mark.parametrize("name,s", SCENES, ids=IDS)
+def test_backward_parity(oracle, name, s):
+    rng = np.random.default_rng(7)
+    P = s["target"].shape[0]
+    dl = (rng.standard_normal((P, 3)) / P).astype(np.float32)
+    o_proj, o_bins, o_ras = oracle.forward(s, "f32")
+    o_dproj, o_grads = oracle.backward(s, o_proj, o_bins, dl.astype(np.float64), "f32")
+    g = run_gpu(s, dL_dimage=dl)
+    assert g["status"] == 0
+    N = s["means"].shape[0]
+    V = s["sizes"].shape[0]
+    ok_vg = o_ras["marginal_vg"] == 0
+    assert ok_vg.mean() > 0.97, ok_vg.mean()
+    grad_close(g["d_projected"], o_dproj, mask=ok_vg, name="d_projected")
+    ok_g = ok_vg.reshape(V, N).all(axis=0)
+    for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        grad_close(g["grads"][k], o_grads[k], mask=ok_g, name=k)
+
+
+def test_capacity_overflow_sets_status_and_recovers(oracle):
+    s = scenes.random_small(105, N=400, width=96, height=80)
+    o_proj, o_bins, _ = oracle.forward(s, "f32")
+    g = run_gpu(s, capacity=17)  # render() grows the buffers and reruns
+    assert g["capacity"] >= o_bins["n_isect"]
+    np.testing.assert_array_equal(g["keys"], o_bins["keys"])
+
+
+def test_empty_and_fully_culled(oracle):
+    s = scenes.random_small(106, N=50, width=40, height=30)
+    s["means"][:, 2] = -3.0
+    g = run_gpu(s, dL_dimage=np.ones((1200, 3), np.float32))
+    assert g["n_isect"] == 0 and g["status"] == 0
+    assert (g["image"] == 0).all() and (g["final_T"] == 1).all() and (g["last"] == 0).all()
+    for k, v in g["grads"].items():
+        assert not v.any(), k
+
+
+def test_single_pixel_image_and_one_gaussian(oracle):
+    s = scenes.random_small(107, N=1, width=1, height=1, log_scale_mu=0.0, depth=3.0, spread=0.01)
+    o_proj, o_bins, o_ras = oracle.forward(s, "f32")
+    g = run_gpu(s)
+    _check_forward(s, g, o_proj, o_bins, o_ras)
+
+
+def test_ties_broken_by_index(oracle):
+    s = scenes.random_small(108, N=200, width=80, height=64)
+    for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        s[k] = np.concatenate([s[k], s[k][:100], s[k][:50]])
+    o_proj, o_bins, o_ras = oracle.forward(s, "f32")
+    g = run_gpu(s)
+    same = o_bins["keys"][1:] == o_bins["keys"][:-1]
+    assert same.sum() > 100
+    np.testing.assert_array_equal(g["keys"], o_bins["keys"])
+    np.testing.assert_array_equal(g["vals"], o_bins["vals"])
+
+
+def test_many_sort_tiles_and_passes(oracle):
+    # > 4096 keys per sort tile and several hundred image tiles: exercises the
+    # look-back across sort tiles and the tile-id digit passes
+    s = scenes.random_small(109, N=20000, width=640, height=480, n_views=2, spread=2.0, log_scale_mu=-2.8)
+    o_proj, o_bins, o_ras = oracle.forward(s, "f32")
+    assert o_bins["n_isect"] > 50000
+    g = run_gpu(s)
+    _check_forward(s, g, o_proj, o_bins, o_ras)
+
+
+def test_image_loss(oracle):
+    import torch
+
+    from paper_2606_11390_gb300 import _native
+
+    rng = np.random.default_rng(3)
+    for n in (1, 7, 4096 * 3 + 5):
+        img = rng.random(n).astype(np.float32)
+        tgt = rng.random(n).astype(np.float32)
+        L, g = oracle.loss(img, tgt, 1.0, 0.2)
+        ti, tt = torch.from_numpy(img).cuda(), torch.from_numpy(tgt).cuda()
+        dl = torch.zeros(n, device="cuda")
+        loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        _native.gs_image_loss(ti, tt, 1.0, 0.2, dl, loss)
+        torch.cuda.synchronize()
+        assert loss.item() == pytest.approx(L, rel=1e-6)
+        np.testing.assert_allclose(dl.cpu().numpy(), g, rtol=1e-5, atol=1e-9)
+
+
+def test_adam(oracle):
+    import torch
+
+    from paper_2606_11390_gb300 import _native
+
+    rng = np.random.default_rng(4)
+    n = 1031
+    p0 = rng.standard_normal(n)
+    m = np.zeros(n)
+    v = np.zeros(n)
+    tp = torch.from_numpy(p0.astype(np.float32)).cuda()
+    tm, tv = torch.zeros(n, device="cuda"), torch.zeros(n, device="cuda")
+    step = torch.zeros(1, dtype=torch.int32, device="cuda")
+    p = p0.astype(np.float32).astype(np.float64)
+    for t in range(1, 6):
+        gr = rng.standard_normal(n).astype(np.float32)
+        p, m, v = oracle.adam(p, gr.astype(np.float64), m, v, 1e-3, 0.9, 0.999, 1e-15, t)
+        step.fill_(t)
+        _native.gs_adam_step(tp, torch.from_numpy(gr).cuda(), tm, tv, 1e-3, 0.9, 0.999, 1e-15, step)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(tp.cpu().numpy(), p, rtol=0, atol=2e-6)
