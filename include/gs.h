@@ -73,6 +73,7 @@ typedef struct CUstream_st* gs_stream_t; /* identical to cudaStream_t */
 #define GS_ERR_ARG 1         /* invalid argument (null pointer, bad size, misaligned, ...) */
 #define GS_ERR_CUDA 2        /* a CUDA call failed while enqueuing */
 #define GS_ERR_UNSUPPORTED 3 /* valid but unsupported configuration (tile size, view count) */
+#define GS_ERR_TOO_LARGE 4   /* the problem needs more scratch than gs_bin_sort_static has */
 
 /* Asynchronous status bits, OR-ed into *status_dev. */
 #define GS_STATUS_CAPACITY 1 /* more tile intersections than `capacity`: keys clipped, ranges invalid */
@@ -175,6 +176,30 @@ GS_API int gs_bin_sort(const float* projected, const int16_t* rects, const uint3
                 int32_t V, const gs_config* cfg, uint64_t* keys, uint32_t* vals, int64_t capacity,
                 uint32_t* tile_ranges, int64_t* n_isect_dev, void* workspace, size_t workspace_bytes,
                 int32_t* status_dev, gs_stream_t stream);
+
+/* gs_bin_sort_static - gs_bin_sort without a caller-provided workspace.
+ * The paper has no counterpart: this variant exists for callers that cannot
+ * allocate device memory where they sort (plug-ins whose host application
+ * owns every device allocation, services that forbid allocation after
+ * start-up, threads that must not risk cudaMalloc's device synchronisation).
+ * It allocates nothing; its scratch is one file-scope device array of
+ * GS_STATIC_SCRATCH_BYTES (64 MiB) that each GPU loading this code holds
+ * until the process exits.
+ * Arguments, outputs and status bits are those of gs_bin_sort, minus the
+ * workspace. Limit: gs_bin_sort_workspace_bytes(N, V, capacity, n_tiles)
+ * must not exceed GS_STATIC_SCRATCH_BYTES (about 4 V N + 16 capacity bytes),
+ * else GS_ERR_TOO_LARGE is returned and nothing is enqueued.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.
+ * All calls share the one array, which keeps the last call's contents (the
+ * parts that must start at zero are cleared by every call): calls that can
+ * overlap on the GPU (different streams, or several threads) race with each
+ * other and must be serialised by the caller. */
+#define GS_STATIC_SCRATCH_BYTES (64u << 20)
+GS_API int gs_bin_sort_static(const float* projected, const int16_t* rects, const uint32_t* counts, int64_t N,
+                              const int32_t* sizes, int32_t V, const gs_config* cfg, uint64_t* keys, uint32_t* vals,
+                              int64_t capacity, uint32_t* tile_ranges, int64_t* n_isect_dev, int32_t* status_dev,
+                              gs_stream_t stream);
 
 /* gs_rasterize_fwd - tile rasterisation (front-to-back alpha compositing).
  * Paper: §4, the rasterisation operator that renders each camera's image;

@@ -17,7 +17,7 @@ import numpy as np
 
 from . import build as _build
 
-GS_OK, GS_ERR_ARG, GS_ERR_CUDA, GS_ERR_UNSUPPORTED = 0, 1, 2, 3
+GS_OK, GS_ERR_ARG, GS_ERR_CUDA, GS_ERR_UNSUPPORTED, GS_ERR_TOO_LARGE = 0, 1, 2, 3, 4
 GS_STATUS_CAPACITY, GS_STATUS_TIMEOUT, GS_STATUS_BOUNDS = 1, 2, 4
 GS_MAX_VIEWS = 64
 GS_FLAG_ACCUMULATE_GRADS = 1
@@ -59,6 +59,7 @@ _SIGNATURES = {
     "gs_bin_sort_workspace_bytes": ([_I64, _I32, _I64, _I64], ctypes.c_size_t),
     "gs_bin_sort": ([_VP, _VP, _VP, _I64, _VP, _I32, _VP, _VP, _VP, _I64, _VP, _VP, _VP, ctypes.c_size_t, _VP, _VP],
                     ctypes.c_int),
+    "gs_bin_sort_static": ([_VP, _VP, _VP, _I64, _VP, _I32, _VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP], ctypes.c_int),
     "gs_rasterize_fwd": ([_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "gs_rasterize_bwd": ([_VP] * 5 + [_I64, _VP, _VP, _I32, _VP] + [_VP] * 7 + [_VP] * 6 + [_VP, _VP], ctypes.c_int),
     "gs_image_loss": ([_VP, _VP, _I64, _F32, _F32, _VP, _VP, _VP], ctypes.c_int),
@@ -161,6 +162,18 @@ def gs_bin_sort(projected, rects, counts, N, sizes, cfg, keys, vals, capacity, t
                             _ptr(keys), _ptr(vals), int(capacity), _ptr(tile_ranges), _ptr(n_isect), _ptr(workspace),
                             workspace.numel() * workspace.element_size(), _ptr(status), _stream(stream))
     _check(rc, "gs_bin_sort")
+
+
+def gs_bin_sort_static(projected, rects, counts, N, sizes, cfg, keys, vals, capacity, tile_ranges, n_isect, status,
+                       stream=None):
+    """gs_bin_sort with the library's fixed device scratch instead of a
+    caller workspace (for callers that cannot allocate device memory)."""
+    sz = _sizes(sizes)
+    c, cref = _cfg_ref(cfg)
+    rc = load().gs_bin_sort_static(_ptr(projected), _ptr(rects), _ptr(counts), int(N), _ptr(sz), sz.shape[0], cref,
+                                   _ptr(keys), _ptr(vals), int(capacity), _ptr(tile_ranges), _ptr(n_isect),
+                                   _ptr(status), _stream(stream))
+    _check(rc, "gs_bin_sort_static")
 
 
 def gs_rasterize_fwd(projected, vals, tile_ranges, sizes, cfg, image, final_T, last, stream=None):

@@ -53,6 +53,7 @@ extern "C" const char* gs_status_string(int code) {
     case GS_ERR_ARG: return "invalid argument";
     case GS_ERR_CUDA: return "CUDA error while enqueuing";
     case GS_ERR_UNSUPPORTED: return "unsupported configuration";
+    case GS_ERR_TOO_LARGE: return "problem too large for the static scratch of gs_bin_sort_static";
     default: break;
   }
   return "device status bits set (capacity / timeout / bounds)";
