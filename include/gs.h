@@ -147,30 +147,37 @@ GS_API int gs_project(const float* means, const float* log_scales, const float* 
                gs_stream_t stream);
 
 /* Bytes of device workspace gs_bin_sort needs for N Gaussians, V views, a
- * key capacity and n_tiles tiles (from gs_layout_totals). */
+ * key capacity and n_tiles tiles (from gs_layout_totals); 0 for invalid
+ * arguments. About 20 V N + 12 capacity bytes. */
 GS_API size_t gs_bin_sort_workspace_bytes(int64_t N, int32_t V, int64_t capacity, int64_t n_tiles);
 
 /* gs_bin_sort - tile keys and per-camera depth sort.
  * Paper: §4, where each camera's Gaussians are depth-sorted before
  * rasterisation, and §3.2 (the paper sorts with CUB's radix sort; this is a
- * CUB-free onesweep LSD radix sort). For every visible record vg (views ascending, Gaussians ascending)
- * and every tile (tx, ty) of its rectangle in row-major order one pair
- *   key = (global tile id << 32) | float bits of depth,  val = vg
- * is emitted; the pairs are then stably sorted by key, so equal keys stay in
- * Gaussian-index order. Finally tile_ranges[t] = [start, end) of tile t's
- * entries in the sorted list ([0, 0) for an empty tile).
+ * CUB-free onesweep LSD radix sort). Result: for every visible record vg
+ * (views ascending, Gaussians ascending) and every tile (tx, ty) of its
+ * rectangle in row-major order one pair
+ *   key = (global tile id << 32) | float bits of depth,  val = vg,
+ * stably sorted by key, so equal keys stay in record-index order; and
+ * tile_ranges[t] = [start, end) of tile t's entries in the sorted list
+ * ([0, 0) for an empty tile). Computed as a depth sort of the visible records
+ * followed by a stable sort of the emitted entries by tile id, which yields
+ * the same order.
  *
  * in  (device): projected, rects, counts from gs_project.
- * in  (host)  : N, sizes [V][2], cfg, capacity (>= 0, < 2^32).
- * out (device): keys [capacity] uint64, vals [capacity] uint32 (first n
- *               entries valid), tile_ranges [n_tiles][2] uint32,
+ * in  (host)  : N, sizes [V][2], cfg, capacity (>= 0, < 2^32 - 1).
+ * out (device): vals [capacity] uint32 (first n entries valid);
+ *               keys [capacity] uint64 (optional: pass NULL to skip writing
+ *               the 64-bit keys; nothing downstream needs them);
+ *               tile_ranges [n_tiles][2] uint32;
  *               n_isect_dev [1] int64 = total number of intersections.
  * workspace (device, caller-owned, >= gs_bin_sort_workspace_bytes, 256-byte
  *   aligned): scratch, contents undefined on return.
  * If the total exceeds `capacity`, only the first `capacity` pairs in
- * emission order are kept, GS_STATUS_CAPACITY is set and keys, vals and
- * ranges must not be used: grow the buffers to *n_isect_dev and call again.
- * A device wait that exceeds its iteration bound sets GS_STATUS_TIMEOUT.
+ * depth-sorted emission order are kept, GS_STATUS_CAPACITY is set and
+ * keys, vals and ranges must not be used: grow the buffers to *n_isect_dev
+ * and call again. A device wait that exceeds its iteration bound sets
+ * GS_STATUS_TIMEOUT.
  * Errors: GS_ERR_ARG (also for a too-small workspace), GS_ERR_CUDA. */
 GS_API int gs_bin_sort(const float* projected, const int16_t* rects, const uint32_t* counts, int64_t N, const int32_t* sizes,
                 int32_t V, const gs_config* cfg, uint64_t* keys, uint32_t* vals, int64_t capacity,
@@ -187,7 +194,7 @@ GS_API int gs_bin_sort(const float* projected, const int16_t* rects, const uint3
  * until the process exits.
  * Arguments, outputs and status bits are those of gs_bin_sort, minus the
  * workspace. Limit: gs_bin_sort_workspace_bytes(N, V, capacity, n_tiles)
- * must not exceed GS_STATIC_SCRATCH_BYTES (about 4 V N + 16 capacity bytes),
+ * must not exceed GS_STATIC_SCRATCH_BYTES (about 20 V N + 12 capacity bytes),
  * else GS_ERR_TOO_LARGE is returned and nothing is enqueued.
  * The first call on a device looks up the array's device address (with that
  * device current); make that first call before any stream capture.

@@ -1,19 +1,28 @@
-// Tile keys and depth sort: scan of per-record tile counts, key emission,
-// CUB-free onesweep LSD radix sort, tile ranges.
+// Tile keys and depth sort: CUB-free onesweep radix sorts producing, per
+// image tile, the list of intersecting splats in (depth, index) order.
 //
 // Paper: arXiv 2606.11390 §4 (each camera's Gaussians are depth-sorted before
-// rasterisation; the multi-GPU merge of §4 is not needed on one GPU) and §3.2
-// (the paper's sort is CUB's radix sort, Merrill & Grimshaw 2011). The sort
-// here follows the onesweep scheme (Adinets & Merrill 2022): one upfront pass
-// builds the digit histograms of all passes, then each 8-bit digit pass is a
-// single read and write of the keys in which every tile of 4096 keys finds
-// its global digit offsets by decoupled look-back over its predecessors.
-// Tiles take their position from an atomic ticket, so a tile only waits on
-// tiles that are already running; every wait is bounded (GS_STATUS_TIMEOUT).
+// rasterisation; the multi-GPU merge sort of §4 is not needed on one GPU) and
+// §3.2 (the paper sorts with CUB's radix sort, Merrill & Grimshaw 2011). The
+// digit passes follow the onesweep scheme (Adinets & Merrill 2022): digit
+// histograms of all passes are gathered up front, and each pass reads and
+// writes the data once, every tile of 4096 items finding its global digit
+// offsets by decoupled look-back over its predecessors. Tiles take their
+// order from an atomic ticket, so a tile only waits on tiles that are already
+// running, and every wait is bounded (GS_STATUS_TIMEOUT).
 //
-// Keys: (global tile id << 32) | float bits of depth (depth > 0, so the bits
-// order like the values). Emission order is (view, Gaussian, row-major tile),
-// and every pass is stable, so equal keys stay in Gaussian-index order.
+// The sorted order is that of the stable sort of the 64-bit keys
+// (tile << 32) | bits(depth) emitted in (view, Gaussian, row-major tile)
+// order. It is reached in two smaller sorts:
+//   1. compact the visible records and sort them by depth bits (4 passes over
+//      32-bit keys; stability keeps equal depths in record-index order);
+//   2. emit one (tile id, record) pair per covered tile, records in depth
+//      order, and stably sort the pairs by tile id (ceil(log2 tiles / 8)
+//      passes over 32-bit keys).
+// Within a tile the entries then run in (depth, record) order, exactly the
+// order of the 64-bit key sort, while the large list (one entry per tile
+// intersection) goes through 2 passes of 16 bytes per entry instead of 6
+// passes of 24 bytes.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -23,20 +32,12 @@
 namespace gs {
 namespace {
 
-// ---------------------------------------------------------------------------
-// Exclusive scan of counts -> offsets (clamped at capacity), decoupled look-back.
-// ---------------------------------------------------------------------------
-constexpr int kScanThreads = 256;
-constexpr int kScanItems = 16;
-constexpr int kScanTile = kScanThreads * kScanItems;
 constexpr uint64_t kFlagAgg = 1ull << 62;
 constexpr uint64_t kFlagIncl = 2ull << 62;
 constexpr uint64_t kValMask = (1ull << 62) - 1;
-
-struct ScanState {
-  uint64_t* tiles;   // [n_tiles] flag | value
-  uint32_t* ticket;  // [1]
-};
+constexpr int kRadix = 256;
+constexpr int kDepthPasses = 4;
+constexpr int kMaxTilePasses = 4;
 
 __device__ __forceinline__ uint64_t warp_incl_scan_u64(uint64_t v) {
   const int lane = threadIdx.x & 31;
@@ -48,7 +49,8 @@ __device__ __forceinline__ uint64_t warp_incl_scan_u64(uint64_t v) {
   return v;
 }
 
-// Look-back for tile `t` (t >= 1) by one warp; returns the exclusive prefix.
+// Decoupled look-back for scan tile `t` (t >= 1), run by one full warp;
+// returns the exclusive prefix of the tile.
 __device__ uint64_t lookback_warp(const uint64_t* tiles, uint32_t t, int32_t* status) {
   const int lane = threadIdx.x & 31;
   uint64_t prefix = 0;
@@ -57,7 +59,6 @@ __device__ uint64_t lookback_warp(const uint64_t* tiles, uint32_t t, int32_t* st
   while (base >= 0) {
     const int64_t j = base - lane;
     uint64_t s = j >= 0 ? ld_relaxed_u64(tiles + j) : kFlagIncl;
-    // wait until every lane sees a published value
     while (__any_sync(0xffffffffu, (s >> 62) == 0)) {
       if (++spins > kSpinLimit) {
         set_status(status, GS_STATUS_TIMEOUT);
@@ -66,7 +67,6 @@ __device__ uint64_t lookback_warp(const uint64_t* tiles, uint32_t t, int32_t* st
       if ((s >> 62) == 0) s = ld_relaxed_u64(tiles + j);
     }
     const uint32_t incl = __ballot_sync(0xffffffffu, (s >> 62) == 2);
-    // sum values of lanes up to and including the first inclusive one
     const int stop = incl ? (__ffs(incl) - 1) : 31;
     uint64_t v = lane <= stop ? (s & kValMask) : 0;
 #pragma unroll
@@ -78,25 +78,21 @@ __device__ uint64_t lookback_warp(const uint64_t* tiles, uint32_t t, int32_t* st
   return prefix;
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_counts_kernel(const uint32_t* __restrict__ counts, int64_t n,
-                                                                     uint32_t* __restrict__ offsets, uint64_t capacity,
-                                                                     ScanState st, int64_t* n_total, int32_t* status) {
-  __shared__ uint32_t s_tile;
-  __shared__ uint64_t s_warp[kScanThreads / 32];
-  __shared__ uint64_t s_prefix;
+// Block-wide exclusive scan (256 threads) of one u64 per thread; also
+// publishes the block total through decoupled look-back and returns the
+// block's global exclusive prefix in *block_prefix.
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+struct ScanState {
+  uint64_t* tiles;   // [n_scan_tiles] flag | value
+  uint32_t* ticket;  // [1]
+};
+
+__device__ __forceinline__ uint64_t block_scan_lookback(uint64_t local, uint32_t t, const ScanState& st,
+                                                        uint64_t* s_warp, uint64_t* s_prefix, int32_t* status) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) s_tile = atomicAdd(st.ticket, 1u);
-  __syncthreads();
-  const uint32_t t = s_tile;
-  const int64_t base = static_cast<int64_t>(t) * kScanTile + static_cast<int64_t>(tid) * kScanItems;
-  uint32_t c[kScanItems];
-  uint64_t local = 0;
-#pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    c[i] = (base + i < n) ? counts[base + i] : 0u;
-    local += c[i];
-  }
-  // block scan of per-thread sums
   const uint64_t incl = warp_incl_scan_u64(local);
   if (lane == 31) s_warp[warp] = incl;
   __syncthreads();
@@ -112,165 +108,245 @@ __global__ void __launch_bounds__(kScanThreads) scan_counts_kernel(const uint32_
     if (t == 0) {
       if (lane == 0) {
         st_relaxed_u64(st.tiles, kFlagIncl | block_total);
-        s_prefix = 0;
+        *s_prefix = 0;
       }
     } else {
       if (lane == 0) st_relaxed_u64(st.tiles + t, kFlagAgg | block_total);
       const uint64_t p = lookback_warp(st.tiles, t, status);
       if (lane == 0) {
         st_relaxed_u64(st.tiles + t, kFlagIncl | (p + block_total));
-        s_prefix = p;
+        *s_prefix = p;
       }
     }
   }
   __syncthreads();
-  uint64_t run = s_prefix + excl_thread;
+  return *s_prefix + excl_thread;
+}
+
+// ---------------------------------------------------------------------------
+// 1a. Compaction of visible records: (depth bits, record) pairs in record
+//     order, plus the digit histograms of the four depth passes.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kScanThreads) compact_visible_kernel(
+    const uint32_t* __restrict__ counts, const float* __restrict__ projected, int64_t n, ScanState st,
+    uint32_t* __restrict__ dkeys, uint32_t* __restrict__ dvals, uint32_t* __restrict__ hist, int64_t* n_visible,
+    int32_t* status) {
+  __shared__ uint32_t s_tile;
+  __shared__ uint64_t s_warp[kScanThreads / 32];
+  __shared__ uint64_t s_prefix;
+  __shared__ uint32_t s_hist[kDepthPasses][kRadix];
+  const int tid = threadIdx.x;
+  for (int i = tid; i < kDepthPasses * kRadix; i += kScanThreads) (&s_hist[0][0])[i] = 0;
+  if (tid == 0) s_tile = atomicAdd(st.ticket, 1u);
+  __syncthreads();
+  const uint32_t t = s_tile;
+  const int64_t base = static_cast<int64_t>(t) * kScanTile + static_cast<int64_t>(tid) * kScanItems;
+  uint32_t vis = 0;  // bit i: item i visible
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i)
+    if (base + i < n && counts[base + i] > 0) vis |= 1u << i;
+  const uint64_t pos0 = block_scan_lookback(__popc(vis), t, st, s_warp, &s_prefix, status);
+  uint64_t pos = pos0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    if (vis & (1u << i)) {
+      const uint32_t d = __float_as_uint(projected[(base + i) * kRecordFloats + 6]);
+      dkeys[pos] = d;
+      dvals[pos] = static_cast<uint32_t>(base + i);
+#pragma unroll
+      for (int p = 0; p < kDepthPasses; ++p) atomicAdd(&s_hist[p][(d >> (8 * p)) & 0xffu], 1u);
+      ++pos;
+    }
+  }
+  if (n > 0 && base <= n - 1 && n - 1 < base + kScanItems) *n_visible = static_cast<int64_t>(pos);
+  __syncthreads();
+  for (int i = tid; i < kDepthPasses * kRadix; i += kScanThreads) {
+    const uint32_t c = (&s_hist[0][0])[i];
+    if (c) atomicAdd(hist + i, c);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 1c. Exclusive scan of the tile counts of the depth-sorted records.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kScanThreads) scan_sorted_counts_kernel(
+    const uint32_t* __restrict__ counts, const uint32_t* __restrict__ order, const int64_t* n_visible, ScanState st,
+    uint32_t* __restrict__ offsets, uint64_t capacity, int64_t* n_total, int32_t* status) {
+  __shared__ uint32_t s_tile;
+  __shared__ uint64_t s_warp[kScanThreads / 32];
+  __shared__ uint64_t s_prefix;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_tile = atomicAdd(st.ticket, 1u);
+  __syncthreads();
+  const uint32_t t = s_tile;
+  const int64_t n = *n_visible;
+  if (static_cast<int64_t>(t) * kScanTile >= n) return;  // past the data: publishes nothing, awaited by nobody
+  const int64_t base = static_cast<int64_t>(t) * kScanTile + static_cast<int64_t>(tid) * kScanItems;
+  uint32_t c[kScanItems];
+  uint64_t local = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    c[i] = (base + i < n) ? counts[order[base + i]] : 0u;
+    local += c[i];
+  }
+  uint64_t run = block_scan_lookback(local, t, st, s_warp, &s_prefix, status);
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     if (base + i < n) offsets[base + i] = static_cast<uint32_t>(run < capacity ? run : capacity);
     run += c[i];
   }
-  // the tile holding the last element reports the total
-  if (n > 0 && base <= n - 1 && n - 1 < base + kScanItems) {
+  if (base <= n - 1 && n - 1 < base + kScanItems) {
     *n_total = static_cast<int64_t>(run);
     if (run > capacity) set_status(status, GS_STATUS_CAPACITY);
   }
 }
 
 // ---------------------------------------------------------------------------
-// Key emission: one thread per record, keys of its rectangle in row-major order.
+// 2a. Emission, one warp per 32 depth-sorted records: lanes write a record's
+//     tiles side by side (coalesced), and the tile-id digit histograms of
+//     the tile passes are gathered on the way.
 // ---------------------------------------------------------------------------
-__global__ void emit_keys_kernel(const float4* __restrict__ projected, const short4* __restrict__ rects,
-                                 const uint32_t* __restrict__ counts, const uint32_t* __restrict__ offsets, int64_t N,
-                                 const Layout L, uint64_t capacity, uint64_t* __restrict__ keys,
-                                 uint32_t* __restrict__ vals) {
-  const int64_t vg = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int64_t VN = N * L.V;
-  if (vg >= VN) return;
-  const uint32_t cnt = counts[vg];
-  if (cnt == 0) return;
-  const int v = static_cast<int>(vg / N);
-  const short4 r = rects[vg];
-  const uint32_t depth_bits = __float_as_uint(projected[3 * vg + 1].z);
-  uint64_t pos = offsets[vg];
-  const uint32_t tb = L.tile_base[v];
-  const int ntx = L.ntx[v];
-  for (int ty = r.y; ty < r.w; ++ty) {
-    for (int tx = r.x; tx < r.z; ++tx) {
-      if (pos >= capacity) return;
-      const uint64_t tile = tb + static_cast<uint32_t>(ty * ntx + tx);
-      keys[pos] = (tile << 32) | depth_bits;
-      vals[pos] = static_cast<uint32_t>(vg);
-      ++pos;
+constexpr int kEmitThreads = 256;
+
+__global__ void __launch_bounds__(kEmitThreads) emit_tiles_kernel(
+    const uint32_t* __restrict__ order, const uint32_t* __restrict__ offsets, const int64_t* n_visible,
+    const uint32_t* __restrict__ counts, const short4* __restrict__ rects, int64_t N, const Layout L,
+    uint64_t capacity, int tile_passes, uint32_t* __restrict__ tkeys, uint32_t* __restrict__ tvals,
+    uint32_t* __restrict__ hist) {
+  __shared__ uint32_t s_hist[kMaxTilePasses][kRadix];
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int i = tid; i < kMaxTilePasses * kRadix; i += kEmitThreads) (&s_hist[0][0])[i] = 0;
+  __syncthreads();
+  const int64_t n = *n_visible;
+  const int64_t warps_total = static_cast<int64_t>(gridDim.x) * (kEmitThreads / 32);
+  for (int64_t w = static_cast<int64_t>(blockIdx.x) * (kEmitThreads / 32) + (tid >> 5); w * 32 < n;
+       w += warps_total) {
+    const int64_t j = w * 32 + lane;
+    uint32_t vg = 0, cnt = 0, off = 0;
+    short4 r = make_short4(0, 0, 0, 0);
+    if (j < n) {
+      vg = order[j];
+      cnt = counts[vg];
+      off = offsets[j];
+      r = rects[vg];
+    }
+    for (int src = 0; src < 32; ++src) {
+      const uint32_t c = __shfl_sync(0xffffffffu, cnt, src);
+      if (c == 0) continue;
+      const uint32_t rvg = __shfl_sync(0xffffffffu, vg, src);
+      const uint32_t roff = __shfl_sync(0xffffffffu, off, src);
+      const int x0 = __shfl_sync(0xffffffffu, static_cast<int>(r.x), src);
+      const int y0 = __shfl_sync(0xffffffffu, static_cast<int>(r.y), src);
+      const int x1 = __shfl_sync(0xffffffffu, static_cast<int>(r.z), src);
+      const int v = static_cast<int>(rvg / static_cast<uint64_t>(N));
+      const uint32_t tb = L.tile_base[v];
+      const int ntx = L.ntx[v];
+      const uint32_t wdt = static_cast<uint32_t>(x1 - x0);
+      for (uint32_t k = lane; k < c; k += 32) {
+        const uint64_t pos = static_cast<uint64_t>(roff) + k;
+        if (pos >= capacity) break;
+        const uint32_t ty = static_cast<uint32_t>(y0) + k / wdt;
+        const uint32_t tx = static_cast<uint32_t>(x0) + k % wdt;
+        const uint32_t tile = tb + ty * static_cast<uint32_t>(ntx) + tx;
+        tkeys[pos] = tile;
+        tvals[pos] = rvg;
+        for (int p = 0; p < tile_passes; ++p) atomicAdd(&s_hist[p][(tile >> (8 * p)) & 0xffu], 1u);
+      }
     }
   }
-}
-
-// ---------------------------------------------------------------------------
-// Onesweep radix sort.
-// ---------------------------------------------------------------------------
-constexpr int kSortThreads = 256;
-constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys
-constexpr int kRadix = 256;
-constexpr int kMaxPasses = 8;
-
-struct SortWork {
-  uint32_t* hist;       // [kMaxPasses][256] digit counts
-  uint32_t* tickets;    // [kMaxPasses]
-  uint64_t* lookback;   // [kMaxPasses][n_tiles][256]
-  int64_t n_tiles;      // sort tiles for the capacity
-};
-
-__device__ __forceinline__ int64_t clamp_n(const int64_t* n_total, int64_t capacity) {
-  const int64_t n = *n_total;
-  return n < capacity ? n : capacity;
-}
-
-// Histogram of every digit position for all passes in one read of the keys.
-__global__ void __launch_bounds__(kSortThreads) sort_histogram_kernel(const uint64_t* __restrict__ keys,
-                                                                        const int64_t* n_total, int64_t capacity,
-                                                                        int passes, uint32_t* __restrict__ hist) {
-  __shared__ uint32_t s_hist[kMaxPasses][kRadix];
-  for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += blockDim.x) (&s_hist[0][0])[i] = 0;
   __syncthreads();
-  const int64_t n = clamp_n(n_total, capacity);
-  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const uint64_t k = keys[i];
-    for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p][(k >> (8 * p)) & 0xff], 1u);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) {
+  for (int i = tid; i < tile_passes * kRadix; i += kEmitThreads) {
     const uint32_t c = (&s_hist[0][0])[i];
     if (c) atomicAdd(hist + i, c);
   }
 }
 
-// Exclusive scan of each pass's 256 digit counts, in place (one block).
-__global__ void sort_hist_scan_kernel(uint32_t* hist, int passes) {
-  __shared__ uint32_t s[kRadix];
-  const int d = threadIdx.x;
+// Exclusive scan of each pass's 256 digit counts, in place (one block of 256).
+__global__ void hist_scan_kernel(uint32_t* hist, int passes) {
+  const int d = threadIdx.x, lane = d & 31, warp = d >> 5;
+  __shared__ uint32_t s_w[kRadix / 32];
   for (int p = 0; p < passes; ++p) {
-    s[d] = hist[p * kRadix + d];
-    __syncthreads();
-    // Hillis-Steele inclusive scan over 256 entries
-    for (int o = 1; o < kRadix; o <<= 1) {
-      const uint32_t v = d >= o ? s[d - o] : 0u;
-      __syncthreads();
-      s[d] += v;
-      __syncthreads();
+    const uint32_t c = hist[p * kRadix + d];
+    uint32_t v = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t nb = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += nb;
     }
-    hist[p * kRadix + d] = d > 0 ? s[d - 1] : 0u;
+    if (lane == 31) s_w[warp] = v;
+    __syncthreads();
+    uint32_t add = 0;
+    for (int w = 0; w < warp; ++w) add += s_w[w];
+    hist[p * kRadix + d] = v - c + add;
     __syncthreads();
   }
 }
 
+// ---------------------------------------------------------------------------
+// Onesweep digit pass over (u32 key, u32 value) pairs.
+// ---------------------------------------------------------------------------
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 items
+
+struct PassArgs {
+  const uint32_t* keys_in;
+  const uint32_t* vals_in;
+  uint32_t* keys_out;
+  uint32_t* vals_out;
+  const int64_t* n_total;   // items = min(*n_total, cap)
+  int64_t cap;
+  int shift;
+  const uint32_t* digit_offsets;  // [256], exclusive
+  uint32_t* ticket;
+  uint64_t* lookback;  // [sort tiles][256]
+};
+
 struct __align__(16) SortSmem {
-  uint64_t keys[kSortTile];             // 32 KB
-  uint32_t vals[kSortTile];             // 16 KB
+  uint32_t keys[kSortTile];                // 16 KB
+  uint32_t vals[kSortTile];                // 16 KB
   uint32_t warp_hist[kSortWarps][kRadix];  // 8 KB
   uint32_t local_start[kRadix];
-  int64_t base[kRadix];                 // global position of this tile's first key of each digit, minus local start
+  int64_t base[kRadix];
+  uint32_t wsum[kSortWarps];
   uint32_t tile;
 };
 
-__global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(const uint64_t* __restrict__ keys_in,
-                                                                   const uint32_t* __restrict__ vals_in,
-                                                                   uint64_t* __restrict__ keys_out,
-                                                                   uint32_t* __restrict__ vals_out,
-                                                                   const int64_t* n_total, int64_t capacity, int pass,
-                                                                   SortWork W, int32_t* status) {
+__global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(PassArgs a, int32_t* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SortSmem& sm = *reinterpret_cast<SortSmem*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int shift = 8 * pass;
-  const int64_t n = clamp_n(n_total, capacity);
-  if (tid == 0) sm.tile = atomicAdd(W.tickets + pass, 1u);
+  int64_t n = *a.n_total;
+  if (n > a.cap) n = a.cap;
+  if (tid == 0) sm.tile = atomicAdd(a.ticket, 1u);
   for (int i = tid; i < kSortWarps * kRadix; i += kSortThreads) (&sm.warp_hist[0][0])[i] = 0;
   __syncthreads();
   const uint32_t t = sm.tile;
   const int64_t tile_start = static_cast<int64_t>(t) * kSortTile;
-  if (tile_start >= n) return;  // tiles past the data publish nothing and nobody waits on them
+  if (tile_start >= n) return;  // past the data: publishes nothing, awaited by nobody
   const int n_valid = static_cast<int>(n - tile_start < kSortTile ? n - tile_start : kSortTile);
 
-  // 1. load (warp-striped) and rank within each warp, stably
-  uint64_t key[kSortItems];
-  uint32_t val[kSortItems];
-  uint32_t rank[kSortItems];
+  // 1. load everything first (warp-striped), so the loads overlap
+  uint32_t key[kSortItems], val[kSortItems];
   const int warp_base = warp * 32 * kSortItems;
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    const int li = warp_base + i * 32 + lane;
+    key[i] = li < n_valid ? a.keys_in[tile_start + li] : 0u;
+    val[i] = li < n_valid ? a.vals_in[tile_start + li] : 0u;
+  }
+  // 2. stable rank within the warp (match_any on the digit, item by item)
+  uint32_t rank[kSortItems];
   const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
     const int li = warp_base + i * 32 + lane;
     const bool valid = li < n_valid;
-    key[i] = valid ? keys_in[tile_start + li] : 0ull;
-    val[i] = valid ? vals_in[tile_start + li] : 0u;
     const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
     rank[i] = 0;
     if (valid) {
-      const uint32_t d = static_cast<uint32_t>(key[i] >> shift) & 0xffu;
+      const uint32_t d = (key[i] >> a.shift) & 0xffu;
       const uint32_t peers = __match_any_sync(vmask, d);
       const int leader = __ffs(peers) - 1;
       uint32_t before = 0;
@@ -283,7 +359,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(const uint64_t*
   }
   __syncthreads();
 
-  // 2. per digit: offsets of each warp, tile total; publish and look back
+  // 3. per digit: warp offsets, tile total, publish, local start, look-back
   const int d = tid;  // kSortThreads == kRadix
   uint32_t total = 0;
 #pragma unroll
@@ -292,10 +368,8 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(const uint64_t*
     sm.warp_hist[w][d] = total;
     total += c;
   }
-  uint64_t* lb = W.lookback + (static_cast<int64_t>(pass) * W.n_tiles) * kRadix;
-  if (t == 0) st_relaxed_u64(lb + d, kFlagIncl | total);
-  else st_relaxed_u64(lb + static_cast<int64_t>(t) * kRadix + d, kFlagAgg | total);
-  // local exclusive scan of tile totals over digits (block scan)
+  uint64_t* lb = a.lookback;
+  st_relaxed_u64(lb + static_cast<int64_t>(t) * kRadix + d, (t == 0 ? kFlagIncl : kFlagAgg) | total);
   {
     uint32_t v = total;
 #pragma unroll
@@ -303,11 +377,10 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(const uint64_t*
       const uint32_t nb = __shfl_up_sync(0xffffffffu, v, o);
       if (lane >= o) v += nb;
     }
-    __shared__ uint32_t s_wsum[kSortWarps];
-    if (lane == 31) s_wsum[warp] = v;
+    if (lane == 31) sm.wsum[warp] = v;
     __syncthreads();
     uint32_t add = 0;
-    for (int w = 0; w < warp; ++w) add += s_wsum[w];
+    for (int w = 0; w < warp; ++w) add += sm.wsum[w];
     sm.local_start[d] = v - total + add;
   }
   uint64_t prefix = 0;
@@ -330,50 +403,62 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(const uint64_t*
     }
     st_relaxed_u64(lb + static_cast<int64_t>(t) * kRadix + d, kFlagIncl | (prefix + total));
   }
-  const uint32_t digit_offset = W.hist[pass * kRadix + d];
-  sm.base[d] = static_cast<int64_t>(digit_offset) + static_cast<int64_t>(prefix) - sm.local_start[d];
+  sm.base[d] = static_cast<int64_t>(a.digit_offsets[d]) + static_cast<int64_t>(prefix) - sm.local_start[d];
   __syncthreads();
 
-  // 3. scatter into shared memory in local sorted order
+  // 4. scatter into shared memory in local sorted order
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
     const int li = warp_base + i * 32 + lane;
     if (li < n_valid) {
-      const uint32_t dd = static_cast<uint32_t>(key[i] >> shift) & 0xffu;
-      const uint32_t pos = sm.local_start[dd] + sm.warp_hist[warp][dd] + rank[i];
-      sm.keys[pos] = key[i];
-      sm.vals[pos] = val[i];
+      const uint32_t dd = (key[i] >> a.shift) & 0xffu;
+      const uint32_t p = sm.local_start[dd] + sm.warp_hist[warp][dd] + rank[i];
+      sm.keys[p] = key[i];
+      sm.vals[p] = val[i];
     }
   }
   __syncthreads();
 
-  // 4. write out: runs of equal digits land contiguously
+  // 5. write out: runs of equal digits land contiguously
   for (int idx = tid; idx < n_valid; idx += kSortThreads) {
-    const uint64_t k = sm.keys[idx];
-    const uint32_t dd = static_cast<uint32_t>(k >> shift) & 0xffu;
-    const int64_t pos = sm.base[dd] + idx;
-    if (pos >= 0 && pos < n) {
-      keys_out[pos] = k;
-      vals_out[pos] = sm.vals[idx];
+    const uint32_t k = sm.keys[idx];
+    const int64_t p = sm.base[(k >> a.shift) & 0xffu] + idx;
+    if (p >= 0 && p < n) {
+      a.keys_out[p] = k;
+      a.vals_out[p] = sm.vals[idx];
     } else {
       set_status(status, GS_STATUS_BOUNDS);
     }
   }
 }
 
-// Tile ranges from the sorted keys (ranges zeroed beforehand).
-__global__ void tile_ranges_kernel(const uint64_t* __restrict__ keys, const int64_t* n_total, int64_t capacity,
+// Tile ranges from the sorted tile ids (ranges zeroed beforehand).
+__global__ void tile_ranges_kernel(const uint32_t* __restrict__ tkeys, const int64_t* n_total, int64_t capacity,
                                    uint32_t n_tiles, uint2* __restrict__ ranges, int32_t* status) {
-  const int64_t n = clamp_n(n_total, capacity);
+  int64_t n = *n_total;
+  if (n > capacity) n = capacity;
   for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const uint32_t tile = static_cast<uint32_t>(keys[i] >> 32);
+    const uint32_t tile = tkeys[i];
     if (tile >= n_tiles) {
       set_status(status, GS_STATUS_BOUNDS);
       continue;
     }
-    if (i == 0 || static_cast<uint32_t>(keys[i - 1] >> 32) != tile) ranges[tile].x = static_cast<uint32_t>(i);
-    if (i == n - 1 || static_cast<uint32_t>(keys[i + 1] >> 32) != tile) ranges[tile].y = static_cast<uint32_t>(i + 1);
+    if (i == 0 || tkeys[i - 1] != tile) ranges[tile].x = static_cast<uint32_t>(i);
+    if (i == n - 1 || tkeys[i + 1] != tile) ranges[tile].y = static_cast<uint32_t>(i + 1);
+  }
+}
+
+// Optional 64-bit keys (tile << 32) | bits(depth) of the sorted list.
+__global__ void keys64_kernel(const uint32_t* __restrict__ tkeys, const uint32_t* __restrict__ vals,
+                              const float* __restrict__ projected, const int64_t* n_total, int64_t capacity,
+                              uint64_t* __restrict__ keys) {
+  int64_t n = *n_total;
+  if (n > capacity) n = capacity;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const uint32_t d = __float_as_uint(projected[static_cast<int64_t>(vals[i]) * kRecordFloats + 6]);
+    keys[i] = (static_cast<uint64_t>(tkeys[i]) << 32) | d;
   }
 }
 
@@ -382,44 +467,69 @@ __global__ void tile_ranges_kernel(const uint64_t* __restrict__ keys, const int6
 // ---------------------------------------------------------------------------
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+int tile_passes_for(int64_t n_tiles) {
+  int bits = 0;
+  while ((int64_t(1) << bits) < n_tiles) ++bits;
+  return (bits + 7) / 8;
+}
+
 struct WsLayout {
-  size_t offsets, scan_tiles, alt_keys, alt_vals, hist, tickets, lookback, total;
-  size_t zero_begin, zero_end;  // region cleared at the start of every call
-  int64_t n_scan_tiles, n_sort_tiles;
+  size_t dkeys0, dvals0, dkeys1, dvals1, offsets, tkeys0, tkeys1, tvals_alt;
+  size_t zero_begin, scan1, scan2, hist_d, hist_t, tickets, n_visible, lb_depth, lb_tile, zero_end, total;
+  int64_t n_scan_tiles, n_depth_tiles, n_tile_tiles;
+  int tile_passes;
 };
 
-WsLayout ws_layout(int64_t N, int32_t V, int64_t capacity) {
+WsLayout ws_layout(int64_t N, int32_t V, int64_t capacity, int64_t n_tiles) {
   WsLayout w;
   const int64_t VN = N * V;
+  const size_t vn = static_cast<size_t>(VN > 0 ? VN : 1), cap = static_cast<size_t>(capacity > 0 ? capacity : 1);
+  w.tile_passes = tile_passes_for(n_tiles);
   w.n_scan_tiles = (VN + kScanTile - 1) / kScanTile;
-  w.n_sort_tiles = (capacity + kSortTile - 1) / kSortTile;
+  w.n_depth_tiles = (VN + kSortTile - 1) / kSortTile;
+  w.n_tile_tiles = (capacity + kSortTile - 1) / kSortTile;
   size_t o = 0;
-  w.offsets = o; o = align256(o + sizeof(uint32_t) * static_cast<size_t>(VN > 0 ? VN : 1));
-  w.alt_keys = o; o = align256(o + sizeof(uint64_t) * static_cast<size_t>(capacity > 0 ? capacity : 1));
-  w.alt_vals = o; o = align256(o + sizeof(uint32_t) * static_cast<size_t>(capacity > 0 ? capacity : 1));
+  w.dkeys0 = o; o = align256(o + 4 * vn);
+  w.dvals0 = o; o = align256(o + 4 * vn);
+  w.dkeys1 = o; o = align256(o + 4 * vn);
+  w.dvals1 = o; o = align256(o + 4 * vn);
+  w.offsets = o; o = align256(o + 4 * vn);
+  w.tkeys0 = o; o = align256(o + 4 * cap);
+  w.tkeys1 = o; o = align256(o + 4 * cap);
+  w.tvals_alt = o; o = align256(o + 4 * cap);
   w.zero_begin = o;
-  w.scan_tiles = o; o = align256(o + sizeof(uint64_t) * static_cast<size_t>(w.n_scan_tiles + 1));
-  w.hist = o; o = align256(o + sizeof(uint32_t) * kMaxPasses * kRadix);
-  w.tickets = o; o = align256(o + sizeof(uint32_t) * (kMaxPasses + 1));
-  w.lookback = o; o = align256(o + sizeof(uint64_t) * kMaxPasses * kRadix * static_cast<size_t>(w.n_sort_tiles + 1));
+  w.scan1 = o; o = align256(o + 8 * static_cast<size_t>(w.n_scan_tiles + 1));
+  w.scan2 = o; o = align256(o + 8 * static_cast<size_t>(w.n_scan_tiles + 1));
+  w.hist_d = o; o = align256(o + 4 * kDepthPasses * kRadix);
+  w.hist_t = o; o = align256(o + 4 * kMaxTilePasses * kRadix);
+  w.tickets = o; o = align256(o + 4 * 16);
+  w.n_visible = o; o = align256(o + 8);
+  w.lb_depth = o; o = align256(o + 8 * kRadix * kDepthPasses * static_cast<size_t>(w.n_depth_tiles + 1));
+  w.lb_tile = o; o = align256(o + 8 * kRadix * static_cast<size_t>(w.tile_passes) * static_cast<size_t>(w.n_tile_tiles + 1));
   w.zero_end = o;
   w.total = o;
   return w;
 }
 
-int num_passes(int64_t n_tiles) {
-  int bits = 1;
-  while ((int64_t(1) << bits) < n_tiles) ++bits;
-  return 4 + (bits + 7) / 8;
+int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 148;
+  if (!cached[dev]) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = n > 0 ? n : 148;
+  }
+  return cached[dev];
 }
 
 }  // namespace
 }  // namespace gs
 
 extern "C" size_t gs_bin_sort_workspace_bytes(int64_t N, int32_t V, int64_t capacity, int64_t n_tiles) {
-  (void)n_tiles;
-  if (N < 0 || V < 1 || capacity < 0) return 0;
-  return gs::ws_layout(N, V, capacity).total;
+  if (N < 0 || V < 1 || capacity < 0 || n_tiles < 1) return 0;
+  return gs::ws_layout(N, V, capacity, n_tiles).total;
 }
 
 extern "C" int gs_bin_sort(const float* projected, const int16_t* rects, const uint32_t* counts, int64_t N,
@@ -432,25 +542,17 @@ extern "C" int gs_bin_sort(const float* projected, const int16_t* rects, const u
   int rc = build_layout(sizes, V, cfg, &L, nullptr);
   if (rc != GS_OK) return rc;
   if (N < 0 || capacity < 0 || capacity >= (int64_t(1) << 32) - 1) return GS_ERR_ARG;
-  if (N * static_cast<int64_t>(V) >= (int64_t(1) << 32)) return GS_ERR_ARG;
+  if (N * static_cast<int64_t>(V) >= (int64_t(1) << 32) - 1) return GS_ERR_ARG;
   if (!tile_ranges || !n_isect_dev || !workspace) return GS_ERR_ARG;
   if (N > 0 && (!projected || !rects || !counts)) return GS_ERR_ARG;
-  if (capacity > 0 && (!keys || !vals)) return GS_ERR_ARG;
-  if (reinterpret_cast<uintptr_t>(workspace) & 255u) return GS_ERR_ARG;
-  const WsLayout w = ws_layout(N, V, capacity);
+  if (capacity > 0 && !vals) return GS_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255u) || (reinterpret_cast<uintptr_t>(rects) & 7u)) return GS_ERR_ARG;
+  const WsLayout w = ws_layout(N, V, capacity, L.n_tiles);
   if (workspace_bytes < w.total) return GS_ERR_ARG;
   unsigned char* ws = static_cast<unsigned char*>(workspace);
-  uint32_t* offsets = reinterpret_cast<uint32_t*>(ws + w.offsets);
-  uint64_t* alt_keys = reinterpret_cast<uint64_t*>(ws + w.alt_keys);
-  uint32_t* alt_vals = reinterpret_cast<uint32_t*>(ws + w.alt_vals);
-  ScanState st;
-  st.tiles = reinterpret_cast<uint64_t*>(ws + w.scan_tiles);
-  SortWork sw;
-  sw.hist = reinterpret_cast<uint32_t*>(ws + w.hist);
-  sw.tickets = reinterpret_cast<uint32_t*>(ws + w.tickets);
-  st.ticket = sw.tickets + kMaxPasses;
-  sw.lookback = reinterpret_cast<uint64_t*>(ws + w.lookback);
-  sw.n_tiles = w.n_sort_tiles;
+  auto u32 = [&](size_t off) { return reinterpret_cast<uint32_t*>(ws + off); };
+  uint32_t* tickets = u32(w.tickets);
+  int64_t* n_visible = reinterpret_cast<int64_t*>(ws + w.n_visible);
 
   cudaError_t e = cudaMemsetAsync(ws + w.zero_begin, 0, w.zero_end - w.zero_begin, stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * static_cast<size_t>(L.n_tiles), stream);
@@ -458,35 +560,6 @@ extern "C" int gs_bin_sort(const float* projected, const int16_t* rects, const u
   if (e != cudaSuccess) return GS_ERR_CUDA;
   const int64_t VN = N * V;
   if (VN == 0) return GS_OK;
-
-  // 1. scan of counts
-  scan_counts_kernel<<<static_cast<unsigned>(w.n_scan_tiles), kScanThreads, 0, stream>>>(
-      counts, VN, offsets, static_cast<uint64_t>(capacity), st, n_isect_dev, status_dev);
-  if (capacity == 0) return cuda_status(cudaGetLastError());
-  const int passes = num_passes(L.n_tiles);
-  // 2. emission into the buffer that makes the last pass land in keys/vals
-  uint64_t* k0 = (passes % 2 == 0) ? keys : alt_keys;
-  uint32_t* v0 = (passes % 2 == 0) ? vals : alt_vals;
-  uint64_t* k1 = (passes % 2 == 0) ? alt_keys : keys;
-  uint32_t* v1 = (passes % 2 == 0) ? alt_vals : vals;
-  {
-    const int threads = 256;
-    const int64_t blocks = (VN + threads - 1) / threads;
-    emit_keys_kernel<<<static_cast<unsigned>(blocks), threads, 0, stream>>>(
-        reinterpret_cast<const float4*>(projected), reinterpret_cast<const short4*>(rects), counts, offsets, N, L,
-        static_cast<uint64_t>(capacity), k0, v0);
-  }
-  // 3. histograms of all passes
-  int n_sm = 148;
-  {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-  }
-  sort_histogram_kernel<<<static_cast<unsigned>(2 * n_sm), kSortThreads, 0, stream>>>(k0, n_isect_dev, capacity, passes,
-                                                                                         sw.hist);
-  sort_hist_scan_kernel<<<1, kRadix, 0, stream>>>(sw.hist, passes);
-  // 4. digit passes
   static bool attr_set = false;
   if (!attr_set) {
     if (cudaFuncSetAttribute(sort_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -494,18 +567,62 @@ extern "C" int gs_bin_sort(const float* projected, const int16_t* rects, const u
       return GS_ERR_CUDA;
     attr_set = true;
   }
-  for (int p = 0; p < passes; ++p) {
-    const uint64_t* kin = (p % 2 == 0) ? k0 : k1;
-    const uint32_t* vin = (p % 2 == 0) ? v0 : v1;
-    uint64_t* kout = (p % 2 == 0) ? k1 : k0;
-    uint32_t* vout = (p % 2 == 0) ? v1 : v0;
-    sort_pass_kernel<<<static_cast<unsigned>(w.n_sort_tiles), kSortThreads, sizeof(SortSmem), stream>>>(
-        kin, vin, kout, vout, n_isect_dev, capacity, p, sw, status_dev);
+  const unsigned scan_grid = static_cast<unsigned>(w.n_scan_tiles);
+
+  // 1a. visible records -> (depth bits, record), depth digit histograms
+  ScanState st1{reinterpret_cast<uint64_t*>(ws + w.scan1), tickets + 0};
+  uint32_t* dk[2] = {u32(w.dkeys0), u32(w.dkeys1)};
+  uint32_t* dv[2] = {u32(w.dvals0), u32(w.dvals1)};
+  uint32_t* hist_d = u32(w.hist_d);
+  compact_visible_kernel<<<scan_grid, kScanThreads, 0, stream>>>(counts, projected, VN, st1, dk[0], dv[0], hist_d,
+                                                                   n_visible, status_dev);
+  hist_scan_kernel<<<1, kRadix, 0, stream>>>(hist_d, kDepthPasses);
+  // 1b. four depth passes (even count: the result is back in dk[0], dv[0])
+  for (int p = 0; p < kDepthPasses; ++p) {
+    PassArgs a;
+    a.keys_in = dk[p & 1]; a.vals_in = dv[p & 1]; a.keys_out = dk[(p + 1) & 1]; a.vals_out = dv[(p + 1) & 1];
+    a.n_total = n_visible; a.cap = VN; a.shift = 8 * p; a.digit_offsets = hist_d + p * kRadix;
+    a.ticket = tickets + 2 + p;
+    a.lookback = reinterpret_cast<uint64_t*>(ws + w.lb_depth) + static_cast<size_t>(p) * (w.n_depth_tiles + 1) * kRadix;
+    sort_pass_kernel<<<static_cast<unsigned>(w.n_depth_tiles), kSortThreads, sizeof(SortSmem), stream>>>(a, status_dev);
   }
-  // 5. tile ranges
-  tile_ranges_kernel<<<static_cast<unsigned>(4 * n_sm), 256, 0, stream>>>(keys, n_isect_dev, capacity,
-                                                                            static_cast<uint32_t>(L.n_tiles),
-                                                                            reinterpret_cast<uint2*>(tile_ranges),
-                                                                            status_dev);
+  const uint32_t* order = dv[0];
+  // 1c. tile-count offsets in depth order
+  ScanState st2{reinterpret_cast<uint64_t*>(ws + w.scan2), tickets + 1};
+  uint32_t* offsets = u32(w.offsets);
+  scan_sorted_counts_kernel<<<scan_grid, kScanThreads, 0, stream>>>(counts, order, n_visible, st2, offsets,
+                                                                      static_cast<uint64_t>(capacity), n_isect_dev,
+                                                                      status_dev);
+  if (capacity == 0) return cuda_status(cudaGetLastError());
+  // 2a. emission in depth order; the buffers are chosen so that the last tile
+  //     pass writes the values into `vals`
+  const int TP = w.tile_passes;
+  uint32_t* tk[2] = {u32(w.tkeys0), u32(w.tkeys1)};
+  uint32_t* tv[2];
+  tv[TP & 1] = vals;
+  tv[(TP + 1) & 1] = u32(w.tvals_alt);
+  uint32_t* hist_t = u32(w.hist_t);
+  const int n_sm = sm_count();
+  emit_tiles_kernel<<<static_cast<unsigned>(4 * n_sm), kEmitThreads, 0, stream>>>(
+      order, offsets, n_visible, counts, reinterpret_cast<const short4*>(rects), N, L,
+      static_cast<uint64_t>(capacity), TP, tk[0], tv[0], hist_t);
+  // 2b. stable tile-id passes
+  if (TP > 0) hist_scan_kernel<<<1, kRadix, 0, stream>>>(hist_t, TP);
+  for (int p = 0; p < TP; ++p) {
+    PassArgs a;
+    a.keys_in = tk[p & 1]; a.vals_in = tv[p & 1]; a.keys_out = tk[(p + 1) & 1]; a.vals_out = tv[(p + 1) & 1];
+    a.n_total = n_isect_dev; a.cap = capacity; a.shift = 8 * p; a.digit_offsets = hist_t + p * kRadix;
+    a.ticket = tickets + 6 + p;
+    a.lookback = reinterpret_cast<uint64_t*>(ws + w.lb_tile) + static_cast<size_t>(p) * (w.n_tile_tiles + 1) * kRadix;
+    sort_pass_kernel<<<static_cast<unsigned>(w.n_tile_tiles), kSortThreads, sizeof(SortSmem), stream>>>(a, status_dev);
+  }
+  const uint32_t* tkeys_final = tk[TP & 1];
+  // 2c. tile ranges, optional 64-bit keys
+  tile_ranges_kernel<<<static_cast<unsigned>(4 * n_sm), 256, 0, stream>>>(
+      tkeys_final, n_isect_dev, capacity, static_cast<uint32_t>(L.n_tiles), reinterpret_cast<uint2*>(tile_ranges),
+      status_dev);
+  if (keys)
+    keys64_kernel<<<static_cast<unsigned>(4 * n_sm), 256, 0, stream>>>(tkeys_final, vals, projected, n_isect_dev,
+                                                                        capacity, keys);
   return cuda_status(cudaGetLastError());
 }

@@ -7,7 +7,6 @@ in libgs_gb300 kernels (see include/gs.h).
 """
 from __future__ import annotations
 
-import math
 
 import numpy as np
 import torch
@@ -86,9 +85,11 @@ class Frame:
     """Device buffers of one rendering call for N Gaussians and a camera
     layout, with a key capacity that grows on demand."""
 
-    def __init__(self, N: int, cams: Cameras, cfg: dict, capacity: int | None = None, device="cuda"):
+    def __init__(self, N: int, cams: Cameras, cfg: dict, capacity: int | None = None, device="cuda",
+                 keep_keys: bool = False):
         self.N, self.cams, self.cfg = N, cams, dict(cfg)
         self.device = device
+        self.keep_keys = keep_keys  # materialise the 64-bit sort keys (tests and inspection only)
         V = cams.V
         self.n_tiles, self.n_pixels = gs.gs_layout_totals(cams.sizes, cfg)
         i32 = dict(dtype=torch.int32, device=device)
@@ -113,7 +114,8 @@ class Frame:
         if capacity == self.capacity:
             return
         self.capacity = capacity
-        self.keys = torch.zeros(max(capacity, 1), dtype=torch.int64, device=self.device)
+        self.keys = (torch.zeros(max(capacity, 1), dtype=torch.int64, device=self.device) if self.keep_keys
+                     else None)
         self.vals = torch.zeros(max(capacity, 1), dtype=torch.int32, device=self.device)
         ws = gs.gs_bin_sort_workspace_bytes(self.N, self.cams.V, capacity, self.n_tiles)
         self.workspace = torch.zeros(ws, dtype=torch.uint8, device=self.device)
@@ -270,7 +272,7 @@ class TrainStep:
             a, b = int(self.cams.pix_base[v]) * 3, int(self.cams.pix_base[v + 1 if pv else -1]) * 3
             fr.image = self.image[a:b]
             rasterize_fwd(fr, stream)
-            n += 1 + self._sort_launches(fr) + 1
+            n += 1 + self._sort_launches(fr) + 1  # project, sort, raster
         gs.gs_image_loss(self.image, self.target, self.w_l1, self.w_l2, self.dL_dimage, self.loss, stream)
         n += 1
         for v, (fr, cams) in enumerate(zip(self.frames, self.frame_cams)):
@@ -285,9 +287,14 @@ class TrainStep:
 
     @staticmethod
     def _sort_launches(fr: Frame) -> int:
-        bits = max(1, math.ceil(math.log2(max(fr.n_tiles, 2))))
-        passes = 4 + (bits + 7) // 8
-        return 1 + 1 + 1 + 1 + passes + 1  # scan, emit, histogram, hist scan, passes, ranges
+        """Kernels gs_bin_sort launches: compaction, histogram scan, 4 depth
+        passes, count scan, emission, histogram scan, the tile-id passes,
+        ranges (and the optional 64-bit keys)."""
+        bits = 0
+        while (1 << bits) < fr.n_tiles:
+            bits += 1
+        tile_passes = (bits + 7) // 8
+        return 1 + 1 + 4 + 1 + 1 + (1 if tile_passes else 0) + tile_passes + 1 + (1 if fr.keep_keys else 0)
 
     def prepare(self, warmup_checks=2):
         """Sizes the key capacity from an eager run, then (batched mode)

@@ -25,7 +25,7 @@ def run_gpu(scene, dL_dimage=None, capacity=None, tile=None, graph=False):
     N = int(scene["means"].shape[0])
     params = R.FlatParams(N).load_from(scene)
     cams = R.Cameras(scene["cams"], scene["sizes"])
-    frame = R.Frame(N, cams, cfg, capacity=capacity)
+    frame = R.Frame(N, cams, cfg, capacity=capacity, keep_keys=True)
     R.render(params, cams, frame)
     torch.cuda.synchronize()
     out = {

@@ -31,7 +31,7 @@ def _sorted_both_ways(rt, scene):
     N = int(scene["means"].shape[0])
     params = R.FlatParams(N).load_from(scene)
     cams = R.Cameras(scene["cams"], scene["sizes"])
-    frame = R.Frame(N, cams, scene["cfg"])
+    frame = R.Frame(N, cams, scene["cfg"], keep_keys=True)
     R.render(params, cams, frame)  # gs_project + gs_bin_sort (workspace) with capacity sizing
     torch.cuda.synchronize()
     n = int(frame.n_isect.item())
