@@ -8,17 +8,22 @@
 // for the tile's depth-sorted entries, alpha = min(cap, o exp(-power)),
 // skip alpha < alpha_min, stop before T(1 - alpha) < t_stop, C += c alpha T.
 //
-// GB300 design. One CTA per (view, tile) with one thread per pixel; the tile's
-// splats are staged into shared memory in batches of one per thread. The
+// GB300 design. One CTA per (view, tile); each thread owns two pixels and
+// each warp an 8x8 pixel block. The tile's splats are staged into shared
+// memory in batches of one per thread; while staging, each splat gets a
+// bitmask of the warps whose block meets the ellipse on which its alpha can
+// reach alpha_min (bounding box of that ellipse, widened by a safety margin),
+// so a warp skips splats that cannot touch its pixels. Skipped pairs are pairs
+// the compositing rule would skip anyway, so the result is unchanged. The
 // per-pair arithmetic is written with explicitly rounded operations and a
 // fixed ex2.approx so that the backward recomputes bit-identical alphas and
-// takes exactly the forward's skip / stop decisions. The backward walks each
-// tile's list in reverse from the largest `last` of its pixels, recovers
-// T_k = T_{k+1} / (1 - alpha_k) from the stored final T, reduces the 9
-// per-pixel gradient values of a splat across the warp with a 12-shuffle
-// reduce-scatter (instead of 9 x 5 butterfly shuffles), sums the warps of the
-// CTA in shared memory, and issues one FP32 atomic per value per (tile,
-// splat) to the per-record gradient buffer.
+// takes exactly the forward's skip / stop decisions. The backward walks the
+// list in reverse, each warp from the largest `last` among its pixels,
+// recovers T_k = T_{k+1} / (1 - alpha_k) from the stored final T, sums a
+// splat's 9 gradient values over the thread's two pixels, reduces them across
+// the warp with a 12-shuffle reduce-scatter (instead of 9 x 5 butterfly
+// shuffles), sums the warps of the CTA in shared memory and issues one FP32
+// atomic per value per (tile, splat) to the per-record gradient buffer.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -57,34 +62,104 @@ __device__ __forceinline__ float splat_exponent(float px, float py, const float4
   return __fmaf_rn(q, dx, __fmul_rn(__fmul_rn(Cp, dy), dy));
 }
 
+// Warp w of a TW x TH tile covers the 8x8 block (8*(w % (TW/8)), 8*(w / (TW/8)));
+// lane l owns pixels (l & 7, l >> 3) and (l & 7, (l >> 3) + 4) of that block.
+template <int TW>
+__device__ __forceinline__ void pixel_of(int tid, int& x, int& y0) {
+  const int w = tid >> 5, l = tid & 31;
+  x = 8 * (w % (TW / 8)) + (l & 7);
+  y0 = 8 * (w / (TW / 8)) + (l >> 3);
+}
+
+// Bitmask of the warps of a TW x TH tile at (tx0, ty0) whose 8x8 block meets
+// the bounding box of {d : alpha(d) >= alpha_min}. With the scaled conic
+// M = [[-2A', -B'], [-B', -2C']] (so e = -d^T M d / 2) the set is
+// d^T M d / 2 <= ts, ts = log2(o / alpha_min), whose bounding box has
+// half-widths sqrt(2 ts (M^-1)_00) and sqrt(2 ts (M^-1)_11). ts and the
+// half-widths are widened (x1.001 + margin), far beyond the rounding of the
+// per-pixel evaluation, so no pixel outside the box can pass the alpha test.
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW* TH) raster_fwd_kernel(const float4* __restrict__ projected,
-                                                             const uint32_t* __restrict__ vals,
-                                                             const uint2* __restrict__ ranges, const Layout L,
-                                                             const Consts K, float* __restrict__ image,
-                                                             float* __restrict__ final_T, uint32_t* __restrict__ last) {
-  constexpr int B = TW * TH;
+__device__ __forceinline__ uint32_t warp_cull_mask(const float4& a, const float4& b, float tx0, float ty0,
+                                                    float amin) {
+  constexpr int WX = TW / 8, NW = (TW / 8) * (TH / 8);
+  constexpr uint32_t kAll = (NW >= 32) ? 0xffffffffu : ((1u << NW) - 1u);
+  const float o = b.y;
+  if (!(o > amin)) return 0u;
+  const float m00 = -2.0f * a.z, m01 = -a.w, m11 = -2.0f * b.x;
+  const float det = m00 * m11 - m01 * m01;
+  if (!(det > 0.0f) || !(m00 > 0.0f) || !(m11 > 0.0f)) return kAll;
+  const float ts = (__log2f(o) - __log2f(amin)) * 1.001f + 0.01f;
+  const float hx = sqrtf(2.0f * ts * m11 / det) * 1.001f + 0.05f;
+  const float hy = sqrtf(2.0f * ts * m00 / det) * 1.001f + 0.05f;
+  if (!(hx < 1e30f) || !(hy < 1e30f)) return kAll;
+  uint32_t mask = 0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    const float xlo = tx0 + 8.0f * (w % WX) + 0.5f, ylo = ty0 + 8.0f * (w / WX) + 0.5f;
+    if (a.x + hx >= xlo && a.x - hx <= xlo + 7.0f && a.y + hy >= ylo && a.y - hy <= ylo + 7.0f) mask |= 1u << w;
+  }
+  return mask;
+}
+
+struct PixelFwd {
+  float T, c0, c1, c2;
+  uint32_t last;
+  bool done;
+};
+
+// One compositing step of one pixel (forward rule).
+__device__ __forceinline__ void composite_step(PixelFwd& P, float px, float py, const float4& a, const float4& b,
+                                               float cb, uint32_t rel, float cap, float amin, float tstop) {
+  float dx, dy;
+  const float e = splat_exponent(px, py, a, b.x, dx, dy);
+  if (e > 0.0f) return;
+  const float alpha = fminf(cap, __fmul_rn(b.y, ex2_approx(e)));
+  if (alpha < amin) return;
+  const float Tn = __fmul_rn(P.T, __fsub_rn(1.0f, alpha));
+  if (Tn < tstop) {
+    P.done = true;
+    return;
+  }
+  const float w = __fmul_rn(alpha, P.T);
+  P.c0 = __fmaf_rn(b.z, w, P.c0);
+  P.c1 = __fmaf_rn(b.w, w, P.c1);
+  P.c2 = __fmaf_rn(cb, w, P.c2);
+  P.T = Tn;
+  P.last = rel + 1;
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW* TH / 2) raster_fwd_kernel(const float4* __restrict__ projected,
+                                                                 const uint32_t* __restrict__ vals,
+                                                                 const uint2* __restrict__ ranges, const Layout L,
+                                                                 const Consts K, float* __restrict__ image,
+                                                                 float* __restrict__ final_T,
+                                                                 uint32_t* __restrict__ last) {
+  constexpr int B = TW * TH / 2;
   __shared__ float4 s_a[B];
   __shared__ float4 s_b[B];
   __shared__ float s_c[B];
+  __shared__ uint32_t s_m[B];
   const uint32_t tile = blockIdx.x;
   const int v = view_of_tile(L, tile);
   const uint32_t local = tile - L.tile_base[v];
   const int ntx = L.ntx[v];
   const int tx = static_cast<int>(local % ntx), ty = static_cast<int>(local / ntx);
   const int tid = threadIdx.x;
-  const int x = tx * TW + (tid % TW), y = ty * TH + (tid / TW);
+  const uint32_t wbit = 1u << (tid >> 5);
+  int lx, ly;
+  pixel_of<TW>(tid, lx, ly);
+  const int x = tx * TW + lx, y0 = ty * TH + ly, y1 = y0 + 4;
   const int W = L.width[v], H = L.height[v];
-  const bool inside = x < W && y < H;
-  const float px = static_cast<float>(x) + 0.5f, py = static_cast<float>(y) + 0.5f;
+  const bool in0 = x < W && y0 < H, in1 = x < W && y1 < H;
+  const float px = static_cast<float>(x) + 0.5f, py0 = static_cast<float>(y0) + 0.5f, py1 = py0 + 4.0f;
   const uint2 range = ranges[tile];
   const int n = static_cast<int>(range.y - range.x);
   const float cap = K.alpha_cap, amin = K.alpha_min, tstop = K.t_stop;
-  float T = 1.0f, c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
-  uint32_t lastc = 0;
-  bool done = !inside;
+  const float tx0 = static_cast<float>(tx * TW), ty0 = static_cast<float>(ty * TH);
+  PixelFwd P0{1.0f, 0.0f, 0.0f, 0.0f, 0u, !in0}, P1{1.0f, 0.0f, 0.0f, 0.0f, 0u, !in1};
   for (int b0 = 0; b0 < n; b0 += B) {
-    if (__syncthreads_count(done) == B) break;
+    if (__syncthreads_count(P0.done && P1.done) == B) break;
     if (b0 + tid < n) {
       float4 a, b;
       float c;
@@ -92,39 +167,37 @@ __global__ void __launch_bounds__(TW* TH) raster_fwd_kernel(const float4* __rest
       s_a[tid] = a;
       s_b[tid] = b;
       s_c[tid] = c;
+      s_m[tid] = warp_cull_mask<TW, TH>(a, b, tx0, ty0, amin);
     }
     __syncthreads();
     const int cnt = min(B, n - b0);
-    if (!done) {
-      for (int j = 0; j < cnt; ++j) {
-        const float4 a = s_a[j];
-        const float4 b = s_b[j];
-        float dx, dy;
-        const float e = splat_exponent(px, py, a, b.x, dx, dy);
-        if (e > 0.0f) continue;
-        const float alpha = fminf(cap, __fmul_rn(b.y, ex2_approx(e)));
-        if (alpha < amin) continue;
-        const float Tn = __fmul_rn(T, __fsub_rn(1.0f, alpha));
-        if (Tn < tstop) {
-          done = true;
-          break;
-        }
-        const float w = __fmul_rn(alpha, T);
-        c0 = __fmaf_rn(b.z, w, c0);
-        c1 = __fmaf_rn(b.w, w, c1);
-        c2 = __fmaf_rn(s_c[j], w, c2);
-        T = Tn;
-        lastc = static_cast<uint32_t>(b0 + j + 1);
-      }
+    for (int j = 0; j < cnt; ++j) {
+      if (P0.done && P1.done) break;
+      if (!(s_m[j] & wbit)) continue;
+      const float4 a = s_a[j];
+      const float4 b = s_b[j];
+      const float cb = s_c[j];
+      const uint32_t rel = static_cast<uint32_t>(b0 + j);
+      if (!P0.done) composite_step(P0, px, py0, a, b, cb, rel, cap, amin, tstop);
+      if (!P1.done) composite_step(P1, px, py1, a, b, cb, rel, cap, amin, tstop);
     }
   }
-  if (inside) {
-    const size_t p = static_cast<size_t>(L.pix_base[v]) + static_cast<size_t>(y) * W + x;
-    image[3 * p] = c0 + T * K.bg[0];
-    image[3 * p + 1] = c1 + T * K.bg[1];
-    image[3 * p + 2] = c2 + T * K.bg[2];
-    final_T[p] = T;
-    last[p] = lastc;
+  const size_t pb = L.pix_base[v];
+  if (in0) {
+    const size_t p = pb + static_cast<size_t>(y0) * W + x;
+    image[3 * p] = P0.c0 + P0.T * K.bg[0];
+    image[3 * p + 1] = P0.c1 + P0.T * K.bg[1];
+    image[3 * p + 2] = P0.c2 + P0.T * K.bg[2];
+    final_T[p] = P0.T;
+    last[p] = P0.last;
+  }
+  if (in1) {
+    const size_t p = pb + static_cast<size_t>(y1) * W + x;
+    image[3 * p] = P1.c0 + P1.T * K.bg[0];
+    image[3 * p + 1] = P1.c1 + P1.T * K.bg[1];
+    image[3 * p + 2] = P1.c2 + P1.T * K.bg[2];
+    final_T[p] = P1.T;
+    last[p] = P1.last;
   }
 }
 
@@ -166,16 +239,60 @@ __device__ __forceinline__ int slot_of_lane(int lane) {
   return h1 ? u[1] : u[0];
 }
 
+struct PixelBwd {
+  float T, g0, g1, g2, gbg, ar0, ar1, ar2;
+  uint32_t last;
+};
+
+// Backward contribution of splat (a, b, cb) at relative position `rel` to one
+// pixel, added into gv[9]; returns whether the pixel took part.
+__device__ __forceinline__ bool pixel_grad(PixelBwd& P, float px, float py, const float4& a, const float4& b,
+                                           float cb, uint32_t rel, float cap, float amin, float gv[9]) {
+  if (rel >= P.last) return false;
+  float dx, dy;
+  const float e = splat_exponent(px, py, a, b.x, dx, dy);
+  if (e > 0.0f) return false;
+  const float G = ex2_approx(e);
+  const float oG = __fmul_rn(b.y, G);
+  const float alpha = fminf(cap, oG);
+  if (alpha < amin) return false;
+  const float inv = rcp_approx(__fsub_rn(1.0f, alpha));
+  P.T *= inv;  // transmittance in front of this entry
+  const float w = alpha * P.T;
+  gv[5] += w * P.g0;
+  gv[6] += w * P.g1;
+  gv[7] += w * P.g2;
+  const float d0 = b.z - P.ar0, d1 = b.w - P.ar1, d2 = cb - P.ar2;
+  const float dalpha = P.T * (d0 * P.g0 + d1 * P.g1 + d2 * P.g2) - P.gbg * inv;
+  P.ar0 += alpha * d0;
+  P.ar1 += alpha * d1;
+  P.ar2 += alpha * d2;
+  if (!(oG > cap)) {
+    gv[8] += dalpha * G;
+    // d power = -dalpha alpha; with A = -2A'/log2e, B = -B'/log2e, C = -2C'/log2e
+    const float dpow = -dalpha * alpha;
+    const float dpl = dpow * (1.0f / kLog2e);
+    gv[0] += dpl * (2.0f * a.z * dx + a.w * dy);
+    gv[1] += dpl * (a.w * dx + 2.0f * b.x * dy);
+    const float hd = 0.5f * dpow;
+    gv[2] += hd * dx * dx;
+    gv[3] += dpow * dx * dy;
+    gv[4] += hd * dy * dy;
+  }
+  return true;
+}
+
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW* TH) raster_bwd_kernel(
+__global__ void __launch_bounds__(TW* TH / 2) raster_bwd_kernel(
     const float4* __restrict__ projected, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
     const Layout L, const Consts K, const float* __restrict__ final_T, const uint32_t* __restrict__ last,
     const float* __restrict__ dL_dimage, float* __restrict__ d_proj) {
-  constexpr int B = TW * TH;
+  constexpr int B = TW * TH / 2;
   constexpr int NW = B / 32;
   __shared__ float4 s_a[B];
   __shared__ float4 s_b[B];
   __shared__ float s_c[B];
+  __shared__ uint32_t s_m[B];
   __shared__ uint32_t s_vg[B];
   __shared__ float s_grad[B * 9];
   __shared__ uint32_t s_wmax[NW];
@@ -185,31 +302,33 @@ __global__ void __launch_bounds__(TW* TH) raster_bwd_kernel(
   const int ntx = L.ntx[v];
   const int tx = static_cast<int>(local % ntx), ty = static_cast<int>(local / ntx);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int x = tx * TW + (tid % TW), y = ty * TH + (tid / TW);
+  const uint32_t wbit = 1u << warp;
+  int lx, ly;
+  pixel_of<TW>(tid, lx, ly);
+  const int x = tx * TW + lx, y0 = ty * TH + ly, y1 = y0 + 4;
   const int W = L.width[v], H = L.height[v];
-  const bool inside = x < W && y < H;
-  const float px = static_cast<float>(x) + 0.5f, py = static_cast<float>(y) + 0.5f;
+  const float px = static_cast<float>(x) + 0.5f, py0 = static_cast<float>(y0) + 0.5f, py1 = py0 + 4.0f;
   const uint2 range = ranges[tile];
   const float cap = K.alpha_cap, amin = K.alpha_min;
-  float T = 1.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
-  uint32_t lastp = 0;
-  if (inside) {
-    const size_t p = static_cast<size_t>(L.pix_base[v]) + static_cast<size_t>(y) * W + x;
-    T = final_T[p];
-    lastp = last[p];
-    g0 = dL_dimage[3 * p];
-    g1 = dL_dimage[3 * p + 1];
-    g2 = dL_dimage[3 * p + 2];
-  }
-  const float Tfin = T;
-  const float gbg = Tfin * (g0 * K.bg[0] + g1 * K.bg[1] + g2 * K.bg[2]);
-  float ar0 = 0.0f, ar1 = 0.0f, ar2 = 0.0f;  // colour accumulated behind the current entry
+  const float tx0 = static_cast<float>(tx * TW), ty0 = static_cast<float>(ty * TH);
+  auto init = [&](PixelBwd& P, int yy) {
+    P = PixelBwd{1.0f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u};
+    if (x < W && yy < H) {
+      const size_t p = static_cast<size_t>(L.pix_base[v]) + static_cast<size_t>(yy) * W + x;
+      P.T = final_T[p];
+      P.last = last[p];
+      P.g0 = dL_dimage[3 * p];
+      P.g1 = dL_dimage[3 * p + 1];
+      P.g2 = dL_dimage[3 * p + 2];
+      P.gbg = P.T * (P.g0 * K.bg[0] + P.g1 * K.bg[1] + P.g2 * K.bg[2]);
+    }
+  };
+  PixelBwd P0, P1;
+  init(P0, y0);
+  init(P1, y1);
   const int my_slot = slot_of_lane(lane);
-  // number of entries any pixel of the tile needs
-  {
-    const uint32_t m = __reduce_max_sync(0xffffffffu, lastp);
-    if (lane == 0) s_wmax[warp] = m;
-  }
+  const uint32_t wmax = __reduce_max_sync(0xffffffffu, max(P0.last, P1.last));
+  if (lane == 0) s_wmax[warp] = wmax;
   for (int i = tid; i < B * 9; i += B) s_grad[i] = 0.0f;
   __syncthreads();
   uint32_t max_last = 0;
@@ -227,52 +346,22 @@ __global__ void __launch_bounds__(TW* TH) raster_bwd_kernel(
       s_b[tid] = b;
       s_c[tid] = c;
       s_vg[tid] = vg;
+      s_m[tid] = warp_cull_mask<TW, TH>(a, b, tx0, ty0, amin);
     }
     __syncthreads();
-    for (int j = 0; j < cnt; ++j) {
+    // entries j hold relative position b_end-1-j; this warp needs rel < wmax
+    const int j0 = max(0, b_end - static_cast<int>(wmax));
+    for (int j = j0; j < cnt; ++j) {
+      if (!(s_m[j] & wbit)) continue;
+      const float4 a = s_a[j];
+      const float4 b = s_b[j];
+      const float cb = s_c[j];
       const uint32_t rel = static_cast<uint32_t>(b_end - 1 - j);
       float gv[9];
 #pragma unroll
       for (int i = 0; i < 9; ++i) gv[i] = 0.0f;
-      bool contrib = false;
-      if (rel < lastp) {
-        const float4 a = s_a[j];
-        const float4 b = s_b[j];
-        float dx, dy;
-        const float e = splat_exponent(px, py, a, b.x, dx, dy);
-        if (e <= 0.0f) {
-          const float G = ex2_approx(e);
-          const float oG = __fmul_rn(b.y, G);
-          const float alpha = fminf(cap, oG);
-          if (alpha >= amin) {
-            contrib = true;
-            const float one_m = __fsub_rn(1.0f, alpha);
-            const float inv = rcp_approx(one_m);
-            T = T * inv;  // transmittance in front of this entry
-            const float w = alpha * T;
-            const float c2v = s_c[j];
-            gv[5] = w * g0;
-            gv[6] = w * g1;
-            gv[7] = w * g2;
-            const float dalpha = T * ((b.z - ar0) * g0 + (b.w - ar1) * g1 + (c2v - ar2) * g2) - gbg * inv;
-            ar0 += alpha * (b.z - ar0);
-            ar1 += alpha * (b.w - ar1);
-            ar2 += alpha * (c2v - ar2);
-            if (!(oG > cap)) {
-              gv[8] = dalpha * G;
-              // d power = -dalpha * alpha; power gradients in terms of the
-              // unscaled conic: A = -2 A'/log2e, B = -B'/log2e, C = -2 C'/log2e
-              const float dpow = -dalpha * alpha;
-              const float il = 1.0f / kLog2e;
-              gv[0] = dpow * (2.0f * a.z * dx + a.w * dy) * il;
-              gv[1] = dpow * (a.w * dx + 2.0f * b.x * dy) * il;
-              gv[2] = dpow * 0.5f * dx * dx;
-              gv[3] = dpow * dx * dy;
-              gv[4] = dpow * 0.5f * dy * dy;
-            }
-          }
-        }
-      }
+      bool contrib = pixel_grad(P0, px, py0, a, b, cb, rel, cap, amin, gv);
+      contrib |= pixel_grad(P1, px, py1, a, b, cb, rel, cap, amin, gv);
       if (__any_sync(0xffffffffu, contrib)) {
         const float r = warp_reduce9(gv, lane);
         if (!(lane & 1) && my_slot >= 0 && r != 0.0f) atomicAdd(&s_grad[j * 9 + my_slot], r);
@@ -297,7 +386,7 @@ __global__ void __launch_bounds__(TW* TH) raster_bwd_kernel(
 template <int TW, int TH>
 int launch_fwd(const float4* projected, const uint32_t* vals, const uint2* ranges, const Layout& L, const Consts& K,
                float* image, float* final_T, uint32_t* last, cudaStream_t stream) {
-  raster_fwd_kernel<TW, TH><<<static_cast<unsigned>(L.n_tiles), TW * TH, 0, stream>>>(projected, vals, ranges, L, K,
+  raster_fwd_kernel<TW, TH><<<static_cast<unsigned>(L.n_tiles), TW * TH / 2, 0, stream>>>(projected, vals, ranges, L, K,
                                                                                       image, final_T, last);
   return cuda_status(cudaGetLastError());
 }
@@ -306,7 +395,7 @@ template <int TW, int TH>
 int launch_bwd(const float4* projected, const uint32_t* vals, const uint2* ranges, const Layout& L, const Consts& K,
                const float* final_T, const uint32_t* last, const float* dL_dimage, float* d_proj,
                cudaStream_t stream) {
-  raster_bwd_kernel<TW, TH><<<static_cast<unsigned>(L.n_tiles), TW * TH, 0, stream>>>(
+  raster_bwd_kernel<TW, TH><<<static_cast<unsigned>(L.n_tiles), TW * TH / 2, 0, stream>>>(
       projected, vals, ranges, L, K, final_T, last, dL_dimage, d_proj);
   return cuda_status(cudaGetLastError());
 }
