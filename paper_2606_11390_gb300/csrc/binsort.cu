@@ -432,20 +432,40 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(PassArgs a, int
   }
 }
 
-// Tile ranges from the sorted tile ids (ranges zeroed beforehand).
+// Tile ranges from the sorted tile ids (ranges zeroed beforehand): four ids
+// per thread from one 16-byte load; a range starts where the id differs from
+// its predecessor and ends where it differs from its successor.
 __global__ void tile_ranges_kernel(const uint32_t* __restrict__ tkeys, const int64_t* n_total, int64_t capacity,
                                    uint32_t n_tiles, uint2* __restrict__ ranges, int32_t* status) {
   int64_t n = *n_total;
   if (n > capacity) n = capacity;
-  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const uint32_t tile = tkeys[i];
-    if (tile >= n_tiles) {
-      set_status(status, GS_STATUS_BOUNDS);
-      continue;
+  const int64_t n4 = (n + 3) / 4;
+  for (int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < n4;
+       q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i0 = 4 * q;
+    uint32_t k[4];
+    if (i0 + 3 < n) {
+      const uint4 v = reinterpret_cast<const uint4*>(tkeys)[q];
+      k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
+    } else {
+      for (int j = 0; j < 4; ++j) k[j] = i0 + j < n ? tkeys[i0 + j] : 0xffffffffu;
     }
-    if (i == 0 || tkeys[i - 1] != tile) ranges[tile].x = static_cast<uint32_t>(i);
-    if (i == n - 1 || tkeys[i + 1] != tile) ranges[tile].y = static_cast<uint32_t>(i + 1);
+    uint32_t prev = i0 > 0 ? tkeys[i0 - 1] : 0xffffffffu;
+    const uint32_t next = i0 + 4 < n ? tkeys[i0 + 4] : 0xffffffffu;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t i = i0 + j;
+      if (i >= n) break;
+      const uint32_t t = k[j];
+      const uint32_t nx = j < 3 ? (i + 1 < n ? k[j + 1] : 0xffffffffu) : next;
+      if (t >= n_tiles) {
+        set_status(status, GS_STATUS_BOUNDS);
+      } else {
+        if (t != prev) ranges[t].x = static_cast<uint32_t>(i);
+        if (t != nx) ranges[t].y = static_cast<uint32_t>(i + 1);
+      }
+      prev = t;
+    }
   }
 }
 

@@ -31,6 +31,10 @@ namespace gs {
 namespace {
 
 constexpr int kProjBlock = 128;
+// CTAs per SM the backward is compiled for (register cap 65536 / (128 x this)).
+#ifndef GS_PBWD_MIN_BLOCKS
+#define GS_PBWD_MIN_BLOCKS 3
+#endif
 
 __device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
@@ -201,19 +205,20 @@ constexpr float kSH2a = 1.0925484305920792f, kSH2b = 0.31539156525252005f, kSH2c
 constexpr float kSH3a = 0.5900435899266435f, kSH3b = 2.890611442640554f, kSH3c = 0.4570457994644658f;
 constexpr float kSH3d = 0.3731763325901154f, kSH3e = 1.445305721320277f;
 
-__device__ __forceinline__ void sh_basis(const float d[3], int degree, float Y[16]) {
+template <int DEG>
+__device__ __forceinline__ void sh_basis(const float d[3], float Y[16]) {
   const float x = d[0], y = d[1], z = d[2];
   Y[0] = kSH0;
-  if (degree < 1) return;
+  if (DEG < 1) return;
   Y[1] = -kSH1 * y; Y[2] = kSH1 * z; Y[3] = -kSH1 * x;
-  if (degree < 2) return;
+  if (DEG < 2) return;
   const float xx = x * x, yy = y * y, zz = z * z;
   Y[4] = kSH2a * x * y;
   Y[5] = -kSH2a * y * z;
   Y[6] = kSH2b * (2.0f * zz - xx - yy);
   Y[7] = -kSH2a * x * z;
   Y[8] = kSH2c * (xx - yy);
-  if (degree < 3) return;
+  if (DEG < 3) return;
   Y[9] = -kSH3a * y * (3.0f * xx - yy);
   Y[10] = kSH3b * x * y * z;
   Y[11] = -kSH3c * y * (4.0f * zz - xx - yy);
@@ -224,26 +229,28 @@ __device__ __forceinline__ void sh_basis(const float d[3], int degree, float Y[1
 }
 
 // Adds sum_i coef_i * grad(Y_i)(d) to g.
-__device__ __forceinline__ void sh_basis_grad_acc(const float d[3], int degree, const float coef[16], float g[3]) {
+template <int DEG>
+__device__ __forceinline__ void sh_basis_grad_acc(const float d[3], const float coef[16], float g[3]) {
   const float x = d[0], y = d[1], z = d[2];
-  if (degree < 1) return;
+  if (DEG < 1) return;
   g[0] += -kSH1 * coef[3];
   g[1] += -kSH1 * coef[1];
   g[2] += kSH1 * coef[2];
-  if (degree < 2) return;
+  if (DEG < 2) return;
   const float xx = x * x, yy = y * y, zz = z * z;
   g[0] += kSH2a * y * coef[4] - kSH2a * z * coef[7] + kSH2b * (-2.0f * x) * coef[6] + kSH2c * 2.0f * x * coef[8];
   g[1] += kSH2a * x * coef[4] - kSH2a * z * coef[5] + kSH2b * (-2.0f * y) * coef[6] - kSH2c * 2.0f * y * coef[8];
   g[2] += -kSH2a * y * coef[5] + kSH2b * 4.0f * z * coef[6] - kSH2a * x * coef[7];
-  if (degree < 3) return;
+  if (DEG < 3) return;
   g[0] += -kSH3a * 6.0f * x * y * coef[9] + kSH3b * y * z * coef[10] - kSH3c * (-2.0f * x * y) * coef[11] +
           kSH3d * (-6.0f * x * z) * coef[12] - kSH3c * (4.0f * zz - 3.0f * xx - yy) * coef[13] +
           kSH3e * 2.0f * x * z * coef[14] - kSH3a * (3.0f * xx - 3.0f * yy) * coef[15];
   g[1] += -kSH3a * (3.0f * xx - 3.0f * yy) * coef[9] + kSH3b * x * z * coef[10] -
           kSH3c * (4.0f * zz - xx - 3.0f * yy) * coef[11] + kSH3d * (-6.0f * y * z) * coef[12] -
           kSH3c * (-2.0f * x * y) * coef[13] - kSH3e * 2.0f * y * z * coef[14] - kSH3a * (-6.0f * x * y) * coef[15];
-  g[2] += kSH3b * x * y * coef[10] - kSH3c * 8.0f * y * z * coef[11] + kSH3d * (6.0f * zz - 3.0f * xx - 3.0f * yy) * coef[12] -
-          kSH3c * 8.0f * x * z * coef[13] + kSH3e * (xx - yy) * coef[14];
+  g[2] += kSH3b * x * y * coef[10] - kSH3c * 8.0f * y * z * coef[11] +
+          kSH3d * (6.0f * zz - 3.0f * xx - 3.0f * yy) * coef[12] - kSH3c * 8.0f * x * z * coef[13] +
+          kSH3e * (xx - yy) * coef[14];
 }
 
 // View direction from the camera centre c = -R^T t_cam to the mean.
@@ -321,6 +328,7 @@ struct __align__(16) ProjFwdSmem {
   float4 out[kProjBlock * 3];  // 6 KB staging of projected records
 };
 
+template <int DEG>
 __global__ void __launch_bounds__(kProjBlock) project_fwd_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ opac, const float* __restrict__ sh, int64_t N, const gs_camera* __restrict__ cams,
@@ -332,18 +340,15 @@ __global__ void __launch_bounds__(kProjBlock) project_fwd_kernel(
   const int n = static_cast<int>(N - g0 < kProjBlock ? N - g0 : kProjBlock);
   stage_params(sm.p, means, log_scales, quats, opac, sh, g0, n, cams, L.V, use_bulk != 0, status);
   const bool active = tid < n;
+  constexpr int NB = (DEG + 1) * (DEG + 1);
   GaussLocal G;
-  float shc[48];
+  float shc[3 * NB];
   if (active) {
     gauss_local(&sm.p.means[3 * tid], &sm.p.log_scales[3 * tid], sm.p.quats[tid], sm.p.opac[tid], G);
-    const float4* s4 = &sm.p.sh[12 * tid];
+    const float* s1 = reinterpret_cast<const float*>(&sm.p.sh[12 * tid]);
 #pragma unroll
-    for (int i = 0; i < 12; ++i) {
-      const float4 v = s4[i];
-      shc[4 * i] = v.x; shc[4 * i + 1] = v.y; shc[4 * i + 2] = v.z; shc[4 * i + 3] = v.w;
-    }
+    for (int i = 0; i < 3 * NB; ++i) shc[i] = s1[i];
   }
-  const int nb = (K.sh_degree + 1) * (K.sh_degree + 1);
   for (int v = 0; v < L.V; ++v) {
     float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
     if (active) {
@@ -359,11 +364,13 @@ __global__ void __launch_bounds__(kProjBlock) project_fwd_kernel(
         const float inv = 1.0f / dnorm;
         const float d[3] = {dvec[0] * inv, dvec[1] * inv, dvec[2] * inv};
         float Y[16];
-        sh_basis(d, K.sh_degree, Y);
+        sh_basis<DEG>(d, Y);
         float rgb[3];
+#pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
           float acc = 0.0f;
-          for (int i = 0; i < nb; ++i) acc += Y[i] * shc[3 * i + ch];
+#pragma unroll
+          for (int i = 0; i < NB; ++i) acc += Y[i] * shc[3 * i + ch];
           acc += 0.5f;
           rgb[ch] = acc > 0.0f ? acc : 0.0f;
         }
@@ -383,32 +390,37 @@ __global__ void __launch_bounds__(kProjBlock) project_fwd_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// Backward: one thread per Gaussian, summed over views (no atomics).
+// Backward: one thread per Gaussian, summed over views (no atomics). The SH
+// gradient accumulates in registers and leaves through the thread's own slot
+// of the shared-memory staging area, then as coalesced stores.
 // ---------------------------------------------------------------------------
-struct __align__(16) ProjBwdSmem {
-  ParamSmem p;
-  float gsh[48 * kProjBlock];  // transposed accumulators [coef*3+ch][thread], 24 KB
-};
-
-__global__ void __launch_bounds__(kProjBlock) project_bwd_kernel(
+template <int DEG>
+__global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ opac, const float* __restrict__ sh, int64_t N, const gs_camera* __restrict__ cams,
     const Layout L, const Consts K, const uint32_t* __restrict__ counts, const float* __restrict__ d_proj,
     float* __restrict__ d_means, float* __restrict__ d_log_scales, float* __restrict__ d_quats,
     float* __restrict__ d_opac, float* __restrict__ d_sh, int use_bulk, int32_t* status) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  ProjBwdSmem& sm = *reinterpret_cast<ProjBwdSmem*>(smem_raw);
+  constexpr int NB = (DEG + 1) * (DEG + 1);
+  __shared__ ParamSmem sm_p;
+  struct {
+    ParamSmem& p;
+  } sm{sm_p};
   const int tid = threadIdx.x;
   const int64_t g0 = static_cast<int64_t>(blockIdx.x) * kProjBlock;
   const int n = static_cast<int>(N - g0 < kProjBlock ? N - g0 : kProjBlock);
   stage_params(sm.p, means, log_scales, quats, opac, sh, g0, n, cams, L.V, use_bulk != 0, status);
-  for (int i = 0; i < 48; ++i) sm.gsh[i * kProjBlock + tid] = 0.0f;
   const bool active = tid < n;
-  const int nb = (K.sh_degree + 1) * (K.sh_degree + 1);
   float gm[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, go = 0.f;
+  float shc[3 * NB], gsh[3 * NB];
   GaussLocal G;
+  float* my_sh = reinterpret_cast<float*>(&sm.p.sh[12 * tid]);
+#pragma unroll
+  for (int i = 0; i < 3 * NB; ++i) {
+    shc[i] = my_sh[i];
+    gsh[i] = 0.0f;
+  }
   if (active) gauss_local(&sm.p.means[3 * tid], &sm.p.log_scales[3 * tid], sm.p.quats[tid], sm.p.opac[tid], G);
-  const float* shc = reinterpret_cast<const float*>(&sm.p.sh[12 * tid]);
   for (int v = 0; active && v < L.V; ++v) {
     const int64_t vg = static_cast<int64_t>(v) * N + g0 + tid;
     if (counts[vg] == 0) continue;
@@ -429,25 +441,29 @@ __global__ void __launch_bounds__(kProjBlock) project_bwd_kernel(
       const float inv = 1.0f / dnorm;
       const float d[3] = {dvec[0] * inv, dvec[1] * inv, dvec[2] * inv};
       float Y[16];
-      sh_basis(d, K.sh_degree, Y);
+      sh_basis<DEG>(d, Y);
       float graw[3];
+#pragma unroll
       for (int ch = 0; ch < 3; ++ch) {
         float acc = 0.0f;
-        for (int i = 0; i < nb; ++i) acc += Y[i] * shc[3 * i + ch];
+#pragma unroll
+        for (int i = 0; i < NB; ++i) acc += Y[i] * shc[3 * i + ch];
         acc += 0.5f;
         graw[ch] = acc > 0.0f ? g9[5 + ch] : 0.0f;
       }
       float coef[16];
-      for (int i = 0; i < nb; ++i) {
+#pragma unroll
+      for (int i = 0; i < NB; ++i) {
         coef[i] = shc[3 * i] * graw[0] + shc[3 * i + 1] * graw[1] + shc[3 * i + 2] * graw[2];
-        for (int ch = 0; ch < 3; ++ch) sm.gsh[(3 * i + ch) * kProjBlock + tid] += Y[i] * graw[ch];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) gsh[3 * i + ch] += Y[i] * graw[ch];
       }
       float gdir[3] = {0.f, 0.f, 0.f};
-      sh_basis_grad_acc(d, K.sh_degree, coef, gdir);
+      sh_basis_grad_acc<DEG>(d, coef, gdir);
       const float dd = d[0] * gdir[0] + d[1] * gdir[1] + d[2] * gdir[2];
       for (int k = 0; k < 3; ++k) gm[k] += (gdir[k] - d[k] * dd) * inv;
     }
-    // conic -> Sigma2 (a, b, c)
+  // conic -> Sigma2 (a, b, c)
     const float idet = 1.0f / P.det;
     const float gA = g9[2], gB = g9[3], gC = g9[4];
     const float gdet = -(gA * P.c - gB * P.b + gC * P.a) * idet * idet;
@@ -516,15 +532,18 @@ __global__ void __launch_bounds__(kProjBlock) project_bwd_kernel(
     const float4 q = sm.p.quats[tid];
     const float qnorm = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
     const float dotp = gq[0] * G.qn[0] + gq[1] * G.qn[1] + gq[2] * G.qn[2] + gq[3] * G.qn[3];
-    for (int k = 0; k < 4; ++k) d_quats[4 * g + k] = (gq[k] - G.qn[k] * dotp) / qnorm + (acc ? d_quats[4 * g + k] : 0.0f);
+    for (int k = 0; k < 4; ++k)
+      d_quats[4 * g + k] = (gq[k] - G.qn[k] * dotp) / qnorm + (acc ? d_quats[4 * g + k] : 0.0f);
     d_opac[g] = go + (acc ? d_opac[g] : 0.0f);
   }
+  // SH gradients through the thread's own staging slot (coefficients past
+  // the degree get 0), then coalesced stores
+#pragma unroll
+  for (int i = 0; i < 48; ++i) my_sh[i] = i < 3 * NB ? gsh[i < 3 * NB ? i : 0] : 0.0f;
   __syncthreads();
   float* dst = d_sh + g0 * 48;
-  for (int i = tid; i < n * 48; i += kProjBlock) {
-    const int t = i / 48, c = i - t * 48;
-    dst[i] = sm.gsh[c * kProjBlock + t] + (acc ? dst[i] : 0.0f);
-  }
+  const float* src = reinterpret_cast<const float*>(sm.p.sh);
+  for (int i = tid; i < n * 48; i += kProjBlock) dst[i] = src[i] + (acc ? dst[i] : 0.0f);
 }
 
 }  // namespace
@@ -536,18 +555,18 @@ int launch_project_bwd(const float* means, const float* log_scales, const float*
   if (N == 0) return GS_OK;
   const bool bulk = aligned16(means) && aligned16(log_scales) && aligned16(quats) && aligned16(opacity_logits) &&
                     aligned16(sh);
-  const int64_t blocks = (N + kProjBlock - 1) / kProjBlock;
-  const size_t smem = sizeof(ProjBwdSmem);
-  static bool attr_set = false;
-  if (!attr_set) {
-    if (cudaFuncSetAttribute(project_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return GS_ERR_CUDA;
-    attr_set = true;
+  const unsigned blocks = static_cast<unsigned>((N + kProjBlock - 1) / kProjBlock);
+#define GS_PBWD(D)                                                                                              \
+  project_bwd_kernel<D><<<blocks, kProjBlock, 0, stream>>>(means, log_scales, quats, opacity_logits, sh, N, cams, L, \
+                                                           K, counts, d_projected, d_means, d_log_scales, d_quats,      \
+                                                           d_opacity_logits, d_sh, bulk ? 1 : 0, status)
+  switch (K.sh_degree) {
+    case 0: GS_PBWD(0); break;
+    case 1: GS_PBWD(1); break;
+    case 2: GS_PBWD(2); break;
+    default: GS_PBWD(3); break;
   }
-  project_bwd_kernel<<<static_cast<unsigned>(blocks), kProjBlock, smem, stream>>>(
-      means, log_scales, quats, opacity_logits, sh, N, cams, L, K, counts, d_projected, d_means, d_log_scales, d_quats,
-      d_opacity_logits, d_sh, bulk ? 1 : 0, status);
+#undef GS_PBWD
   return cuda_status(cudaGetLastError());
 }
 
@@ -569,9 +588,20 @@ extern "C" int gs_project(const float* means, const float* log_scales, const flo
   if (!aligned16(projected) || (reinterpret_cast<uintptr_t>(rects) & 7u)) return GS_ERR_ARG;
   const bool bulk = aligned16(means) && aligned16(log_scales) && aligned16(quats) && aligned16(opacity_logits) &&
                     aligned16(sh);
-  const int64_t blocks = (N + kProjBlock - 1) / kProjBlock;
-  project_fwd_kernel<<<static_cast<unsigned>(blocks), kProjBlock, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
-      means, log_scales, quats, opacity_logits, sh, N, cams_dev, L, make_consts(*cfg),
-      reinterpret_cast<float4*>(projected), reinterpret_cast<short4*>(rects), counts, bulk ? 1 : 0, status_dev);
+  const unsigned blocks = static_cast<unsigned>((N + kProjBlock - 1) / kProjBlock);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const Consts K = make_consts(*cfg);
+#define GS_PFWD(D)                                                                                               \
+  project_fwd_kernel<D><<<blocks, kProjBlock, 0, st>>>(means, log_scales, quats, opacity_logits, sh, N, cams_dev, L, K, \
+                                                       reinterpret_cast<float4*>(projected),                           \
+                                                       reinterpret_cast<short4*>(rects), counts, bulk ? 1 : 0,          \
+                                                       status_dev)
+  switch (cfg->sh_degree) {
+    case 0: GS_PFWD(0); break;
+    case 1: GS_PFWD(1); break;
+    case 2: GS_PFWD(2); break;
+    default: GS_PFWD(3); break;
+  }
+#undef GS_PFWD
   return cuda_status(cudaGetLastError());
 }
