@@ -175,19 +175,22 @@ def workload_config(scene, args, tile):
 # per-stage timing of an eager step (for the roofline of the dominant kernel)
 # ---------------------------------------------------------------------------
 def stage_times(step, iters=5):
+    """Per-stage times of an eager step on the launching stream (CUDA events
+    between the C-ABI calls; the backward timed as its two halves)."""
     import torch
 
     from paper_2606_11390_gb300 import _native as gs
     from paper_2606_11390_gb300 import renderer as R
 
-    names = ["project", "bin_sort", "raster_fwd", "loss", "raster_bwd+project_bwd"]
+    names = ["project", "bin_sort", "raster_fwd", "loss", "raster_bwd", "project_bwd"]
     acc = {n: 0.0 for n in names}
     fr, cams = step.frames[0], step.frame_cams[0]
     stream = torch.cuda.current_stream()
+    p, gr = step.params, step.grads
     for _ in range(iters):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
         ev[0].record(stream)
-        R.project(step.params, cams, fr)
+        R.project(p, cams, fr)
         ev[1].record(stream)
         R.bin_sort(fr)
         ev[2].record(stream)
@@ -196,33 +199,17 @@ def stage_times(step, iters=5):
         ev[3].record(stream)
         gs.gs_image_loss(step.image, step.target, step.w_l1, step.w_l2, step.dL_dimage, step.loss)
         ev[4].record(stream)
-        R.rasterize_bwd(step.params, cams, fr, step.dL_dimage, step.grads)
+        gs.gs_rasterize_bwd_pixels(fr.projected, fr.vals, fr.tile_ranges, cams.sizes, fr.cfg, fr.N, fr.final_T,
+                                   fr.last, step.dL_dimage, fr.d_projected)
         ev[5].record(stream)
+        gs.gs_project_bwd(p["means"], p["log_scales"], p["quats"], p["opacity_logits"], p["sh"], cams.dev,
+                          cams.sizes, fr.cfg, fr.counts, fr.d_projected, gr["means"], gr["log_scales"],
+                          gr["quats"], gr["opacity_logits"], gr["sh"], fr.status)
+        ev[6].record(stream)
         torch.cuda.synchronize()
         for i, n in enumerate(names):
             acc[n] += ev[i].elapsed_time(ev[i + 1])
     return {n: acc[n] / iters for n in names}
-
-
-def raster_bwd_only_time(step, iters=5):
-    """Time of the rasterisation-backward kernel alone (d_projected), on the
-    launching stream, with the per-Gaussian backward excluded."""
-    import torch
-
-    from paper_2606_11390_gb300 import renderer as R
-
-    fr, cams = step.frames[0], step.frame_cams[0]
-    stream = torch.cuda.current_stream()
-    # project_bwd alone: time it by running the full backward and subtracting
-    t_full = 0.0
-    for _ in range(iters):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        R.rasterize_bwd(step.params, cams, fr, step.dL_dimage, step.grads)
-        b.record(stream)
-        torch.cuda.synchronize()
-        t_full += a.elapsed_time(b)
-    return t_full / iters
 
 
 def pair_counts(step):
@@ -337,6 +324,7 @@ def main():
     tile = tuple(int(x) for x in args.tile.split("x")) if args.tile else (scene["cfg"]["tile_w"], scene["cfg"]["tile_h"])
     step = R.TrainStep(scene, mode=args.mode, graph=not args.no_graph, tile=tile).prepare()
     P = step.cams.n_pixels
+    launches = step.launches_per_step
     stream = torch.cuda.current_stream()
 
     for _ in range(args.warmup):
@@ -369,30 +357,16 @@ def main():
             st = stage_times(step)
             extra["stage_ms"] = {k: round(v, 4) for k, v in st.items()}
             extra["n_isect"] = step.n_isect()
-            extra["pairs_bwd"] = pair_counts(step)
+            extra["pairs_to_last"] = pair_counts(step)
             dom = max(st, key=st.get)
             peaks, src = measured_peaks()
-            # roofline of the dominant stage
-            roof = roofline_for(dom, st[dom], step, peaks, src)
-            extra["roofline"] = roof
-        # batched vs per-view on the same GPU
-        if args.mode == "batched" and not args.no_compare and step.cams.V > 1:
-            pv = R.TrainStep(scene, mode="per_view", tile=tile, params=step.params).prepare()
-            for _ in range(2):
-                pv.run()
-            torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            for _ in range(max(3, args.steps // 2)):
-                pv.run()
-            b.record(stream)
-            torch.cuda.synchronize()
-            pms = a.elapsed_time(b) / max(3, args.steps // 2)
-            extra["per_view"] = {"ms_per_step": pms, "value": P / (pms * 1e-3) / 1e6,
-                                 "batched_speedup": pms / ms_local}
-            del pv
+            extra["roofline"] = roofline_for(dom, st[dom], step, peaks, src, scene["name"])
         if not args.no_e2e:
             extra["e2e"] = e2e_measure(step, args, dist.world)
+        del step
+        torch.cuda.empty_cache()
+        if not args.no_compare and args.workload == "diff_4k":
+            extra["batched_vs_per_view"] = batched_vs_per_view(args)
         if not args.no_cpu_baseline:
             extra["cpu_baseline"] = cpu_sample(scene)
 
@@ -401,43 +375,119 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": workload_config(scene, args, tile), "clocks": clk,
-                "gpu_launches": step.launches_per_step * args.steps}
+                "gpu_launches": launches * args.steps}
         line.update(extra)
         print(json.dumps(line), flush=True)
     dist.close()
     return 0
 
 
-def roofline_for(stage, ms, step, peaks, src):
-    """Achieved vs peak for the dominant stage. Raster stages are bound by FP32
-    issue (ALU): algorithmic work = evaluated (pixel, splat) pairs x FP32
-    operations per pair; per-Gaussian and sort stages are HBM-bound with the
+# Algorithmic FP32 work of the method per (pixel, splat) pair, mul and add
+# counted separately.
+FLOP_PER_PAIR = {"raster_fwd": 24, "raster_bwd": 60}
+
+
+def kernel_digest():
+    """Digest of the CUDA sources, to tie recorded ncu traffic to a build."""
+    import hashlib
+
+    from paper_2606_11390_gb300 import build as B
+
+    h = hashlib.sha256()
+    for f in B.sources():
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from profiles/dram_traffic.json,
+    if they were captured from the current sources; else None."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = d.get(f"{kernel}|{workload}")
+    if not e or e.get("digest") != kernel_digest():
+        return None
+    return e.get("bytes_per_launch")
+
+
+def roofline_for(stage, ms, step, peaks, src, workload):
+    """Achieved vs peak for the dominant stage. The rasteriser is bound by
+    FP32 issue: algorithmic FLOPs = (pixel, splat) pairs up to each pixel's
+    last contributor x FLOPs per pair of the method; peak = SMs x 128 FP32
+    lanes x 2 (FMA) x max SM clock. The other stages are HBM-bound with the
     algorithmic bytes of their inputs and outputs."""
     import torch
 
-    fr = step.frames[0]
     N, V, I, P = step.N, step.cams.V, step.n_isect(), step.cams.n_pixels
-    if stage in ("raster_fwd", "raster_bwd+project_bwd"):
+    traffic = recorded_traffic(stage, workload)
+    if stage in FLOP_PER_PAIR:
         pairs = pair_counts(step)
-        ops_per_pair = 22 if stage == "raster_fwd" else 60
         sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
         n_sm = torch.cuda.get_device_properties(0).multi_processor_count
-        peak = n_sm * 128 * sm_mhz * 1e6 / 1e12  # FP32 lane-ops/s in T
-        achieved = pairs * ops_per_pair / (ms * 1e-3) / 1e12
-        return {"stage": stage, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": f"{n_sm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({src} max SM clock)",
-                "work": f"{pairs} pairs x {ops_per_pair} FP32 ops"}
+        peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+        achieved = pairs * FLOP_PER_PAIR[stage] / (ms * 1e-3) / 1e12
+        return {"kernel": stage, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz ({src} max SM clock; no measured FP32 peak)",
+                "work": f"{pairs} pixel-splat pairs x {FLOP_PER_PAIR[stage]} FLOP", "ms": ms}
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     if stage == "project":
         bytes_ = N * 236 + V * N * (48 + 8 + 4)
+    elif stage == "project_bwd":
+        bytes_ = N * 236 * 2 + V * N * 40
     elif stage == "bin_sort":
-        bytes_ = V * N * 8 + I * (12 + 8 + 24 * 6 + 8)
+        bytes_ = V * N * 8 + I * (8 + 16 * 2 + 4)
     else:
         bytes_ = P * 3 * 4 * 3
     achieved = bytes_ / (ms * 1e-3) / 1e9
-    return {"stage": stage, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None, "peak_source": src}
+    return {"kernel": stage, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": traffic, "peak_source": f"{src} hbm_gbs", "ms": ms}
+
+
+def batched_vs_per_view(args, tile=None):
+    """The 16-view workload through the batched, graph-captured step and the
+    plain per-view step on the same GPU; tile size from the autotuner."""
+    import torch
+
+    from paper_2606_11390_gb300 import autotune
+    from paper_2606_11390_gb300 import renderer as R
+
+    scene = make_scene("batch16")
+    if tile is None:
+        tile, tune = autotune.best_tile(scene, steps=2)
+    else:
+        tune = {}
+    out = {"workload": "batch16", "gaussians": int(scene["means"].shape[0]), "views": 16,
+           "tile": f"{tile[0]}x{tile[1]}", "autotune_ms": {f"{t[0]}x{t[1]}": round(v, 3) for t, v in tune.items()}}
+    n = max(3, args.steps // 4)
+    res = {}
+    params = None
+    for mode in ("batched", "per_view"):
+        step = R.TrainStep(scene, mode=mode, tile=tile, params=params).prepare()
+        params = step.params
+        for _ in range(2):
+            step.run()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(n):
+            step.run()
+        b.record()
+        torch.cuda.synchronize()
+        step.check()
+        ms = a.elapsed_time(b) / n
+        res[mode] = {"ms_per_step": ms, "Mpix_s": step.cams.n_pixels / (ms * 1e-3) / 1e6,
+                     "launches_per_step": step.launches_per_step, "n_isect": step.n_isect()}
+        del step
+        torch.cuda.empty_cache()
+    out.update(res)
+    out["batched_speedup"] = res["per_view"]["ms_per_step"] / res["batched"]["ms_per_step"]
+    return out
 
 
 def e2e_measure(step, args, world):

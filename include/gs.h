@@ -237,6 +237,7 @@ GS_API int gs_rasterize_fwd(const float* projected, const uint32_t* vals, const 
  * A second kernel then chains d_projected through colour, conic, 2D mean,
  * Jacobian, view transform, covariance and the activations to the parameter
  * gradients, one thread per Gaussian summing over views (no atomics).
+ * Equivalent to gs_rasterize_bwd_pixels followed by gs_project_bwd.
  *
  * in  (device): the parameters and cams_dev given to gs_project; projected,
  *               counts from gs_project; vals, tile_ranges from gs_bin_sort;
@@ -256,6 +257,27 @@ GS_API int gs_rasterize_bwd(const float* means, const float* log_scales, const f
                      const uint32_t* tile_ranges, const float* final_T, const uint32_t* last, const float* dL_dimage,
                      float* d_projected, float* d_means, float* d_log_scales, float* d_quats, float* d_opacity_logits,
                      float* d_sh, int32_t* status_dev, gs_stream_t stream);
+
+/* gs_rasterize_bwd_pixels - first half of gs_rasterize_bwd: the per-pixel
+ * reverse compositing only. Zeroes d_projected [V*N][9] (device) and
+ * accumulates into it dL/d(mean2d, conic, colour, opacity) of every record;
+ * the other arguments are those of gs_rasterize_bwd.
+ * Errors: GS_ERR_ARG, GS_ERR_UNSUPPORTED, GS_ERR_CUDA. */
+GS_API int gs_rasterize_bwd_pixels(const float* projected, const uint32_t* vals, const uint32_t* tile_ranges,
+                                   const int32_t* sizes, int32_t V, const gs_config* cfg, int64_t N,
+                                   const float* final_T, const uint32_t* last, const float* dL_dimage,
+                                   float* d_projected, gs_stream_t stream);
+
+/* gs_project_bwd - second half of gs_rasterize_bwd: chains d_projected
+ * (from gs_rasterize_bwd_pixels) through SH colour and projection to the
+ * parameter gradients, one thread per Gaussian summing over views. Outputs
+ * and flags as in gs_rasterize_bwd. Errors: GS_ERR_ARG, GS_ERR_UNSUPPORTED,
+ * GS_ERR_CUDA. */
+GS_API int gs_project_bwd(const float* means, const float* log_scales, const float* quats, const float* opacity_logits,
+                          const float* sh, int64_t N, const gs_camera* cams_dev, const int32_t* sizes, int32_t V,
+                          const gs_config* cfg, const uint32_t* counts, const float* d_projected, float* d_means,
+                          float* d_log_scales, float* d_quats, float* d_opacity_logits, float* d_sh,
+                          int32_t* status_dev, gs_stream_t stream);
 
 /* gs_image_loss - image-space loss and its gradient.
  * Paper: §4 names an image-space loss per camera (fused SSIM); this is the

@@ -62,6 +62,8 @@ _SIGNATURES = {
     "gs_bin_sort_static": ([_VP, _VP, _VP, _I64, _VP, _I32, _VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP], ctypes.c_int),
     "gs_rasterize_fwd": ([_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "gs_rasterize_bwd": ([_VP] * 5 + [_I64, _VP, _VP, _I32, _VP] + [_VP] * 7 + [_VP] * 6 + [_VP, _VP], ctypes.c_int),
+    "gs_rasterize_bwd_pixels": ([_VP, _VP, _VP, _VP, _I32, _VP, _I64, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "gs_project_bwd": ([_VP] * 5 + [_I64, _VP, _VP, _I32, _VP, _VP, _VP] + [_VP] * 5 + [_VP, _VP], ctypes.c_int),
     "gs_image_loss": ([_VP, _VP, _I64, _F32, _F32, _VP, _VP, _VP], ctypes.c_int),
     "gs_adam_step": ([_VP, _VP, _VP, _VP, _I64, _F32, _F32, _F32, _F32, _VP, _VP], ctypes.c_int),
 }
@@ -195,6 +197,27 @@ def gs_rasterize_bwd(means, log_scales, quats, opacity_logits, sh, cams, sizes, 
                                  _ptr(dL_dimage), _ptr(d_projected), _ptr(d_means), _ptr(d_log_scales), _ptr(d_quats),
                                  _ptr(d_opacity_logits), _ptr(d_sh), _ptr(status), _stream(stream))
     _check(rc, "gs_rasterize_bwd")
+
+
+def gs_rasterize_bwd_pixels(projected, vals, tile_ranges, sizes, cfg, N, final_T, last, dL_dimage, d_projected,
+                            stream=None):
+    sz = _sizes(sizes)
+    c, cref = _cfg_ref(cfg)
+    rc = load().gs_rasterize_bwd_pixels(_ptr(projected), _ptr(vals), _ptr(tile_ranges), _ptr(sz), sz.shape[0], cref,
+                                        int(N), _ptr(final_T), _ptr(last), _ptr(dL_dimage), _ptr(d_projected),
+                                        _stream(stream))
+    _check(rc, "gs_rasterize_bwd_pixels")
+
+
+def gs_project_bwd(means, log_scales, quats, opacity_logits, sh, cams, sizes, cfg, counts, d_projected, d_means,
+                   d_log_scales, d_quats, d_opacity_logits, d_sh, status, stream=None):
+    sz = _sizes(sizes)
+    c, cref = _cfg_ref(cfg)
+    rc = load().gs_project_bwd(_ptr(means), _ptr(log_scales), _ptr(quats), _ptr(opacity_logits), _ptr(sh),
+                               means.shape[0], _ptr(cams), _ptr(sz), sz.shape[0], cref, _ptr(counts),
+                               _ptr(d_projected), _ptr(d_means), _ptr(d_log_scales), _ptr(d_quats),
+                               _ptr(d_opacity_logits), _ptr(d_sh), _ptr(status), _stream(stream))
+    _check(rc, "gs_project_bwd")
 
 
 def gs_image_loss(image, target, w_l1, w_l2, dL_dimage, loss, stream=None):

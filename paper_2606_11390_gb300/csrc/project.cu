@@ -605,3 +605,23 @@ extern "C" int gs_project(const float* means, const float* log_scales, const flo
 #undef GS_PFWD
   return cuda_status(cudaGetLastError());
 }
+
+extern "C" int gs_project_bwd(const float* means, const float* log_scales, const float* quats,
+                              const float* opacity_logits, const float* sh, int64_t N, const gs_camera* cams_dev,
+                              const int32_t* sizes, int32_t V, const gs_config* cfg, const uint32_t* counts,
+                              const float* d_projected, float* d_means, float* d_log_scales, float* d_quats,
+                              float* d_opacity_logits, float* d_sh, int32_t* status_dev, gs_stream_t stream) {
+  using namespace gs;
+  Layout L;
+  int rc = build_layout(sizes, V, cfg, &L, nullptr);
+  if (rc != GS_OK) return rc;
+  if (N < 0 || cfg->sh_degree < 0 || cfg->sh_degree > 3) return GS_ERR_ARG;
+  if (N == 0) return GS_OK;
+  if (N * static_cast<int64_t>(V) >= (int64_t(1) << 32)) return GS_ERR_ARG;
+  if (!means || !log_scales || !quats || !opacity_logits || !sh || !cams_dev || !counts || !d_projected || !d_means ||
+      !d_log_scales || !d_quats || !d_opacity_logits || !d_sh)
+    return GS_ERR_ARG;
+  return launch_project_bwd(means, log_scales, quats, opacity_logits, sh, N, cams_dev, L, make_consts(*cfg), counts,
+                            d_projected, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, status_dev,
+                            reinterpret_cast<cudaStream_t>(stream));
+}

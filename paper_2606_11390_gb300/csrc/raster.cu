@@ -422,25 +422,19 @@ extern "C" int gs_rasterize_fwd(const float* projected, const uint32_t* vals, co
   return GS_ERR_UNSUPPORTED;
 }
 
-extern "C" int gs_rasterize_bwd(const float* means, const float* log_scales, const float* quats,
-                                const float* opacity_logits, const float* sh, int64_t N, const gs_camera* cams_dev,
-                                const int32_t* sizes, int32_t V, const gs_config* cfg, const float* projected,
-                                const uint32_t* counts, const uint32_t* vals, const uint32_t* tile_ranges,
-                                const float* final_T, const uint32_t* last, const float* dL_dimage,
-                                float* d_projected, float* d_means, float* d_log_scales, float* d_quats,
-                                float* d_opacity_logits, float* d_sh, int32_t* status_dev, gs_stream_t stream_) {
+extern "C" int gs_rasterize_bwd_pixels(const float* projected, const uint32_t* vals, const uint32_t* tile_ranges,
+                                       const int32_t* sizes, int32_t V, const gs_config* cfg, int64_t N,
+                                       const float* final_T, const uint32_t* last, const float* dL_dimage,
+                                       float* d_projected, gs_stream_t stream_) {
   using namespace gs;
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   Layout L;
   int rc = build_layout(sizes, V, cfg, &L, nullptr);
   if (rc != GS_OK) return rc;
-  if (N < 0 || cfg->sh_degree < 0 || cfg->sh_degree > 3) return GS_ERR_ARG;
+  if (N < 0) return GS_ERR_ARG;
   if (N == 0) return GS_OK;
   if (N * static_cast<int64_t>(V) >= (int64_t(1) << 32)) return GS_ERR_ARG;
-  if (!means || !log_scales || !quats || !opacity_logits || !sh || !cams_dev || !projected || !counts ||
-      !tile_ranges || !final_T || !last || !dL_dimage || !d_projected || !d_means || !d_log_scales || !d_quats ||
-      !d_opacity_logits || !d_sh)
-    return GS_ERR_ARG;
+  if (!projected || !tile_ranges || !final_T || !last || !dL_dimage || !d_projected) return GS_ERR_ARG;
   if (!aligned16(projected) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7u)) return GS_ERR_ARG;
   const Consts K = make_consts(*cfg);
   if (cudaMemsetAsync(d_projected, 0, sizeof(float) * kDRecordFloats * static_cast<size_t>(N) * V, stream) !=
@@ -448,15 +442,22 @@ extern "C" int gs_rasterize_bwd(const float* means, const float* log_scales, con
     return GS_ERR_CUDA;
   const float4* pr = reinterpret_cast<const float4*>(projected);
   const uint2* rg = reinterpret_cast<const uint2*>(tile_ranges);
-  if (L.tile_w == 16 && L.tile_h == 16)
-    rc = launch_bwd<16, 16>(pr, vals, rg, L, K, final_T, last, dL_dimage, d_projected, stream);
-  else if (L.tile_w == 8 && L.tile_h == 8)
-    rc = launch_bwd<8, 8>(pr, vals, rg, L, K, final_T, last, dL_dimage, d_projected, stream);
-  else if (L.tile_w == 32 && L.tile_h == 16)
-    rc = launch_bwd<32, 16>(pr, vals, rg, L, K, final_T, last, dL_dimage, d_projected, stream);
-  else
-    return GS_ERR_UNSUPPORTED;
+  if (L.tile_w == 16 && L.tile_h == 16) return launch_bwd<16, 16>(pr, vals, rg, L, K, final_T, last, dL_dimage, d_projected, stream);
+  if (L.tile_w == 8 && L.tile_h == 8) return launch_bwd<8, 8>(pr, vals, rg, L, K, final_T, last, dL_dimage, d_projected, stream);
+  if (L.tile_w == 32 && L.tile_h == 16) return launch_bwd<32, 16>(pr, vals, rg, L, K, final_T, last, dL_dimage, d_projected, stream);
+  return GS_ERR_UNSUPPORTED;
+}
+
+extern "C" int gs_rasterize_bwd(const float* means, const float* log_scales, const float* quats,
+                                const float* opacity_logits, const float* sh, int64_t N, const gs_camera* cams_dev,
+                                const int32_t* sizes, int32_t V, const gs_config* cfg, const float* projected,
+                                const uint32_t* counts, const uint32_t* vals, const uint32_t* tile_ranges,
+                                const float* final_T, const uint32_t* last, const float* dL_dimage,
+                                float* d_projected, float* d_means, float* d_log_scales, float* d_quats,
+                                float* d_opacity_logits, float* d_sh, int32_t* status_dev, gs_stream_t stream) {
+  const int rc = gs_rasterize_bwd_pixels(projected, vals, tile_ranges, sizes, V, cfg, N, final_T, last, dL_dimage,
+                                         d_projected, stream);
   if (rc != GS_OK) return rc;
-  return launch_project_bwd(means, log_scales, quats, opacity_logits, sh, N, cams_dev, L, K, counts, d_projected,
-                            d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, status_dev, stream);
+  return gs_project_bwd(means, log_scales, quats, opacity_logits, sh, N, cams_dev, sizes, V, cfg, counts, d_projected,
+                        d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, status_dev, stream);
 }
