@@ -217,6 +217,16 @@ __global__ void __launch_bounds__(kEmitThreads) emit_tiles_kernel(
   const int tid = threadIdx.x, lane = tid & 31;
   for (int i = tid; i < kMaxTilePasses * kRadix; i += kEmitThreads) (&s_hist[0][0])[i] = 0;
   __syncthreads();
+  // Digit histograms: the lowest digit goes straight to a shared atomic (the
+  // lanes hold consecutive tiles, so their low digits differ); the higher
+  // digits change rarely along a lane's entries and are run-length counted
+  // in registers, flushed when the digit changes.
+  uint32_t run_d[kMaxTilePasses - 1], run_c[kMaxTilePasses - 1];
+#pragma unroll
+  for (int p = 0; p < kMaxTilePasses - 1; ++p) {
+    run_d[p] = 0;
+    run_c[p] = 0;
+  }
   const int64_t n = *n_visible;
   const int64_t warps_total = static_cast<int64_t>(gridDim.x) * (kEmitThreads / 32);
   for (int64_t w = static_cast<int64_t>(blockIdx.x) * (kEmitThreads / 32) + (tid >> 5); w * 32 < n;
@@ -240,20 +250,39 @@ __global__ void __launch_bounds__(kEmitThreads) emit_tiles_kernel(
       const int x1 = __shfl_sync(0xffffffffu, static_cast<int>(r.z), src);
       const int v = static_cast<int>(rvg / static_cast<uint64_t>(N));
       const uint32_t tb = L.tile_base[v];
-      const int ntx = L.ntx[v];
-      const uint32_t wdt = static_cast<uint32_t>(x1 - x0);
+      const uint32_t ntx = static_cast<uint32_t>(L.ntx[v]);
+      const int wdt = x1 - x0;
+      const float inv_w = 1.0f / static_cast<float>(wdt);
       for (uint32_t k = lane; k < c; k += 32) {
         const uint64_t pos = static_cast<uint64_t>(roff) + k;
         if (pos >= capacity) break;
-        const uint32_t ty = static_cast<uint32_t>(y0) + k / wdt;
-        const uint32_t tx = static_cast<uint32_t>(x0) + k % wdt;
-        const uint32_t tile = tb + ty * static_cast<uint32_t>(ntx) + tx;
+        // k = row * wdt + col, division by the float reciprocal with an exact fix-up
+        int row = __float2int_rz(static_cast<float>(k) * inv_w);
+        int col = static_cast<int>(k) - row * wdt;
+        if (col < 0) { --row; col += wdt; }
+        if (col >= wdt) { ++row; col -= wdt; }
+        const uint32_t tile = tb + static_cast<uint32_t>(y0 + row) * ntx + static_cast<uint32_t>(x0 + col);
         tkeys[pos] = tile;
         tvals[pos] = rvg;
-        for (int p = 0; p < tile_passes; ++p) atomicAdd(&s_hist[p][(tile >> (8 * p)) & 0xffu], 1u);
+        if (tile_passes > 0) atomicAdd(&s_hist[0][tile & 0xffu], 1u);
+#pragma unroll
+        for (int p = 1; p < kMaxTilePasses; ++p) {
+          if (p < tile_passes) {
+            const uint32_t d = (tile >> (8 * p)) & 0xffu;
+            if (d != run_d[p - 1]) {
+              if (run_c[p - 1]) atomicAdd(&s_hist[p][run_d[p - 1]], run_c[p - 1]);
+              run_d[p - 1] = d;
+              run_c[p - 1] = 0;
+            }
+            ++run_c[p - 1];
+          }
+        }
       }
     }
   }
+#pragma unroll
+  for (int p = 1; p < kMaxTilePasses; ++p)
+    if (p < tile_passes && run_c[p - 1]) atomicAdd(&s_hist[p][run_d[p - 1]], run_c[p - 1]);
   __syncthreads();
   for (int i = tid; i < tile_passes * kRadix; i += kEmitThreads) {
     const uint32_t c = (&s_hist[0][0])[i];
@@ -287,8 +316,12 @@ __global__ void hist_scan_kernel(uint32_t* hist, int passes) {
 // ---------------------------------------------------------------------------
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 items
+// Items per thread of a digit pass (tile = 256 x items).
+#ifndef GS_SORT_ITEMS
+#define GS_SORT_ITEMS 16
+#endif
+constexpr int kSortItems = GS_SORT_ITEMS;
+constexpr int kSortTile = kSortThreads * kSortItems;
 
 struct PassArgs {
   const uint32_t* keys_in;
@@ -336,25 +369,27 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(PassArgs a, int
     key[i] = li < n_valid ? a.keys_in[tile_start + li] : 0u;
     val[i] = li < n_valid ? a.vals_in[tile_start + li] : 0u;
   }
-  // 2. stable rank within the warp (match_any on the digit, item by item)
+  // 2. stable rank within the warp, item by item: the lanes holding the same
+  //    digit are found with one ballot per digit bit (cheaper than match_any)
   uint32_t rank[kSortItems];
   const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
     const int li = warp_base + i * 32 + lane;
     const bool valid = li < n_valid;
-    const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
-    rank[i] = 0;
-    if (valid) {
-      const uint32_t d = (key[i] >> a.shift) & 0xffu;
-      const uint32_t peers = __match_any_sync(vmask, d);
-      const int leader = __ffs(peers) - 1;
-      uint32_t before = 0;
-      if (lane == leader) before = sm.warp_hist[warp][d];
-      before = __shfl_sync(vmask, before, leader);
-      rank[i] = before + __popc(peers & lt_mask);
-      if (lane == leader) sm.warp_hist[warp][d] = before + __popc(peers);
+    const uint32_t d = (key[i] >> a.shift) & 0xffu;
+    uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+    for (int bit = 0; bit < 8; ++bit) {
+      const uint32_t bal = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+      peers &= ((d >> bit) & 1u) ? bal : ~bal;
     }
+    const int leader = valid ? __ffs(peers) - 1 : 0;
+    uint32_t before = 0;
+    if (valid && lane == leader) before = sm.warp_hist[warp][d];
+    before = __shfl_sync(0xffffffffu, before, leader);
+    rank[i] = before + __popc(peers & lt_mask);
+    if (valid && lane == leader) sm.warp_hist[warp][d] = before + __popc(peers);
     __syncwarp();
   }
   __syncthreads();

@@ -53,14 +53,20 @@ __device__ __forceinline__ void load_splat(const float4* __restrict__ projected,
   c = r2.z;
 }
 
-// e = -power*log2(e) for pixel centre (px, py). Every operation explicitly
+// e = -power*log2(e) for pixel centre (px, py); q = A' dx + B' dy and
+// cdy = C' dy are returned for the backward. Every operation explicitly
 // rounded so forward and backward compute the same bits.
-__device__ __forceinline__ float splat_exponent(float px, float py, const float4& a, float Cp, float& dx, float& dy) {
+__device__ __forceinline__ float splat_exponent(float px, float py, const float4& a, float Cp, float& dx, float& dy,
+                                                float& q, float& cdy) {
   dx = __fsub_rn(px, a.x);
   dy = __fsub_rn(py, a.y);
-  const float q = __fmaf_rn(a.z, dx, __fmul_rn(a.w, dy));
-  return __fmaf_rn(q, dx, __fmul_rn(__fmul_rn(Cp, dy), dy));
+  q = __fmaf_rn(a.z, dx, __fmul_rn(a.w, dy));
+  cdy = __fmul_rn(Cp, dy);
+  return __fmaf_rn(q, dx, __fmul_rn(cdy, dy));
 }
+
+// Splats staged per thread per shared-memory batch.
+constexpr int kSplatsPerThread = 2;
 
 // Warp w of a TW x TH tile covers the 8x8 block (8*(w % (TW/8)), 8*(w / (TW/8)));
 // lane l owns pixels (l & 7, l >> 3) and (l & 7, (l >> 3) + 4) of that block.
@@ -110,8 +116,8 @@ struct PixelFwd {
 // One compositing step of one pixel (forward rule).
 __device__ __forceinline__ void composite_step(PixelFwd& P, float px, float py, const float4& a, const float4& b,
                                                float cb, uint32_t rel, float cap, float amin, float tstop) {
-  float dx, dy;
-  const float e = splat_exponent(px, py, a, b.x, dx, dy);
+  float dx, dy, q, cdy;
+  const float e = splat_exponent(px, py, a, b.x, dx, dy, q, cdy);
   if (e > 0.0f) return;
   const float alpha = fminf(cap, __fmul_rn(b.y, ex2_approx(e)));
   if (alpha < amin) return;
@@ -135,7 +141,8 @@ __global__ void __launch_bounds__(TW* TH / 2) raster_fwd_kernel(const float4* __
                                                                  const Consts K, float* __restrict__ image,
                                                                  float* __restrict__ final_T,
                                                                  uint32_t* __restrict__ last) {
-  constexpr int B = TW * TH / 2;
+  constexpr int NT = TW * TH / 2;             // threads
+  constexpr int B = NT * kSplatsPerThread;    // splats per batch
   __shared__ float4 s_a[B];
   __shared__ float4 s_b[B];
   __shared__ float s_c[B];
@@ -159,15 +166,15 @@ __global__ void __launch_bounds__(TW* TH / 2) raster_fwd_kernel(const float4* __
   const float tx0 = static_cast<float>(tx * TW), ty0 = static_cast<float>(ty * TH);
   PixelFwd P0{1.0f, 0.0f, 0.0f, 0.0f, 0u, !in0}, P1{1.0f, 0.0f, 0.0f, 0.0f, 0u, !in1};
   for (int b0 = 0; b0 < n; b0 += B) {
-    if (__syncthreads_count(P0.done && P1.done) == B) break;
-    if (b0 + tid < n) {
+    if (__syncthreads_count(P0.done && P1.done) == NT) break;
+    for (int k = tid; k < B && b0 + k < n; k += NT) {
       float4 a, b;
       float c;
-      load_splat(projected, vals[range.x + b0 + tid], a, b, c);
-      s_a[tid] = a;
-      s_b[tid] = b;
-      s_c[tid] = c;
-      s_m[tid] = warp_cull_mask<TW, TH>(a, b, tx0, ty0, amin);
+      load_splat(projected, vals[range.x + b0 + k], a, b, c);
+      s_a[k] = a;
+      s_b[k] = b;
+      s_c[k] = c;
+      s_m[k] = warp_cull_mask<TW, TH>(a, b, tx0, ty0, amin);
     }
     __syncthreads();
     const int cnt = min(B, n - b0);
@@ -245,12 +252,16 @@ struct PixelBwd {
 };
 
 // Backward contribution of splat (a, b, cb) at relative position `rel` to one
-// pixel, added into gv[9]; returns whether the pixel took part.
+// pixel, added into gv[9]; returns whether the pixel took part. Constant
+// factors are applied once per splat when the sums are flushed:
+//   gv[0..1] = sum dalpha*alpha*(2A'dx + B'dy, B'dx + 2C'dy)  -> dmean = -gv/log2e
+//   gv[2..4] = sum dalpha*alpha*(dx^2, dx dy, dy^2)          -> dconic = -(gv2/2, gv3, gv4/2)
+//   gv[5..7] = sum alpha T dL/dC, gv[8] = sum dalpha G          (as is)
 __device__ __forceinline__ bool pixel_grad(PixelBwd& P, float px, float py, const float4& a, const float4& b,
                                            float cb, uint32_t rel, float cap, float amin, float gv[9]) {
   if (rel >= P.last) return false;
-  float dx, dy;
-  const float e = splat_exponent(px, py, a, b.x, dx, dy);
+  float dx, dy, q, cdy;
+  const float e = splat_exponent(px, py, a, b.x, dx, dy, q, cdy);
   if (e > 0.0f) return false;
   const float G = ex2_approx(e);
   const float oG = __fmul_rn(b.y, G);
@@ -269,15 +280,13 @@ __device__ __forceinline__ bool pixel_grad(PixelBwd& P, float px, float py, cons
   P.ar2 += alpha * d2;
   if (!(oG > cap)) {
     gv[8] += dalpha * G;
-    // d power = -dalpha alpha; with A = -2A'/log2e, B = -B'/log2e, C = -2C'/log2e
-    const float dpow = -dalpha * alpha;
-    const float dpl = dpow * (1.0f / kLog2e);
-    gv[0] += dpl * (2.0f * a.z * dx + a.w * dy);
-    gv[1] += dpl * (a.w * dx + 2.0f * b.x * dy);
-    const float hd = 0.5f * dpow;
-    gv[2] += hd * dx * dx;
-    gv[3] += dpow * dx * dy;
-    gv[4] += hd * dy * dy;
+    const float dpw = dalpha * alpha;
+    gv[0] += dpw * fmaf(a.z, dx, q);
+    gv[1] += dpw * fmaf(a.w, dx, cdy + cdy);
+    const float px_ = dpw * dx;
+    gv[2] += px_ * dx;
+    gv[3] += px_ * dy;
+    gv[4] += (dpw * dy) * dy;
   }
   return true;
 }
@@ -287,8 +296,9 @@ __global__ void __launch_bounds__(TW* TH / 2) raster_bwd_kernel(
     const float4* __restrict__ projected, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
     const Layout L, const Consts K, const float* __restrict__ final_T, const uint32_t* __restrict__ last,
     const float* __restrict__ dL_dimage, float* __restrict__ d_proj) {
-  constexpr int B = TW * TH / 2;
-  constexpr int NW = B / 32;
+  constexpr int NT = TW * TH / 2;            // threads
+  constexpr int B = NT * kSplatsPerThread;   // splats per batch
+  constexpr int NW = NT / 32;
   __shared__ float4 s_a[B];
   __shared__ float4 s_b[B];
   __shared__ float s_c[B];
@@ -329,7 +339,7 @@ __global__ void __launch_bounds__(TW* TH / 2) raster_bwd_kernel(
   const int my_slot = slot_of_lane(lane);
   const uint32_t wmax = __reduce_max_sync(0xffffffffu, max(P0.last, P1.last));
   if (lane == 0) s_wmax[warp] = wmax;
-  for (int i = tid; i < B * 9; i += B) s_grad[i] = 0.0f;
+  for (int i = tid; i < B * 9; i += NT) s_grad[i] = 0.0f;
   __syncthreads();
   uint32_t max_last = 0;
 #pragma unroll
@@ -337,16 +347,16 @@ __global__ void __launch_bounds__(TW* TH / 2) raster_bwd_kernel(
 
   for (int b_end = static_cast<int>(max_last); b_end > 0; b_end -= B) {
     const int cnt = min(B, b_end);
-    if (tid < cnt) {
-      const uint32_t vg = vals[range.x + b_end - 1 - tid];
+    for (int k = tid; k < cnt; k += NT) {
+      const uint32_t vg = vals[range.x + b_end - 1 - k];
       float4 a, b;
       float c;
       load_splat(projected, vg, a, b, c);
-      s_a[tid] = a;
-      s_b[tid] = b;
-      s_c[tid] = c;
-      s_vg[tid] = vg;
-      s_m[tid] = warp_cull_mask<TW, TH>(a, b, tx0, ty0, amin);
+      s_a[k] = a;
+      s_b[k] = b;
+      s_c[k] = c;
+      s_vg[k] = vg;
+      s_m[k] = warp_cull_mask<TW, TH>(a, b, tx0, ty0, amin);
     }
     __syncthreads();
     // entries j hold relative position b_end-1-j; this warp needs rel < wmax
@@ -368,14 +378,15 @@ __global__ void __launch_bounds__(TW* TH / 2) raster_bwd_kernel(
       }
     }
     __syncthreads();
-    if (tid < cnt) {
-      float* dst = d_proj + static_cast<size_t>(s_vg[tid]) * kDRecordFloats;
+    for (int k = tid; k < cnt; k += NT) {
+      float* dst = d_proj + static_cast<size_t>(s_vg[k]) * kDRecordFloats;
+      constexpr float kScale[9] = {-1.0f / kLog2e, -1.0f / kLog2e, -0.5f, -1.0f, -0.5f, 1.0f, 1.0f, 1.0f, 1.0f};
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
-        const float gval = s_grad[tid * 9 + i];
+        const float gval = s_grad[k * 9 + i];
         if (gval != 0.0f) {
-          atomicAdd(dst + i, gval);
-          s_grad[tid * 9 + i] = 0.0f;
+          atomicAdd(dst + i, gval * kScale[i]);
+          s_grad[k * 9 + i] = 0.0f;
         }
       }
     }
