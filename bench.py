@@ -37,13 +37,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="diff_4k", choices=["diff_4k", "batch16", "train_1080p", "tiny"])
+    ap.add_argument("--workload", default="diff_4k", choices=["diff_4k", "batch16", "train_1080p", "tiny", "street"])
     ap.add_argument("--mode", default="batched", choices=["batched", "per_view"])
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the per-view comparison leg")
     ap.add_argument("--tile", default=None, help="WxH tile override, e.g. 16x16")
+    ap.add_argument("--gaussians", type=int, default=None, help="override the workload's Gaussian count")
     return ap.parse_args()
 
 
@@ -155,10 +156,10 @@ def measured_peaks():
 # ---------------------------------------------------------------------------
 # workload
 # ---------------------------------------------------------------------------
-def make_scene(name):
+def make_scene(name, gaussians=None):
     from paper_2606_11390_gb300 import scenes
 
-    return scenes.make(name)
+    return scenes.make(name) if gaussians is None else scenes.make(name, N=gaussians)
 
 
 def workload_config(scene, args, tile):
@@ -167,8 +168,9 @@ def workload_config(scene, args, tile):
             "resolutions": sorted({f"{w}x{h}" for w, h in s["sizes"]}), "pixels": int(
                 (s["sizes"][:, 0].astype(np.int64) * s["sizes"][:, 1]).sum()),
             "tile": f"{tile[0]}x{tile[1]}", "sh_degree": int(s["cfg"]["sh_degree"]), "mode": args.mode,
-            "cuda_graph": args.mode == "batched" and not args.no_graph,
-            "loss": f"L1 + {s['loss'][1]} L2", "l2_flush": "none: inputs (params 0.94 GB + keys) exceed the 129 MB L2"}
+            "cuda_graph": args.mode == "batched" and not args.no_graph, "adam": s["name"] == "street",
+            "loss": f"L1 + {s['loss'][1]} L2",
+            "l2_flush": f"none: inputs (parameters {int(s['means'].shape[0]) * 236 / 1e9:.2f} GB, plus keys) exceed the 129 MB L2"}
 
 
 # ---------------------------------------------------------------------------
@@ -320,9 +322,10 @@ def main():
     dev = dist.local_rank if torch.cuda.is_available() else 0
     torch.cuda.set_device(dev)
     gs.load()
-    scene = make_scene(args.workload)
+    scene = make_scene(args.workload, args.gaussians)
     tile = tuple(int(x) for x in args.tile.split("x")) if args.tile else (scene["cfg"]["tile_w"], scene["cfg"]["tile_h"])
-    step = R.TrainStep(scene, mode=args.mode, graph=not args.no_graph, tile=tile).prepare()
+    adam = scene["name"] == "street"  # the street workload's step includes the fused Adam update
+    step = R.TrainStep(scene, mode=args.mode, graph=not args.no_graph, tile=tile, adam=adam).prepare()
     P = step.cams.n_pixels
     launches = step.launches_per_step
     stream = torch.cuda.current_stream()

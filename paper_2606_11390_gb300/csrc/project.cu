@@ -36,6 +36,7 @@ constexpr int kProjBlock = 128;
 #define GS_PBWD_MIN_BLOCKS 3
 #endif
 
+
 __device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
@@ -194,6 +195,46 @@ __device__ __forceinline__ void project_view(const GaussLocal& G, const gs_camer
   if (visible && P.x1 > P.x0 && P.y1 > P.y0) count = static_cast<uint32_t>((P.x1 - P.x0) * (P.y1 - P.y0));
   P.visible = visible && count > 0;
   P.count = P.visible ? count : 0u;
+}
+
+// Per-view quantities the backward needs (everything but the rectangle),
+// with fast reciprocals. Only the frustum-clamp decision must match the
+// forward exactly, so u = tx/tz and w = ty/tz are divided with correct
+// rounding as there; the rest only needs to be accurate.
+__device__ __forceinline__ void project_view_bwd(const GaussLocal& G, const gs_camera& cam, int W, int H,
+                                                 const Consts& K, ViewProj& P) {
+  const float* vm = cam.viewmat;
+  for (int i = 0; i < 3; ++i)
+    P.t[i] = fadd(dot3(vm[4 * i], G.mean[0], vm[4 * i + 1], G.mean[1], vm[4 * i + 2], G.mean[2]), vm[4 * i + 3]);
+  const float tz = P.t[2];
+  const float itz = rcp_approx(tz);
+  const float Wf = static_cast<float>(W), Hf = static_cast<float>(H);
+  P.u = fdiv(P.t[0], tz);
+  P.w = fdiv(P.t[1], tz);
+  const float lox = fdiv(fsub(fmul(-0.15f, Wf), cam.cx), cam.fx);
+  const float hix = fdiv(fsub(fmul(1.15f, Wf), cam.cx), cam.fx);
+  const float loy = fdiv(fsub(fmul(-0.15f, Hf), cam.cy), cam.fy);
+  const float hiy = fdiv(fsub(fmul(1.15f, Hf), cam.cy), cam.fy);
+  P.uc = P.u < lox ? lox : (P.u > hix ? hix : P.u);
+  P.wc = P.w < loy ? loy : (P.w > hiy ? hiy : P.w);
+  P.clamp_x = !(P.u > lox && P.u < hix);
+  P.clamp_y = !(P.w > loy && P.w < hiy);
+  P.J00 = cam.fx * itz;
+  P.J02 = -cam.fx * P.uc * itz;
+  P.J11 = cam.fy * itz;
+  P.J12 = -cam.fy * P.wc * itz;
+  for (int j = 0; j < 3; ++j) {
+    P.T[j] = P.J00 * vm[j] + P.J02 * vm[8 + j];
+    P.T[3 + j] = P.J11 * vm[4 + j] + P.J12 * vm[8 + j];
+  }
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 3; ++j)
+      P.U[3 * i + j] = P.T[3 * i] * sig_at(G.Sig, 0, j) + P.T[3 * i + 1] * sig_at(G.Sig, 1, j) +
+                       P.T[3 * i + 2] * sig_at(G.Sig, 2, j);
+  P.a = P.U[0] * P.T[0] + P.U[1] * P.T[1] + P.U[2] * P.T[2] + K.eps2d;
+  P.b = P.U[0] * P.T[3] + P.U[1] * P.T[4] + P.U[2] * P.T[5];
+  P.c = P.U[3] * P.T[3] + P.U[4] * P.T[4] + P.U[5] * P.T[5] + K.eps2d;
+  P.det = P.a * P.c - P.b * P.b;
 }
 
 // Real SH basis (degree <= 3) in 3DGS coefficient order, Cartesian form.
@@ -414,12 +455,17 @@ __global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_ke
   float gm[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, go = 0.f;
   float shc[3 * NB], gsh[3 * NB];
   GaussLocal G;
-  float* my_sh = reinterpret_cast<float*>(&sm.p.sh[12 * tid]);
+  float4* my_sh4 = &sm.p.sh[12 * tid];
 #pragma unroll
-  for (int i = 0; i < 3 * NB; ++i) {
-    shc[i] = my_sh[i];
-    gsh[i] = 0.0f;
+  for (int i = 0; i < (3 * NB + 3) / 4; ++i) {
+    const float4 q4 = my_sh4[i];
+    const float q[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (4 * i + k < 3 * NB) shc[4 * i + k] = q[k];
   }
+#pragma unroll
+  for (int i = 0; i < 3 * NB; ++i) gsh[i] = 0.0f;
   if (active) gauss_local(&sm.p.means[3 * tid], &sm.p.log_scales[3 * tid], sm.p.quats[tid], sm.p.opac[tid], G);
   for (int v = 0; active && v < L.V; ++v) {
     const int64_t vg = static_cast<int64_t>(v) * N + g0 + tid;
@@ -430,7 +476,7 @@ __global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_ke
     for (int i = 0; i < 9; ++i) g9[i] = dp[i];
     const gs_camera& cam = sm.p.cams[v];
     ViewProj P;
-    project_view(G, cam, L.width[v], L.height[v], L.tile_w, L.tile_h, L.ntx[v], L.nty[v], K, P);
+    project_view_bwd(G, cam, L.width[v], L.height[v], K, P);
     const float* vm = cam.viewmat;
     // opacity
     go += g9[8] * G.o * (1.0f - G.o);
@@ -539,7 +585,12 @@ __global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_ke
   // SH gradients through the thread's own staging slot (coefficients past
   // the degree get 0), then coalesced stores
 #pragma unroll
-  for (int i = 0; i < 48; ++i) my_sh[i] = i < 3 * NB ? gsh[i < 3 * NB ? i : 0] : 0.0f;
+  for (int i = 0; i < 12; ++i) {
+    float q[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) q[k] = (4 * i + k < 3 * NB) ? gsh[(4 * i + k < 3 * NB) ? 4 * i + k : 0] : 0.0f;
+    my_sh4[i] = make_float4(q[0], q[1], q[2], q[3]);
+  }
   __syncthreads();
   float* dst = d_sh + g0 * 48;
   const float* src = reinterpret_cast<const float*>(sm.p.sh);
