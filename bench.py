@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip the per-view comparison leg")
     ap.add_argument("--tile", default=None, help="WxH tile override, e.g. 16x16")
     ap.add_argument("--gaussians", type=int, default=None, help="override the workload's Gaussian count")
+    ap.add_argument("--raster-px", type=int, default=4, choices=[2, 4], help="pixels per thread in the rasteriser")
     return ap.parse_args()
 
 
@@ -323,6 +324,8 @@ def main():
     torch.cuda.set_device(dev)
     gs.load()
     scene = make_scene(args.workload, args.gaussians)
+    if args.raster_px == 2:
+        scene["cfg"] = dict(scene["cfg"], flags=gs.GS_FLAG_RASTER_2PX)
     tile = tuple(int(x) for x in args.tile.split("x")) if args.tile else (scene["cfg"]["tile_w"], scene["cfg"]["tile_h"])
     adam = scene["name"] == "street"  # the street workload's step includes the fused Adam update
     step = R.TrainStep(scene, mode=args.mode, graph=not args.no_graph, tile=tile, adam=adam).prepare()

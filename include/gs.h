@@ -104,6 +104,10 @@ typedef struct gs_config {
 /* gs_config.flags: gs_rasterize_bwd adds the parameter gradients to the
  * output arrays instead of overwriting them (to sum over separate calls). */
 #define GS_FLAG_ACCUMULATE_GRADS 1
+/* gs_config.flags: the rasteriser gives each thread 2 pixels (8-column warp
+ * blocks) instead of 4 (16-column warp blocks) for 16x16 and 32x16 tiles;
+ * a performance choice only, results are the same. */
+#define GS_FLAG_RASTER_2PX 2
 
 /* Number of 32-bit floats in one projected record (see gs_project). */
 #define GS_RECORD_FLOATS 12

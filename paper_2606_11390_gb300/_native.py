@@ -21,6 +21,7 @@ GS_OK, GS_ERR_ARG, GS_ERR_CUDA, GS_ERR_UNSUPPORTED, GS_ERR_TOO_LARGE = 0, 1, 2, 
 GS_STATUS_CAPACITY, GS_STATUS_TIMEOUT, GS_STATUS_BOUNDS = 1, 2, 4
 GS_MAX_VIEWS = 64
 GS_FLAG_ACCUMULATE_GRADS = 1
+GS_FLAG_RASTER_2PX = 2
 RECORD_FLOATS = 12
 DRECORD_FLOATS = 9
 

@@ -321,6 +321,10 @@ constexpr int kSortWarps = kSortThreads / 32;
 #define GS_SORT_ITEMS 16
 #endif
 constexpr int kSortItems = GS_SORT_ITEMS;
+// CTAs per SM the digit pass is compiled for (caps registers at 65536 / (256 x this)).
+#ifndef GS_SORT_MIN_BLOCKS
+#define GS_SORT_MIN_BLOCKS 4
+#endif
 constexpr int kSortTile = kSortThreads * kSortItems;
 
 struct PassArgs {
@@ -346,7 +350,7 @@ struct __align__(16) SortSmem {
   uint32_t tile;
 };
 
-__global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(PassArgs a, int32_t* status) {
+__global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) sort_pass_kernel(PassArgs a, int32_t* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SortSmem& sm = *reinterpret_cast<SortSmem*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -618,7 +622,9 @@ extern "C" int gs_bin_sort(const float* projected, const int16_t* rects, const u
   static bool attr_set = false;
   if (!attr_set) {
     if (cudaFuncSetAttribute(sort_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(sizeof(SortSmem))) != cudaSuccess)
+                             static_cast<int>(sizeof(SortSmem))) != cudaSuccess ||
+        cudaFuncSetAttribute(sort_pass_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared) != cudaSuccess)
       return GS_ERR_CUDA;
     attr_set = true;
   }

@@ -65,30 +65,41 @@ __device__ __forceinline__ float splat_exponent(float px, float py, const float4
   return __fmaf_rn(q, dx, __fmul_rn(cdy, dy));
 }
 
-// Splats staged per thread per shared-memory batch.
-constexpr int kSplatsPerThread = 2;
+// Splats staged per shared-memory batch.
+constexpr int kBatch = 256;
 
-// Warp w of a TW x TH tile covers the 8x8 block (8*(w % (TW/8)), 8*(w / (TW/8)));
-// lane l owns pixels (l & 7, l >> 3) and (l & 7, (l >> 3) + 4) of that block.
-template <int TW>
-__device__ __forceinline__ void pixel_of(int tid, int& x, int& y0) {
-  const int w = tid >> 5, l = tid & 31;
-  x = 8 * (w % (TW / 8)) + (l & 7);
-  y0 = 8 * (w / (TW / 8)) + (l >> 3);
-}
+// Thread / pixel geometry. With PPT pixels per thread a warp covers a block
+// of WB = 4 PPT columns by 8 rows: lane l owns column l % WB and rows
+// l / WB + r * (32 / WB), r < PPT. The warps of a TW x TH tile tile it in
+// TW / WB columns and TH / 8 rows of blocks.
+template <int TW, int TH, int PPT>
+struct Geo {
+  static constexpr int WB = 4 * PPT;
+  static constexpr int RS = 32 / WB;
+  static constexpr int NT = TW * TH / PPT;
+  static constexpr int NW = NT / 32;
+  static constexpr int WXN = TW / WB;
+  static constexpr int B = NT > kBatch ? NT : kBatch;
+  static_assert(TW % WB == 0 && TH % 8 == 0 && PPT * RS == 8, "unsupported tile / pixels-per-thread");
+  static_assert(NW <= 32, "at most 32 warps");
+  __device__ static void pixel_of(int tid, int& x, int& y0) {
+    const int w = tid >> 5, l = tid & 31;
+    x = WB * (w % WXN) + (l % WB);
+    y0 = 8 * (w / WXN) + (l / WB);
+  }
+};
 
-// Bitmask of the warps of a TW x TH tile at (tx0, ty0) whose 8x8 block meets
+// Bitmask of the warps of the tile at (tx0, ty0) whose pixel block meets
 // the bounding box of {d : alpha(d) >= alpha_min}. With the scaled conic
 // M = [[-2A', -B'], [-B', -2C']] (so e = -d^T M d / 2) the set is
 // d^T M d / 2 <= ts, ts = log2(o / alpha_min), whose bounding box has
 // half-widths sqrt(2 ts (M^-1)_00) and sqrt(2 ts (M^-1)_11). ts and the
 // half-widths are widened (x1.001 + margin), far beyond the rounding of the
 // per-pixel evaluation, so no pixel outside the box can pass the alpha test.
-template <int TW, int TH>
+template <class G>
 __device__ __forceinline__ uint32_t warp_cull_mask(const float4& a, const float4& b, float tx0, float ty0,
                                                     float amin) {
-  constexpr int WX = TW / 8, NW = (TW / 8) * (TH / 8);
-  constexpr uint32_t kAll = (NW >= 32) ? 0xffffffffu : ((1u << NW) - 1u);
+  constexpr uint32_t kAll = (G::NW >= 32) ? 0xffffffffu : ((1u << G::NW) - 1u);
   const float o = b.y;
   if (!(o > amin)) return 0u;
   const float m00 = -2.0f * a.z, m01 = -a.w, m11 = -2.0f * b.x;
@@ -100,9 +111,12 @@ __device__ __forceinline__ uint32_t warp_cull_mask(const float4& a, const float4
   if (!(hx < 1e30f) || !(hy < 1e30f)) return kAll;
   uint32_t mask = 0;
 #pragma unroll
-  for (int w = 0; w < NW; ++w) {
-    const float xlo = tx0 + 8.0f * (w % WX) + 0.5f, ylo = ty0 + 8.0f * (w / WX) + 0.5f;
-    if (a.x + hx >= xlo && a.x - hx <= xlo + 7.0f && a.y + hy >= ylo && a.y - hy <= ylo + 7.0f) mask |= 1u << w;
+  for (int w = 0; w < G::NW; ++w) {
+    const float xlo = tx0 + static_cast<float>(G::WB * (w % G::WXN)) + 0.5f;
+    const float ylo = ty0 + static_cast<float>(8 * (w / G::WXN)) + 0.5f;
+    if (a.x + hx >= xlo && a.x - hx <= xlo + static_cast<float>(G::WB - 1) && a.y + hy >= ylo &&
+        a.y - hy <= ylo + 7.0f)
+      mask |= 1u << w;
   }
   return mask;
 }
@@ -134,15 +148,15 @@ __device__ __forceinline__ void composite_step(PixelFwd& P, float px, float py, 
   P.last = rel + 1;
 }
 
-template <int TW, int TH>
-__global__ void __launch_bounds__(TW* TH / 2) raster_fwd_kernel(const float4* __restrict__ projected,
-                                                                 const uint32_t* __restrict__ vals,
-                                                                 const uint2* __restrict__ ranges, const Layout L,
-                                                                 const Consts K, float* __restrict__ image,
-                                                                 float* __restrict__ final_T,
-                                                                 uint32_t* __restrict__ last) {
-  constexpr int NT = TW * TH / 2;             // threads
-  constexpr int B = NT * kSplatsPerThread;    // splats per batch
+template <int TW, int TH, int PPT>
+__global__ void __launch_bounds__(TW* TH / PPT) raster_fwd_kernel(const float4* __restrict__ projected,
+                                                                   const uint32_t* __restrict__ vals,
+                                                                   const uint2* __restrict__ ranges, const Layout L,
+                                                                   const Consts K, float* __restrict__ image,
+                                                                   float* __restrict__ final_T,
+                                                                   uint32_t* __restrict__ last) {
+  using G = Geo<TW, TH, PPT>;
+  constexpr int NT = G::NT, B = G::B;
   __shared__ float4 s_a[B];
   __shared__ float4 s_b[B];
   __shared__ float s_c[B];
@@ -155,18 +169,23 @@ __global__ void __launch_bounds__(TW* TH / 2) raster_fwd_kernel(const float4* __
   const int tid = threadIdx.x;
   const uint32_t wbit = 1u << (tid >> 5);
   int lx, ly;
-  pixel_of<TW>(tid, lx, ly);
-  const int x = tx * TW + lx, y0 = ty * TH + ly, y1 = y0 + 4;
+  G::pixel_of(tid, lx, ly);
   const int W = L.width[v], H = L.height[v];
-  const bool in0 = x < W && y0 < H, in1 = x < W && y1 < H;
-  const float px = static_cast<float>(x) + 0.5f, py0 = static_cast<float>(y0) + 0.5f, py1 = py0 + 4.0f;
+  const int x = tx * TW + lx, y0 = ty * TH + ly;
+  const float px = static_cast<float>(x) + 0.5f, py0 = static_cast<float>(y0) + 0.5f;
   const uint2 range = ranges[tile];
   const int n = static_cast<int>(range.y - range.x);
   const float cap = K.alpha_cap, amin = K.alpha_min, tstop = K.t_stop;
   const float tx0 = static_cast<float>(tx * TW), ty0 = static_cast<float>(ty * TH);
-  PixelFwd P0{1.0f, 0.0f, 0.0f, 0.0f, 0u, !in0}, P1{1.0f, 0.0f, 0.0f, 0.0f, 0u, !in1};
+  PixelFwd P[PPT];
+  bool all_done = true;
+#pragma unroll
+  for (int r = 0; r < PPT; ++r) {
+    P[r] = PixelFwd{1.0f, 0.0f, 0.0f, 0.0f, 0u, !(x < W && y0 + r * G::RS < H)};
+    all_done = all_done && P[r].done;
+  }
   for (int b0 = 0; b0 < n; b0 += B) {
-    if (__syncthreads_count(P0.done && P1.done) == NT) break;
+    if (__syncthreads_count(all_done) == NT) break;
     for (int k = tid; k < B && b0 + k < n; k += NT) {
       float4 a, b;
       float c;
@@ -174,37 +193,36 @@ __global__ void __launch_bounds__(TW* TH / 2) raster_fwd_kernel(const float4* __
       s_a[k] = a;
       s_b[k] = b;
       s_c[k] = c;
-      s_m[k] = warp_cull_mask<TW, TH>(a, b, tx0, ty0, amin);
+      s_m[k] = warp_cull_mask<G>(a, b, tx0, ty0, amin);
     }
     __syncthreads();
     const int cnt = min(B, n - b0);
-    for (int j = 0; j < cnt; ++j) {
-      if (P0.done && P1.done) break;
+    for (int j = 0; j < cnt && !all_done; ++j) {
       if (!(s_m[j] & wbit)) continue;
       const float4 a = s_a[j];
       const float4 b = s_b[j];
       const float cb = s_c[j];
       const uint32_t rel = static_cast<uint32_t>(b0 + j);
-      if (!P0.done) composite_step(P0, px, py0, a, b, cb, rel, cap, amin, tstop);
-      if (!P1.done) composite_step(P1, px, py1, a, b, cb, rel, cap, amin, tstop);
+      all_done = true;
+#pragma unroll
+      for (int r = 0; r < PPT; ++r) {
+        if (!P[r].done) composite_step(P[r], px, py0 + static_cast<float>(r * G::RS), a, b, cb, rel, cap, amin, tstop);
+        all_done = all_done && P[r].done;
+      }
     }
   }
   const size_t pb = L.pix_base[v];
-  if (in0) {
-    const size_t p = pb + static_cast<size_t>(y0) * W + x;
-    image[3 * p] = P0.c0 + P0.T * K.bg[0];
-    image[3 * p + 1] = P0.c1 + P0.T * K.bg[1];
-    image[3 * p + 2] = P0.c2 + P0.T * K.bg[2];
-    final_T[p] = P0.T;
-    last[p] = P0.last;
-  }
-  if (in1) {
-    const size_t p = pb + static_cast<size_t>(y1) * W + x;
-    image[3 * p] = P1.c0 + P1.T * K.bg[0];
-    image[3 * p + 1] = P1.c1 + P1.T * K.bg[1];
-    image[3 * p + 2] = P1.c2 + P1.T * K.bg[2];
-    final_T[p] = P1.T;
-    last[p] = P1.last;
+#pragma unroll
+  for (int r = 0; r < PPT; ++r) {
+    const int yy = y0 + r * G::RS;
+    if (x < W && yy < H) {
+      const size_t p = pb + static_cast<size_t>(yy) * W + x;
+      image[3 * p] = P[r].c0 + P[r].T * K.bg[0];
+      image[3 * p + 1] = P[r].c1 + P[r].T * K.bg[1];
+      image[3 * p + 2] = P[r].c2 + P[r].T * K.bg[2];
+      final_T[p] = P[r].T;
+      last[p] = P[r].last;
+    }
   }
 }
 
@@ -291,14 +309,13 @@ __device__ __forceinline__ bool pixel_grad(PixelBwd& P, float px, float py, cons
   return true;
 }
 
-template <int TW, int TH>
-__global__ void __launch_bounds__(TW* TH / 2) raster_bwd_kernel(
+template <int TW, int TH, int PPT>
+__global__ void __launch_bounds__(TW* TH / PPT) raster_bwd_kernel(
     const float4* __restrict__ projected, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
     const Layout L, const Consts K, const float* __restrict__ final_T, const uint32_t* __restrict__ last,
     const float* __restrict__ dL_dimage, float* __restrict__ d_proj) {
-  constexpr int NT = TW * TH / 2;            // threads
-  constexpr int B = NT * kSplatsPerThread;   // splats per batch
-  constexpr int NW = NT / 32;
+  using Gm = Geo<TW, TH, PPT>;
+  constexpr int NT = Gm::NT, B = Gm::B, NW = Gm::NW;
   __shared__ float4 s_a[B];
   __shared__ float4 s_b[B];
   __shared__ float s_c[B];
@@ -314,30 +331,32 @@ __global__ void __launch_bounds__(TW* TH / 2) raster_bwd_kernel(
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t wbit = 1u << warp;
   int lx, ly;
-  pixel_of<TW>(tid, lx, ly);
-  const int x = tx * TW + lx, y0 = ty * TH + ly, y1 = y0 + 4;
+  Gm::pixel_of(tid, lx, ly);
   const int W = L.width[v], H = L.height[v];
-  const float px = static_cast<float>(x) + 0.5f, py0 = static_cast<float>(y0) + 0.5f, py1 = py0 + 4.0f;
+  const int x = tx * TW + lx, y0 = ty * TH + ly;
+  const float px = static_cast<float>(x) + 0.5f, py0 = static_cast<float>(y0) + 0.5f;
   const uint2 range = ranges[tile];
   const float cap = K.alpha_cap, amin = K.alpha_min;
   const float tx0 = static_cast<float>(tx * TW), ty0 = static_cast<float>(ty * TH);
-  auto init = [&](PixelBwd& P, int yy) {
-    P = PixelBwd{1.0f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u};
+  PixelBwd P[PPT];
+  uint32_t lmax = 0;
+#pragma unroll
+  for (int r = 0; r < PPT; ++r) {
+    P[r] = PixelBwd{1.0f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u};
+    const int yy = y0 + r * Gm::RS;
     if (x < W && yy < H) {
       const size_t p = static_cast<size_t>(L.pix_base[v]) + static_cast<size_t>(yy) * W + x;
-      P.T = final_T[p];
-      P.last = last[p];
-      P.g0 = dL_dimage[3 * p];
-      P.g1 = dL_dimage[3 * p + 1];
-      P.g2 = dL_dimage[3 * p + 2];
-      P.gbg = P.T * (P.g0 * K.bg[0] + P.g1 * K.bg[1] + P.g2 * K.bg[2]);
+      P[r].T = final_T[p];
+      P[r].last = last[p];
+      P[r].g0 = dL_dimage[3 * p];
+      P[r].g1 = dL_dimage[3 * p + 1];
+      P[r].g2 = dL_dimage[3 * p + 2];
+      P[r].gbg = P[r].T * (P[r].g0 * K.bg[0] + P[r].g1 * K.bg[1] + P[r].g2 * K.bg[2]);
     }
-  };
-  PixelBwd P0, P1;
-  init(P0, y0);
-  init(P1, y1);
+    lmax = max(lmax, P[r].last);
+  }
   const int my_slot = slot_of_lane(lane);
-  const uint32_t wmax = __reduce_max_sync(0xffffffffu, max(P0.last, P1.last));
+  const uint32_t wmax = __reduce_max_sync(0xffffffffu, lmax);
   if (lane == 0) s_wmax[warp] = wmax;
   for (int i = tid; i < B * 9; i += NT) s_grad[i] = 0.0f;
   __syncthreads();
@@ -356,7 +375,7 @@ __global__ void __launch_bounds__(TW* TH / 2) raster_bwd_kernel(
       s_b[k] = b;
       s_c[k] = c;
       s_vg[k] = vg;
-      s_m[k] = warp_cull_mask<TW, TH>(a, b, tx0, ty0, amin);
+      s_m[k] = warp_cull_mask<Gm>(a, b, tx0, ty0, amin);
     }
     __syncthreads();
     // entries j hold relative position b_end-1-j; this warp needs rel < wmax
@@ -370,11 +389,13 @@ __global__ void __launch_bounds__(TW* TH / 2) raster_bwd_kernel(
       float gv[9];
 #pragma unroll
       for (int i = 0; i < 9; ++i) gv[i] = 0.0f;
-      bool contrib = pixel_grad(P0, px, py0, a, b, cb, rel, cap, amin, gv);
-      contrib |= pixel_grad(P1, px, py1, a, b, cb, rel, cap, amin, gv);
+      bool contrib = false;
+#pragma unroll
+      for (int r = 0; r < PPT; ++r)
+        contrib |= pixel_grad(P[r], px, py0 + static_cast<float>(r * Gm::RS), a, b, cb, rel, cap, amin, gv);
       if (__any_sync(0xffffffffu, contrib)) {
-        const float r = warp_reduce9(gv, lane);
-        if (!(lane & 1) && my_slot >= 0 && r != 0.0f) atomicAdd(&s_grad[j * 9 + my_slot], r);
+        const float red = warp_reduce9(gv, lane);
+        if (!(lane & 1) && my_slot >= 0 && red != 0.0f) atomicAdd(&s_grad[j * 9 + my_slot], red);
       }
     }
     __syncthreads();
@@ -394,21 +415,28 @@ __global__ void __launch_bounds__(TW* TH / 2) raster_bwd_kernel(
   }
 }
 
-template <int TW, int TH>
+template <int TW, int TH, int PPT>
 int launch_fwd(const float4* projected, const uint32_t* vals, const uint2* ranges, const Layout& L, const Consts& K,
                float* image, float* final_T, uint32_t* last, cudaStream_t stream) {
-  raster_fwd_kernel<TW, TH><<<static_cast<unsigned>(L.n_tiles), TW * TH / 2, 0, stream>>>(projected, vals, ranges, L, K,
-                                                                                      image, final_T, last);
+  raster_fwd_kernel<TW, TH, PPT><<<static_cast<unsigned>(L.n_tiles), TW * TH / PPT, 0, stream>>>(
+      projected, vals, ranges, L, K, image, final_T, last);
   return cuda_status(cudaGetLastError());
 }
 
-template <int TW, int TH>
+template <int TW, int TH, int PPT>
 int launch_bwd(const float4* projected, const uint32_t* vals, const uint2* ranges, const Layout& L, const Consts& K,
                const float* final_T, const uint32_t* last, const float* dL_dimage, float* d_proj,
                cudaStream_t stream) {
-  raster_bwd_kernel<TW, TH><<<static_cast<unsigned>(L.n_tiles), TW * TH / 2, 0, stream>>>(
+  raster_bwd_kernel<TW, TH, PPT><<<static_cast<unsigned>(L.n_tiles), TW * TH / PPT, 0, stream>>>(
       projected, vals, ranges, L, K, final_T, last, dL_dimage, d_proj);
   return cuda_status(cudaGetLastError());
+}
+
+// Pixels per thread: 4 for 16x16 and 32x16 tiles unless the configuration asks
+// for 2 (GS_FLAG_RASTER_2PX); 8x8 tiles always use 2.
+inline int pixels_per_thread(const Layout& L, const Consts& K) {
+  if (L.tile_w == 8) return 2;
+  return (K.flags & GS_FLAG_RASTER_2PX) ? 2 : 4;
 }
 
 }  // namespace
@@ -427,9 +455,14 @@ extern "C" int gs_rasterize_fwd(const float* projected, const uint32_t* vals, co
   const Consts K = make_consts(*cfg);
   const float4* pr = reinterpret_cast<const float4*>(projected);
   const uint2* rg = reinterpret_cast<const uint2*>(tile_ranges);
-  if (L.tile_w == 16 && L.tile_h == 16) return launch_fwd<16, 16>(pr, vals, rg, L, K, image, final_T, last, stream);
-  if (L.tile_w == 8 && L.tile_h == 8) return launch_fwd<8, 8>(pr, vals, rg, L, K, image, final_T, last, stream);
-  if (L.tile_w == 32 && L.tile_h == 16) return launch_fwd<32, 16>(pr, vals, rg, L, K, image, final_T, last, stream);
+  const int ppt = pixels_per_thread(L, K);
+  if (L.tile_w == 16 && L.tile_h == 16)
+    return ppt == 4 ? launch_fwd<16, 16, 4>(pr, vals, rg, L, K, image, final_T, last, stream)
+                    : launch_fwd<16, 16, 2>(pr, vals, rg, L, K, image, final_T, last, stream);
+  if (L.tile_w == 8 && L.tile_h == 8) return launch_fwd<8, 8, 2>(pr, vals, rg, L, K, image, final_T, last, stream);
+  if (L.tile_w == 32 && L.tile_h == 16)
+    return ppt == 4 ? launch_fwd<32, 16, 4>(pr, vals, rg, L, K, image, final_T, last, stream)
+                    : launch_fwd<32, 16, 2>(pr, vals, rg, L, K, image, final_T, last, stream);
   return GS_ERR_UNSUPPORTED;
 }
 
@@ -453,9 +486,15 @@ extern "C" int gs_rasterize_bwd_pixels(const float* projected, const uint32_t* v
     return GS_ERR_CUDA;
   const float4* pr = reinterpret_cast<const float4*>(projected);
   const uint2* rg = reinterpret_cast<const uint2*>(tile_ranges);
-  if (L.tile_w == 16 && L.tile_h == 16) return launch_bwd<16, 16>(pr, vals, rg, L, K, final_T, last, dL_dimage, d_projected, stream);
-  if (L.tile_w == 8 && L.tile_h == 8) return launch_bwd<8, 8>(pr, vals, rg, L, K, final_T, last, dL_dimage, d_projected, stream);
-  if (L.tile_w == 32 && L.tile_h == 16) return launch_bwd<32, 16>(pr, vals, rg, L, K, final_T, last, dL_dimage, d_projected, stream);
+  const int ppt = pixels_per_thread(L, K);
+  if (L.tile_w == 16 && L.tile_h == 16)
+    return ppt == 4 ? launch_bwd<16, 16, 4>(pr, vals, rg, L, K, final_T, last, dL_dimage, d_projected, stream)
+                    : launch_bwd<16, 16, 2>(pr, vals, rg, L, K, final_T, last, dL_dimage, d_projected, stream);
+  if (L.tile_w == 8 && L.tile_h == 8)
+    return launch_bwd<8, 8, 2>(pr, vals, rg, L, K, final_T, last, dL_dimage, d_projected, stream);
+  if (L.tile_w == 32 && L.tile_h == 16)
+    return ppt == 4 ? launch_bwd<32, 16, 4>(pr, vals, rg, L, K, final_T, last, dL_dimage, d_projected, stream)
+                    : launch_bwd<32, 16, 2>(pr, vals, rg, L, K, final_T, last, dL_dimage, d_projected, stream);
   return GS_ERR_UNSUPPORTED;
 }
 

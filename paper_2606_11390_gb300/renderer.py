@@ -144,7 +144,8 @@ def rasterize_fwd(frame: Frame, stream=None):
 
 def rasterize_bwd(params: FlatParams, cams: Cameras, frame: Frame, dL_dimage, grads: FlatParams, stream=None,
                   accumulate=False):
-    cfg = dict(frame.cfg, flags=gs.GS_FLAG_ACCUMULATE_GRADS if accumulate else 0)
+    flags = int(frame.cfg.get("flags", 0)) & ~gs.GS_FLAG_ACCUMULATE_GRADS
+    cfg = dict(frame.cfg, flags=flags | (gs.GS_FLAG_ACCUMULATE_GRADS if accumulate else 0))
     gs.gs_rasterize_bwd(params["means"], params["log_scales"], params["quats"], params["opacity_logits"],
                         params["sh"], cams.dev, cams.sizes, cfg, frame.projected, frame.counts, frame.vals,
                         frame.tile_ranges, frame.final_T, frame.last, dL_dimage, frame.d_projected, grads["means"],

@@ -36,6 +36,12 @@ def _scenes():
     s["cfg"] = scenes.make_cfg(tile_w=32, tile_h=16, bg=(0.2, 0.5, 0.9))
     yield "tile32x16_bg", s
     yield "sh_deg1", scenes.random_small(104, N=300, width=64, height=64, sh_degree=1)
+    s = scenes.random_small(110, N=900, width=150, height=100, n_views=2, spread=1.5)
+    s["cfg"] = scenes.make_cfg(flags=2)  # two pixels per rasteriser thread
+    yield "two_px_per_thread", s
+    s = scenes.random_small(111, N=900, width=150, height=100, n_views=1, spread=1.5)
+    s["cfg"] = scenes.make_cfg(tile_w=32, tile_h=16, flags=2)
+    yield "tile32x16_two_px", s
 
 
 SCENES = list(_scenes())
