@@ -68,6 +68,17 @@ __device__ __forceinline__ float splat_exponent(float px, float py, const float4
 // Splats staged per shared-memory batch.
 constexpr int kBatch = 256;
 
+// Resident warps per SM the backward kernel is compiled for (0: no register
+// cap); the cap trades registers for latency hiding.
+#ifndef GS_RBWD_TARGET_WARPS
+#define GS_RBWD_TARGET_WARPS 0
+#endif
+#if GS_RBWD_TARGET_WARPS > 0
+#define GS_RBWD_BOUNDS(NT) __launch_bounds__(NT, GS_RBWD_TARGET_WARPS / ((NT) / 32))
+#else
+#define GS_RBWD_BOUNDS(NT) __launch_bounds__(NT)
+#endif
+
 // Thread / pixel geometry. With PPT pixels per thread a warp covers a block
 // of WB = 4 PPT columns by 8 rows: lane l owns column l % WB and rows
 // l / WB + r * (32 / WB), r < PPT. The warps of a TW x TH tile tile it in
@@ -310,7 +321,7 @@ __device__ __forceinline__ bool pixel_grad(PixelBwd& P, float px, float py, cons
 }
 
 template <int TW, int TH, int PPT>
-__global__ void __launch_bounds__(TW* TH / PPT) raster_bwd_kernel(
+__global__ void GS_RBWD_BOUNDS(TW* TH / PPT) raster_bwd_kernel(
     const float4* __restrict__ projected, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
     const Layout L, const Consts K, const float* __restrict__ final_T, const uint32_t* __restrict__ last,
     const float* __restrict__ dL_dimage, float* __restrict__ d_proj) {
