@@ -100,13 +100,22 @@ struct Geo {
   }
 };
 
-// Bitmask of the warps of the tile at (tx0, ty0) whose pixel block meets
-// the bounding box of {d : alpha(d) >= alpha_min}. With the scaled conic
-// M = [[-2A', -B'], [-B', -2C']] (so e = -d^T M d / 2) the set is
-// d^T M d / 2 <= ts, ts = log2(o / alpha_min), whose bounding box has
-// half-widths sqrt(2 ts (M^-1)_00) and sqrt(2 ts (M^-1)_11). ts and the
-// half-widths are widened (x1.001 + margin), far beyond the rounding of the
-// per-pixel evaluation, so no pixel outside the box can pass the alpha test.
+// Minimum over y in [y0, y1] of q(x, y) = m00 x^2 + 2 m01 x y + m11 y^2 for
+// fixed x (the quadratic in y is minimised at y = -m01 x / m11, clamped).
+__device__ __forceinline__ float edge_min_y(float x, float y0, float y1, float m00, float m01, float m11) {
+  const float y = fminf(fmaxf(-m01 * x / m11, y0), y1);
+  return m00 * x * x + 2.0f * m01 * x * y + m11 * y * y;
+}
+
+// Bitmask of the warps of the tile at (tx0, ty0) whose pixel block can hold a
+// pixel with alpha >= alpha_min. With the scaled conic
+// M = [[-2A', -B'], [-B', -2C']] (so e = -d^T M d / 2) that set is the
+// ellipse d^T M d <= 2 ts, ts = log2(o / alpha_min). A block is kept if its
+// rectangle of pixel centres meets the ellipse: the minimum of d^T M d over
+// the rectangle is 0 when the centre lies inside, else the smallest of the
+// four edge minima. ts and the rectangle are widened (x1.001 + margins), far
+// beyond the rounding of the per-pixel evaluation, so no pixel of a dropped
+// block can pass the alpha test.
 template <class G>
 __device__ __forceinline__ uint32_t warp_cull_mask(const float4& a, const float4& b, float tx0, float ty0,
                                                     float amin) {
@@ -117,17 +126,27 @@ __device__ __forceinline__ uint32_t warp_cull_mask(const float4& a, const float4
   const float det = m00 * m11 - m01 * m01;
   if (!(det > 0.0f) || !(m00 > 0.0f) || !(m11 > 0.0f)) return kAll;
   const float ts = (__log2f(o) - __log2f(amin)) * 1.001f + 0.01f;
-  const float hx = sqrtf(2.0f * ts * m11 / det) * 1.001f + 0.05f;
-  const float hy = sqrtf(2.0f * ts * m00 / det) * 1.001f + 0.05f;
+  const float lim = 2.0f * ts;
+  const float hx = sqrtf(lim * m11 / det) * 1.001f + 0.05f;
+  const float hy = sqrtf(lim * m00 / det) * 1.001f + 0.05f;
   if (!(hx < 1e30f) || !(hy < 1e30f)) return kAll;
   uint32_t mask = 0;
 #pragma unroll
   for (int w = 0; w < G::NW; ++w) {
-    const float xlo = tx0 + static_cast<float>(G::WB * (w % G::WXN)) + 0.5f;
-    const float ylo = ty0 + static_cast<float>(8 * (w / G::WXN)) + 0.5f;
-    if (a.x + hx >= xlo && a.x - hx <= xlo + static_cast<float>(G::WB - 1) && a.y + hy >= ylo &&
-        a.y - hy <= ylo + 7.0f)
-      mask |= 1u << w;
+    // rectangle of the block's pixel centres relative to the mean, widened
+    const float x0 = tx0 + static_cast<float>(G::WB * (w % G::WXN)) + 0.45f - a.x;
+    const float x1 = x0 + static_cast<float>(G::WB - 1) + 0.1f;
+    const float y0 = ty0 + static_cast<float>(8 * (w / G::WXN)) + 0.45f - a.y;
+    const float y1 = y0 + 7.1f;
+    if (x1 < -hx || x0 > hx || y1 < -hy || y0 > hy) continue;  // outside the bounding box
+    if (x0 <= 0.0f && x1 >= 0.0f && y0 <= 0.0f && y1 >= 0.0f) {
+      mask |= 1u << w;  // the centre lies in the block
+      continue;
+    }
+    float qmin = fminf(edge_min_y(x0, y0, y1, m00, m01, m11), edge_min_y(x1, y0, y1, m00, m01, m11));
+    qmin = fminf(qmin, edge_min_y(y0, x0, x1, m11, m01, m00));
+    qmin = fminf(qmin, edge_min_y(y1, x0, x1, m11, m01, m00));
+    if (qmin <= lim * 1.001f + 0.01f) mask |= 1u << w;
   }
   return mask;
 }
