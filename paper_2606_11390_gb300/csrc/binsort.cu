@@ -228,6 +228,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_tiles_kernel(
     run_c[p] = 0;
   }
   const int64_t n = *n_visible;
+  const float invN = 1.0f / static_cast<float>(N);
   const int64_t warps_total = static_cast<int64_t>(gridDim.x) * (kEmitThreads / 32);
   for (int64_t w = static_cast<int64_t>(blockIdx.x) * (kEmitThreads / 32) + (tid >> 5); w * 32 < n;
        w += warps_total) {
@@ -248,15 +249,23 @@ __global__ void __launch_bounds__(kEmitThreads) emit_tiles_kernel(
       const int x0 = __shfl_sync(0xffffffffu, static_cast<int>(r.x), src);
       const int y0 = __shfl_sync(0xffffffffu, static_cast<int>(r.y), src);
       const int x1 = __shfl_sync(0xffffffffu, static_cast<int>(r.z), src);
-      const int v = static_cast<int>(rvg / static_cast<uint64_t>(N));
+      // view index v = rvg / N without an integer division: float quotient,
+      // then an exact fix-up (one view: v = 0)
+      int v = 0;
+      if (L.V > 1) {
+        v = __float2int_rz(static_cast<float>(rvg) * invN);
+        while (v > 0 && static_cast<int64_t>(v) * N > static_cast<int64_t>(rvg)) --v;
+        while (static_cast<int64_t>(v + 1) * N <= static_cast<int64_t>(rvg)) ++v;
+      }
       const uint32_t tb = L.tile_base[v];
       const uint32_t ntx = static_cast<uint32_t>(L.ntx[v]);
       const int wdt = x1 - x0;
-      const float inv_w = 1.0f / static_cast<float>(wdt);
+      const float inv_w = rcp_approx(static_cast<float>(wdt));
       for (uint32_t k = lane; k < c; k += 32) {
         const uint64_t pos = static_cast<uint64_t>(roff) + k;
         if (pos >= capacity) break;
-        // k = row * wdt + col, division by the float reciprocal with an exact fix-up
+        // k = row * wdt + col: quotient from the approximate reciprocal, then an
+        // exact fix-up (the estimate is off by at most one)
         int row = __float2int_rz(static_cast<float>(k) * inv_w);
         int col = static_cast<int>(k) - row * wdt;
         if (col < 0) { --row; col += wdt; }
