@@ -365,6 +365,9 @@ __global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) sort_pass_ke
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int64_t n = *a.n_total;
   if (n > a.cap) n = a.cap;
+  // Persistent CTA: take tiles in ticket order until the data is exhausted.
+  // A tile only waits on tiles with smaller tickets, all held by running CTAs.
+  for (;;) {
   if (tid == 0) sm.tile = atomicAdd(a.ticket, 1u);
   for (int i = tid; i < kSortWarps * kRadix; i += kSortThreads) (&sm.warp_hist[0][0])[i] = 0;
   __syncthreads();
@@ -477,6 +480,8 @@ __global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) sort_pass_ke
     } else {
       set_status(status, GS_STATUS_BOUNDS);
     }
+  }
+  __syncthreads();  // shared memory is reused by the next tile
   }
 }
 
@@ -629,14 +634,23 @@ extern "C" int gs_bin_sort(const float* projected, const int16_t* rects, const u
   const int64_t VN = N * V;
   if (VN == 0) return GS_OK;
   static bool attr_set = false;
+  static int sort_ctas_per_sm = 0;
   if (!attr_set) {
     if (cudaFuncSetAttribute(sort_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(sizeof(SortSmem))) != cudaSuccess ||
         cudaFuncSetAttribute(sort_pass_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared) != cudaSuccess)
       return GS_ERR_CUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sort_ctas_per_sm, sort_pass_kernel, kSortThreads,
+                                                      sizeof(SortSmem)) != cudaSuccess ||
+        sort_ctas_per_sm < 1)
+      sort_ctas_per_sm = 1;
     attr_set = true;
   }
+  const int64_t sort_grid_cap = static_cast<int64_t>(sm_count()) * sort_ctas_per_sm;
+  auto sort_grid = [&](int64_t tiles) {
+    return static_cast<unsigned>(tiles < sort_grid_cap ? (tiles > 0 ? tiles : 1) : sort_grid_cap);
+  };
   const unsigned scan_grid = static_cast<unsigned>(w.n_scan_tiles);
 
   // 1a. visible records -> (depth bits, record), depth digit histograms
@@ -654,7 +668,7 @@ extern "C" int gs_bin_sort(const float* projected, const int16_t* rects, const u
     a.n_total = n_visible; a.cap = VN; a.shift = 8 * p; a.digit_offsets = hist_d + p * kRadix;
     a.ticket = tickets + 2 + p;
     a.lookback = reinterpret_cast<uint64_t*>(ws + w.lb_depth) + static_cast<size_t>(p) * (w.n_depth_tiles + 1) * kRadix;
-    sort_pass_kernel<<<static_cast<unsigned>(w.n_depth_tiles), kSortThreads, sizeof(SortSmem), stream>>>(a, status_dev);
+    sort_pass_kernel<<<sort_grid(w.n_depth_tiles), kSortThreads, sizeof(SortSmem), stream>>>(a, status_dev);
   }
   const uint32_t* order = dv[0];
   // 1c. tile-count offsets in depth order
@@ -684,7 +698,7 @@ extern "C" int gs_bin_sort(const float* projected, const int16_t* rects, const u
     a.n_total = n_isect_dev; a.cap = capacity; a.shift = 8 * p; a.digit_offsets = hist_t + p * kRadix;
     a.ticket = tickets + 6 + p;
     a.lookback = reinterpret_cast<uint64_t*>(ws + w.lb_tile) + static_cast<size_t>(p) * (w.n_tile_tiles + 1) * kRadix;
-    sort_pass_kernel<<<static_cast<unsigned>(w.n_tile_tiles), kSortThreads, sizeof(SortSmem), stream>>>(a, status_dev);
+    sort_pass_kernel<<<sort_grid(w.n_tile_tiles), kSortThreads, sizeof(SortSmem), stream>>>(a, status_dev);
   }
   const uint32_t* tkeys_final = tk[TP & 1];
   // 2c. tile ranges, optional 64-bit keys
