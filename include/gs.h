@@ -108,6 +108,12 @@ typedef struct gs_config {
  * blocks) instead of 4 (16-column warp blocks) for 16x16 and 32x16 tiles;
  * a performance choice only, results are the same. */
 #define GS_FLAG_RASTER_2PX 2
+/* gs_config.flags, test hook for the bounded device waits: in gs_bin_sort the
+ * first tile of the first depth pass withholds its prefix, so the next tile's
+ * look-back runs out its (here shortened) iteration bound and the call
+ * reports GS_STATUS_TIMEOUT; its outputs are then invalid but every access
+ * stays in bounds and the context stays usable. Never set in normal use. */
+#define GS_FLAG_TEST_STALL_LOOKBACK 4
 
 /* Number of 32-bit floats in one projected record (see gs_project). */
 #define GS_RECORD_FLOATS 12

@@ -22,6 +22,7 @@ GS_STATUS_CAPACITY, GS_STATUS_TIMEOUT, GS_STATUS_BOUNDS = 1, 2, 4
 GS_MAX_VIEWS = 64
 GS_FLAG_ACCUMULATE_GRADS = 1
 GS_FLAG_RASTER_2PX = 2
+GS_FLAG_TEST_STALL_LOOKBACK = 4
 RECORD_FLOATS = 12
 DRECORD_FLOATS = 9
 

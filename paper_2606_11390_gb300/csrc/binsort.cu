@@ -37,6 +37,8 @@ constexpr uint64_t kFlagIncl = 2ull << 62;
 constexpr uint64_t kValMask = (1ull << 62) - 1;
 constexpr int kRadix = 256;
 constexpr int kDepthPasses = 4;
+// Wait bound used with GS_FLAG_TEST_STALL_LOOKBACK (milliseconds, not seconds).
+constexpr uint32_t kTestSpinLimit = 1u << 12;
 constexpr int kMaxTilePasses = 4;
 
 __device__ __forceinline__ uint64_t warp_incl_scan_u64(uint64_t v) {
@@ -347,6 +349,8 @@ struct PassArgs {
   const uint32_t* digit_offsets;  // [256], exclusive
   uint32_t* ticket;
   uint64_t* lookback;  // [sort tiles][256]
+  int32_t stall_tile;   // test hook: this tile never publishes (-1: none)
+  uint32_t spin_limit;  // bound on each look-back wait
 };
 
 struct __align__(16) SortSmem {
@@ -420,7 +424,8 @@ __global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) sort_pass_ke
     total += c;
   }
   uint64_t* lb = a.lookback;
-  st_relaxed_u64(lb + static_cast<int64_t>(t) * kRadix + d, (t == 0 ? kFlagIncl : kFlagAgg) | total);
+  const bool publish = static_cast<int32_t>(t) != a.stall_tile;
+  if (publish) st_relaxed_u64(lb + static_cast<int64_t>(t) * kRadix + d, (t == 0 ? kFlagIncl : kFlagAgg) | total);
   {
     uint32_t v = total;
 #pragma unroll
@@ -442,7 +447,7 @@ __global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) sort_pass_ke
       const uint64_t s = ld_relaxed_u64(lb + j * kRadix + d);
       const uint64_t f = s >> 62;
       if (f == 0) {
-        if (++spins > kSpinLimit) {
+        if (++spins > a.spin_limit) {
           set_status(status, GS_STATUS_TIMEOUT);
           break;
         }
@@ -452,7 +457,7 @@ __global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) sort_pass_ke
       if (f == 2) break;
       --j;
     }
-    st_relaxed_u64(lb + static_cast<int64_t>(t) * kRadix + d, kFlagIncl | (prefix + total));
+    if (publish) st_relaxed_u64(lb + static_cast<int64_t>(t) * kRadix + d, kFlagIncl | (prefix + total));
   }
   sm.base[d] = static_cast<int64_t>(a.digit_offsets[d]) + static_cast<int64_t>(prefix) - sm.local_start[d];
   __syncthreads();
@@ -667,6 +672,8 @@ extern "C" int gs_bin_sort(const float* projected, const int16_t* rects, const u
     a.keys_in = dk[p & 1]; a.vals_in = dv[p & 1]; a.keys_out = dk[(p + 1) & 1]; a.vals_out = dv[(p + 1) & 1];
     a.n_total = n_visible; a.cap = VN; a.shift = 8 * p; a.digit_offsets = hist_d + p * kRadix;
     a.ticket = tickets + 2 + p;
+    a.stall_tile = (p == 0 && (cfg->flags & GS_FLAG_TEST_STALL_LOOKBACK)) ? 0 : -1;
+    a.spin_limit = (cfg->flags & GS_FLAG_TEST_STALL_LOOKBACK) ? kTestSpinLimit : kSpinLimit;
     a.lookback = reinterpret_cast<uint64_t*>(ws + w.lb_depth) + static_cast<size_t>(p) * (w.n_depth_tiles + 1) * kRadix;
     sort_pass_kernel<<<sort_grid(w.n_depth_tiles), kSortThreads, sizeof(SortSmem), stream>>>(a, status_dev);
   }
@@ -697,6 +704,8 @@ extern "C" int gs_bin_sort(const float* projected, const int16_t* rects, const u
     a.keys_in = tk[p & 1]; a.vals_in = tv[p & 1]; a.keys_out = tk[(p + 1) & 1]; a.vals_out = tv[(p + 1) & 1];
     a.n_total = n_isect_dev; a.cap = capacity; a.shift = 8 * p; a.digit_offsets = hist_t + p * kRadix;
     a.ticket = tickets + 6 + p;
+    a.stall_tile = -1;
+    a.spin_limit = kSpinLimit;
     a.lookback = reinterpret_cast<uint64_t*>(ws + w.lb_tile) + static_cast<size_t>(p) * (w.n_tile_tiles + 1) * kRadix;
     sort_pass_kernel<<<sort_grid(w.n_tile_tiles), kSortThreads, sizeof(SortSmem), stream>>>(a, status_dev);
   }
