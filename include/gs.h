@@ -90,7 +90,7 @@ typedef struct gs_camera {
 } gs_camera;
 
 /* Rendering constants, 52 bytes. tile_w x tile_h must be one of 8x8, 16x16,
- * 32x16. sh_degree in 0..3. flags: GS_FLAG_* bits. Culling: near_plane < depth < far_plane. eps2d is
+ * 32x16, 32x32. sh_degree in 0..3. flags: GS_FLAG_* bits. Culling: near_plane < depth < far_plane. eps2d is
  * added to the diagonal of every 2D covariance. Compositing: alpha =
  * min(alpha_cap, opacity * exp(-power)); entries with alpha < alpha_min are
  * skipped; compositing stops before the entry that would take the
@@ -105,7 +105,7 @@ typedef struct gs_config {
  * output arrays instead of overwriting them (to sum over separate calls). */
 #define GS_FLAG_ACCUMULATE_GRADS 1
 /* gs_config.flags: the rasteriser gives each thread 2 pixels (8-column warp
- * blocks) instead of 4 (16-column warp blocks) for 16x16 and 32x16 tiles;
+ * blocks) instead of 4 (16-column warp blocks) for 16x16, 32x16 and 32x32 tiles;
  * a performance choice only, results are the same. */
 #define GS_FLAG_RASTER_2PX 2
 /* gs_config.flags, test hook for the bounded device waits: in gs_bin_sort the
@@ -129,7 +129,8 @@ GS_API const char* gs_status_string(int code);
 /* Tile and pixel totals of a view layout (host only, nothing enqueued).
  * sizes: V (W, H) pairs, host. Writes *n_tiles and *n_pixels (either may be
  * NULL). Errors: GS_ERR_ARG for V outside 1..GS_MAX_VIEWS or non-positive
- * sizes; GS_ERR_UNSUPPORTED for a tile size other than 8x8, 16x16, 32x16. */
+ * sizes; GS_ERR_UNSUPPORTED for a tile size other than 8x8, 16x16, 32x16,
+ * 32x32. */
 GS_API int gs_layout_totals(const int32_t* sizes, int32_t V, const gs_config* cfg, int64_t* n_tiles, int64_t* n_pixels);
 
 /* gs_project - per-(view, Gaussian) SH colour and EWA projection.

@@ -1,8 +1,8 @@
 """Tile-size autotuner for the batched step.
 
 For a workload (Gaussian count, view sizes, SH degree) it times the captured
-training step with each supported tile shape (8x8, 16x16, 32x16) and keeps the
-fastest. Results are cached per GPU name and workload signature in a JSON file
+training step with each supported tile shape (8x8, 16x16, 32x16, 32x32) and
+keeps the fastest. Results are cached per GPU name and workload signature in a JSON file
 (default ~/.cache/gs_gb300/autotune.json, override with GS_AUTOTUNE_CACHE).
 """
 from __future__ import annotations
@@ -13,7 +13,7 @@ import os
 
 import numpy as np
 
-TILES = ((16, 16), (8, 8), (32, 16))
+TILES = ((16, 16), (8, 8), (32, 16), (32, 32))
 
 
 def _cache_path():

@@ -12,7 +12,8 @@ int build_layout(const int32_t* sizes, int32_t V, const gs_config* cfg, Layout* 
   if (!sizes || !cfg || !L) return GS_ERR_ARG;
   if (V < 1 || V > kMaxViews) return GS_ERR_ARG;
   const int tw = cfg->tile_w, th = cfg->tile_h;
-  if (!((tw == 8 && th == 8) || (tw == 16 && th == 16) || (tw == 32 && th == 16))) return GS_ERR_UNSUPPORTED;
+  if (!((tw == 8 && th == 8) || (tw == 16 && th == 16) || (tw == 32 && th == 16) || (tw == 32 && th == 32)))
+    return GS_ERR_UNSUPPORTED;
   L->V = V;
   L->tile_w = tw;
   L->tile_h = th;

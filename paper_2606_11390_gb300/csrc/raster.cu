@@ -493,6 +493,9 @@ extern "C" int gs_rasterize_fwd(const float* projected, const uint32_t* vals, co
   if (L.tile_w == 32 && L.tile_h == 16)
     return ppt == 4 ? launch_fwd<32, 16, 4>(pr, vals, rg, L, K, image, final_T, last, stream)
                     : launch_fwd<32, 16, 2>(pr, vals, rg, L, K, image, final_T, last, stream);
+  if (L.tile_w == 32 && L.tile_h == 32)
+    return ppt == 4 ? launch_fwd<32, 32, 4>(pr, vals, rg, L, K, image, final_T, last, stream)
+                    : launch_fwd<32, 32, 2>(pr, vals, rg, L, K, image, final_T, last, stream);
   return GS_ERR_UNSUPPORTED;
 }
 
@@ -525,6 +528,9 @@ extern "C" int gs_rasterize_bwd_pixels(const float* projected, const uint32_t* v
   if (L.tile_w == 32 && L.tile_h == 16)
     return ppt == 4 ? launch_bwd<32, 16, 4>(pr, vals, rg, L, K, final_T, last, dL_dimage, d_projected, stream)
                     : launch_bwd<32, 16, 2>(pr, vals, rg, L, K, final_T, last, dL_dimage, d_projected, stream);
+  if (L.tile_w == 32 && L.tile_h == 32)
+    return ppt == 4 ? launch_bwd<32, 32, 4>(pr, vals, rg, L, K, final_T, last, dL_dimage, d_projected, stream)
+                    : launch_bwd<32, 32, 2>(pr, vals, rg, L, K, final_T, last, dL_dimage, d_projected, stream);
   return GS_ERR_UNSUPPORTED;
 }
 

@@ -1,5 +1,6 @@
 """Parity at full size: the 4M-Gaussian 3840x2160 workload in the launch
-configuration bench.py times (graph-captured batched step, 16x16 tiles).
+configuration bench.py times (graph-captured batched step, the workload's
+tile shape).
 
 - every tile count, rectangle and projected record of the 4M Gaussians against
   the oracle's projection;
@@ -67,7 +68,8 @@ def test_full_size_4k_sampled(oracle):
     assert st.n_isect() == I
 
     # 2. sampled tiles: lists and pixels
-    ntx, nty = -(-W // 16), -(-H // 16)
+    tw, th = s["cfg"]["tile_w"], s["cfg"]["tile_h"]
+    ntx, nty = -(-W // tw), -(-H // th)
     rng = np.random.default_rng(11)
     lens = g_ranges[:, 1].astype(np.int64) - g_ranges[:, 0]
     heavy = np.argsort(lens)[-4:]
@@ -102,7 +104,7 @@ def test_full_size_4k_sampled(oracle):
     pix = []
     for t in all_tiles:
         tx, ty = int(t) % ntx, int(t) // ntx
-        ys, xs = np.mgrid[ty * 16:min(ty * 16 + 16, H), tx * 16:min(tx * 16 + 16, W)]
+        ys, xs = np.mgrid[ty * th:min(ty * th + th, H), tx * tw:min(tx * tw + tw, W)]
         pix.append((ys * W + xs).reshape(-1))
     pix = np.concatenate(pix)
     marg = ras["marginal_pix"][pix].astype(bool)

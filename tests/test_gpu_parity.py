@@ -42,6 +42,9 @@ def _scenes():
     s = scenes.random_small(111, N=900, width=150, height=100, n_views=1, spread=1.5)
     s["cfg"] = scenes.make_cfg(tile_w=32, tile_h=16, flags=2)
     yield "tile32x16_two_px", s
+    s = scenes.random_small(112, N=1500, width=200, height=150, n_views=2, spread=1.5)
+    s["cfg"] = scenes.make_cfg(tile_w=32, tile_h=32)
+    yield "tile32x32", s
 
 
 SCENES = list(_scenes())
