@@ -204,9 +204,13 @@ __global__ void __launch_bounds__(kScanThreads) scan_sorted_counts_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// 2a. Emission, one warp per 32 depth-sorted records: lanes write a record's
-//     tiles side by side (coalesced), and the tile-id digit histograms of
-//     the tile passes are gathered on the way.
+// 2a. Emission, one warp per 32 depth-sorted records, load-balanced: the
+//     warp scans the records' tile counts, and lane l produces entries
+//     l, l + 32, ... of the warp's concatenated output, finding the record of
+//     each entry by a 5-step shuffle search. All lanes stay busy whatever the
+//     record sizes, and each warp store writes 32 consecutive positions
+//     except at record boundaries. The tile-id digit histograms of the tile
+//     passes are gathered on the way with shared atomics.
 // ---------------------------------------------------------------------------
 constexpr int kEmitThreads = 256;
 
@@ -219,81 +223,76 @@ __global__ void __launch_bounds__(kEmitThreads) emit_tiles_kernel(
   const int tid = threadIdx.x, lane = tid & 31;
   for (int i = tid; i < kMaxTilePasses * kRadix; i += kEmitThreads) (&s_hist[0][0])[i] = 0;
   __syncthreads();
-  // Digit histograms: the lowest digit goes straight to a shared atomic (the
-  // lanes hold consecutive tiles, so their low digits differ); the higher
-  // digits change rarely along a lane's entries and are run-length counted
-  // in registers, flushed when the digit changes.
-  uint32_t run_d[kMaxTilePasses - 1], run_c[kMaxTilePasses - 1];
-#pragma unroll
-  for (int p = 0; p < kMaxTilePasses - 1; ++p) {
-    run_d[p] = 0;
-    run_c[p] = 0;
-  }
   const int64_t n = *n_visible;
   const float invN = 1.0f / static_cast<float>(N);
   const int64_t warps_total = static_cast<int64_t>(gridDim.x) * (kEmitThreads / 32);
   for (int64_t w = static_cast<int64_t>(blockIdx.x) * (kEmitThreads / 32) + (tid >> 5); w * 32 < n;
        w += warps_total) {
     const int64_t j = w * 32 + lane;
-    uint32_t vg = 0, cnt = 0, off = 0;
-    short4 r = make_short4(0, 0, 0, 0);
+    uint32_t vg = 0, cnt = 0, off = 0, tb = 0, ntx = 0;
+    int x0 = 0, y0 = 0, wdt = 1;
+    float inv_w = 1.0f;
     if (j < n) {
       vg = order[j];
       cnt = counts[vg];
       off = offsets[j];
-      r = rects[vg];
-    }
-    for (int src = 0; src < 32; ++src) {
-      const uint32_t c = __shfl_sync(0xffffffffu, cnt, src);
-      if (c == 0) continue;
-      const uint32_t rvg = __shfl_sync(0xffffffffu, vg, src);
-      const uint32_t roff = __shfl_sync(0xffffffffu, off, src);
-      const int x0 = __shfl_sync(0xffffffffu, static_cast<int>(r.x), src);
-      const int y0 = __shfl_sync(0xffffffffu, static_cast<int>(r.y), src);
-      const int x1 = __shfl_sync(0xffffffffu, static_cast<int>(r.z), src);
-      // view index v = rvg / N without an integer division: float quotient,
-      // then an exact fix-up (one view: v = 0)
+      const short4 r = rects[vg];
+      x0 = r.x;
+      y0 = r.y;
+      wdt = r.z - r.x;
+      inv_w = rcp_approx(static_cast<float>(wdt));
+      // view index v = vg / N by float quotient and exact fix-up (one view: 0)
       int v = 0;
       if (L.V > 1) {
-        v = __float2int_rz(static_cast<float>(rvg) * invN);
-        while (v > 0 && static_cast<int64_t>(v) * N > static_cast<int64_t>(rvg)) --v;
-        while (static_cast<int64_t>(v + 1) * N <= static_cast<int64_t>(rvg)) ++v;
+        v = __float2int_rz(static_cast<float>(vg) * invN);
+        while (v > 0 && static_cast<int64_t>(v) * N > static_cast<int64_t>(vg)) --v;
+        while (static_cast<int64_t>(v + 1) * N <= static_cast<int64_t>(vg)) ++v;
       }
-      const uint32_t tb = L.tile_base[v];
-      const uint32_t ntx = static_cast<uint32_t>(L.ntx[v]);
-      const int wdt = x1 - x0;
-      const float inv_w = rcp_approx(static_cast<float>(wdt));
-      for (uint32_t k = lane; k < c; k += 32) {
-        const uint64_t pos = static_cast<uint64_t>(roff) + k;
-        if (pos >= capacity) break;
-        // k = row * wdt + col: quotient from the approximate reciprocal, then an
-        // exact fix-up (the estimate is off by at most one)
-        int row = __float2int_rz(static_cast<float>(k) * inv_w);
-        int col = static_cast<int>(k) - row * wdt;
-        if (col < 0) { --row; col += wdt; }
-        if (col >= wdt) { ++row; col -= wdt; }
-        const uint32_t tile = tb + static_cast<uint32_t>(y0 + row) * ntx + static_cast<uint32_t>(x0 + col);
-        tkeys[pos] = tile;
-        tvals[pos] = rvg;
-        if (tile_passes > 0) atomicAdd(&s_hist[0][tile & 0xffu], 1u);
+      tb = L.tile_base[v];
+      ntx = static_cast<uint32_t>(L.ntx[v]);
+    }
+    // exclusive prefix of the counts within the warp
+    uint32_t incl = cnt;
 #pragma unroll
-        for (int p = 1; p < kMaxTilePasses; ++p) {
-          if (p < tile_passes) {
-            const uint32_t d = (tile >> (8 * p)) & 0xffu;
-            if (d != run_d[p - 1]) {
-              if (run_c[p - 1]) atomicAdd(&s_hist[p][run_d[p - 1]], run_c[p - 1]);
-              run_d[p - 1] = d;
-              run_c[p - 1] = 0;
-            }
-            ++run_c[p - 1];
-          }
-        }
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t nb = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += nb;
+    }
+    const uint32_t excl = incl - cnt;
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    for (uint32_t base = 0; base < total; base += 32) {
+      const uint32_t e = base + lane;
+      // record of entry e: the last lane s with excl[s] <= e
+      int src = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const uint32_t ex = __shfl_sync(0xffffffffu, excl, src + step);
+        if (ex <= e) src += step;
+      }
+      const uint32_t k = e - __shfl_sync(0xffffffffu, excl, src);
+      const uint32_t r_vg = __shfl_sync(0xffffffffu, vg, src);
+      const uint32_t r_off = __shfl_sync(0xffffffffu, off, src);
+      const int r_x0 = __shfl_sync(0xffffffffu, x0, src);
+      const int r_y0 = __shfl_sync(0xffffffffu, y0, src);
+      const int r_w = __shfl_sync(0xffffffffu, wdt, src);
+      const float r_inv = __shfl_sync(0xffffffffu, inv_w, src);
+      const uint32_t r_tb = __shfl_sync(0xffffffffu, tb, src);
+      const uint32_t r_ntx = __shfl_sync(0xffffffffu, ntx, src);
+      const uint64_t pos = static_cast<uint64_t>(r_off) + k;
+      if (e < total && pos < capacity) {
+        // k = row * w + col: quotient from the approximate reciprocal, then an
+        // exact fix-up (the estimate is off by at most one)
+        int row = __float2int_rz(static_cast<float>(k) * r_inv);
+        int col = static_cast<int>(k) - row * r_w;
+        if (col < 0) { --row; col += r_w; }
+        if (col >= r_w) { ++row; col -= r_w; }
+        const uint32_t tile = r_tb + static_cast<uint32_t>(r_y0 + row) * r_ntx + static_cast<uint32_t>(r_x0 + col);
+        tkeys[pos] = tile;
+        tvals[pos] = r_vg;
+        for (int p = 0; p < tile_passes; ++p) atomicAdd(&s_hist[p][(tile >> (8 * p)) & 0xffu], 1u);
       }
     }
   }
-#pragma unroll
-  for (int p = 1; p < kMaxTilePasses; ++p)
-    if (p < tile_passes && run_c[p - 1]) atomicAdd(&s_hist[p][run_d[p - 1]], run_c[p - 1]);
   __syncthreads();
   for (int i = tid; i < tile_passes * kRadix; i += kEmitThreads) {
     const uint32_t c = (&s_hist[0][0])[i];
