@@ -46,6 +46,11 @@ def parse():
     ap.add_argument("--tile", default=None, help="WxH tile override, e.g. 16x16")
     ap.add_argument("--gaussians", type=int, default=None, help="override the workload's Gaussian count")
     ap.add_argument("--raster-px", type=int, default=4, choices=[2, 4], help="pixels per thread in the rasteriser")
+    ap.add_argument("--loss", default="l1l2", choices=["l1l2", "ssim"],
+                    help="image loss of the step: the workload's L1 + L2, or the fused SSIM loss")
+    ap.add_argument("--kernel", default="step", choices=["step", "ssim_loss"],
+                    help="step: the training step (default); ssim_loss: the fused SSIM loss kernel alone on a "
+                         "seeded image pair of the workload's view sizes")
     return ap.parse_args()
 
 
@@ -170,7 +175,7 @@ def workload_config(scene, args, tile):
                 (s["sizes"][:, 0].astype(np.int64) * s["sizes"][:, 1]).sum()),
             "tile": f"{tile[0]}x{tile[1]}", "sh_degree": int(s["cfg"]["sh_degree"]), "mode": args.mode,
             "cuda_graph": args.mode == "batched" and not args.no_graph, "adam": s["name"] == "street",
-            "loss": f"L1 + {s['loss'][1]} L2",
+            "loss": (f"L1 + {s['loss'][1]} L2" if args.loss == "l1l2" else "0.8 L1 + 0.2 (1 - SSIM), fused kernel"),
             "l2_flush": f"none: inputs (parameters {int(s['means'].shape[0]) * 236 / 1e9:.2f} GB, plus keys) exceed the 129 MB L2"}
 
 
@@ -200,7 +205,7 @@ def stage_times(step, iters=5):
         fr.image = step.image
         R.rasterize_fwd(fr)
         ev[3].record(stream)
-        gs.gs_image_loss(step.image, step.target, step.w_l1, step.w_l2, step.dL_dimage, step.loss)
+        step.enqueue_loss()
         ev[4].record(stream)
         gs.gs_rasterize_bwd_pixels(fr.projected, fr.vals, fr.tile_ranges, cams.sizes, fr.cfg, fr.N, fr.final_T,
                                    fr.last, step.dL_dimage, fr.d_projected)
@@ -323,12 +328,16 @@ def main():
     dev = dist.local_rank if torch.cuda.is_available() else 0
     torch.cuda.set_device(dev)
     gs.load()
+    if args.kernel == "ssim_loss":
+        rc = ssim_only(args, dist)
+        dist.close()
+        return rc
     scene = make_scene(args.workload, args.gaussians)
     if args.raster_px == 2:
         scene["cfg"] = dict(scene["cfg"], flags=gs.GS_FLAG_RASTER_2PX)
     tile = tuple(int(x) for x in args.tile.split("x")) if args.tile else (scene["cfg"]["tile_w"], scene["cfg"]["tile_h"])
     adam = scene["name"] == "street"  # the street workload's step includes the fused Adam update
-    step = R.TrainStep(scene, mode=args.mode, graph=not args.no_graph, tile=tile, adam=adam).prepare()
+    step = R.TrainStep(scene, mode=args.mode, graph=not args.no_graph, tile=tile, adam=adam, loss=args.loss).prepare()
     P = step.cams.n_pixels
     launches = step.launches_per_step
     stream = torch.cuda.current_stream()
@@ -367,6 +376,7 @@ def main():
             dom = max(st, key=st.get)
             peaks, src = measured_peaks()
             extra["roofline"] = roofline_for(dom, st[dom], step, peaks, src, scene["name"])
+            extra["ssim_loss"] = ssim_kernel_measure(step.image, step.target, step.cams.sizes, peaks, src)
         if not args.no_e2e:
             extra["e2e"] = e2e_measure(step, args, dist.world)
         del step
@@ -393,22 +403,30 @@ def main():
 FLOP_PER_PAIR = {"raster_fwd": 24, "raster_bwd": 60}
 
 
-def kernel_digest():
-    """Digest of the CUDA sources, to tie recorded ncu traffic to a build."""
+# CUDA sources that make up each timed stage (plus the shared headers).
+KERNEL_SOURCES = {"raster_fwd": ["raster.cu"], "raster_bwd": ["raster.cu"], "project": ["project.cu"],
+                  "project_bwd": ["project.cu"], "bin_sort": ["binsort.cu"], "loss": ["loss_adam.cu"],
+                  "ssim_loss": ["ssim.cu"]}
+COMMON_SOURCES = ["gs_common.cuh", "gs_internal.h"]
+
+
+def kernel_digest(kernel):
+    """Digest of the CUDA sources of one stage, to tie recorded ncu traffic to
+    the kernel it was measured on."""
     import hashlib
 
     from paper_2606_11390_gb300 import build as B
 
     h = hashlib.sha256()
-    for f in B.sources():
-        with open(f, "rb") as fh:
+    for name in KERNEL_SOURCES[kernel] + COMMON_SOURCES:
+        with open(os.path.join(B.CSRC, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(kernel, workload):
     """DRAM bytes per launch of `kernel` on `workload` from profiles/dram_traffic.json,
-    if they were captured from the current sources; else None."""
+    if they were captured from the kernel's current sources; else None."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(p) as f:
@@ -416,7 +434,7 @@ def recorded_traffic(kernel, workload):
     except (OSError, ValueError):
         return None
     e = d.get(f"{kernel}|{workload}")
-    if not e or e.get("digest") != kernel_digest():
+    if not e or kernel not in KERNEL_SOURCES or e.get("digest") != kernel_digest(kernel):
         return None
     return e.get("bytes_per_launch")
 
@@ -453,6 +471,81 @@ def roofline_for(stage, ms, step, peaks, src, workload):
     achieved = bytes_ / (ms * 1e-3) / 1e9
     return {"kernel": stage, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": traffic, "peak_source": f"{src} hbm_gbs", "ms": ms}
+
+
+# Algorithmic FP32 work of the fused SSIM loss per pixel and channel, from the
+# separable form without halo recomputation: five window sums (x, y, xx, yy,
+# xy) as two 11-tap passes (5 x 2 x 11 x 2 = 220), SSIM and its three
+# partials (30), three backward window sums (3 x 2 x 11 x 2 = 132) and the
+# final combination with the L1 term (6).
+SSIM_FLOP_PER_VALUE = 388
+
+
+def ssim_kernel_measure(image, target, sizes, peaks, src, iters=20, warmup=3):
+    """The fused SSIM loss kernel alone on an image and target (CUDA events
+    on the launching stream; at 3840x2160 the three images together exceed
+    L2). Bound: FP32 issue."""
+    import torch
+
+    from paper_2606_11390_gb300 import _native as gs
+
+    sizes = np.asarray(sizes, np.int32).reshape(-1, 2)
+    P = int((sizes[:, 0].astype(np.int64) * sizes[:, 1]).sum())
+    g = torch.empty_like(image)
+    loss = torch.zeros(1, dtype=torch.float64, device=image.device)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        gs.gs_ssim_loss(image, target, sizes, 0.2, g, loss)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(iters):
+        gs.gs_ssim_loss(image, target, sizes, 0.2, g, loss)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / iters
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved = 3 * P * SSIM_FLOP_PER_VALUE / (ms * 1e-3) / 1e12
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    gbs = 3 * P * 12 / (ms * 1e-3) / 1e9
+    return {"ms": ms, "loss": float(loss.item()), "launches": 1,
+            "roofline": {"kernel": "ssim_loss", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "work": f"{3 * P} values x {SSIM_FLOP_PER_VALUE} FLOP",
+                         "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz ({src} max SM clock)"},
+            "hbm": {"achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm, "bytes": 3 * P * 12}}
+
+
+def ssim_only(args, dist):
+    """--kernel ssim_loss: the fused SSIM loss alone on a seeded image pair
+    (uniform image, target = image + N(0, 0.05) clipped) of the workload's
+    view sizes; K timed launches after W warm-up launches."""
+    import torch
+
+    from paper_2606_11390_gb300 import scenes
+
+    sizes = scenes.make_sizes(args.workload)
+    P = int((sizes[:, 0].astype(np.int64) * sizes[:, 1]).sum())
+    rng = np.random.default_rng(2024)
+    img = rng.uniform(0.0, 1.0, (P * 3,)).astype(np.float32)
+    tgt = np.clip(img + 0.05 * rng.standard_normal(P * 3), 0.0, 1.0).astype(np.float32)
+    image, target = torch.from_numpy(img).cuda(), torch.from_numpy(tgt).cuda()
+    peaks, src = measured_peaks()
+    r = ssim_kernel_measure(image, target, sizes, peaks, src, iters=args.steps, warmup=max(args.warmup, 1))
+    ms = dist.max(r["ms"])
+    if dist.rank == 0:
+        line = {"metric": "fused SSIM loss fwd+bwd", "value": dist.world * P / (ms * 1e-3) / 1e6, "unit": "Mpix/s",
+                "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic", "config": {"workload": f"ssim_loss@{args.workload}",
+                                                "resolutions": sorted({f"{w}x{h}" for w, h in sizes}),
+                                                "pixels": P, "l2_flush": "none: image, target and gradient exceed L2"
+                                                if P * 36 > 129e6 else "none (fits L2)"},
+                "roofline": r["roofline"], "hbm": r["hbm"], "gpu_launches": args.steps}
+        print(json.dumps(line), flush=True)
+    return 0
 
 
 def batched_vs_per_view(args, tile=None):

@@ -299,6 +299,22 @@ GS_API int gs_project_bwd(const float* means, const float* log_scales, const flo
 GS_API int gs_image_loss(const float* image, const float* target, int64_t n, float w_l1, float w_l2, float* dL_dimage,
                   double* loss_dev, gs_stream_t stream);
 
+/* gs_ssim_loss - fused SSIM image loss and its gradient, one kernel.
+ * Paper: §4 runs a fused SSIM loss operator per camera (SSIM of Wang et al.
+ * 2004, fused as in Taming 3DGS). L = (1 - lambda) mean|x - y|
+ * + lambda (1 - mean SSIM(x, y)), means over every pixel and channel of all
+ * views; SSIM per channel with an 11x11 Gaussian window (sigma 1.5, weights
+ * summing to 1), C1 = 0.01^2, C2 = 0.03^2, pixels outside the image taken as
+ * zero in every window sum. The usual training weight is lambda = 0.2.
+ * in  (device): image, target [P][3] packed by view like the rendered image
+ *     (view v: sizes[2v] x sizes[2v+1] pixels, row-major, RGB interleaved).
+ * in  (host): sizes [V][2] int32 (width, height), 1 <= V <= 64.
+ * out (device): dL_dimage [P][3] (overwritten), loss_dev [1] double
+ *     (overwritten). No workspace: each CTA recomputes its halo on chip.
+ * Errors: GS_ERR_ARG (null pointer, bad sizes, lambda outside [0, 1]), GS_ERR_CUDA. */
+GS_API int gs_ssim_loss(const float* image, const float* target, const int32_t* sizes, int32_t V, float lambda,
+                        float* dL_dimage, double* loss_dev, gs_stream_t stream);
+
 /* gs_adam_step - fused Adam update over a flat parameter array.
  * Paper: §3.2 (fused Adam with vectorised loads and stores and
  * transcendental results cached in shared memory); update of Kingma & Ba

@@ -61,14 +61,27 @@ def window_sum(f: np.ndarray, w1: np.ndarray) -> np.ndarray:
     return out
 
 
-def ssim_maps(x: np.ndarray, y: np.ndarray, w1=None):
+def window_sum_separable(f: np.ndarray, w1: np.ndarray) -> np.ndarray:
+    """The same zero-padded window sum as window_sum, as two 1D correlations
+    (scipy.ndimage.correlate1d along rows, then columns): equal up to rounding
+    because the 2D window is an outer product. Used for full-size images,
+    where the direct 121-term sum is too slow."""
+    from scipy import ndimage
+
+    f = np.asarray(f, np.float64)
+    t = ndimage.correlate1d(f, w1, axis=1, mode="constant", cval=0.0)
+    return ndimage.correlate1d(t, w1, axis=0, mode="constant", cval=0.0)
+
+
+def ssim_maps(x: np.ndarray, y: np.ndarray, w1=None, fast: bool = False):
     """Per-pixel SSIM of one channel and its partials with respect to the
     window sums mu_x, G*(x x) and G*(x y). Returns (S, dS_dmux, dS_dexx, dS_dexy)."""
     w1 = gaussian_window() if w1 is None else w1
+    ws = window_sum_separable if fast else window_sum
     x = np.asarray(x, np.float64)
     y = np.asarray(y, np.float64)
-    mux, muy = window_sum(x, w1), window_sum(y, w1)
-    exx, eyy, exy = window_sum(x * x, w1), window_sum(y * y, w1), window_sum(x * y, w1)
+    mux, muy = ws(x, w1), ws(y, w1)
+    exx, eyy, exy = ws(x * x, w1), ws(y * y, w1), ws(x * y, w1)
     sxx = exx - mux * mux
     syy = eyy - muy * muy
     sxy = exy - mux * muy
@@ -101,13 +114,15 @@ def _split_views(flat: np.ndarray, sizes) -> list:
     return out
 
 
-def ssim_loss(image, target, sizes, lam: float = LAMBDA):
+def ssim_loss(image, target, sizes, lam: float = LAMBDA, fast: bool = False):
     """L = (1 - lam) mean|x - y| + lam (1 - mean SSIM) over all views and
-    channels; returns (L, dL/dimage shaped like image, mean SSIM)."""
+    channels; returns (L, dL/dimage shaped like image, mean SSIM). fast=True
+    takes the separable window sums (full-size images)."""
     xs = _split_views(image, sizes)
     ys = _split_views(target, sizes)
     M = sum(x.size for x in xs)
     w1 = gaussian_window()
+    ws = window_sum_separable if fast else window_sum
     l1 = 0.0
     s_sum = 0.0
     grads = []
@@ -115,11 +130,11 @@ def ssim_loss(image, target, sizes, lam: float = LAMBDA):
         g = np.zeros_like(x)
         for c in range(3):
             xc, yc = x[:, :, c], y[:, :, c]
-            S, d_mux, d_exx, d_exy = ssim_maps(xc, yc, w1)
+            S, d_mux, d_exx, d_exy = ssim_maps(xc, yc, w1, fast)
             s_sum += S.sum()
             # d(sum_p S(p)) / dx(q) = G^T d_mux + 2 x G^T d_exx + y G^T d_exy;
             # the window is symmetric, so G^T is the same zero-padded sum
-            dssim = window_sum(d_mux, w1) + 2.0 * xc * window_sum(d_exx, w1) + yc * window_sum(d_exy, w1)
+            dssim = ws(d_mux, w1) + 2.0 * xc * ws(d_exx, w1) + yc * ws(d_exy, w1)
             r = xc - yc
             l1 += np.abs(r).sum()
             g[:, :, c] = (1.0 - lam) * np.sign(r) / M - lam * dssim / M

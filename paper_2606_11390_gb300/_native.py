@@ -68,6 +68,7 @@ _SIGNATURES = {
     "gs_project_bwd": ([_VP] * 5 + [_I64, _VP, _VP, _I32, _VP, _VP, _VP] + [_VP] * 5 + [_VP, _VP], ctypes.c_int),
     "gs_image_loss": ([_VP, _VP, _I64, _F32, _F32, _VP, _VP, _VP], ctypes.c_int),
     "gs_adam_step": ([_VP, _VP, _VP, _VP, _I64, _F32, _F32, _F32, _F32, _VP, _VP], ctypes.c_int),
+    "gs_ssim_loss": ([_VP, _VP, _VP, _I32, _F32, _VP, _VP, _VP], ctypes.c_int),
 }
 
 _lock = threading.Lock()
@@ -226,6 +227,13 @@ def gs_image_loss(image, target, w_l1, w_l2, dL_dimage, loss, stream=None):
     rc = load().gs_image_loss(_ptr(image), _ptr(target), image.numel(), float(w_l1), float(w_l2), _ptr(dL_dimage),
                               _ptr(loss), _stream(stream))
     _check(rc, "gs_image_loss")
+
+
+def gs_ssim_loss(image, target, sizes, lam, dL_dimage, loss, stream=None):
+    sz = _sizes(sizes)
+    rc = load().gs_ssim_loss(_ptr(image), _ptr(target), _ptr(sz), sz.shape[0], float(lam), _ptr(dL_dimage),
+                             _ptr(loss), _stream(stream))
+    _check(rc, "gs_ssim_loss")
 
 
 def gs_adam_step(param, grad, exp_avg, exp_avg_sq, lr, beta1, beta2, eps, step, stream=None):

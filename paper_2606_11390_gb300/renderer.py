@@ -231,10 +231,16 @@ class TrainStep:
     whole step is captured into a CUDA graph and `run()` is one graph replay.
     mode="per_view": every stage launched separately per view (the plain path
     a per-camera training loop would take), without graph capture.
+    loss="l1l2": the scene's w_l1 mean|r| + w_l2 mean(r^2); loss="ssim": the
+    fused SSIM loss (1 - ssim_lambda) mean|r| + ssim_lambda (1 - mean SSIM).
     """
 
     def __init__(self, scene: dict, mode="batched", adam=False, lr=1e-3, betas=(0.9, 0.999), eps=1e-15,
-                 tile=None, device="cuda", graph=True, params: FlatParams | None = None):
+                 tile=None, device="cuda", graph=True, params: FlatParams | None = None, loss="l1l2",
+                 ssim_lambda=0.2):
+        if loss not in ("l1l2", "ssim"):
+            raise ValueError(f"unknown loss {loss!r}")
+        self.loss_kind, self.ssim_lambda = loss, float(ssim_lambda)
         self.mode, self.adam_on, self.graph_on = mode, adam, graph and mode == "batched"
         self.lr, self.betas, self.eps = lr, betas, eps
         self.cfg = dict(scene["cfg"])
@@ -274,7 +280,7 @@ class TrainStep:
             fr.image = self.image[a:b]
             rasterize_fwd(fr, stream)
             n += 1 + self._sort_launches(fr) + 1  # project, sort, raster
-        gs.gs_image_loss(self.image, self.target, self.w_l1, self.w_l2, self.dL_dimage, self.loss, stream)
+        self.enqueue_loss(stream)
         n += 1
         for v, (fr, cams) in enumerate(zip(self.frames, self.frame_cams)):
             a, b = int(self.cams.pix_base[v]) * 3, int(self.cams.pix_base[v + 1 if pv else -1]) * 3
@@ -285,6 +291,14 @@ class TrainStep:
                             self.betas[1], self.eps, self.step_count, stream)
             n += 1
         return n
+
+    def enqueue_loss(self, stream=None):
+        """The image loss of the step: its value into self.loss, its gradient into self.dL_dimage."""
+        if self.loss_kind == "ssim":
+            gs.gs_ssim_loss(self.image, self.target, self.cams.sizes, self.ssim_lambda, self.dL_dimage, self.loss,
+                            stream)
+        else:
+            gs.gs_image_loss(self.image, self.target, self.w_l1, self.w_l2, self.dL_dimage, self.loss, stream)
 
     @staticmethod
     def _sort_launches(fr: Frame) -> int:

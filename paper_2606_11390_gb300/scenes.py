@@ -237,3 +237,12 @@ NAMED = {"tiny": tiny, "train_1080p": train_1080p, "diff_4k": diff_4k, "batch16"
 
 def make(name, **kw):
     return NAMED[name](**kw)
+
+
+VIEW_SIZES = {"tiny": [(256, 256)], "train_1080p": [(1920, 1080)], "diff_4k": [(3840, 2160)],
+              "batch16": [BATCH16_SIZES[k % 4] for k in range(16)], "street": [(3840, 2160)] * 4}
+
+
+def make_sizes(name) -> np.ndarray:
+    """The (W, H) of every view of a named workload, without building it."""
+    return np.array(VIEW_SIZES[name], np.int32)

@@ -26,6 +26,18 @@ def test_window_sum_matches_scipy_correlate2d():
         np.testing.assert_allclose(S.window_sum(f, w1), ref, rtol=1e-12, atol=1e-13)
 
 
+def test_separable_path_equals_direct_sum():
+    rng = np.random.default_rng(7)
+    f = rng.uniform(0, 1, (23, 40))
+    np.testing.assert_allclose(S.window_sum_separable(f, S.gaussian_window()), S.window_sum(f, S.gaussian_window()),
+                               rtol=1e-12, atol=1e-14)
+    img, tgt = rng.uniform(0, 1, (40 * 23 + 6 * 9, 3)), rng.uniform(0, 1, (40 * 23 + 6 * 9, 3))
+    sizes = np.array([[40, 23], [6, 9]])
+    a, b = S.ssim_loss(img, tgt, sizes), S.ssim_loss(img, tgt, sizes, fast=True)
+    assert a[0] == pytest.approx(b[0], rel=1e-13)
+    np.testing.assert_allclose(a[1], b[1], rtol=1e-9, atol=1e-15)
+
+
 def _ssim_scalar(x, y):
     """SSIM map by plain loops: every window sum over the in-image pixels."""
     H, W = x.shape
