@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--raster-px", type=int, default=4, choices=[2, 4], help="pixels per thread in the rasteriser")
     ap.add_argument("--loss", default="l1l2", choices=["l1l2", "ssim"],
                     help="image loss of the step: the workload's L1 + L2, or the fused SSIM loss")
+    ap.add_argument("--no-morton", action="store_true", help="skip the Morton-order leg")
     ap.add_argument("--kernel", default="step", choices=["step", "ssim_loss"],
                     help="step: the training step (default); ssim_loss: the fused SSIM loss kernel alone on a "
                          "seeded image pair of the workload's view sizes")
@@ -377,6 +378,8 @@ def main():
             peaks, src = measured_peaks()
             extra["roofline"] = roofline_for(dom, st[dom], step, peaks, src, scene["name"])
             extra["ssim_loss"] = ssim_kernel_measure(step.image, step.target, step.cams.sizes, peaks, src)
+            if not args.no_morton and scene["name"] != "street":
+                extra["morton"] = morton_measure(step, scene, args, tile, ms)
         if not args.no_e2e:
             extra["e2e"] = e2e_measure(step, args, dist.world)
         del step
@@ -516,6 +519,47 @@ def ssim_kernel_measure(image, target, sizes, peaks, src, iters=20, warmup=3):
                          "work": f"{3 * P} values x {SSIM_FLOP_PER_VALUE} FLOP",
                          "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz ({src} max SM clock)"},
             "hbm": {"achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm, "bytes": 3 * P * 12}}
+
+
+def morton_measure(step, scene, args, tile, ms_input_order):
+    """The same step after reordering the Gaussians along a 3D Morton curve
+    (gs_morton_order + gs_gather_rows, timed separately), as the paper does at
+    densification; the input order of the synthetic scenes is random."""
+    import torch
+
+    from paper_2606_11390_gb300 import renderer as R
+
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    out = R.FlatParams(step.N)
+    for _ in range(2):  # warm-up, then timed
+        ev[0].record(stream)
+        perm, status = R.morton_permutation(step.params)
+        ev[1].record(stream)
+        R.permute_gaussians(step.params, perm, out=out, status=status)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+    if status.item() != 0:
+        raise RuntimeError(f"morton status {status.item()}")
+    order_ms, gather_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    st = R.TrainStep(scene, mode=args.mode, graph=not args.no_graph, tile=tile, params=out, loss=args.loss).prepare()
+    for _ in range(args.warmup):
+        st.run()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        st.run()
+    b.record(stream)
+    torch.cuda.synchronize()
+    st.check()
+    ms = a.elapsed_time(b) / args.steps
+    stages = stage_times(st)
+    del st
+    torch.cuda.empty_cache()
+    return {"order_ms": order_ms, "gather_ms": gather_ms, "ms_per_step": ms,
+            "Mpix_s": step.cams.n_pixels / (ms * 1e-3) / 1e6, "speedup_vs_input_order": ms_input_order / ms,
+            "stage_ms": {k: round(v, 4) for k, v in stages.items()}}
 
 
 def ssim_only(args, dist):

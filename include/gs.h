@@ -315,6 +315,40 @@ GS_API int gs_image_loss(const float* image, const float* target, int64_t n, flo
 GS_API int gs_ssim_loss(const float* image, const float* target, const int32_t* sizes, int32_t V, float lambda,
                         float* dL_dimage, double* loss_dev, gs_stream_t stream);
 
+/* gs_morton_workspace_bytes - device scratch gs_morton_order needs for N
+ * Gaussians (about 12 N bytes plus look-back state). Returns 0 for N < 0. */
+GS_API size_t gs_morton_workspace_bytes(int64_t N);
+
+/* gs_morton_order - permutation that orders Gaussians along a 3D Morton curve.
+ * Paper: §6 Morton-sorts the Gaussians in three dimensions during
+ * densification for memory locality in rasterisation (5-10 %).
+ * lo/hi = per-axis min/max of the means; q = clamp(floor((x - lo) *
+ * (1024 / (hi - lo))), 0, 1023) per axis, each operation a single rounded
+ * float operation in that order (q = 0 where hi == lo, and for NaN);
+ * code = bits of qx, qy, qz interleaved, x lowest (30 bits); perm = the
+ * stable sort of the codes (equal codes keep index order).
+ * in  (device): means [N][3] float32.
+ * out (device): perm [N] u32 (perm[i] = old index of the i-th Gaussian in
+ *     the new order); codes [N] u32, the sorted codes (optional, may be NULL).
+ * workspace: gs_morton_workspace_bytes(N) bytes, 256-byte aligned, owned by
+ *     the caller; status_dev as for gs_bin_sort (bounded waits).
+ * Errors: GS_ERR_ARG (N >= 2^32 - 1, null pointers, short or misaligned
+ * workspace), GS_ERR_CUDA. */
+GS_API int gs_morton_order(const float* means, int64_t N, uint32_t* perm, uint32_t* codes, void* workspace,
+                           size_t workspace_bytes, int32_t* status_dev, gs_stream_t stream);
+
+/* gs_gather_rows - dst[i] = src[perm[i]] for n_rows rows of row_floats
+ * floats (applies a gs_morton_order permutation to any per-Gaussian array:
+ * parameters, gradients, optimiser moments). The paper has no separate
+ * operator for it (§6 reindexes during densification).
+ * in  (device): src [n][row_floats], perm [n] (values < n_rows; others are
+ *     skipped and set GS_STATUS_BOUNDS in *status_dev).
+ * out (device): dst [n][row_floats], distinct from src; 16-byte aligned when
+ *     row_floats is a multiple of 4 (then rows move as float4).
+ * Errors: GS_ERR_ARG, GS_ERR_CUDA. */
+GS_API int gs_gather_rows(const float* src, float* dst, int64_t n_rows, int32_t row_floats, const uint32_t* perm,
+                          int32_t* status_dev, gs_stream_t stream);
+
 /* gs_adam_step - fused Adam update over a flat parameter array.
  * Paper: §3.2 (fused Adam with vectorised loads and stores and
  * transcendental results cached in shared memory); update of Kingma & Ba

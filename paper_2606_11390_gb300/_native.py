@@ -69,6 +69,9 @@ _SIGNATURES = {
     "gs_image_loss": ([_VP, _VP, _I64, _F32, _F32, _VP, _VP, _VP], ctypes.c_int),
     "gs_adam_step": ([_VP, _VP, _VP, _VP, _I64, _F32, _F32, _F32, _F32, _VP, _VP], ctypes.c_int),
     "gs_ssim_loss": ([_VP, _VP, _VP, _I32, _F32, _VP, _VP, _VP], ctypes.c_int),
+    "gs_morton_workspace_bytes": ([_I64], ctypes.c_size_t),
+    "gs_morton_order": ([_VP, _I64, _VP, _VP, _VP, ctypes.c_size_t, _VP, _VP], ctypes.c_int),
+    "gs_gather_rows": ([_VP, _VP, _I64, _I32, _VP, _VP, _VP], ctypes.c_int),
 }
 
 _lock = threading.Lock()
@@ -234,6 +237,23 @@ def gs_ssim_loss(image, target, sizes, lam, dL_dimage, loss, stream=None):
     rc = load().gs_ssim_loss(_ptr(image), _ptr(target), _ptr(sz), sz.shape[0], float(lam), _ptr(dL_dimage),
                              _ptr(loss), _stream(stream))
     _check(rc, "gs_ssim_loss")
+
+
+def gs_morton_workspace_bytes(N):
+    return int(load().gs_morton_workspace_bytes(int(N)))
+
+
+def gs_morton_order(means, N, perm, codes, workspace, status, stream=None):
+    rc = load().gs_morton_order(_ptr(means), int(N), _ptr(perm), _ptr(codes) if codes is not None else None,
+                                _ptr(workspace), workspace.numel() * workspace.element_size(), _ptr(status),
+                                _stream(stream))
+    _check(rc, "gs_morton_order")
+
+
+def gs_gather_rows(src, dst, n_rows, row_floats, perm, status, stream=None):
+    rc = load().gs_gather_rows(_ptr(src), _ptr(dst), int(n_rows), int(row_floats), _ptr(perm), _ptr(status),
+                               _stream(stream))
+    _check(rc, "gs_gather_rows")
 
 
 def gs_adam_step(param, grad, exp_avg, exp_avg_sq, lr, beta1, beta2, eps, step, stream=None):

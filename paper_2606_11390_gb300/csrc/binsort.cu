@@ -602,6 +602,55 @@ int sm_count() {
 }
 
 }  // namespace
+
+// Occupancy-derived persistent grid for the digit passes; sets the kernel's
+// shared-memory attributes on first use.
+int sort_grid_cap(int64_t* cap) {
+  static bool attr_set = false;
+  static int ctas_per_sm = 0;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(sort_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(sizeof(SortSmem))) != cudaSuccess ||
+        cudaFuncSetAttribute(sort_pass_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+      return GS_ERR_CUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, sort_pass_kernel, kSortThreads,
+                                                      sizeof(SortSmem)) != cudaSuccess ||
+        ctas_per_sm < 1)
+      ctas_per_sm = 1;
+    attr_set = true;
+  }
+  *cap = static_cast<int64_t>(sm_count()) * ctas_per_sm;
+  return GS_OK;
+}
+
+int64_t sort_tiles_for(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
+
+void launch_hist_scan(uint32_t* hist, int passes, cudaStream_t stream) {
+  hist_scan_kernel<<<1, kRadix, 0, stream>>>(hist, passes);
+}
+
+int run_u32_sort_passes(uint32_t* const keys[2], uint32_t* const vals[2], const int64_t* n_dev, int64_t cap,
+                        int passes, const uint32_t* hist, uint32_t* tickets, uint64_t* lookback, int32_t* status,
+                        cudaStream_t stream) {
+  int64_t grid_cap = 0;
+  const int rc = sort_grid_cap(&grid_cap);
+  if (rc != GS_OK) return rc;
+  const int64_t tiles = sort_tiles_for(cap);
+  const unsigned grid = static_cast<unsigned>(tiles < grid_cap ? (tiles > 0 ? tiles : 1) : grid_cap);
+  for (int p = 0; p < passes; ++p) {
+    PassArgs a;
+    a.keys_in = keys[p & 1]; a.vals_in = vals[p & 1]; a.keys_out = keys[(p + 1) & 1]; a.vals_out = vals[(p + 1) & 1];
+    a.n_total = n_dev; a.cap = cap; a.shift = 8 * p; a.digit_offsets = hist + p * kRadix;
+    a.ticket = tickets + p;
+    a.stall_tile = -1;
+    a.spin_limit = kSpinLimit;
+    a.lookback = lookback + static_cast<size_t>(p) * (tiles + 1) * kRadix;
+    sort_pass_kernel<<<grid, kSortThreads, sizeof(SortSmem), stream>>>(a, status);
+  }
+  return cuda_status(cudaGetLastError());
+}
+
 }  // namespace gs
 
 extern "C" size_t gs_bin_sort_workspace_bytes(int64_t N, int32_t V, int64_t capacity, int64_t n_tiles) {
@@ -637,21 +686,9 @@ extern "C" int gs_bin_sort(const float* projected, const int16_t* rects, const u
   if (e != cudaSuccess) return GS_ERR_CUDA;
   const int64_t VN = N * V;
   if (VN == 0) return GS_OK;
-  static bool attr_set = false;
-  static int sort_ctas_per_sm = 0;
-  if (!attr_set) {
-    if (cudaFuncSetAttribute(sort_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(sizeof(SortSmem))) != cudaSuccess ||
-        cudaFuncSetAttribute(sort_pass_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared) != cudaSuccess)
-      return GS_ERR_CUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sort_ctas_per_sm, sort_pass_kernel, kSortThreads,
-                                                      sizeof(SortSmem)) != cudaSuccess ||
-        sort_ctas_per_sm < 1)
-      sort_ctas_per_sm = 1;
-    attr_set = true;
-  }
-  const int64_t sort_grid_cap = static_cast<int64_t>(sm_count()) * sort_ctas_per_sm;
+  int64_t sort_grid_cap = 0;
+  rc = gs::sort_grid_cap(&sort_grid_cap);
+  if (rc != GS_OK) return rc;
   auto sort_grid = [&](int64_t tiles) {
     return static_cast<unsigned>(tiles < sort_grid_cap ? (tiles > 0 ? tiles : 1) : sort_grid_cap);
   };

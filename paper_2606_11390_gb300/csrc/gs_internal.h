@@ -21,4 +21,17 @@ int launch_project_bwd(const float* means, const float* log_scales, const float*
                        const uint32_t* counts, const float* d_projected, float* d_means, float* d_log_scales,
                        float* d_quats, float* d_opacity_logits, float* d_sh, int32_t* status, cudaStream_t stream);
 
+// Onesweep digit passes over (u32 key, u32 value) pairs (binsort.cu), shared
+// with the Morton ordering. A pass p sorts stably by key bits [8p, 8p + 8)
+// using the exclusive digit offsets hist[p][256]; pairs alternate between
+// keys[0]/vals[0] and keys[1]/vals[1], so after an even number of passes the
+// result is back in buffer 0. The item count is read on the device from
+// *n_dev (clamped to cap). tickets[passes] and the look-back words
+// ((sort_tiles_for(cap) + 1) * 256 per pass) must be zero.
+int64_t sort_tiles_for(int64_t n);
+void launch_hist_scan(uint32_t* hist, int passes, cudaStream_t stream);
+int run_u32_sort_passes(uint32_t* const keys[2], uint32_t* const vals[2], const int64_t* n_dev, int64_t cap,
+                        int passes, const uint32_t* hist, uint32_t* tickets, uint64_t* lookback, int32_t* status,
+                        cudaStream_t stream);
+
 }  // namespace gs

@@ -173,6 +173,29 @@ def render(params: FlatParams, cams: Cameras, frame: Frame, max_retries: int = 3
     return frame
 
 
+def morton_permutation(params: FlatParams, stream=None):
+    """Permutation (int32 on the device) that lists the Gaussians along a 3D
+    Morton curve of their means (gs_morton_order); returns (perm, status)."""
+    N = params.N
+    dev = params.flat.device
+    perm = torch.empty(max(N, 1), dtype=torch.int32, device=dev)
+    ws = torch.empty(max(gs.gs_morton_workspace_bytes(N), 1), dtype=torch.uint8, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    if ws.data_ptr() % 256:
+        raise gs.GSError("workspace allocation is not 256-byte aligned")
+    gs.gs_morton_order(params["means"], N, perm, None, ws, status, stream)
+    return perm, status
+
+
+def permute_gaussians(params: FlatParams, perm, out: FlatParams | None = None, status=None, stream=None) -> FlatParams:
+    """out[name][i] = params[name][perm[i]] for every parameter array (gs_gather_rows)."""
+    out = out if out is not None else params.like()
+    status = status if status is not None else torch.zeros(1, dtype=torch.int32, device=params.flat.device)
+    for name in PARAM_NAMES:
+        gs.gs_gather_rows(params[name], out[name], params.N, PARAM_WIDTH[name], perm, status, stream)
+    return out
+
+
 class GaussianRasterize(torch.autograd.Function):
     """image[P, 3] = render(means, log_scales, quats, opacity_logits, sh).
 
