@@ -378,6 +378,7 @@ def main():
             peaks, src = measured_peaks()
             extra["roofline"] = roofline_for(dom, st[dom], step, peaks, src, scene["name"])
             extra["ssim_loss"] = ssim_kernel_measure(step.image, step.target, step.cams.sizes, peaks, src)
+            extra["densify_stats"] = densify_measure(step, peaks, src)
             if not args.no_morton and scene["name"] != "street":
                 extra["morton"] = morton_measure(step, scene, args, tile, ms)
         if not args.no_e2e:
@@ -519,6 +520,37 @@ def ssim_kernel_measure(image, target, sizes, peaks, src, iters=20, warmup=3):
                          "work": f"{3 * P} values x {SSIM_FLOP_PER_VALUE} FLOP",
                          "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz ({src} max SM clock)"},
             "hbm": {"achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm, "bytes": 3 * P * 12}}
+
+
+def densify_measure(step, peaks, src, iters=20):
+    """gs_densify_stats alone on the step's backward buffers (one launch per
+    step when TrainStep(densify_stats=True)); HBM-bound: per (view, Gaussian)
+    the tile count, the 2D-mean gradient and the radius (16 B), per Gaussian
+    three running statistics read and written (24 B)."""
+    import torch
+
+    from paper_2606_11390_gb300 import _native as gs
+
+    fr = step.frames[0]
+    N, V = step.N, step.cams.V
+    arrs = [torch.zeros(N, dtype=torch.float32, device=step.image.device) for _ in range(3)]
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        gs.gs_densify_stats(fr.projected, fr.counts, fr.d_projected, N, step.cams.sizes, *arrs)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(iters):
+        gs.gs_densify_stats(fr.projected, fr.counts, fr.d_projected, N, step.cams.sizes, *arrs)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / iters
+    bytes_ = V * N * 16 + N * 24
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    gbs = bytes_ / (ms * 1e-3) / 1e9
+    return {"ms": ms, "launches": 1, "roofline": {"kernel": "densify_stats", "bound": "hbm", "achieved": gbs,
+                                                  "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
+                                                  "peak_source": f"{src} hbm_gbs"}}
 
 
 def morton_measure(step, scene, args, tile, ms_input_order):

@@ -320,7 +320,7 @@ GS_API int gs_ssim_loss(const float* image, const float* target, const int32_t* 
 GS_API size_t gs_morton_workspace_bytes(int64_t N);
 
 /* gs_morton_order - permutation that orders Gaussians along a 3D Morton curve.
- * Paper: §6 Morton-sorts the Gaussians in three dimensions during
+ * Paper: §5.2 Morton-sorts the Gaussians in three dimensions during
  * densification for memory locality in rasterisation (5-10 %).
  * lo/hi = per-axis min/max of the means; q = clamp(floor((x - lo) *
  * (1024 / (hi - lo))), 0, 1023) per axis, each operation a single rounded
@@ -340,7 +340,7 @@ GS_API int gs_morton_order(const float* means, int64_t N, uint32_t* perm, uint32
 /* gs_gather_rows - dst[i] = src[perm[i]] for n_rows rows of row_floats
  * floats (applies a gs_morton_order permutation to any per-Gaussian array:
  * parameters, gradients, optimiser moments). The paper has no separate
- * operator for it (§6 reindexes during densification).
+ * operator for it (§5.2 reindexes during densification).
  * in  (device): src [n][row_floats], perm [n] (values < n_rows; others are
  *     skipped and set GS_STATUS_BOUNDS in *status_dev).
  * out (device): dst [n][row_floats], distinct from src; 16-byte aligned when
@@ -348,6 +348,25 @@ GS_API int gs_morton_order(const float* means, int64_t N, uint32_t* perm, uint32
  * Errors: GS_ERR_ARG, GS_ERR_CUDA. */
 GS_API int gs_gather_rows(const float* src, float* dst, int64_t n_rows, int32_t row_floats, const uint32_t* perm,
                           int32_t* status_dev, gs_stream_t stream);
+
+/* gs_densify_stats - densification statistics of one backward pass.
+ * Paper: §5.2 densifies (Kerbl et al. 2023) to large Gaussian counts; the
+ * decisions use the accumulated screen-space positional gradient and the
+ * largest screen-space radius of each Gaussian. For every view v where
+ * Gaussian g is visible (counts[v*N+g] > 0):
+ *   grad_accum[g] += sqrt((dmx * W_v/2)^2 + (dmy * H_v/2)^2), with (dmx, dmy)
+ *                    = dL/dmean2d from d_projected (pixel units; the factors
+ *                    give the gradient in normalised device coordinates);
+ *   denom[g] += 1;  max_radii[g] = max(max_radii[g], radius in pixels).
+ * in  (device): projected [V*N][12], counts [V*N] (gs_project), d_projected
+ *     [V*N][9] (gs_rasterize_bwd). in (host): sizes [V][2], 1 <= V <= 64.
+ * in/out (device): grad_accum [N], denom [N], max_radii [N] float32,
+ *     accumulated (the caller zeroes them when it starts a statistics window).
+ * One thread per Gaussian over all views: no atomics, deterministic.
+ * Errors: GS_ERR_ARG, GS_ERR_CUDA. */
+GS_API int gs_densify_stats(const float* projected, const uint32_t* counts, const float* d_projected, int64_t N,
+                            const int32_t* sizes, int32_t V, float* grad_accum, float* denom, float* max_radii,
+                            gs_stream_t stream);
 
 /* gs_adam_step - fused Adam update over a flat parameter array.
  * Paper: §3.2 (fused Adam with vectorised loads and stores and

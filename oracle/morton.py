@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY: tests/, the smoke check in __graft_entry__ and the
 CPU-baseline leg of bench.py may use this module; the product package never
 does. It shares no code with the CUDA library.
 
-What it computes. The paper (arXiv 2606.11390, §6) orders the Gaussians along
+What it computes. The paper (arXiv 2606.11390, §5.2) orders the Gaussians along
 a three-dimensional Morton curve during densification, for memory locality in
 rasterisation; it gives no quantisation. The reading taken here: per axis,
 lo and hi are the minimum and maximum of the means; a coordinate becomes the

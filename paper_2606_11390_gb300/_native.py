@@ -72,6 +72,7 @@ _SIGNATURES = {
     "gs_morton_workspace_bytes": ([_I64], ctypes.c_size_t),
     "gs_morton_order": ([_VP, _I64, _VP, _VP, _VP, ctypes.c_size_t, _VP, _VP], ctypes.c_int),
     "gs_gather_rows": ([_VP, _VP, _I64, _I32, _VP, _VP, _VP], ctypes.c_int),
+    "gs_densify_stats": ([_VP, _VP, _VP, _I64, _VP, _I32, _VP, _VP, _VP, _VP], ctypes.c_int),
 }
 
 _lock = threading.Lock()
@@ -254,6 +255,13 @@ def gs_gather_rows(src, dst, n_rows, row_floats, perm, status, stream=None):
     rc = load().gs_gather_rows(_ptr(src), _ptr(dst), int(n_rows), int(row_floats), _ptr(perm), _ptr(status),
                                _stream(stream))
     _check(rc, "gs_gather_rows")
+
+
+def gs_densify_stats(projected, counts, d_projected, N, sizes, grad_accum, denom, max_radii, stream=None):
+    sz = _sizes(sizes)
+    rc = load().gs_densify_stats(_ptr(projected), _ptr(counts), _ptr(d_projected), int(N), _ptr(sz), sz.shape[0],
+                                 _ptr(grad_accum), _ptr(denom), _ptr(max_radii), _stream(stream))
+    _check(rc, "gs_densify_stats")
 
 
 def gs_adam_step(param, grad, exp_avg, exp_avg_sq, lr, beta1, beta2, eps, step, stream=None):

@@ -1,6 +1,6 @@
 // Morton (Z-order) ordering of Gaussians in 3D and row gathers.
 //
-// Paper: arXiv 2606.11390 §6 sorts the Gaussians along a three-dimensional
+// Paper: arXiv 2606.11390 §5.2 sorts the Gaussians along a three-dimensional
 // Morton curve (Morton 1966, as in LiteGS) during densification, so that
 // Gaussians near each other in space sit near each other in memory; the
 // rasteriser's gathers of projected records and its gradient atomics then

@@ -260,7 +260,7 @@ class TrainStep:
 
     def __init__(self, scene: dict, mode="batched", adam=False, lr=1e-3, betas=(0.9, 0.999), eps=1e-15,
                  tile=None, device="cuda", graph=True, params: FlatParams | None = None, loss="l1l2",
-                 ssim_lambda=0.2):
+                 ssim_lambda=0.2, densify_stats=False):
         if loss not in ("l1l2", "ssim"):
             raise ValueError(f"unknown loss {loss!r}")
         self.loss_kind, self.ssim_lambda = loss, float(ssim_lambda)
@@ -284,6 +284,11 @@ class TrainStep:
         self.dL_dimage = torch.zeros_like(self.image)
         self.loss = torch.zeros(1, dtype=torch.float64, device=device)
         self.step_count = torch.zeros(1, dtype=torch.int32, device=device)
+        self.densify_on = densify_stats
+        if densify_stats:  # accumulated over steps until the caller resets them
+            self.grad_accum = torch.zeros(self.N, dtype=torch.float32, device=device)
+            self.denom = torch.zeros_like(self.grad_accum)
+            self.max_radii = torch.zeros_like(self.grad_accum)
         if adam:
             self.exp_avg = torch.zeros_like(self.params.flat)
             self.exp_avg_sq = torch.zeros_like(self.params.flat)
@@ -309,6 +314,10 @@ class TrainStep:
             a, b = int(self.cams.pix_base[v]) * 3, int(self.cams.pix_base[v + 1 if pv else -1]) * 3
             rasterize_bwd(self.params, cams, fr, self.dL_dimage[a:b], self.grads, stream, accumulate=pv and v > 0)
             n += 2
+            if self.densify_on:
+                gs.gs_densify_stats(fr.projected, fr.counts, fr.d_projected, self.N, cams.sizes, self.grad_accum,
+                                    self.denom, self.max_radii, stream)
+                n += 1
         if self.adam_on:
             gs.gs_adam_step(self.params.flat, self.grads.flat, self.exp_avg, self.exp_avg_sq, self.lr, self.betas[0],
                             self.betas[1], self.eps, self.step_count, stream)
@@ -370,7 +379,16 @@ class TrainStep:
             with torch.cuda.graph(self.graph):
                 self._enqueue(torch.cuda.current_stream())
             torch.cuda.synchronize()
+        if self.densify_on:  # the sizing and capture steps do not count
+            self.reset_densify_stats()
+            torch.cuda.synchronize()
         return self
+
+    def reset_densify_stats(self):
+        """Starts a new densification-statistics window."""
+        self.grad_accum.zero_()
+        self.denom.zero_()
+        self.max_radii.zero_()
 
     def run(self):
         """Enqueues one step (graph replay in batched mode)."""
