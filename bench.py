@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--loss", default="l1l2", choices=["l1l2", "ssim"],
                     help="image loss of the step: the workload's L1 + L2, or the fused SSIM loss")
     ap.add_argument("--no-morton", action="store_true", help="skip the Morton-order leg")
+    ap.add_argument("--no-partitioned", action="store_true", help="skip the partitioned-sort leg")
     ap.add_argument("--kernel", default="step", choices=["step", "ssim_loss"],
                     help="step: the training step (default); ssim_loss: the fused SSIM loss kernel alone on a "
                          "seeded image pair of the workload's view sizes")
@@ -379,6 +380,8 @@ def main():
             extra["roofline"] = roofline_for(dom, st[dom], step, peaks, src, scene["name"])
             extra["ssim_loss"] = ssim_kernel_measure(step.image, step.target, step.cams.sizes, peaks, src)
             extra["densify_stats"] = densify_measure(step, peaks, src)
+            if not args.no_partitioned and scene["name"] != "street":
+                extra["partitioned_sort"] = partitioned_sort_measure(step)
             if not args.no_morton and scene["name"] != "street":
                 extra["morton"] = morton_measure(step, scene, args, tile, ms)
         if not args.no_e2e:
@@ -520,6 +523,39 @@ def ssim_kernel_measure(image, target, sizes, peaks, src, iters=20, warmup=3):
                          "work": f"{3 * P} values x {SSIM_FLOP_PER_VALUE} FLOP",
                          "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz ({src} max SM clock)"},
             "hbm": {"achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm, "bytes": 3 * P * 12}}
+
+
+def partitioned_sort_measure(step, parts=(1, 2, 4, 8), iters=10):
+    """gs_bin_sort_partitioned on the step's projected records for several
+    partition counts (1 = the plain gs_bin_sort): the paper's multi-device
+    depth sort (local sorts + merge-path merge tree) emulated on one GPU."""
+    import torch
+
+    from paper_2606_11390_gb300 import renderer as R
+
+    fr0 = step.frames[0]
+    stream = torch.cuda.current_stream()
+    out = {}
+    for P in parts:
+        fr = R.Frame(step.N, fr0.cams, fr0.cfg, capacity=fr0.capacity, partitions=P)
+        fr.projected.copy_(fr0.projected)
+        fr.rects.copy_(fr0.rects)
+        fr.counts.copy_(fr0.counts)
+        for _ in range(2):
+            R.bin_sort(fr)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(iters):
+            R.bin_sort(fr)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if fr.read_status() != 0:
+            raise RuntimeError(f"partitioned sort status {fr.read_status()}")
+        out[str(P)] = a.elapsed_time(b) / iters
+        del fr
+        torch.cuda.empty_cache()
+    return {"bin_sort_ms_by_partitions": out}
 
 
 def densify_measure(step, peaks, src, iters=20):

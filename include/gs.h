@@ -195,6 +195,28 @@ GS_API int gs_bin_sort(const float* projected, const int16_t* rects, const uint3
                 uint32_t* tile_ranges, int64_t* n_isect_dev, void* workspace, size_t workspace_bytes,
                 int32_t* status_dev, gs_stream_t stream);
 
+/* gs_bin_sort_partitioned_workspace_bytes - workspace of
+ * gs_bin_sort_partitioned; 0 for invalid arguments (partitions not a power of
+ * two in [1, 64]). */
+GS_API size_t gs_bin_sort_partitioned_workspace_bytes(int64_t N, int32_t V, int64_t capacity, int64_t n_tiles,
+                                                      int32_t partitions);
+
+/* gs_bin_sort_partitioned - gs_bin_sort with its depth sort run the way the
+ * paper sorts across devices (§4): the V*N records are split into
+ * `partitions` contiguous ranges, each range is compacted and depth-sorted on
+ * its own, and the sorted ranges are combined by a log2(partitions)-level
+ * merge tree in which every output block finds its split of the two input
+ * runs by a merge-path binary search. Here the partitions share one GPU (an
+ * emulation of the multi-device sort); the result is identical, bit for bit,
+ * to gs_bin_sort's. Arguments as gs_bin_sort, plus partitions (a power of two
+ * in [1, 64]) and a workspace of gs_bin_sort_partitioned_workspace_bytes.
+ * Errors: as gs_bin_sort. */
+GS_API int gs_bin_sort_partitioned(const float* projected, const int16_t* rects, const uint32_t* counts, int64_t N,
+                                   const int32_t* sizes, int32_t V, const gs_config* cfg, uint64_t* keys,
+                                   uint32_t* vals, int64_t capacity, uint32_t* tile_ranges, int64_t* n_isect_dev,
+                                   int32_t partitions, void* workspace, size_t workspace_bytes, int32_t* status_dev,
+                                   gs_stream_t stream);
+
 /* gs_bin_sort_static - gs_bin_sort without a caller-provided workspace.
  * The paper has no counterpart: this variant exists for callers that cannot
  * allocate device memory where they sort (plug-ins whose host application

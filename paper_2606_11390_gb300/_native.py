@@ -72,6 +72,9 @@ _SIGNATURES = {
     "gs_morton_workspace_bytes": ([_I64], ctypes.c_size_t),
     "gs_morton_order": ([_VP, _I64, _VP, _VP, _VP, ctypes.c_size_t, _VP, _VP], ctypes.c_int),
     "gs_gather_rows": ([_VP, _VP, _I64, _I32, _VP, _VP, _VP], ctypes.c_int),
+    "gs_bin_sort_partitioned_workspace_bytes": ([_I64, _I32, _I64, _I64, _I32], ctypes.c_size_t),
+    "gs_bin_sort_partitioned": ([_VP, _VP, _VP, _I64, _VP, _I32, _VP, _VP, _VP, _I64, _VP, _VP, _I32, _VP,
+                                 ctypes.c_size_t, _VP, _VP], ctypes.c_int),
     "gs_densify_stats": ([_VP, _VP, _VP, _I64, _VP, _I32, _VP, _VP, _VP, _VP], ctypes.c_int),
 }
 
@@ -171,6 +174,22 @@ def gs_bin_sort(projected, rects, counts, N, sizes, cfg, keys, vals, capacity, t
                             _ptr(keys), _ptr(vals), int(capacity), _ptr(tile_ranges), _ptr(n_isect), _ptr(workspace),
                             workspace.numel() * workspace.element_size(), _ptr(status), _stream(stream))
     _check(rc, "gs_bin_sort")
+
+
+def gs_bin_sort_partitioned_workspace_bytes(N, V, capacity, n_tiles, partitions) -> int:
+    return int(load().gs_bin_sort_partitioned_workspace_bytes(int(N), int(V), int(capacity), int(n_tiles),
+                                                              int(partitions)))
+
+
+def gs_bin_sort_partitioned(projected, rects, counts, N, sizes, cfg, keys, vals, capacity, tile_ranges, n_isect,
+                            partitions, workspace, status, stream=None):
+    sz = _sizes(sizes)
+    c, cref = _cfg_ref(cfg)
+    rc = load().gs_bin_sort_partitioned(_ptr(projected), _ptr(rects), _ptr(counts), int(N), _ptr(sz), sz.shape[0],
+                                        cref, _ptr(keys), _ptr(vals), int(capacity), _ptr(tile_ranges),
+                                        _ptr(n_isect), int(partitions), _ptr(workspace),
+                                        workspace.numel() * workspace.element_size(), _ptr(status), _stream(stream))
+    _check(rc, "gs_bin_sort_partitioned")
 
 
 def gs_bin_sort_static(projected, rects, counts, N, sizes, cfg, keys, vals, capacity, tile_ranges, n_isect, status,

@@ -130,9 +130,9 @@ __device__ __forceinline__ uint64_t block_scan_lookback(uint64_t local, uint32_t
 //     order, plus the digit histograms of the four depth passes.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kScanThreads) compact_visible_kernel(
-    const uint32_t* __restrict__ counts, const float* __restrict__ projected, int64_t n, ScanState st,
-    uint32_t* __restrict__ dkeys, uint32_t* __restrict__ dvals, uint32_t* __restrict__ hist, int64_t* n_visible,
-    int32_t* status) {
+    const uint32_t* __restrict__ counts, const float* __restrict__ projected, int64_t n, uint32_t index_base,
+    ScanState st, uint32_t* __restrict__ dkeys, uint32_t* __restrict__ dvals, uint32_t* __restrict__ hist,
+    int64_t* n_visible, int32_t* status) {
   __shared__ uint32_t s_tile;
   __shared__ uint64_t s_warp[kScanThreads / 32];
   __shared__ uint64_t s_prefix;
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kScanThreads) compact_visible_kernel(
     if (vis & (1u << i)) {
       const uint32_t d = __float_as_uint(projected[(base + i) * kRecordFloats + 6]);
       dkeys[pos] = d;
-      dvals[pos] = static_cast<uint32_t>(base + i);
+      dvals[pos] = index_base + static_cast<uint32_t>(base + i);
 #pragma unroll
       for (int p = 0; p < kDepthPasses; ++p) atomicAdd(&s_hist[p][(d >> (8 * p)) & 0xffu], 1u);
       ++pos;
@@ -489,6 +489,130 @@ __global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) sort_pass_ke
   }
 }
 
+// ---------------------------------------------------------------------------
+// Merge of sorted partitions (the emulated multi-partition depth sort).
+//
+// The paper (§4) sorts a camera's Gaussians across devices by sorting each
+// device's shard locally and combining the sorted shards in a log2(P)-level
+// merge tree, every pair of partitions locating the split of each output
+// range with a merge-path binary search (Green et al. 2012), so no partition
+// has to gather all the data. Here the P partitions are record ranges of one
+// GPU: each is compacted and depth-sorted on its own (4 digit passes), then
+// every merge level is one launch in which each CTA owns 2048 consecutive
+// outputs of one pair of runs, finds where its output range starts and ends
+// in the two inputs by binary search, stages both input pieces in shared
+// memory and merges them, each thread producing 8 outputs from its own
+// merge-path split. Ties take the left run first, and runs hold increasing
+// record ranges, so the result equals the stable depth sort of all records.
+// ---------------------------------------------------------------------------
+constexpr int kMergeThreads = 256;
+constexpr int kMergeItems = 8;
+constexpr int kMergeTile = kMergeThreads * kMergeItems;
+
+struct MergeArgs {
+  const uint32_t* keys_in;
+  const uint32_t* vals_in;
+  uint32_t* keys_out;
+  uint32_t* vals_out;
+  const int64_t* part_n;    // [P] sorted items per partition
+  int64_t stride;           // partition p's items start at p * stride
+  int level;                // inputs are runs of 2^level partitions
+  int64_t ctas_per_pair;
+  int64_t* n_total;         // written by the last level (one pair)
+};
+
+// Number of elements of a taken among the first d outputs (a first on ties).
+__device__ __forceinline__ int64_t merge_path_split(const uint32_t* a, int64_t na, const uint32_t* b, int64_t nb,
+                                                    int64_t d) {
+  int64_t lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (a[mid] <= b[d - 1 - mid]) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kMergeThreads) merge_runs_kernel(MergeArgs m) {
+  __shared__ uint32_t s_keys[kMergeTile];
+  __shared__ uint32_t s_vals[kMergeTile];
+  __shared__ int64_t s_split[2];
+  const int tid = threadIdx.x;
+  const int64_t pair = blockIdx.x / m.ctas_per_pair;
+  const int64_t c = blockIdx.x - pair * m.ctas_per_pair;
+  const int span = 1 << m.level;
+  const int pa = static_cast<int>(2 * pair) * span, pb = pa + span;
+  int64_t na = 0, nb = 0;
+  for (int q = 0; q < span; ++q) {
+    na += m.part_n[pa + q];
+    nb += m.part_n[pb + q];
+  }
+  const int64_t n = na + nb;
+  if (c == 0 && tid == 0 && m.n_total) *m.n_total = n;
+  const int64_t d0 = c * kMergeTile;
+  if (d0 >= n) return;
+  const int64_t d1 = d0 + kMergeTile < n ? d0 + kMergeTile : n;
+  const uint32_t* ak = m.keys_in + pa * m.stride;
+  const uint32_t* bk = m.keys_in + pb * m.stride;
+  const uint32_t* av = m.vals_in + pa * m.stride;
+  const uint32_t* bv = m.vals_in + pb * m.stride;
+  if (tid < 2) s_split[tid] = merge_path_split(ak, na, bk, nb, tid == 0 ? d0 : d1);
+  __syncthreads();
+  const int64_t a0 = s_split[0], a1 = s_split[1];
+  const int64_t b0 = d0 - a0, b1 = d1 - a1;
+  const int la = static_cast<int>(a1 - a0), lb = static_cast<int>(b1 - b0);
+  for (int i = tid; i < la; i += kMergeThreads) {
+    s_keys[i] = ak[a0 + i];
+    s_vals[i] = av[a0 + i];
+  }
+  for (int i = tid; i < lb; i += kMergeThreads) {
+    s_keys[la + i] = bk[b0 + i];
+    s_vals[la + i] = bv[b0 + i];
+  }
+  __syncthreads();
+  // this thread's 8 outputs
+  const int len = la + lb;
+  const int dl = tid * kMergeItems;
+  uint32_t ok[kMergeItems], ov[kMergeItems];
+  int cnt = 0;
+  if (dl < len) {
+    int lo = dl > lb ? dl - lb : 0, hi = dl < la ? dl : la;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (s_keys[mid] <= s_keys[la + dl - 1 - mid]) lo = mid + 1;
+      else hi = mid;
+    }
+    int ai = lo, bi = dl - lo;
+#pragma unroll
+    for (int i = 0; i < kMergeItems; ++i) {
+      if (dl + i < len) {
+        const bool take_a = ai < la && (bi >= lb || s_keys[ai] <= s_keys[la + bi]);
+        const int src = take_a ? ai : la + bi;
+        ok[i] = s_keys[src];
+        ov[i] = s_vals[src];
+        ai += take_a ? 1 : 0;
+        bi += take_a ? 0 : 1;
+        ++cnt;
+      }
+    }
+  }
+  __syncthreads();  // all reads of the staged inputs are done
+#pragma unroll
+  for (int i = 0; i < kMergeItems; ++i) {
+    if (i < cnt) {
+      s_keys[dl + i] = ok[i];
+      s_vals[dl + i] = ov[i];
+    }
+  }
+  __syncthreads();
+  uint32_t* ok_g = m.keys_out + pa * m.stride + d0;
+  uint32_t* ov_g = m.vals_out + pa * m.stride + d0;
+  for (int i = tid; i < len; i += kMergeThreads) {
+    ok_g[i] = s_keys[i];
+    ov_g[i] = s_vals[i];
+  }
+}
+
 // Tile ranges from the sorted tile ids (ranges zeroed beforehand): four ids
 // per thread from one 16-byte load; a range starts where the id differs from
 // its predecessor and ends where it differs from its successor.
@@ -552,24 +676,34 @@ int tile_passes_for(int64_t n_tiles) {
 
 struct WsLayout {
   size_t dkeys0, dvals0, dkeys1, dvals1, offsets, tkeys0, tkeys1, tvals_alt;
-  size_t zero_begin, scan1, scan2, hist_d, hist_t, tickets, n_visible, lb_depth, lb_tile, zero_end, total;
+  size_t zero_begin, scan1, scan2, hist_d, hist_t, tickets, n_visible, lb_depth, lb_tile;
+  size_t part_scan, part_hist, part_tickets, part_n, part_lb, zero_end, total;
   int64_t n_scan_tiles, n_depth_tiles, n_tile_tiles;
+  int64_t part_stride, part_scan_tiles, part_sort_tiles;
   int tile_passes;
 };
 
-WsLayout ws_layout(int64_t N, int32_t V, int64_t capacity, int64_t n_tiles) {
+constexpr int kPartTickets = 8;  // per partition: compaction + 4 depth passes
+
+// P > 1: the depth sort runs as P partitions of the records, merged after.
+WsLayout ws_layout(int64_t N, int32_t V, int64_t capacity, int64_t n_tiles, int P = 1) {
   WsLayout w;
   const int64_t VN = N * V;
+  w.part_stride = P > 1 ? (VN + P - 1) / P : VN;
+  const int64_t depth_slots = P > 1 ? w.part_stride * P : VN;
   const size_t vn = static_cast<size_t>(VN > 0 ? VN : 1), cap = static_cast<size_t>(capacity > 0 ? capacity : 1);
+  const size_t ds = static_cast<size_t>(depth_slots > 0 ? depth_slots : 1);
   w.tile_passes = tile_passes_for(n_tiles);
   w.n_scan_tiles = (VN + kScanTile - 1) / kScanTile;
   w.n_depth_tiles = (VN + kSortTile - 1) / kSortTile;
   w.n_tile_tiles = (capacity + kSortTile - 1) / kSortTile;
+  w.part_scan_tiles = (w.part_stride + kScanTile - 1) / kScanTile;
+  w.part_sort_tiles = (w.part_stride + kSortTile - 1) / kSortTile;
   size_t o = 0;
-  w.dkeys0 = o; o = align256(o + 4 * vn);
-  w.dvals0 = o; o = align256(o + 4 * vn);
-  w.dkeys1 = o; o = align256(o + 4 * vn);
-  w.dvals1 = o; o = align256(o + 4 * vn);
+  w.dkeys0 = o; o = align256(o + 4 * ds);
+  w.dvals0 = o; o = align256(o + 4 * ds);
+  w.dkeys1 = o; o = align256(o + 4 * ds);
+  w.dvals1 = o; o = align256(o + 4 * ds);
   w.offsets = o; o = align256(o + 4 * vn);
   w.tkeys0 = o; o = align256(o + 4 * cap);
   w.tkeys1 = o; o = align256(o + 4 * cap);
@@ -583,6 +717,12 @@ WsLayout ws_layout(int64_t N, int32_t V, int64_t capacity, int64_t n_tiles) {
   w.n_visible = o; o = align256(o + 8);
   w.lb_depth = o; o = align256(o + 8 * kRadix * kDepthPasses * static_cast<size_t>(w.n_depth_tiles + 1));
   w.lb_tile = o; o = align256(o + 8 * kRadix * static_cast<size_t>(w.tile_passes) * static_cast<size_t>(w.n_tile_tiles + 1));
+  const size_t np = static_cast<size_t>(P > 1 ? P : 0);
+  w.part_scan = o; o = align256(o + 8 * np * static_cast<size_t>(w.part_scan_tiles + 1));
+  w.part_hist = o; o = align256(o + 4 * np * kDepthPasses * kRadix);
+  w.part_tickets = o; o = align256(o + 4 * np * kPartTickets);
+  w.part_n = o; o = align256(o + 8 * np);
+  w.part_lb = o; o = align256(o + 8 * np * kRadix * kDepthPasses * static_cast<size_t>(w.part_sort_tiles + 1));
   w.zero_end = o;
   w.total = o;
   return w;
@@ -653,17 +793,15 @@ int run_u32_sort_passes(uint32_t* const keys[2], uint32_t* const vals[2], const 
 
 }  // namespace gs
 
-extern "C" size_t gs_bin_sort_workspace_bytes(int64_t N, int32_t V, int64_t capacity, int64_t n_tiles) {
-  if (N < 0 || V < 1 || capacity < 0 || n_tiles < 1) return 0;
-  return gs::ws_layout(N, V, capacity, n_tiles).total;
-}
+namespace gs {
+namespace {
 
-extern "C" int gs_bin_sort(const float* projected, const int16_t* rects, const uint32_t* counts, int64_t N,
-                           const int32_t* sizes, int32_t V, const gs_config* cfg, uint64_t* keys, uint32_t* vals,
-                           int64_t capacity, uint32_t* tile_ranges, int64_t* n_isect_dev, void* workspace,
-                           size_t workspace_bytes, int32_t* status_dev, gs_stream_t stream_) {
-  using namespace gs;
-  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+bool valid_partitions(int P) { return P >= 1 && P <= 64 && (P & (P - 1)) == 0; }
+
+int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* counts, int64_t N,
+                  const int32_t* sizes, int32_t V, const gs_config* cfg, uint64_t* keys, uint32_t* vals,
+                  int64_t capacity, uint32_t* tile_ranges, int64_t* n_isect_dev, void* workspace,
+                  size_t workspace_bytes, int32_t* status_dev, cudaStream_t stream, int P) {
   Layout L;
   int rc = build_layout(sizes, V, cfg, &L, nullptr);
   if (rc != GS_OK) return rc;
@@ -673,7 +811,8 @@ extern "C" int gs_bin_sort(const float* projected, const int16_t* rects, const u
   if (N > 0 && (!projected || !rects || !counts)) return GS_ERR_ARG;
   if (capacity > 0 && !vals) return GS_ERR_ARG;
   if ((reinterpret_cast<uintptr_t>(workspace) & 255u) || (reinterpret_cast<uintptr_t>(rects) & 7u)) return GS_ERR_ARG;
-  const WsLayout w = ws_layout(N, V, capacity, L.n_tiles);
+  if (!valid_partitions(P)) return GS_ERR_ARG;
+  const WsLayout w = ws_layout(N, V, capacity, L.n_tiles, P);
   if (workspace_bytes < w.total) return GS_ERR_ARG;
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   auto u32 = [&](size_t off) { return reinterpret_cast<uint32_t*>(ws + off); };
@@ -695,25 +834,73 @@ extern "C" int gs_bin_sort(const float* projected, const int16_t* rects, const u
   const unsigned scan_grid = static_cast<unsigned>(w.n_scan_tiles);
 
   // 1a. visible records -> (depth bits, record), depth digit histograms
-  ScanState st1{reinterpret_cast<uint64_t*>(ws + w.scan1), tickets + 0};
   uint32_t* dk[2] = {u32(w.dkeys0), u32(w.dkeys1)};
   uint32_t* dv[2] = {u32(w.dvals0), u32(w.dvals1)};
-  uint32_t* hist_d = u32(w.hist_d);
-  compact_visible_kernel<<<scan_grid, kScanThreads, 0, stream>>>(counts, projected, VN, st1, dk[0], dv[0], hist_d,
-                                                                   n_visible, status_dev);
-  hist_scan_kernel<<<1, kRadix, 0, stream>>>(hist_d, kDepthPasses);
-  // 1b. four depth passes (even count: the result is back in dk[0], dv[0])
-  for (int p = 0; p < kDepthPasses; ++p) {
-    PassArgs a;
-    a.keys_in = dk[p & 1]; a.vals_in = dv[p & 1]; a.keys_out = dk[(p + 1) & 1]; a.vals_out = dv[(p + 1) & 1];
-    a.n_total = n_visible; a.cap = VN; a.shift = 8 * p; a.digit_offsets = hist_d + p * kRadix;
-    a.ticket = tickets + 2 + p;
-    a.stall_tile = (p == 0 && (cfg->flags & GS_FLAG_TEST_STALL_LOOKBACK)) ? 0 : -1;
-    a.spin_limit = (cfg->flags & GS_FLAG_TEST_STALL_LOOKBACK) ? kTestSpinLimit : kSpinLimit;
-    a.lookback = reinterpret_cast<uint64_t*>(ws + w.lb_depth) + static_cast<size_t>(p) * (w.n_depth_tiles + 1) * kRadix;
-    sort_pass_kernel<<<sort_grid(w.n_depth_tiles), kSortThreads, sizeof(SortSmem), stream>>>(a, status_dev);
-  }
   const uint32_t* order = dv[0];
+  if (P == 1) {
+    ScanState st1{reinterpret_cast<uint64_t*>(ws + w.scan1), tickets + 0};
+    uint32_t* hist_d = u32(w.hist_d);
+    compact_visible_kernel<<<scan_grid, kScanThreads, 0, stream>>>(counts, projected, VN, 0u, st1, dk[0], dv[0],
+                                                                     hist_d, n_visible, status_dev);
+    hist_scan_kernel<<<1, kRadix, 0, stream>>>(hist_d, kDepthPasses);
+    // 1b. four depth passes (even count: the result is back in dk[0], dv[0])
+    for (int p = 0; p < kDepthPasses; ++p) {
+      PassArgs a;
+      a.keys_in = dk[p & 1]; a.vals_in = dv[p & 1]; a.keys_out = dk[(p + 1) & 1]; a.vals_out = dv[(p + 1) & 1];
+      a.n_total = n_visible; a.cap = VN; a.shift = 8 * p; a.digit_offsets = hist_d + p * kRadix;
+      a.ticket = tickets + 2 + p;
+      a.stall_tile = (p == 0 && (cfg->flags & GS_FLAG_TEST_STALL_LOOKBACK)) ? 0 : -1;
+      a.spin_limit = (cfg->flags & GS_FLAG_TEST_STALL_LOOKBACK) ? kTestSpinLimit : kSpinLimit;
+      a.lookback = reinterpret_cast<uint64_t*>(ws + w.lb_depth) + static_cast<size_t>(p) * (w.n_depth_tiles + 1) * kRadix;
+      sort_pass_kernel<<<sort_grid(w.n_depth_tiles), kSortThreads, sizeof(SortSmem), stream>>>(a, status_dev);
+    }
+  } else {
+    // 1a'/1b'. P partitions of the records, each compacted and depth-sorted
+    //          on its own into its slot of part_stride entries ...
+    const int64_t S = w.part_stride;
+    uint64_t* part_scan = reinterpret_cast<uint64_t*>(ws + w.part_scan);
+    uint32_t* part_hist = u32(w.part_hist);
+    uint32_t* part_tickets = u32(w.part_tickets);
+    int64_t* part_n = reinterpret_cast<int64_t*>(ws + w.part_n);
+    uint64_t* part_lb = reinterpret_cast<uint64_t*>(ws + w.part_lb);
+    for (int p = 0; p < P; ++p) {
+      const int64_t lo = p * S, cnt = VN - lo < S ? VN - lo : S;
+      if (cnt <= 0) continue;  // an empty partition keeps part_n = 0
+      ScanState stp{part_scan + static_cast<size_t>(p) * (w.part_scan_tiles + 1), part_tickets + p * kPartTickets};
+      compact_visible_kernel<<<static_cast<unsigned>((cnt + kScanTile - 1) / kScanTile), kScanThreads, 0, stream>>>(
+          counts + lo, projected + lo * kRecordFloats, cnt, static_cast<uint32_t>(lo), stp, dk[0] + lo, dv[0] + lo,
+          part_hist + p * kDepthPasses * kRadix, part_n + p, status_dev);
+    }
+    hist_scan_kernel<<<1, kRadix, 0, stream>>>(part_hist, kDepthPasses * P);
+    for (int p = 0; p < P; ++p) {
+      const int64_t lo = p * S;
+      if (VN - lo <= 0) continue;
+      uint32_t* const pk[2] = {dk[0] + lo, dk[1] + lo};
+      uint32_t* const pv[2] = {dv[0] + lo, dv[1] + lo};
+      rc = run_u32_sort_passes(pk, pv, part_n + p, S, kDepthPasses, part_hist + p * kDepthPasses * kRadix,
+                               part_tickets + p * kPartTickets + 1,
+                               part_lb + static_cast<size_t>(p) * kDepthPasses * (w.part_sort_tiles + 1) * kRadix,
+                               status_dev, stream);
+      if (rc != GS_OK) return rc;
+    }
+    // ... then merged pairwise, log2(P) levels, into one run at offset 0
+    int src = 0;
+    int levels = 0;
+    while ((1 << levels) < P) ++levels;
+    for (int level = 0; level < levels; ++level) {
+      MergeArgs m;
+      m.keys_in = dk[src]; m.vals_in = dv[src]; m.keys_out = dk[1 - src]; m.vals_out = dv[1 - src];
+      m.part_n = part_n;
+      m.stride = S;
+      m.level = level;
+      m.ctas_per_pair = ((S << (level + 1)) + kMergeTile - 1) / kMergeTile;
+      m.n_total = level == levels - 1 ? n_visible : nullptr;
+      const int64_t grid = static_cast<int64_t>(P >> (level + 1)) * m.ctas_per_pair;
+      merge_runs_kernel<<<static_cast<unsigned>(grid), kMergeThreads, 0, stream>>>(m);
+      src = 1 - src;
+    }
+    order = dv[src];
+  }
   // 1c. tile-count offsets in depth order
   ScanState st2{reinterpret_cast<uint64_t*>(ws + w.scan2), tickets + 1};
   uint32_t* offsets = u32(w.offsets);
@@ -754,4 +941,35 @@ extern "C" int gs_bin_sort(const float* projected, const int16_t* rects, const u
     keys64_kernel<<<static_cast<unsigned>(4 * n_sm), 256, 0, stream>>>(tkeys_final, vals, projected, n_isect_dev,
                                                                         capacity, keys);
   return cuda_status(cudaGetLastError());
+}
+
+}  // namespace
+}  // namespace gs
+
+extern "C" size_t gs_bin_sort_workspace_bytes(int64_t N, int32_t V, int64_t capacity, int64_t n_tiles) {
+  if (N < 0 || V < 1 || capacity < 0 || n_tiles < 1) return 0;
+  return gs::ws_layout(N, V, capacity, n_tiles).total;
+}
+
+extern "C" int gs_bin_sort(const float* projected, const int16_t* rects, const uint32_t* counts, int64_t N,
+                           const int32_t* sizes, int32_t V, const gs_config* cfg, uint64_t* keys, uint32_t* vals,
+                           int64_t capacity, uint32_t* tile_ranges, int64_t* n_isect_dev, void* workspace,
+                           size_t workspace_bytes, int32_t* status_dev, gs_stream_t stream) {
+  return gs::bin_sort_impl(projected, rects, counts, N, sizes, V, cfg, keys, vals, capacity, tile_ranges, n_isect_dev,
+                           workspace, workspace_bytes, status_dev, reinterpret_cast<cudaStream_t>(stream), 1);
+}
+
+extern "C" size_t gs_bin_sort_partitioned_workspace_bytes(int64_t N, int32_t V, int64_t capacity, int64_t n_tiles,
+                                                          int32_t partitions) {
+  if (N < 0 || V < 1 || capacity < 0 || n_tiles < 1 || !gs::valid_partitions(partitions)) return 0;
+  return gs::ws_layout(N, V, capacity, n_tiles, partitions).total;
+}
+
+extern "C" int gs_bin_sort_partitioned(const float* projected, const int16_t* rects, const uint32_t* counts, int64_t N,
+                                       const int32_t* sizes, int32_t V, const gs_config* cfg, uint64_t* keys,
+                                       uint32_t* vals, int64_t capacity, uint32_t* tile_ranges, int64_t* n_isect_dev,
+                                       int32_t partitions, void* workspace, size_t workspace_bytes,
+                                       int32_t* status_dev, gs_stream_t stream) {
+  return gs::bin_sort_impl(projected, rects, counts, N, sizes, V, cfg, keys, vals, capacity, tile_ranges, n_isect_dev,
+                           workspace, workspace_bytes, status_dev, reinterpret_cast<cudaStream_t>(stream), partitions);
 }

@@ -86,8 +86,9 @@ class Frame:
     layout, with a key capacity that grows on demand."""
 
     def __init__(self, N: int, cams: Cameras, cfg: dict, capacity: int | None = None, device="cuda",
-                 keep_keys: bool = False):
+                 keep_keys: bool = False, partitions: int = 1):
         self.N, self.cams, self.cfg = N, cams, dict(cfg)
+        self.partitions = int(partitions)  # > 1: the depth sort runs as merged partitions
         self.device = device
         self.keep_keys = keep_keys  # materialise the 64-bit sort keys (tests and inspection only)
         V = cams.V
@@ -117,7 +118,13 @@ class Frame:
         self.keys = (torch.zeros(max(capacity, 1), dtype=torch.int64, device=self.device) if self.keep_keys
                      else None)
         self.vals = torch.zeros(max(capacity, 1), dtype=torch.int32, device=self.device)
-        ws = gs.gs_bin_sort_workspace_bytes(self.N, self.cams.V, capacity, self.n_tiles)
+        if self.partitions == 1:
+            ws = gs.gs_bin_sort_workspace_bytes(self.N, self.cams.V, capacity, self.n_tiles)
+        else:
+            ws = gs.gs_bin_sort_partitioned_workspace_bytes(self.N, self.cams.V, capacity, self.n_tiles,
+                                                            self.partitions)
+            if ws == 0:
+                raise ValueError("partitions must be a power of two in [1, 64]")
         self.workspace = torch.zeros(ws, dtype=torch.uint8, device=self.device)
 
     def read_status(self) -> int:
@@ -133,8 +140,14 @@ def project(params: FlatParams, cams: Cameras, frame: Frame, stream=None):
 
 
 def bin_sort(frame: Frame, stream=None):
-    gs.gs_bin_sort(frame.projected, frame.rects, frame.counts, frame.N, frame.cams.sizes, frame.cfg, frame.keys,
-                   frame.vals, frame.capacity, frame.tile_ranges, frame.n_isect, frame.workspace, frame.status, stream)
+    if frame.partitions == 1:
+        gs.gs_bin_sort(frame.projected, frame.rects, frame.counts, frame.N, frame.cams.sizes, frame.cfg, frame.keys,
+                       frame.vals, frame.capacity, frame.tile_ranges, frame.n_isect, frame.workspace, frame.status,
+                       stream)
+    else:
+        gs.gs_bin_sort_partitioned(frame.projected, frame.rects, frame.counts, frame.N, frame.cams.sizes, frame.cfg,
+                                   frame.keys, frame.vals, frame.capacity, frame.tile_ranges, frame.n_isect,
+                                   frame.partitions, frame.workspace, frame.status, stream)
 
 
 def rasterize_fwd(frame: Frame, stream=None):

@@ -12,7 +12,7 @@ def to_np(t, dtype=None):
     return a.view(dtype) if dtype is not None else a
 
 
-def run_gpu(scene, dL_dimage=None, capacity=None, tile=None, graph=False):
+def run_gpu(scene, dL_dimage=None, capacity=None, tile=None, graph=False, partitions=1):
     """project -> bin_sort -> rasterize_fwd [-> rasterize_bwd with the given
     upstream gradient] on cuda:0. Returns numpy outputs."""
     import torch
@@ -25,7 +25,7 @@ def run_gpu(scene, dL_dimage=None, capacity=None, tile=None, graph=False):
     N = int(scene["means"].shape[0])
     params = R.FlatParams(N).load_from(scene)
     cams = R.Cameras(scene["cams"], scene["sizes"])
-    frame = R.Frame(N, cams, cfg, capacity=capacity, keep_keys=True)
+    frame = R.Frame(N, cams, cfg, capacity=capacity, keep_keys=True, partitions=partitions)
     R.render(params, cams, frame)
     torch.cuda.synchronize()
     out = {
