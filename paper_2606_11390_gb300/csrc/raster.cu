@@ -157,25 +157,27 @@ struct PixelFwd {
   bool done;
 };
 
-// One compositing step of one pixel (forward rule).
+// One compositing step of one pixel (forward rule), without branches: every
+// lane evaluates the splat and the decisions select what changes, so the
+// compiler can interleave the independent pixels of a thread (a branch only
+// saves issue slots when all 32 lanes agree, which a partly covered block
+// rarely does). Adding w = 0 leaves the colour unchanged bit for bit.
 __device__ __forceinline__ void composite_step(PixelFwd& P, float px, float py, const float4& a, const float4& b,
                                                float cb, uint32_t rel, float cap, float amin, float tstop) {
   float dx, dy, q, cdy;
   const float e = splat_exponent(px, py, a, b.x, dx, dy, q, cdy);
-  if (e > 0.0f) return;
   const float alpha = fminf(cap, __fmul_rn(b.y, ex2_approx(e)));
-  if (alpha < amin) return;
   const float Tn = __fmul_rn(P.T, __fsub_rn(1.0f, alpha));
-  if (Tn < tstop) {
-    P.done = true;
-    return;
-  }
-  const float w = __fmul_rn(alpha, P.T);
+  const bool ok = !P.done && !(e > 0.0f) && !(alpha < amin);
+  const bool stop = ok && Tn < tstop;
+  const bool take = ok && !stop;
+  const float w = take ? __fmul_rn(alpha, P.T) : 0.0f;
   P.c0 = __fmaf_rn(b.z, w, P.c0);
   P.c1 = __fmaf_rn(b.w, w, P.c1);
   P.c2 = __fmaf_rn(cb, w, P.c2);
-  P.T = Tn;
-  P.last = rel + 1;
+  P.T = take ? Tn : P.T;
+  P.last = take ? rel + 1 : P.last;
+  P.done = P.done || stop;
 }
 
 template <int TW, int TH, int PPT>
@@ -236,7 +238,7 @@ __global__ void __launch_bounds__(TW* TH / PPT) raster_fwd_kernel(const float4* 
       all_done = true;
 #pragma unroll
       for (int r = 0; r < PPT; ++r) {
-        if (!P[r].done) composite_step(P[r], px, py0 + static_cast<float>(r * G::RS), a, b, cb, rel, cap, amin, tstop);
+        composite_step(P[r], px, py0 + static_cast<float>(r * G::RS), a, b, cb, rel, cap, amin, tstop);
         all_done = all_done && P[r].done;
       }
     }
@@ -307,36 +309,35 @@ struct PixelBwd {
 //   gv[5..7] = sum alpha T dL/dC, gv[8] = sum dalpha G          (as is)
 __device__ __forceinline__ bool pixel_grad(PixelBwd& P, float px, float py, const float4& a, const float4& b,
                                            float cb, uint32_t rel, float cap, float amin, float gv[9]) {
-  if (rel >= P.last) return false;
+  // branch-free, like the forward step: decisions select, zeros add nothing
   float dx, dy, q, cdy;
   const float e = splat_exponent(px, py, a, b.x, dx, dy, q, cdy);
-  if (e > 0.0f) return false;
   const float G = ex2_approx(e);
   const float oG = __fmul_rn(b.y, G);
   const float alpha = fminf(cap, oG);
-  if (alpha < amin) return false;
+  const bool ok = rel < P.last && !(e > 0.0f) && !(alpha < amin);
   const float inv = rcp_approx(__fsub_rn(1.0f, alpha));
-  P.T *= inv;  // transmittance in front of this entry
-  const float w = alpha * P.T;
+  P.T = ok ? P.T * inv : P.T;  // transmittance in front of this entry
+  const float aok = ok ? alpha : 0.0f;
+  const float w = aok * P.T;
   gv[5] += w * P.g0;
   gv[6] += w * P.g1;
   gv[7] += w * P.g2;
   const float d0 = b.z - P.ar0, d1 = b.w - P.ar1, d2 = cb - P.ar2;
   const float dalpha = P.T * (d0 * P.g0 + d1 * P.g1 + d2 * P.g2) - P.gbg * inv;
-  P.ar0 += alpha * d0;
-  P.ar1 += alpha * d1;
-  P.ar2 += alpha * d2;
-  if (!(oG > cap)) {
-    gv[8] += dalpha * G;
-    const float dpw = dalpha * alpha;
-    gv[0] += dpw * fmaf(a.z, dx, q);
-    gv[1] += dpw * fmaf(a.w, dx, cdy + cdy);
-    const float px_ = dpw * dx;
-    gv[2] += px_ * dx;
-    gv[3] += px_ * dy;
-    gv[4] += (dpw * dy) * dy;
-  }
-  return true;
+  P.ar0 += aok * d0;
+  P.ar1 += aok * d1;
+  P.ar2 += aok * d2;
+  const float da = (ok && !(oG > cap)) ? dalpha : 0.0f;
+  gv[8] += da * G;
+  const float dpw = da * alpha;
+  gv[0] += dpw * fmaf(a.z, dx, q);
+  gv[1] += dpw * fmaf(a.w, dx, cdy + cdy);
+  const float px_ = dpw * dx;
+  gv[2] += px_ * dx;
+  gv[3] += px_ * dy;
+  gv[4] += (dpw * dy) * dy;
+  return ok;
 }
 
 template <int TW, int TH, int PPT>
