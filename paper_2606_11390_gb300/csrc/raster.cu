@@ -53,16 +53,27 @@ __device__ __forceinline__ void load_splat(const float4* __restrict__ projected,
   c = r2.z;
 }
 
-// e = -power*log2(e) for pixel centre (px, py); q = A' dx + B' dy and
-// cdy = C' dy are returned for the backward. Every operation explicitly
-// rounded so forward and backward compute the same bits.
-__device__ __forceinline__ float splat_exponent(float px, float py, const float4& a, float Cp, float& dx, float& dy,
-                                                float& q, float& cdy) {
-  dx = __fsub_rn(px, a.x);
+// e = -power*log2(e) = A' dx^2 + B' dx dy + C' dy^2 for pixel centre
+// (px, py), dx = px - mean.x, dy = py - mean.y. A thread's pixels share a
+// column, so the dx terms are formed once per splat (SplatCol) and each pixel
+// adds dy * (C' dy + B' dx) to A' dx^2: one subtraction and two FMAs. Every
+// operation is explicitly rounded so the forward and the backward compute
+// the same bits.
+struct SplatCol {
+  float dx, adx2, bdx;
+};
+
+__device__ __forceinline__ SplatCol splat_column(float px, const float4& a) {
+  SplatCol c;
+  c.dx = __fsub_rn(px, a.x);
+  c.adx2 = __fmul_rn(__fmul_rn(a.z, c.dx), c.dx);
+  c.bdx = __fmul_rn(a.w, c.dx);
+  return c;
+}
+
+__device__ __forceinline__ float splat_exponent(const SplatCol& c, float py, const float4& a, float Cp, float& dy) {
   dy = __fsub_rn(py, a.y);
-  q = __fmaf_rn(a.z, dx, __fmul_rn(a.w, dy));
-  cdy = __fmul_rn(Cp, dy);
-  return __fmaf_rn(q, dx, __fmul_rn(cdy, dy));
+  return __fmaf_rn(dy, __fmaf_rn(Cp, dy, c.bdx), c.adx2);
 }
 
 // Splats staged per shared-memory batch.
@@ -162,10 +173,11 @@ struct PixelFwd {
 // compiler can interleave the independent pixels of a thread (a branch only
 // saves issue slots when all 32 lanes agree, which a partly covered block
 // rarely does). Adding w = 0 leaves the colour unchanged bit for bit.
-__device__ __forceinline__ void composite_step(PixelFwd& P, float px, float py, const float4& a, const float4& b,
-                                               float cb, uint32_t rel, float cap, float amin, float tstop) {
-  float dx, dy, q, cdy;
-  const float e = splat_exponent(px, py, a, b.x, dx, dy, q, cdy);
+__device__ __forceinline__ void composite_step(PixelFwd& P, const SplatCol& col, float py, const float4& a,
+                                               const float4& b, float cb, uint32_t rel, float cap, float amin,
+                                               float tstop) {
+  float dy;
+  const float e = splat_exponent(col, py, a, b.x, dy);
   const float alpha = fminf(cap, __fmul_rn(b.y, ex2_approx(e)));
   const float Tn = __fmul_rn(P.T, __fsub_rn(1.0f, alpha));
   const bool ok = !P.done && !(e > 0.0f) && !(alpha < amin);
@@ -235,10 +247,11 @@ __global__ void __launch_bounds__(TW* TH / PPT) raster_fwd_kernel(const float4* 
       const float4 b = s_b[j];
       const float cb = s_c[j];
       const uint32_t rel = static_cast<uint32_t>(b0 + j);
+      const SplatCol col = splat_column(px, a);
       all_done = true;
 #pragma unroll
       for (int r = 0; r < PPT; ++r) {
-        composite_step(P[r], px, py0 + static_cast<float>(r * G::RS), a, b, cb, rel, cap, amin, tstop);
+        composite_step(P[r], col, py0 + static_cast<float>(r * G::RS), a, b, cb, rel, cap, amin, tstop);
         all_done = all_done && P[r].done;
       }
     }
@@ -307,11 +320,13 @@ struct PixelBwd {
 //   gv[0..1] = sum dalpha*alpha*(2A'dx + B'dy, B'dx + 2C'dy)  -> dmean = -gv/log2e
 //   gv[2..4] = sum dalpha*alpha*(dx^2, dx dy, dy^2)          -> dconic = -(gv2/2, gv3, gv4/2)
 //   gv[5..7] = sum alpha T dL/dC, gv[8] = sum dalpha G          (as is)
-__device__ __forceinline__ bool pixel_grad(PixelBwd& P, float px, float py, const float4& a, const float4& b,
-                                           float cb, uint32_t rel, float cap, float amin, float gv[9]) {
+__device__ __forceinline__ bool pixel_grad(PixelBwd& P, const SplatCol& col, float py, const float4& a,
+                                           const float4& b, float cb, uint32_t rel, float cap, float amin,
+                                           float gv[9]) {
   // branch-free, like the forward step: decisions select, zeros add nothing
-  float dx, dy, q, cdy;
-  const float e = splat_exponent(px, py, a, b.x, dx, dy, q, cdy);
+  float dy;
+  const float e = splat_exponent(col, py, a, b.x, dy);
+  const float dx = col.dx;
   const float G = ex2_approx(e);
   const float oG = __fmul_rn(b.y, G);
   const float alpha = fminf(cap, oG);
@@ -331,8 +346,8 @@ __device__ __forceinline__ bool pixel_grad(PixelBwd& P, float px, float py, cons
   const float da = (ok && !(oG > cap)) ? dalpha : 0.0f;
   gv[8] += da * G;
   const float dpw = da * alpha;
-  gv[0] += dpw * fmaf(a.z, dx, q);
-  gv[1] += dpw * fmaf(a.w, dx, cdy + cdy);
+  gv[0] += dpw * fmaf(a.w, dy, 2.0f * a.z * dx);     // 2A' dx + B' dy
+  gv[1] += dpw * fmaf(2.0f * b.x, dy, col.bdx);      // B' dx + 2C' dy
   const float px_ = dpw * dx;
   gv[2] += px_ * dx;
   gv[3] += px_ * dy;
@@ -421,9 +436,10 @@ __global__ void GS_RBWD_BOUNDS(TW* TH / PPT) raster_bwd_kernel(
 #pragma unroll
       for (int i = 0; i < 9; ++i) gv[i] = 0.0f;
       bool contrib = false;
+      const SplatCol col = splat_column(px, a);
 #pragma unroll
       for (int r = 0; r < PPT; ++r)
-        contrib |= pixel_grad(P[r], px, py0 + static_cast<float>(r * Gm::RS), a, b, cb, rel, cap, amin, gv);
+        contrib |= pixel_grad(P[r], col, py0 + static_cast<float>(r * Gm::RS), a, b, cb, rel, cap, amin, gv);
       if (__any_sync(0xffffffffu, contrib)) {
         const float red = warp_reduce9(gv, lane);
         if (!(lane & 1) && my_slot >= 0 && red != 0.0f) atomicAdd(&s_grad[j * 9 + my_slot], red);
