@@ -401,14 +401,14 @@ __global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) sort_pass_ke
 #pragma unroll
     for (int bit = 0; bit < 8; ++bit) {
       const uint32_t bal = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
-      peers &= ((d >> bit) & 1u) ? bal : ~bal;
+      peers &= bal ^ (((d >> bit) & 1u) - 1u);  // bal where the bit is set, ~bal where not
     }
-    const int leader = valid ? __ffs(peers) - 1 : 0;
-    uint32_t before = 0;
-    if (valid && lane == leader) before = sm.warp_hist[warp][d];
-    before = __shfl_sync(0xffffffffu, before, leader);
+    // Every lane of a digit group reads the group's running count (a
+    // broadcast) and writes the same new value: no leader, no divergence.
+    const uint32_t before = sm.warp_hist[warp][d];
     rank[i] = before + __popc(peers & lt_mask);
-    if (valid && lane == leader) sm.warp_hist[warp][d] = before + __popc(peers);
+    __syncwarp();
+    if (valid) sm.warp_hist[warp][d] = before + __popc(peers);
     __syncwarp();
   }
   __syncthreads();
