@@ -357,7 +357,7 @@ struct __align__(16) SortSmem {
   uint32_t vals[kSortTile];                // 16 KB
   uint32_t warp_hist[kSortWarps][kRadix];  // 8 KB
   uint32_t local_start[kRadix];
-  int64_t base[kRadix];
+  uint32_t base[kRadix];  // output position of local index 0 of each digit, modulo 2^32
   uint32_t wsum[kSortWarps];
   uint32_t tile;
 };
@@ -382,11 +382,13 @@ __global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) sort_pass_ke
   // 1. load everything first (warp-striped), so the loads overlap
   uint32_t key[kSortItems], val[kSortItems];
   const int warp_base = warp * 32 * kSortItems;
+  const uint32_t* kin = a.keys_in + tile_start + warp_base + lane;
+  const uint32_t* vin = a.vals_in + tile_start + warp_base + lane;
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
-    const int li = warp_base + i * 32 + lane;
-    key[i] = li < n_valid ? a.keys_in[tile_start + li] : 0u;
-    val[i] = li < n_valid ? a.vals_in[tile_start + li] : 0u;
+    const bool ok = warp_base + i * 32 + lane < n_valid;
+    key[i] = ok ? kin[i * 32] : 0u;
+    val[i] = ok ? vin[i * 32] : 0u;
   }
   // 2. stable rank within the warp, item by item: the lanes holding the same
   //    digit are found with one ballot per digit bit (cheaper than match_any)
@@ -458,7 +460,7 @@ __global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) sort_pass_ke
     }
     if (publish) st_relaxed_u64(lb + static_cast<int64_t>(t) * kRadix + d, kFlagIncl | (prefix + total));
   }
-  sm.base[d] = static_cast<int64_t>(a.digit_offsets[d]) + static_cast<int64_t>(prefix) - sm.local_start[d];
+  sm.base[d] = a.digit_offsets[d] + static_cast<uint32_t>(prefix) - sm.local_start[d];
   __syncthreads();
 
   // 4. scatter into shared memory in local sorted order
@@ -475,10 +477,12 @@ __global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) sort_pass_ke
   __syncthreads();
 
   // 5. write out: runs of equal digits land contiguously
+  // (positions are below n < 2^32 - 1, so 32-bit wrapping arithmetic is exact)
+  const uint32_t n32 = static_cast<uint32_t>(n);
   for (int idx = tid; idx < n_valid; idx += kSortThreads) {
     const uint32_t k = sm.keys[idx];
-    const int64_t p = sm.base[(k >> a.shift) & 0xffu] + idx;
-    if (p >= 0 && p < n) {
+    const uint32_t p = sm.base[(k >> a.shift) & 0xffu] + static_cast<uint32_t>(idx);
+    if (p < n32) {
       a.keys_out[p] = k;
       a.vals_out[p] = sm.vals[idx];
     } else {
