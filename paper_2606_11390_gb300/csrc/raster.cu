@@ -320,6 +320,7 @@ struct PixelBwd {
 //   gv[0..1] = sum dalpha*alpha*(2A'dx + B'dy, B'dx + 2C'dy)  -> dmean = -gv/log2e
 //   gv[2..4] = sum dalpha*alpha*(dx^2, dx dy, dy^2)          -> dconic = -(gv2/2, gv3, gv4/2)
 //   gv[5..7] = sum alpha T dL/dC, gv[8] = sum dalpha G          (as is)
+template <bool BG>
 __device__ __forceinline__ bool pixel_grad(PixelBwd& P, const SplatCol& col, float py, const float4& a,
                                            const float4& b, float cb, uint32_t rel, float cap, float amin,
                                            float gv[9]) {
@@ -339,7 +340,9 @@ __device__ __forceinline__ bool pixel_grad(PixelBwd& P, const SplatCol& col, flo
   gv[6] += w * P.g1;
   gv[7] += w * P.g2;
   const float d0 = b.z - P.ar0, d1 = b.w - P.ar1, d2 = cb - P.ar2;
-  const float dalpha = P.T * (d0 * P.g0 + d1 * P.g1 + d2 * P.g2) - P.gbg * inv;
+  // with a zero background (the default) the background term vanishes
+  const float dalpha = BG ? P.T * (d0 * P.g0 + d1 * P.g1 + d2 * P.g2) - P.gbg * inv
+                          : P.T * (d0 * P.g0 + d1 * P.g1 + d2 * P.g2);
   P.ar0 += aok * d0;
   P.ar1 += aok * d1;
   P.ar2 += aok * d2;
@@ -355,7 +358,7 @@ __device__ __forceinline__ bool pixel_grad(PixelBwd& P, const SplatCol& col, flo
   return ok;
 }
 
-template <int TW, int TH, int PPT>
+template <int TW, int TH, int PPT, bool BG>
 __global__ void GS_RBWD_BOUNDS(TW* TH / PPT) raster_bwd_kernel(
     const float4* __restrict__ projected, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
     const Layout L, const Consts K, const float* __restrict__ final_T, const uint32_t* __restrict__ last,
@@ -439,7 +442,7 @@ __global__ void GS_RBWD_BOUNDS(TW* TH / PPT) raster_bwd_kernel(
       const SplatCol col = splat_column(px, a);
 #pragma unroll
       for (int r = 0; r < PPT; ++r)
-        contrib |= pixel_grad(P[r], col, py0 + static_cast<float>(r * Gm::RS), a, b, cb, rel, cap, amin, gv);
+        contrib |= pixel_grad<BG>(P[r], col, py0 + static_cast<float>(r * Gm::RS), a, b, cb, rel, cap, amin, gv);
       if (__any_sync(0xffffffffu, contrib)) {
         const float red = warp_reduce9(gv, lane);
         if (!(lane & 1) && my_slot >= 0 && red != 0.0f) atomicAdd(&s_grad[j * 9 + my_slot], red);
@@ -474,8 +477,13 @@ template <int TW, int TH, int PPT>
 int launch_bwd(const float4* projected, const uint32_t* vals, const uint2* ranges, const Layout& L, const Consts& K,
                const float* final_T, const uint32_t* last, const float* dL_dimage, float* d_proj,
                cudaStream_t stream) {
-  raster_bwd_kernel<TW, TH, PPT><<<static_cast<unsigned>(L.n_tiles), TW * TH / PPT, 0, stream>>>(
-      projected, vals, ranges, L, K, final_T, last, dL_dimage, d_proj);
+  const bool bg = K.bg[0] != 0.0f || K.bg[1] != 0.0f || K.bg[2] != 0.0f;
+  if (bg)
+    raster_bwd_kernel<TW, TH, PPT, true><<<static_cast<unsigned>(L.n_tiles), TW * TH / PPT, 0, stream>>>(
+        projected, vals, ranges, L, K, final_T, last, dL_dimage, d_proj);
+  else
+    raster_bwd_kernel<TW, TH, PPT, false><<<static_cast<unsigned>(L.n_tiles), TW * TH / PPT, 0, stream>>>(
+        projected, vals, ranges, L, K, final_T, last, dL_dimage, d_proj);
   return cuda_status(cudaGetLastError());
 }
 
