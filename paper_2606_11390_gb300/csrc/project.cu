@@ -453,50 +453,39 @@ __global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_ke
   stage_params(sm.p, means, log_scales, quats, opac, sh, g0, n, cams, L.V, use_bulk != 0, status);
   const bool active = tid < n;
   float gm[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, go = 0.f;
-  float shc[3 * NB], gsh[3 * NB];
-  GaussLocal G;
   float4* my_sh4 = &sm.p.sh[12 * tid];
+  // Pass 1: colour -> SH coefficients and view direction, over all views.
+  // The coefficients are read from this thread's staging slot when needed
+  // rather than held in registers, and the slot then takes the SH gradients;
+  // the geometric pass below starts with those registers free.
+  {
+    float gsh[3 * NB];
 #pragma unroll
-  for (int i = 0; i < (3 * NB + 3) / 4; ++i) {
-    const float4 q4 = my_sh4[i];
-    const float q[4] = {q4.x, q4.y, q4.z, q4.w};
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (4 * i + k < 3 * NB) shc[4 * i + k] = q[k];
-  }
-#pragma unroll
-  for (int i = 0; i < 3 * NB; ++i) gsh[i] = 0.0f;
-  if (active) gauss_local(&sm.p.means[3 * tid], &sm.p.log_scales[3 * tid], sm.p.quats[tid], sm.p.opac[tid], G);
-  for (int v = 0; active && v < L.V; ++v) {
-    const int64_t vg = static_cast<int64_t>(v) * N + g0 + tid;
-    if (counts[vg] == 0) continue;
-    const float* dp = d_proj + vg * kDRecordFloats;
-    float g9[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) g9[i] = dp[i];
-    const gs_camera& cam = sm.p.cams[v];
-    ViewProj P;
-    project_view_bwd(G, cam, L.width[v], L.height[v], K, P);
-    const float* vm = cam.viewmat;
-    // opacity
-    go += g9[8] * G.o * (1.0f - G.o);
-    // colour -> SH coefficients and view direction
-    {
+    for (int i = 0; i < 3 * NB; ++i) gsh[i] = 0.0f;
+    const float* shc = reinterpret_cast<const float*>(my_sh4);
+    const float* mean = &sm.p.means[3 * tid];
+    const float o = active ? 1.0f / (1.0f + __expf(-sm.p.opac[tid])) : 0.0f;
+    for (int v = 0; active && v < L.V; ++v) {
+      const int64_t vg = static_cast<int64_t>(v) * N + g0 + tid;
+      if (counts[vg] == 0) continue;
+      const float* dp = d_proj + vg * kDRecordFloats;
+      const float gc0 = dp[5], gc1 = dp[6], gc2 = dp[7];
+      go += dp[8] * o * (1.0f - o);
+      const gs_camera& cam = sm.p.cams[v];
       float dvec[3], dnorm;
-      view_dir(cam, G.mean, dvec, dnorm);
+      view_dir(cam, mean, dvec, dnorm);
       const float inv = 1.0f / dnorm;
       const float d[3] = {dvec[0] * inv, dvec[1] * inv, dvec[2] * inv};
       float Y[16];
       sh_basis<DEG>(d, Y);
-      float graw[3];
+      float acc0 = 0.5f, acc1 = 0.5f, acc2 = 0.5f;
 #pragma unroll
-      for (int ch = 0; ch < 3; ++ch) {
-        float acc = 0.0f;
-#pragma unroll
-        for (int i = 0; i < NB; ++i) acc += Y[i] * shc[3 * i + ch];
-        acc += 0.5f;
-        graw[ch] = acc > 0.0f ? g9[5 + ch] : 0.0f;
+      for (int i = 0; i < NB; ++i) {
+        acc0 += Y[i] * shc[3 * i];
+        acc1 += Y[i] * shc[3 * i + 1];
+        acc2 += Y[i] * shc[3 * i + 2];
       }
+      const float graw[3] = {acc0 > 0.0f ? gc0 : 0.0f, acc1 > 0.0f ? gc1 : 0.0f, acc2 > 0.0f ? gc2 : 0.0f};
       float coef[16];
 #pragma unroll
       for (int i = 0; i < NB; ++i) {
@@ -509,6 +498,30 @@ __global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_ke
       const float dd = d[0] * gdir[0] + d[1] * gdir[1] + d[2] * gdir[2];
       for (int k = 0; k < 3; ++k) gm[k] += (gdir[k] - d[k] * dd) * inv;
     }
+    // SH gradients into the thread's own slot (coefficients past the degree
+    // get 0); stored to global memory, coalesced, at the end
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+      float q[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) q[k] = (4 * i + k < 3 * NB) ? gsh[(4 * i + k < 3 * NB) ? 4 * i + k : 0] : 0.0f;
+      my_sh4[i] = make_float4(q[0], q[1], q[2], q[3]);
+    }
+  }
+  // Pass 2: geometry (2D mean and conic -> mean, scales, rotation), over all views.
+  GaussLocal G;
+  if (active) gauss_local(&sm.p.means[3 * tid], &sm.p.log_scales[3 * tid], sm.p.quats[tid], sm.p.opac[tid], G);
+  for (int v = 0; active && v < L.V; ++v) {
+    const int64_t vg = static_cast<int64_t>(v) * N + g0 + tid;
+    if (counts[vg] == 0) continue;
+    const float* dp = d_proj + vg * kDRecordFloats;
+    float g9[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) g9[i] = dp[i];
+    const gs_camera& cam = sm.p.cams[v];
+    ViewProj P;
+    project_view_bwd(G, cam, L.width[v], L.height[v], K, P);
+    const float* vm = cam.viewmat;
   // conic -> Sigma2 (a, b, c)
     const float idet = 1.0f / P.det;
     const float gA = g9[2], gB = g9[3], gC = g9[4];
@@ -581,15 +594,6 @@ __global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_ke
     for (int k = 0; k < 4; ++k)
       d_quats[4 * g + k] = (gq[k] - G.qn[k] * dotp) / qnorm + (acc ? d_quats[4 * g + k] : 0.0f);
     d_opac[g] = go + (acc ? d_opac[g] : 0.0f);
-  }
-  // SH gradients through the thread's own staging slot (coefficients past
-  // the degree get 0), then coalesced stores
-#pragma unroll
-  for (int i = 0; i < 12; ++i) {
-    float q[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) q[k] = (4 * i + k < 3 * NB) ? gsh[(4 * i + k < 3 * NB) ? 4 * i + k : 0] : 0.0f;
-    my_sh4[i] = make_float4(q[0], q[1], q[2], q[3]);
   }
   __syncthreads();
   float* dst = d_sh + g0 * 48;
