@@ -33,7 +33,7 @@ namespace {
 constexpr int kProjBlock = 128;
 // CTAs per SM the backward is compiled for (register cap 65536 / (128 x this)).
 #ifndef GS_PBWD_MIN_BLOCKS
-#define GS_PBWD_MIN_BLOCKS 3
+#define GS_PBWD_MIN_BLOCKS 4
 #endif
 
 
