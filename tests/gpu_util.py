@@ -12,7 +12,7 @@ def to_np(t, dtype=None):
     return a.view(dtype) if dtype is not None else a
 
 
-def run_gpu(scene, dL_dimage=None, capacity=None, tile=None, graph=False, partitions=1):
+def run_gpu(scene, dL_dimage=None, capacity=None, tile=None, graph=False, partitions=1, keep_keys=True):
     """project -> bin_sort -> rasterize_fwd [-> rasterize_bwd with the given
     upstream gradient] on cuda:0. Returns numpy outputs."""
     import torch
@@ -25,7 +25,7 @@ def run_gpu(scene, dL_dimage=None, capacity=None, tile=None, graph=False, partit
     N = int(scene["means"].shape[0])
     params = R.FlatParams(N).load_from(scene)
     cams = R.Cameras(scene["cams"], scene["sizes"])
-    frame = R.Frame(N, cams, cfg, capacity=capacity, keep_keys=True, partitions=partitions)
+    frame = R.Frame(N, cams, cfg, capacity=capacity, keep_keys=keep_keys, partitions=partitions)
     R.render(params, cams, frame)
     torch.cuda.synchronize()
     out = {
@@ -37,7 +37,7 @@ def run_gpu(scene, dL_dimage=None, capacity=None, tile=None, graph=False, partit
         "capacity": frame.capacity,
     }
     I = out["n_isect"]
-    out["keys"] = to_np(frame.keys, np.uint64)[:I]
+    out["keys"] = to_np(frame.keys, np.uint64)[:I] if keep_keys else None
     out["vals"] = to_np(frame.vals, np.uint32)[:I]
     out["ranges"] = to_np(frame.tile_ranges, np.uint32).reshape(-1, 2)
     out["image"] = to_np(frame.image).reshape(-1, 3)

@@ -45,7 +45,8 @@ def test_densify_stats_match_oracle(oracle):
 
 def test_train_step_gathers_densify_stats():
     """Inside the captured step: after two steps the statistics equal two
-    direct calls on the step's own buffers, and the per-view path agrees."""
+    direct calls on the step's own buffers (up to the rounding of the
+    gradient atomics), and the per-view path agrees."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -65,8 +66,11 @@ def test_train_step_gathers_densify_stats():
     for _ in range(2):
         gs.gs_densify_stats(fr.projected, fr.counts, fr.d_projected, st.N, st.cams.sizes, *ref)
     torch.cuda.synchronize()
-    for got, want in zip((st.grad_accum, st.denom, st.max_radii), ref):
-        np.testing.assert_array_equal(got.cpu().numpy(), want.cpu().numpy())
+    # the two steps' d_projected differ in the order of their FP32 atomics,
+    # so the gradient norms agree to rounding; counts and radii exactly
+    grad_close(st.grad_accum.cpu().numpy(), ref[0].cpu().numpy().astype(np.float64), rel=1e-5, name="grad_accum")
+    np.testing.assert_array_equal(st.denom.cpu().numpy(), ref[1].cpu().numpy())
+    np.testing.assert_array_equal(st.max_radii.cpu().numpy(), ref[2].cpu().numpy())
     vis = (fr.counts.view(torch.int32).cpu().numpy().reshape(3, -1) > 0).sum(axis=0)
     np.testing.assert_array_equal(st.denom.cpu().numpy(), 2 * vis)
     pv = R.TrainStep(s, mode="per_view", graph=False, densify_stats=True).prepare()
