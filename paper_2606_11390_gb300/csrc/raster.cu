@@ -320,6 +320,19 @@ struct PixelBwd {
 //   gv[0..1] = sum dalpha*alpha*(2A'dx + B'dy, B'dx + 2C'dy)  -> dmean = -gv/log2e
 //   gv[2..4] = sum dalpha*alpha*(dx^2, dx dy, dy^2)          -> dconic = -(gv2/2, gv3, gv4/2)
 //   gv[5..7] = sum alpha T dL/dC, gv[8] = sum dalpha G          (as is)
+// From the moments m0 = sum dpw, m1 = sum dpw dy, m2 = sum dpw dy^2 of a
+// thread's pixels (common dx) to
+//   gv[0..1] = sum dpw (2A'dx + B'dy, B'dx + 2C'dy),
+//   gv[2..4] = sum dpw (dx^2, dx dy, dy^2).
+__device__ __forceinline__ void finish_geometry(float gv[9], const SplatCol& col, const float4& a, const float4& b) {
+  const float m0 = gv[0], m1 = gv[1], m2 = gv[2], dx = col.dx;
+  gv[0] = fmaf(2.0f * a.z * dx, m0, a.w * m1);
+  gv[1] = fmaf(col.bdx, m0, 2.0f * b.x * m1);
+  gv[2] = dx * dx * m0;
+  gv[3] = dx * m1;
+  gv[4] = m2;
+}
+
 template <bool BG>
 __device__ __forceinline__ bool pixel_grad(PixelBwd& P, const SplatCol& col, float py, const float4& a,
                                            const float4& b, float cb, uint32_t rel, float cap, float amin,
@@ -348,13 +361,14 @@ __device__ __forceinline__ bool pixel_grad(PixelBwd& P, const SplatCol& col, flo
   P.ar2 += aok * d2;
   const float da = (ok && !(oG > cap)) ? dalpha : 0.0f;
   gv[8] += da * G;
+  // The geometric sums need dpw = dalpha * alpha only through its moments in
+  // dy (the thread's pixels share dx): gv[0..2] collect sum dpw, sum dpw dy,
+  // sum dpw dy^2 here and finish_geometry turns them into the five sums.
   const float dpw = da * alpha;
-  gv[0] += dpw * fmaf(a.w, dy, 2.0f * a.z * dx);     // 2A' dx + B' dy
-  gv[1] += dpw * fmaf(2.0f * b.x, dy, col.bdx);      // B' dx + 2C' dy
-  const float px_ = dpw * dx;
-  gv[2] += px_ * dx;
-  gv[3] += px_ * dy;
-  gv[4] += (dpw * dy) * dy;
+  const float dpy = dpw * dy;
+  gv[0] += dpw;
+  gv[1] += dpy;
+  gv[2] += dpy * dy;
   return ok;
 }
 
@@ -443,6 +457,7 @@ __global__ void GS_RBWD_BOUNDS(TW* TH / PPT) raster_bwd_kernel(
 #pragma unroll
       for (int r = 0; r < PPT; ++r)
         contrib |= pixel_grad<BG>(P[r], col, py0 + static_cast<float>(r * Gm::RS), a, b, cb, rel, cap, amin, gv);
+      finish_geometry(gv, col, a, b);
       if (__any_sync(0xffffffffu, contrib)) {
         const float red = warp_reduce9(gv, lane);
         if (!(lane & 1) && my_slot >= 0 && red != 0.0f) atomicAdd(&s_grad[j * 9 + my_slot], red);
