@@ -8,22 +8,26 @@
 // for the tile's depth-sorted entries, alpha = min(cap, o exp(-power)),
 // skip alpha < alpha_min, stop before T(1 - alpha) < t_stop, C += c alpha T.
 //
-// GB300 design. One CTA per (view, tile); each thread owns two pixels and
-// each warp an 8x8 pixel block. The tile's splats are staged into shared
-// memory in batches of one per thread; while staging, each splat gets a
-// bitmask of the warps whose block meets the ellipse on which its alpha can
-// reach alpha_min (bounding box of that ellipse, widened by a safety margin),
-// so a warp skips splats that cannot touch its pixels. Skipped pairs are pairs
-// the compositing rule would skip anyway, so the result is unchanged. The
-// per-pair arithmetic is written with explicitly rounded operations and a
-// fixed ex2.approx so that the backward recomputes bit-identical alphas and
-// takes exactly the forward's skip / stop decisions. The backward walks the
-// list in reverse, each warp from the largest `last` among its pixels,
-// recovers T_k = T_{k+1} / (1 - alpha_k) from the stored final T, sums a
-// splat's 9 gradient values over the thread's two pixels, reduces them across
-// the warp with a 12-shuffle reduce-scatter (instead of 9 x 5 butterfly
-// shuffles), sums the warps of the CTA in shared memory and issues one FP32
-// atomic per value per (tile, splat) to the per-record gradient buffer.
+// GB300 design. One CTA per (view, tile); each thread owns PPT pixels of one
+// column (4 by default: a warp covers a 16x8 block; 2 for 8x8 tiles or on
+// request: 8x8 blocks). The tile's splats are staged into shared memory 256 at
+// a time; while staging, each splat gets a bitmask of the warps whose block
+// meets the ellipse on which its alpha can reach alpha_min (exact
+// ellipse-rectangle test with a safety margin), so a warp skips splats that
+// cannot touch its pixels. Skipped pairs are pairs the compositing rule would
+// skip anyway, so the result is unchanged. The per-pixel step has no
+// branches: every lane evaluates the splat and the decisions select, so a
+// thread's pixels interleave. The per-pair arithmetic is written with
+// explicitly rounded operations and a fixed ex2.approx so that the backward
+// recomputes bit-identical alphas and takes exactly the forward's skip / stop
+// decisions. The backward walks the list in reverse, each warp from the
+// largest `last` among its pixels, recovers T_k = T_{k+1} / (1 - alpha_k) from
+// the stored final T, sums a splat's 9 gradient values over the thread's
+// pixels (the geometric ones as dy-moments, the pixels sharing dx), reduces
+// them across the warp with a 12-shuffle reduce-scatter (instead of 9 x 5
+// butterfly shuffles), sums the warps of the CTA in shared memory and issues
+// one FP32 atomic per value per (tile, splat) to the per-record gradient
+// buffer.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -164,23 +168,24 @@ __device__ __forceinline__ uint32_t warp_cull_mask(const float4& a, const float4
 
 struct PixelFwd {
   float T, c0, c1, c2;
+  float thr;      // alpha threshold: alpha_min while compositing, +inf once stopped or outside the image
   uint32_t last;
-  bool done;
 };
 
 // One compositing step of one pixel (forward rule), without branches: every
 // lane evaluates the splat and the decisions select what changes, so the
 // compiler can interleave the independent pixels of a thread (a branch only
 // saves issue slots when all 32 lanes agree, which a partly covered block
-// rarely does). Adding w = 0 leaves the colour unchanged bit for bit.
+// rarely does). Adding w = 0 leaves the colour unchanged bit for bit. A pixel
+// that has stopped (or lies outside the image) carries an infinite alpha
+// threshold, so no later splat passes its test.
 __device__ __forceinline__ void composite_step(PixelFwd& P, const SplatCol& col, float py, const float4& a,
-                                               const float4& b, float cb, uint32_t rel, float cap, float amin,
-                                               float tstop) {
+                                               const float4& b, float cb, uint32_t rel, float cap, float tstop) {
   float dy;
   const float e = splat_exponent(col, py, a, b.x, dy);
   const float alpha = fminf(cap, __fmul_rn(b.y, ex2_approx(e)));
   const float Tn = __fmul_rn(P.T, __fsub_rn(1.0f, alpha));
-  const bool ok = !P.done && !(e > 0.0f) && !(alpha < amin);
+  const bool ok = !(e > 0.0f) && !(alpha < P.thr);
   const bool stop = ok && Tn < tstop;
   const bool take = ok && !stop;
   const float w = take ? __fmul_rn(alpha, P.T) : 0.0f;
@@ -189,7 +194,7 @@ __device__ __forceinline__ void composite_step(PixelFwd& P, const SplatCol& col,
   P.c2 = __fmaf_rn(cb, w, P.c2);
   P.T = take ? Tn : P.T;
   P.last = take ? rel + 1 : P.last;
-  P.done = P.done || stop;
+  P.thr = stop ? __int_as_float(0x7f800000) : P.thr;
 }
 
 template <int TW, int TH, int PPT>
@@ -221,12 +226,14 @@ __global__ void __launch_bounds__(TW* TH / PPT) raster_fwd_kernel(const float4* 
   const int n = static_cast<int>(range.y - range.x);
   const float cap = K.alpha_cap, amin = K.alpha_min, tstop = K.t_stop;
   const float tx0 = static_cast<float>(tx * TW), ty0 = static_cast<float>(ty * TH);
+  const float kInf = __int_as_float(0x7f800000);
   PixelFwd P[PPT];
   bool all_done = true;
 #pragma unroll
   for (int r = 0; r < PPT; ++r) {
-    P[r] = PixelFwd{1.0f, 0.0f, 0.0f, 0.0f, 0u, !(x < W && y0 + r * G::RS < H)};
-    all_done = all_done && P[r].done;
+    const bool inside = x < W && y0 + r * G::RS < H;
+    P[r] = PixelFwd{1.0f, 0.0f, 0.0f, 0.0f, inside ? amin : kInf, 0u};
+    all_done = all_done && !inside;
   }
   for (int b0 = 0; b0 < n; b0 += B) {
     if (__syncthreads_count(all_done) == NT) break;
@@ -251,8 +258,8 @@ __global__ void __launch_bounds__(TW* TH / PPT) raster_fwd_kernel(const float4* 
       all_done = true;
 #pragma unroll
       for (int r = 0; r < PPT; ++r) {
-        composite_step(P[r], col, py0 + static_cast<float>(r * G::RS), a, b, cb, rel, cap, amin, tstop);
-        all_done = all_done && P[r].done;
+        composite_step(P[r], col, py0 + static_cast<float>(r * G::RS), a, b, cb, rel, cap, tstop);
+        all_done = all_done && P[r].thr == kInf;
       }
     }
   }
