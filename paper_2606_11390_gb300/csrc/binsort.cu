@@ -229,18 +229,12 @@ __global__ void __launch_bounds__(kEmitThreads) emit_tiles_kernel(
   for (int64_t w = static_cast<int64_t>(blockIdx.x) * (kEmitThreads / 32) + (tid >> 5); w * 32 < n;
        w += warps_total) {
     const int64_t j = w * 32 + lane;
-    uint32_t vg = 0, cnt = 0, off = 0, tb = 0, ntx = 0;
-    int x0 = 0, y0 = 0, wdt = 1;
-    float inv_w = 1.0f;
+    uint32_t vg = 0, cnt = 0, off = 0, tb = 0, xy = 0, wn = 1;
     if (j < n) {
       vg = order[j];
       cnt = counts[vg];
       off = offsets[j];
       const short4 r = rects[vg];
-      x0 = r.x;
-      y0 = r.y;
-      wdt = r.z - r.x;
-      inv_w = rcp_approx(static_cast<float>(wdt));
       // view index v = vg / N by float quotient and exact fix-up (one view: 0)
       int v = 0;
       if (L.V > 1) {
@@ -249,9 +243,12 @@ __global__ void __launch_bounds__(kEmitThreads) emit_tiles_kernel(
         while (static_cast<int64_t>(v + 1) * N <= static_cast<int64_t>(vg)) ++v;
       }
       tb = L.tile_base[v];
-      ntx = static_cast<uint32_t>(L.ntx[v]);
+      // packed record fields: (x0, y0) and (width, tiles per row), 16 bits each
+      xy = static_cast<uint32_t>(static_cast<uint16_t>(r.x)) | (static_cast<uint32_t>(static_cast<uint16_t>(r.y)) << 16);
+      wn = static_cast<uint32_t>(r.z - r.x) | (static_cast<uint32_t>(L.ntx[v]) << 16);
     }
-    // exclusive prefix of the counts within the warp
+    // exclusive prefix of the counts within the warp; the warp's entries are
+    // contiguous in the output from the first record's offset
     uint32_t incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -260,29 +257,31 @@ __global__ void __launch_bounds__(kEmitThreads) emit_tiles_kernel(
     }
     const uint32_t excl = incl - cnt;
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    const uint64_t out_base = __shfl_sync(0xffffffffu, off, 0);
+    const uint32_t le_mask = 0xffffffffu >> (31 - lane);  // bits 0..lane
+    uint32_t started = 0;  // records (lanes) whose entries start before this round
     for (uint32_t base = 0; base < total; base += 32) {
+      // bit i: a record's first entry is entry base + i (records have count >= 1,
+      // so the starts are distinct); the record of entry base + lane is the
+      // last one started at or before it
+      const uint32_t st = (cnt > 0 && excl >= base && excl - base < 32u) ? (1u << (excl - base)) : 0u;
+      const uint32_t starts = __reduce_or_sync(0xffffffffu, st);
+      const int src = static_cast<int>(started + __popc(starts & le_mask)) - 1;
+      started += __popc(starts);
       const uint32_t e = base + lane;
-      // record of entry e: the last lane s with excl[s] <= e
-      int src = 0;
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const uint32_t ex = __shfl_sync(0xffffffffu, excl, src + step);
-        if (ex <= e) src += step;
-      }
       const uint32_t k = e - __shfl_sync(0xffffffffu, excl, src);
       const uint32_t r_vg = __shfl_sync(0xffffffffu, vg, src);
-      const uint32_t r_off = __shfl_sync(0xffffffffu, off, src);
-      const int r_x0 = __shfl_sync(0xffffffffu, x0, src);
-      const int r_y0 = __shfl_sync(0xffffffffu, y0, src);
-      const int r_w = __shfl_sync(0xffffffffu, wdt, src);
-      const float r_inv = __shfl_sync(0xffffffffu, inv_w, src);
-      const uint32_t r_tb = __shfl_sync(0xffffffffu, tb, src);
-      const uint32_t r_ntx = __shfl_sync(0xffffffffu, ntx, src);
-      const uint64_t pos = static_cast<uint64_t>(r_off) + k;
+      const uint32_t r_xy = __shfl_sync(0xffffffffu, xy, src);
+      const uint32_t r_wn = __shfl_sync(0xffffffffu, wn, src);
+      const uint32_t r_tb = L.V > 1 ? __shfl_sync(0xffffffffu, tb, src) : tb;
+      const uint64_t pos = out_base + e;
       if (e < total && pos < capacity) {
+        const int r_w = static_cast<int>(r_wn & 0xffffu);
+        const uint32_t r_ntx = r_wn >> 16;
+        const int r_x0 = static_cast<int16_t>(r_xy & 0xffffu), r_y0 = static_cast<int16_t>(r_xy >> 16);
         // k = row * w + col: quotient from the approximate reciprocal, then an
         // exact fix-up (the estimate is off by at most one)
-        int row = __float2int_rz(static_cast<float>(k) * r_inv);
+        int row = __float2int_rz(static_cast<float>(k) * rcp_approx(static_cast<float>(r_w)));
         int col = static_cast<int>(k) - row * r_w;
         if (col < 0) { --row; col += r_w; }
         if (col >= r_w) { ++row; col -= r_w; }
