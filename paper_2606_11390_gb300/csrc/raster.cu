@@ -439,9 +439,29 @@ __global__ void GS_RBWD_BOUNDS(TW* TH / PPT) raster_bwd_kernel(
 #pragma unroll
   for (int w = 0; w < NW; ++w) max_last = max(max_last, s_wmax[w]);
 
+  // Adds the gradients gathered in slot k (one splat of the batch) to its
+  // record with one atomic per non-zero value, and clears the slot.
+  auto flush_slot = [&](int k) {
+    float* dst = d_proj + static_cast<size_t>(s_vg[k]) * kDRecordFloats;
+    constexpr float kScale[9] = {-1.0f / kLog2e, -1.0f / kLog2e, -0.5f, -1.0f, -0.5f, 1.0f, 1.0f, 1.0f, 1.0f};
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const float gval = s_grad[k * 9 + i];
+      if (gval != 0.0f) {
+        atomicAdd(dst + i, gval * kScale[i]);
+        s_grad[k * 9 + i] = 0.0f;
+      }
+    }
+  };
+  int prev_cnt = 0;
   for (int b_end = static_cast<int>(max_last); b_end > 0; b_end -= B) {
     const int cnt = min(B, b_end);
-    for (int k = tid; k < cnt; k += NT) {
+    // each thread flushes the slots it staged for the previous batch, then
+    // stages the same slots for this one: no other thread touches them in
+    // between, so one barrier covers both
+    for (int k = tid; k < B; k += NT) {
+      if (k < prev_cnt) flush_slot(k);
+      if (k >= cnt) continue;
       const uint32_t vg = vals[range.x + b_end - 1 - k];
       float4 a, b;
       float c;
@@ -476,20 +496,9 @@ __global__ void GS_RBWD_BOUNDS(TW* TH / PPT) raster_bwd_kernel(
       }
     }
     __syncthreads();
-    for (int k = tid; k < cnt; k += NT) {
-      float* dst = d_proj + static_cast<size_t>(s_vg[k]) * kDRecordFloats;
-      constexpr float kScale[9] = {-1.0f / kLog2e, -1.0f / kLog2e, -0.5f, -1.0f, -0.5f, 1.0f, 1.0f, 1.0f, 1.0f};
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        const float gval = s_grad[k * 9 + i];
-        if (gval != 0.0f) {
-          atomicAdd(dst + i, gval * kScale[i]);
-          s_grad[k * 9 + i] = 0.0f;
-        }
-      }
-    }
-    __syncthreads();
+    prev_cnt = cnt;
   }
+  for (int k = tid; k < prev_cnt; k += NT) flush_slot(k);
 }
 
 template <int TW, int TH, int PPT>

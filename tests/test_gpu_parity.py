@@ -160,6 +160,24 @@ def test_many_sort_tiles_and_passes(oracle):
     _check_forward(s, g, o_proj, o_bins, o_ras)
 
 
+@pytest.mark.parametrize("keep_keys", [True, False])
+def test_three_tile_id_passes(oracle, keep_keys):
+    """More than 65536 tiles (two 2048x2048 views in 8x8 tiles: 17 tile-id
+    bits) takes three tile-id digit passes; lists, ranges and counts stay
+    bit-exact."""
+    s = scenes.random_small(112, N=3000, width=2048, height=2048, n_views=2, spread=2.5, tile=8, log_scale_mu=-3.5)
+    o_proj = oracle.project(s, "f32")
+    o_bins = oracle.bin_sort(s, o_proj, "f32")
+    assert oracle.num_tiles(s) > 65536 and o_bins["n_isect"] > 1_000_000
+    g = run_gpu(s, keep_keys=keep_keys)
+    assert g["status"] == 0
+    assert g["n_isect"] == o_bins["n_isect"]
+    if keep_keys:
+        np.testing.assert_array_equal(g["keys"], o_bins["keys"])
+    np.testing.assert_array_equal(g["vals"], o_bins["vals"])
+    np.testing.assert_array_equal(g["ranges"], o_bins["ranges"])
+
+
 def test_image_loss(oracle):
     import torch
 
