@@ -114,6 +114,13 @@ typedef struct gs_config {
  * reports GS_STATUS_TIMEOUT; its outputs are then invalid but every access
  * stays in bounds and the context stays usable. Never set in normal use. */
 #define GS_FLAG_TEST_STALL_LOOKBACK 4
+/* gs_config.flags: tile scheduling order. With this flag `tile_ranges` holds
+ * n_tiles x 3 uint32: the [n_tiles][2] ranges followed by a permutation of
+ * the tile ids, longest list first (by half-octaves of the list length),
+ * which gs_bin_sort writes and the rasteriser follows when it hands tiles to
+ * CTAs: the heavy tiles start first and do not form the tail of the launch.
+ * Results are the same with or without it. */
+#define GS_FLAG_TILE_ORDER 8
 
 /* Number of 32-bit floats in one projected record (see gs_project). */
 #define GS_RECORD_FLOATS 12

@@ -19,6 +19,7 @@ from . import build as _build
 
 GS_OK, GS_ERR_ARG, GS_ERR_CUDA, GS_ERR_UNSUPPORTED, GS_ERR_TOO_LARGE = 0, 1, 2, 3, 4
 GS_STATUS_CAPACITY, GS_STATUS_TIMEOUT, GS_STATUS_BOUNDS = 1, 2, 4
+GS_FLAG_TILE_ORDER = 8
 GS_MAX_VIEWS = 64
 GS_FLAG_ACCUMULATE_GRADS = 1
 GS_FLAG_RASTER_2PX = 2

@@ -493,6 +493,47 @@ __global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) sort_pass_ke
 }
 
 // ---------------------------------------------------------------------------
+// Tile scheduling order: tile ids by decreasing list length, counting-sorted
+// into half-octave buckets (one CTA; order within a bucket is arbitrary).
+// ---------------------------------------------------------------------------
+constexpr int kOrderThreads = 1024;
+constexpr int kOrderBuckets = 64;
+
+__device__ __forceinline__ int order_bucket(uint32_t len) {
+  if (len == 0) return kOrderBuckets - 1;  // empty tiles last
+  const int lg2 = 31 - __clz(len);                            // floor(log2 len)
+  const int half = (len >> (lg2 > 0 ? lg2 - 1 : 0)) & 1;     // upper half of the octave
+  const int b = 2 * lg2 + (lg2 > 0 ? half : 0);              // 0 .. 63, increasing with len
+  return kOrderBuckets - 2 - (b < kOrderBuckets - 2 ? b : kOrderBuckets - 2);
+}
+
+__global__ void __launch_bounds__(kOrderThreads) tile_order_kernel(const uint2* __restrict__ ranges, int64_t n_tiles,
+                                                                   uint32_t* __restrict__ order) {
+  __shared__ uint32_t s_cnt[kOrderBuckets];
+  const int tid = threadIdx.x;
+  if (tid < kOrderBuckets) s_cnt[tid] = 0;
+  __syncthreads();
+  for (int64_t t = tid; t < n_tiles; t += kOrderThreads) {
+    const uint2 r = ranges[t];
+    atomicAdd(&s_cnt[order_bucket(r.y - r.x)], 1u);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t run = 0;
+    for (int b = 0; b < kOrderBuckets; ++b) {
+      const uint32_t c = s_cnt[b];
+      s_cnt[b] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  for (int64_t t = tid; t < n_tiles; t += kOrderThreads) {
+    const uint2 r = ranges[t];
+    order[atomicAdd(&s_cnt[order_bucket(r.y - r.x)], 1u)] = static_cast<uint32_t>(t);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Merge of sorted partitions (the emulated multi-partition depth sort).
 //
 // The paper (§4) sorts a camera's Gaussians across devices by sorting each
@@ -827,7 +868,12 @@ int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* 
   if (e == cudaSuccess) e = cudaMemsetAsync(n_isect_dev, 0, sizeof(int64_t), stream);
   if (e != cudaSuccess) return GS_ERR_CUDA;
   const int64_t VN = N * V;
-  if (VN == 0) return GS_OK;
+  if (VN == 0) {
+    if (cfg->flags & GS_FLAG_TILE_ORDER)
+      tile_order_kernel<<<1, kOrderThreads, 0, stream>>>(reinterpret_cast<const uint2*>(tile_ranges), L.n_tiles,
+                                                         tile_ranges + 2 * L.n_tiles);
+    return cuda_status(cudaGetLastError());
+  }
   int64_t sort_grid_cap = 0;
   rc = gs::sort_grid_cap(&sort_grid_cap);
   if (rc != GS_OK) return rc;
@@ -910,7 +956,12 @@ int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* 
   scan_sorted_counts_kernel<<<scan_grid, kScanThreads, 0, stream>>>(counts, order, n_visible, st2, offsets,
                                                                       static_cast<uint64_t>(capacity), n_isect_dev,
                                                                       status_dev);
-  if (capacity == 0) return cuda_status(cudaGetLastError());
+  if (capacity == 0) {
+    if (cfg->flags & GS_FLAG_TILE_ORDER)
+      tile_order_kernel<<<1, kOrderThreads, 0, stream>>>(reinterpret_cast<const uint2*>(tile_ranges), L.n_tiles,
+                                                         tile_ranges + 2 * L.n_tiles);
+    return cuda_status(cudaGetLastError());
+  }
   // 2a. emission in depth order; the buffers are chosen so that the last tile
   //     pass writes the values into `vals`
   const int TP = w.tile_passes;
@@ -943,6 +994,9 @@ int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* 
   if (keys)
     keys64_kernel<<<static_cast<unsigned>(4 * n_sm), 256, 0, stream>>>(tkeys_final, vals, projected, n_isect_dev,
                                                                         capacity, keys);
+  if (cfg->flags & GS_FLAG_TILE_ORDER)
+    tile_order_kernel<<<1, kOrderThreads, 0, stream>>>(reinterpret_cast<const uint2*>(tile_ranges), L.n_tiles,
+                                                       tile_ranges + 2 * L.n_tiles);
   return cuda_status(cudaGetLastError());
 }
 

@@ -204,7 +204,8 @@ __device__ __forceinline__ void composite_step(PixelFwd& P, const SplatCol& col,
 template <int TW, int TH, int PPT>
 __global__ void __launch_bounds__(TW* TH / PPT) raster_fwd_kernel(const float4* __restrict__ projected,
                                                                    const uint32_t* __restrict__ vals,
-                                                                   const uint2* __restrict__ ranges, const Layout L,
+                                                                   const uint2* __restrict__ ranges,
+                                                                   const uint32_t* __restrict__ order, const Layout L,
                                                                    const Consts K, float* __restrict__ image,
                                                                    float* __restrict__ final_T,
                                                                    uint32_t* __restrict__ last) {
@@ -214,7 +215,9 @@ __global__ void __launch_bounds__(TW* TH / PPT) raster_fwd_kernel(const float4* 
   __shared__ float4 s_b[B];
   __shared__ float s_c[B];
   __shared__ uint32_t s_m[B];
-  const uint32_t tile = blockIdx.x;
+  // CTA i takes tile order[i] (longest lists first) when an order is given
+  const uint32_t tile = order ? order[blockIdx.x] : blockIdx.x;
+  if (tile >= L.n_tiles) return;
   const int v = view_of_tile(L, tile);
   const uint32_t local = tile - L.tile_base[v];
   const int ntx = L.ntx[v];
@@ -386,8 +389,8 @@ __device__ __forceinline__ bool pixel_grad(PixelBwd& P, const SplatCol& col, flo
 template <int TW, int TH, int PPT, bool BG>
 __global__ void GS_RBWD_BOUNDS(TW* TH / PPT) raster_bwd_kernel(
     const float4* __restrict__ projected, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
-    const Layout L, const Consts K, const float* __restrict__ final_T, const uint32_t* __restrict__ last,
-    const float* __restrict__ dL_dimage, float* __restrict__ d_proj) {
+    const uint32_t* __restrict__ order, const Layout L, const Consts K, const float* __restrict__ final_T,
+    const uint32_t* __restrict__ last, const float* __restrict__ dL_dimage, float* __restrict__ d_proj) {
   using Gm = Geo<TW, TH, PPT>;
   constexpr int NT = Gm::NT, NW = Gm::NW;
   constexpr int B = NT > kBatchBwd ? NT : kBatchBwd;
@@ -398,7 +401,9 @@ __global__ void GS_RBWD_BOUNDS(TW* TH / PPT) raster_bwd_kernel(
   __shared__ uint32_t s_vg[B];
   __shared__ float s_grad[B * 9];
   __shared__ uint32_t s_wmax[NW];
-  const uint32_t tile = blockIdx.x;
+  // CTA i takes tile order[i] (longest lists first) when an order is given
+  const uint32_t tile = order ? order[blockIdx.x] : blockIdx.x;
+  if (tile >= L.n_tiles) return;
   const int v = view_of_tile(L, tile);
   const uint32_t local = tile - L.tile_base[v];
   const int ntx = L.ntx[v];
@@ -504,8 +509,9 @@ __global__ void GS_RBWD_BOUNDS(TW* TH / PPT) raster_bwd_kernel(
 template <int TW, int TH, int PPT>
 int launch_fwd(const float4* projected, const uint32_t* vals, const uint2* ranges, const Layout& L, const Consts& K,
                float* image, float* final_T, uint32_t* last, cudaStream_t stream) {
+  const uint32_t* order = (K.flags & GS_FLAG_TILE_ORDER) ? reinterpret_cast<const uint32_t*>(ranges + L.n_tiles) : nullptr;
   raster_fwd_kernel<TW, TH, PPT><<<static_cast<unsigned>(L.n_tiles), TW * TH / PPT, 0, stream>>>(
-      projected, vals, ranges, L, K, image, final_T, last);
+      projected, vals, ranges, order, L, K, image, final_T, last);
   return cuda_status(cudaGetLastError());
 }
 
@@ -514,12 +520,13 @@ int launch_bwd(const float4* projected, const uint32_t* vals, const uint2* range
                const float* final_T, const uint32_t* last, const float* dL_dimage, float* d_proj,
                cudaStream_t stream) {
   const bool bg = K.bg[0] != 0.0f || K.bg[1] != 0.0f || K.bg[2] != 0.0f;
+  const uint32_t* order = (K.flags & GS_FLAG_TILE_ORDER) ? reinterpret_cast<const uint32_t*>(ranges + L.n_tiles) : nullptr;
   if (bg)
     raster_bwd_kernel<TW, TH, PPT, true><<<static_cast<unsigned>(L.n_tiles), TW * TH / PPT, 0, stream>>>(
-        projected, vals, ranges, L, K, final_T, last, dL_dimage, d_proj);
+        projected, vals, ranges, order, L, K, final_T, last, dL_dimage, d_proj);
   else
     raster_bwd_kernel<TW, TH, PPT, false><<<static_cast<unsigned>(L.n_tiles), TW * TH / PPT, 0, stream>>>(
-        projected, vals, ranges, L, K, final_T, last, dL_dimage, d_proj);
+        projected, vals, ranges, order, L, K, final_T, last, dL_dimage, d_proj);
   return cuda_status(cudaGetLastError());
 }
 

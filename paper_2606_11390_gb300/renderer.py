@@ -86,8 +86,10 @@ class Frame:
     layout, with a key capacity that grows on demand."""
 
     def __init__(self, N: int, cams: Cameras, cfg: dict, capacity: int | None = None, device="cuda",
-                 keep_keys: bool = False, partitions: int = 1):
+                 keep_keys: bool = False, partitions: int = 1, tile_order: bool = True):
         self.N, self.cams, self.cfg = N, cams, dict(cfg)
+        if tile_order:  # rasterise the longest tile lists first (same results)
+            self.cfg["flags"] = int(self.cfg.get("flags", 0)) | gs.GS_FLAG_TILE_ORDER
         self.partitions = int(partitions)  # > 1: the depth sort runs as merged partitions
         self.device = device
         self.keep_keys = keep_keys  # materialise the 64-bit sort keys (tests and inspection only)
@@ -98,7 +100,9 @@ class Frame:
         self.projected = torch.zeros(V * N * gs.RECORD_FLOATS, **f32)
         self.rects = torch.zeros(V * N * 4, dtype=torch.int16, device=device)
         self.counts = torch.zeros(V * N, **i32)
-        self.tile_ranges = torch.zeros(self.n_tiles * 2, **i32)
+        order = bool(self.cfg.get("flags", 0) & gs.GS_FLAG_TILE_ORDER)
+        self.tile_ranges = torch.zeros(self.n_tiles * (3 if order else 2), **i32)
+        self.ranges = self.tile_ranges[:2 * self.n_tiles]  # [n_tiles][2] start, end
         self.n_isect = torch.zeros(1, dtype=torch.int64, device=device)
         self.status = torch.zeros(1, **i32)
         self.image = torch.zeros(self.n_pixels * 3, **f32)

@@ -39,7 +39,7 @@ def run_gpu(scene, dL_dimage=None, capacity=None, tile=None, graph=False, partit
     I = out["n_isect"]
     out["keys"] = to_np(frame.keys, np.uint64)[:I] if keep_keys else None
     out["vals"] = to_np(frame.vals, np.uint32)[:I]
-    out["ranges"] = to_np(frame.tile_ranges, np.uint32).reshape(-1, 2)
+    out["ranges"] = to_np(frame.ranges, np.uint32).reshape(-1, 2)
     out["image"] = to_np(frame.image).reshape(-1, 3)
     out["final_T"] = to_np(frame.final_T)
     out["last"] = to_np(frame.last, np.uint32)

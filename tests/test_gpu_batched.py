@@ -53,11 +53,11 @@ def test_batched_graph_equals_per_view(R, tile):
     # record indices by v*N
     N = s["means"].shape[0]
     fb = b.frames[0]
-    rb = fb.tile_ranges.cpu().numpy().view(np.uint32).reshape(-1, 2)
+    rb = fb.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2)
     vb = fb.vals.cpu().numpy().view(np.uint32)
     base = 0
     for v, fr in enumerate(p.frames):
-        rp = fr.tile_ranges.cpu().numpy().view(np.uint32).reshape(-1, 2)
+        rp = fr.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2)
         vp = fr.vals.cpu().numpy().view(np.uint32)
         for t in range(rp.shape[0]):
             lb = vb[rb[base + t, 0]:rb[base + t, 1]]

@@ -51,7 +51,7 @@ def test_full_size_4k_sampled(oracle):
     g_counts = to_np(fr.counts, np.uint32)
     g_rects = to_np(fr.rects).reshape(-1, 4)
     g_proj = to_np(fr.projected).reshape(-1, 12)
-    g_ranges = to_np(fr.tile_ranges, np.uint32).reshape(-1, 2)
+    g_ranges = to_np(fr.ranges, np.uint32).reshape(-1, 2)
     g_vals = to_np(fr.vals, np.uint32)
     g_img = to_np(st.image).reshape(-1, 3)
 

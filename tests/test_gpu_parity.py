@@ -12,7 +12,7 @@ import pytest
 
 from paper_2606_11390_gb300 import scenes
 
-from gpu_util import grad_close, run_gpu
+from gpu_util import grad_close, run_gpu, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -218,3 +218,33 @@ def test_adam(oracle):
         _native.gs_adam_step(tp, torch.from_numpy(gr).cuda(), tm, tv, 1e-3, 0.9, 0.999, 1e-15, step)
     torch.cuda.synchronize()
     np.testing.assert_allclose(tp.cpu().numpy(), p, rtol=0, atol=2e-6)
+
+
+def test_tile_order_is_longest_first_permutation(oracle):
+    """With the tile-order flag gs_bin_sort appends a permutation of the tile
+    ids whose list lengths never increase by more than a half-octave bucket,
+    and the images equal those rendered in the natural tile order."""
+    s = scenes.random_small(113, N=4000, width=300, height=200, n_views=2, spread=1.5)
+    a = run_gpu(s)  # Frame default: tile order on
+    from paper_2606_11390_gb300 import renderer as R
+    import torch
+
+    N = s["means"].shape[0]
+    params = R.FlatParams(N).load_from(s)
+    cams = R.Cameras(s["cams"], s["sizes"])
+    fr = R.Frame(N, cams, s["cfg"], keep_keys=False, tile_order=False)
+    R.render(params, cams, fr)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(to_np(fr.image).reshape(-1, 3), a["image"])
+    np.testing.assert_array_equal(to_np(fr.ranges, np.uint32).reshape(-1, 2), a["ranges"])
+    fo = R.Frame(N, cams, s["cfg"], keep_keys=False, tile_order=True)
+    R.render(params, cams, fo)
+    torch.cuda.synchronize()
+    nt = fo.n_tiles
+    order = to_np(fo.tile_ranges, np.uint32)[2 * nt:3 * nt]
+    assert sorted(order.tolist()) == list(range(nt))
+    lens = (a["ranges"][:, 1].astype(np.int64) - a["ranges"][:, 0])[order]
+    nz = lens[lens > 0]
+    # non-increasing up to the bucket width (a factor of 2 at most between neighbours out of order)
+    assert np.all(nz[1:] <= 2 * nz[:-1])
+    assert np.all(lens[len(nz):] == 0)

@@ -82,7 +82,7 @@ def test_partitioned_sort_full_size(oracle):
         torch.cuda.synchronize()
         assert fr.read_status() == 0
         assert int(fr.n_isect.item()) == I
-        out[P] = (to_np(fr.vals, np.uint32)[:I].copy(), to_np(fr.tile_ranges, np.uint32).reshape(-1, 2).copy())
+        out[P] = (to_np(fr.vals, np.uint32)[:I].copy(), to_np(fr.ranges, np.uint32).reshape(-1, 2).copy())
         del fr
         torch.cuda.empty_cache()
     vals, ranges = out[8]

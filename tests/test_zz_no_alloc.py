@@ -35,11 +35,11 @@ def _sorted_both_ways(rt, scene):
     R.render(params, cams, frame)  # gs_project + gs_bin_sort (workspace) with capacity sizing
     torch.cuda.synchronize()
     n = int(frame.n_isect.item())
-    ref = (frame.keys[:n].clone(), frame.vals[:n].clone(), frame.tile_ranges.clone(), n)
+    ref = (frame.keys[:n].clone(), frame.vals[:n].clone(), frame.ranges.clone(), n)
     # the allocation-free variant, into outputs pre-filled with junk
     keys = torch.full_like(frame.keys, -7)
     vals = torch.full_like(frame.vals, -7)
-    ranges = torch.full_like(frame.tile_ranges, -7)
+    ranges = torch.full_like(frame.ranges, -7)
     n_isect = torch.full_like(frame.n_isect, -7)
     status = torch.zeros_like(frame.status)
     gs.gs_bin_sort_static(frame.projected, frame.rects, frame.counts, N, cams.sizes, scene["cfg"], keys, vals,
