@@ -430,3 +430,66 @@ class TrainStep:
 
     def n_isect(self) -> int:
         return int(sum(int(fr.n_isect.item()) for fr in self.frames))
+
+
+class HostFedStep:
+    """Training steps fed from host memory: every step copies its parameters,
+    cameras and target in from (pinned) host buffers and its gradients and
+    loss back out. The copies run on two copy streams, double-buffered in
+    device staging buffers, so the inputs of step k+1 and the outputs of
+    step k move while step k computes; the link carries both directions at
+    once. Stream order keeps every hazard: a staging buffer is refilled only
+    after the step that used it has consumed it, and read out only after the
+    step that fills it is done.
+
+    run(...) enqueues one step and returns at once; the host buffers passed to
+    a step must stay untouched until sync() (or until two later steps have
+    been enqueued and synced)."""
+
+    def __init__(self, step: TrainStep):
+        self.step = step
+        dev = step.params.flat.device
+        self.in_params = [torch.empty_like(step.params.flat) for _ in range(2)]
+        self.in_target = [torch.empty_like(step.target) for _ in range(2)]
+        self.in_cams = [torch.empty_like(step.cams.dev) for _ in range(2)]
+        self.out_grads = [torch.empty_like(step.grads.flat) for _ in range(2)]
+        self.out_loss = [torch.empty_like(step.loss) for _ in range(2)]
+        self.h2d = torch.cuda.Stream(device=dev)
+        self.d2h = torch.cuda.Stream(device=dev)
+        ev = lambda: [torch.cuda.Event() for _ in range(2)]  # noqa: E731
+        self.in_ready, self.in_free, self.out_ready, self.out_free = ev(), ev(), ev(), ev()
+        self.k = 0
+
+    def run(self, host_params, host_target, host_cams, host_grads, host_loss):
+        st, b = self.step, self.k & 1
+        comp = torch.cuda.current_stream()
+        if self.k >= 2:
+            self.h2d.wait_event(self.in_free[b])
+        with torch.cuda.stream(self.h2d):
+            self.in_params[b].copy_(host_params, non_blocking=True)
+            self.in_target[b].copy_(host_target, non_blocking=True)
+            self.in_cams[b].copy_(host_cams, non_blocking=True)
+            self.in_ready[b].record(self.h2d)
+        comp.wait_event(self.in_ready[b])
+        st.params.flat.copy_(self.in_params[b])
+        st.target.copy_(self.in_target[b])
+        st.cams.dev.copy_(self.in_cams[b])
+        self.in_free[b].record(comp)
+        st.run()
+        if self.k >= 2:
+            comp.wait_event(self.out_free[b])
+        self.out_grads[b].copy_(st.grads.flat)
+        self.out_loss[b].copy_(st.loss)
+        self.out_ready[b].record(comp)
+        self.d2h.wait_event(self.out_ready[b])
+        with torch.cuda.stream(self.d2h):
+            host_grads.copy_(self.out_grads[b], non_blocking=True)
+            host_loss.copy_(self.out_loss[b], non_blocking=True)
+            self.out_free[b].record(self.d2h)
+        self.k += 1
+
+    def sync(self):
+        """Waits for every enqueued step, its copies included."""
+        torch.cuda.current_stream().synchronize()
+        self.h2d.synchronize()
+        self.d2h.synchronize()

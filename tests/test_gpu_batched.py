@@ -91,3 +91,36 @@ def test_adam_step_in_graph_moves_parameters(R, oracle):
     g = st.grads.flat.cpu().numpy().astype(np.float64)
     want, _, _ = oracle.adam(p0.cpu().numpy(), g, m0.cpu().numpy(), v0.cpu().numpy(), 1e-3, 0.9, 0.999, 1e-15, t0 + 1)
     np.testing.assert_allclose(st.params.flat.cpu().numpy(), want, rtol=0, atol=5e-6)
+
+
+def test_host_fed_steps_match_direct_steps(R):
+    """HostFedStep (inputs copied in and gradients out every step, overlapped
+    across neighbouring steps) returns, for alternating parameter sets, the
+    gradients and loss of the same steps run directly on the device."""
+    import torch
+
+    s = _scene()
+    st = R.TrainStep(s, mode="batched").prepare()
+    pa = st.params.flat.clone()
+    pb = pa.clone()
+    pb[: st.N * 3] += 0.01  # shifted means
+    want = []
+    for p in (pa, pb):
+        st.params.flat.copy_(p)
+        st.run()
+        torch.cuda.synchronize()
+        want.append((st.grads.flat.cpu().numpy().astype(np.float64), float(st.loss.item())))
+    host_p = [p.cpu().pin_memory() for p in (pa, pb)]
+    host_t = st.target.cpu().pin_memory()
+    host_c = torch.from_numpy(st.cams.host.copy()).pin_memory()
+    host_g = [torch.empty_like(pa, device="cpu").pin_memory() for _ in range(4)]
+    host_l = [torch.empty(1, dtype=torch.float64).pin_memory() for _ in range(4)]
+    fed = R.HostFedStep(st)
+    for k in range(4):
+        fed.run(host_p[k & 1], host_t, host_c, host_g[k], host_l[k])
+    fed.sync()
+    st.check()
+    for k in range(4):
+        g, L = want[k & 1]
+        grad_close(host_g[k].numpy(), g, rel=1e-4, name=f"step {k} grads")
+        assert abs(host_l[k].item() - L) <= 1e-9 * abs(L)
