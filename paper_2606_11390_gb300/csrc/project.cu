@@ -317,9 +317,18 @@ struct __align__(16) ParamSmem {
 
 // Loads the CTA's slice [g0, g0+n) of all parameter arrays and the cameras.
 // Full, aligned slices go through TMA bulk copies; others through plain loads.
+// Optional extra bulk copies that join the parameter staging transaction.
+struct ExtraCopies {
+  int n = 0;
+  void* dst[2];
+  const void* src[2];
+  uint32_t bytes[2];
+};
+
 __device__ __forceinline__ void stage_params(ParamSmem& sm, const float* means, const float* log_scales,
                                              const float* quats, const float* opac, const float* sh, int64_t g0, int n,
-                                             const gs_camera* cams, int V, bool use_bulk, int32_t* status) {
+                                             const gs_camera* cams, int V, bool use_bulk, int32_t* status,
+                                             const ExtraCopies& extra = ExtraCopies()) {
   const int tid = threadIdx.x;
   {
     const float* src = reinterpret_cast<const float*>(cams);
@@ -336,7 +345,10 @@ __device__ __forceinline__ void stage_params(ParamSmem& sm, const float* means, 
     if (tid == 0) {
       const uint32_t b_means = kProjBlock * 12, b_quat = kProjBlock * 16, b_op = kProjBlock * 4,
                      b_sh = kProjBlock * 192;
-      mbar_arrive_expect_tx(&sm.bar, 2 * b_means + b_quat + b_op + b_sh);
+      uint32_t b_extra = 0;
+      for (int i = 0; i < extra.n; ++i) b_extra += extra.bytes[i];
+      mbar_arrive_expect_tx(&sm.bar, 2 * b_means + b_quat + b_op + b_sh + b_extra);
+      for (int i = 0; i < extra.n; ++i) bulk_g2s(extra.dst[i], extra.src[i], extra.bytes[i], &sm.bar);
       bulk_g2s(sm.means, means + g0 * 3, b_means, &sm.bar);
       bulk_g2s(sm.log_scales, log_scales + g0 * 3, b_means, &sm.bar);
       bulk_g2s(sm.quats, quats + g0 * 4, b_quat, &sm.bar);
@@ -450,7 +462,21 @@ __global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_ke
   const int tid = threadIdx.x;
   const int64_t g0 = static_cast<int64_t>(blockIdx.x) * kProjBlock;
   const int n = static_cast<int>(N - g0 < kProjBlock ? N - g0 : kProjBlock);
-  stage_params(sm.p, means, log_scales, quats, opac, sh, g0, n, cams, L.V, use_bulk != 0, status);
+  // one view: the CTA's gradient records and tile counts join the staging
+  __shared__ __align__(16) float s_dp[kProjBlock * kDRecordFloats];
+  __shared__ __align__(16) uint32_t s_cnt[kProjBlock];
+  const bool staged = use_bulk == 2 && L.V == 1 && n == kProjBlock;
+  ExtraCopies ex;
+  if (staged) {
+    ex.n = 2;
+    ex.dst[0] = s_dp;
+    ex.src[0] = d_proj + g0 * kDRecordFloats;
+    ex.bytes[0] = kProjBlock * kDRecordFloats * 4;
+    ex.dst[1] = s_cnt;
+    ex.src[1] = counts + g0;
+    ex.bytes[1] = kProjBlock * 4;
+  }
+  stage_params(sm.p, means, log_scales, quats, opac, sh, g0, n, cams, L.V, use_bulk != 0, status, ex);
   const bool active = tid < n;
   float gm[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, go = 0.f;
   float4* my_sh4 = &sm.p.sh[12 * tid];
@@ -467,8 +493,8 @@ __global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_ke
     const float o = active ? 1.0f / (1.0f + __expf(-sm.p.opac[tid])) : 0.0f;
     for (int v = 0; active && v < L.V; ++v) {
       const int64_t vg = static_cast<int64_t>(v) * N + g0 + tid;
-      if (counts[vg] == 0) continue;
-      const float* dp = d_proj + vg * kDRecordFloats;
+      if ((staged ? s_cnt[tid] : counts[vg]) == 0) continue;
+      const float* dp = staged ? &s_dp[kDRecordFloats * tid] : d_proj + vg * kDRecordFloats;
       const float gc0 = dp[5], gc1 = dp[6], gc2 = dp[7];
       go += dp[8] * o * (1.0f - o);
       const gs_camera& cam = sm.p.cams[v];
@@ -513,8 +539,8 @@ __global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_ke
   if (active) gauss_local(&sm.p.means[3 * tid], &sm.p.log_scales[3 * tid], sm.p.quats[tid], sm.p.opac[tid], G);
   for (int v = 0; active && v < L.V; ++v) {
     const int64_t vg = static_cast<int64_t>(v) * N + g0 + tid;
-    if (counts[vg] == 0) continue;
-    const float* dp = d_proj + vg * kDRecordFloats;
+    if ((staged ? s_cnt[tid] : counts[vg]) == 0) continue;
+    const float* dp = staged ? &s_dp[kDRecordFloats * tid] : d_proj + vg * kDRecordFloats;
     float g9[5];
 #pragma unroll
     for (int i = 0; i < 5; ++i) g9[i] = dp[i];
@@ -610,11 +636,13 @@ int launch_project_bwd(const float* means, const float* log_scales, const float*
   if (N == 0) return GS_OK;
   const bool bulk = aligned16(means) && aligned16(log_scales) && aligned16(quats) && aligned16(opacity_logits) &&
                     aligned16(sh);
+  // 2: the gradient records and counts can join the bulk staging too
+  const int bulk_mode = !bulk ? 0 : (aligned16(d_projected) && aligned16(counts) ? 2 : 1);
   const unsigned blocks = static_cast<unsigned>((N + kProjBlock - 1) / kProjBlock);
 #define GS_PBWD(D)                                                                                              \
   project_bwd_kernel<D><<<blocks, kProjBlock, 0, stream>>>(means, log_scales, quats, opacity_logits, sh, N, cams, L, \
                                                            K, counts, d_projected, d_means, d_log_scales, d_quats,      \
-                                                           d_opacity_logits, d_sh, bulk ? 1 : 0, status)
+                                                           d_opacity_logits, d_sh, bulk_mode, status)
   switch (K.sh_degree) {
     case 0: GS_PBWD(0); break;
     case 1: GS_PBWD(1); break;
