@@ -401,6 +401,7 @@ __global__ void GS_RBWD_BOUNDS(TW* TH / PPT) raster_bwd_kernel(
   __shared__ uint32_t s_vg[B];
   __shared__ float s_grad[B * 9];
   __shared__ uint32_t s_wmax[NW];
+  __shared__ uint16_t s_list[NW][B];  // per warp: the staged splats that can touch its block
   // CTA i takes tile order[i] (longest lists first) when an order is given
   const uint32_t tile = order ? order[blockIdx.x] : blockIdx.x;
   if (tile >= L.n_tiles) return;
@@ -478,10 +479,60 @@ __global__ void GS_RBWD_BOUNDS(TW* TH / PPT) raster_bwd_kernel(
       s_m[k] = warp_cull_mask<Gm>(a, b, tx0, ty0, amin);
     }
     __syncthreads();
-    // entries j hold relative position b_end-1-j; this warp needs rel < wmax
+    // entries j hold relative position b_end-1-j; this warp needs rel < wmax.
+    // The warp first lists the staged splats that can touch its block, then
+    // takes them in pairs: the second splat's pixel work is issued before the
+    // first one's warp reduction, so the reduction's shuffle latency overlaps
+    // independent arithmetic (the pixel state still advances splat by splat).
     const int j0 = max(0, b_end - static_cast<int>(wmax));
-    for (int j = j0; j < cnt; ++j) {
-      if (!(s_m[j] & wbit)) continue;
+    int nl = 0;
+    for (int jb = j0; jb < cnt; jb += 32) {
+      const int j = jb + lane;
+      const bool keep = j < cnt && (s_m[j] & wbit);
+      const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+      if (keep) s_list[warp][nl + __popc(bal & ((1u << lane) - 1u))] = static_cast<uint16_t>(j);
+      nl += __popc(bal);
+    }
+    __syncwarp();
+    int q = 0;
+    for (; q + 1 < nl; q += 2) {
+      const int jA = s_list[warp][q], jB = s_list[warp][q + 1];
+      float gA[9], gB[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) gA[i] = gB[i] = 0.0f;
+      bool cA = false, cB = false;
+      {
+        const float4 a = s_a[jA];
+        const float4 b = s_b[jA];
+        const float cb = s_c[jA];
+        const uint32_t rel = static_cast<uint32_t>(b_end - 1 - jA);
+        const SplatCol col = splat_column(px, a);
+#pragma unroll
+        for (int r = 0; r < PPT; ++r)
+          cA |= pixel_grad<BG>(P[r], col, py0 + static_cast<float>(r * Gm::RS), a, b, cb, rel, cap, amin, gA);
+        finish_geometry(gA, col, a, b);
+      }
+      {
+        const float4 a = s_a[jB];
+        const float4 b = s_b[jB];
+        const float cb = s_c[jB];
+        const uint32_t rel = static_cast<uint32_t>(b_end - 1 - jB);
+        const SplatCol col = splat_column(px, a);
+#pragma unroll
+        for (int r = 0; r < PPT; ++r)
+          cB |= pixel_grad<BG>(P[r], col, py0 + static_cast<float>(r * Gm::RS), a, b, cb, rel, cap, amin, gB);
+        finish_geometry(gB, col, a, b);
+      }
+      const bool anyA = __any_sync(0xffffffffu, cA), anyB = __any_sync(0xffffffffu, cB);
+      const float redA = anyA ? warp_reduce9(gA, lane) : 0.0f;
+      const float redB = anyB ? warp_reduce9(gB, lane) : 0.0f;
+      if (!(lane & 1) && my_slot >= 0) {
+        if (redA != 0.0f) atomicAdd(&s_grad[jA * 9 + my_slot], redA);
+        if (redB != 0.0f) atomicAdd(&s_grad[jB * 9 + my_slot], redB);
+      }
+    }
+    if (q < nl) {
+      const int j = s_list[warp][q];
       const float4 a = s_a[j];
       const float4 b = s_b[j];
       const float cb = s_c[j];
