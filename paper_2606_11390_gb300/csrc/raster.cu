@@ -215,6 +215,7 @@ __global__ void __launch_bounds__(TW* TH / PPT) raster_fwd_kernel(const float4* 
   __shared__ float4 s_b[B];
   __shared__ float s_c[B];
   __shared__ uint32_t s_m[B];
+  __shared__ uint16_t s_list[G::NW][B];  // per warp: the staged splats that can touch its block
   // CTA i takes tile order[i] (longest lists first) when an order is given
   const uint32_t tile = order ? order[blockIdx.x] : blockIdx.x;
   if (tile >= L.n_tiles) return;
@@ -222,8 +223,8 @@ __global__ void __launch_bounds__(TW* TH / PPT) raster_fwd_kernel(const float4* 
   const uint32_t local = tile - L.tile_base[v];
   const int ntx = L.ntx[v];
   const int tx = static_cast<int>(local % ntx), ty = static_cast<int>(local / ntx);
-  const int tid = threadIdx.x;
-  const uint32_t wbit = 1u << (tid >> 5);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t wbit = 1u << warp;
   int lx, ly;
   G::pixel_of(tid, lx, ly);
   const int W = L.width[v], H = L.height[v];
@@ -255,8 +256,18 @@ __global__ void __launch_bounds__(TW* TH / PPT) raster_fwd_kernel(const float4* 
     }
     __syncthreads();
     const int cnt = min(B, n - b0);
-    for (int j = 0; j < cnt && !all_done; ++j) {
-      if (!(s_m[j] & wbit)) continue;
+    // the warp's list of staged splats that can touch its block
+    int nl = 0;
+    for (int jb = 0; jb < cnt; jb += 32) {
+      const int j = jb + lane;
+      const bool keep = j < cnt && (s_m[j] & wbit);
+      const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+      if (keep) s_list[warp][nl + __popc(bal & ((1u << lane) - 1u))] = static_cast<uint16_t>(j);
+      nl += __popc(bal);
+    }
+    __syncwarp();
+    for (int q = 0; q < nl && !all_done; ++q) {
+      const int j = s_list[warp][q];
       const float4 a = s_a[j];
       const float4 b = s_b[j];
       const float cb = s_c[j];
