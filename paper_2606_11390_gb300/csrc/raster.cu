@@ -183,11 +183,18 @@ struct PixelFwd {
 // rarely does). Adding w = 0 leaves the colour unchanged bit for bit. A pixel
 // that has stopped (or lies outside the image) carries an infinite alpha
 // threshold, so no later splat passes its test.
-__device__ __forceinline__ void composite_step(PixelFwd& P, const SplatCol& col, float py, const float4& a,
-                                               const float4& b, float cb, uint32_t rel, float cap, float tstop) {
+// The splat's exponent and alpha at one pixel (independent of the pixel state).
+__device__ __forceinline__ void splat_alpha(const SplatCol& col, float py, const float4& a, const float4& b, float cap,
+                                            float& e, float& alpha) {
   float dy;
-  const float e = splat_exponent(col, py, a, b.x, dy);
-  const float alpha = fminf(cap, __fmul_rn(b.y, ex2_approx(e)));
+  e = splat_exponent(col, py, a, b.x, dy);
+  alpha = fminf(cap, __fmul_rn(b.y, ex2_approx(e)));
+}
+
+// The compositing decisions and update of one pixel for a splat with
+// exponent e and alpha.
+__device__ __forceinline__ void composite_apply(PixelFwd& P, float e, float alpha, const float4& b, float cb,
+                                                uint32_t rel, float tstop) {
   const float Tn = __fmul_rn(P.T, __fsub_rn(1.0f, alpha));
   const bool ok = !(e > 0.0f) && !(alpha < P.thr);
   const bool stop = ok && Tn < tstop;
@@ -199,6 +206,13 @@ __device__ __forceinline__ void composite_step(PixelFwd& P, const SplatCol& col,
   P.T = take ? Tn : P.T;
   P.last = take ? rel + 1 : P.last;
   P.thr = stop ? __int_as_float(0x7f800000) : P.thr;
+}
+
+__device__ __forceinline__ void composite_step(PixelFwd& P, const SplatCol& col, float py, const float4& a,
+                                               const float4& b, float cb, uint32_t rel, float cap, float tstop) {
+  float e, alpha;
+  splat_alpha(col, py, a, b, cap, e, alpha);
+  composite_apply(P, e, alpha, b, cb, rel, tstop);
 }
 
 template <int TW, int TH, int PPT>
@@ -266,7 +280,31 @@ __global__ void __launch_bounds__(TW* TH / PPT) raster_fwd_kernel(const float4* 
       nl += __popc(bal);
     }
     __syncwarp();
-    for (int q = 0; q < nl && !all_done; ++q) {
+    int q = 0;
+    // two splats per iteration: both exponents / alphas are independent of
+    // the pixel state and are issued first; the compositing then applies
+    // them in list order
+    for (; q + 1 < nl && !all_done; q += 2) {
+      const int jA = s_list[warp][q], jB = s_list[warp][q + 1];
+      const float4 aA = s_a[jA], bA = s_b[jA], aB = s_a[jB], bB = s_b[jB];
+      const float cA = s_c[jA], cB = s_c[jB];
+      const SplatCol colA = splat_column(px, aA), colB = splat_column(px, aB);
+      float eA[PPT], alA[PPT], eB[PPT], alB[PPT];
+#pragma unroll
+      for (int r = 0; r < PPT; ++r) {
+        const float py = py0 + static_cast<float>(r * G::RS);
+        splat_alpha(colA, py, aA, bA, cap, eA[r], alA[r]);
+        splat_alpha(colB, py, aB, bB, cap, eB[r], alB[r]);
+      }
+      all_done = true;
+#pragma unroll
+      for (int r = 0; r < PPT; ++r) {
+        composite_apply(P[r], eA[r], alA[r], bA, cA, static_cast<uint32_t>(b0 + jA), tstop);
+        composite_apply(P[r], eB[r], alB[r], bB, cB, static_cast<uint32_t>(b0 + jB), tstop);
+        all_done = all_done && P[r].thr == kInf;
+      }
+    }
+    for (; q < nl && !all_done; ++q) {
       const int j = s_list[warp][q];
       const float4 a = s_a[j];
       const float4 b = s_b[j];
