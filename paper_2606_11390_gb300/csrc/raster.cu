@@ -572,9 +572,12 @@ __global__ void GS_RBWD_BOUNDS(TW* TH / PPT) raster_bwd_kernel(
           cB |= pixel_grad<BG>(P[r], col, py0 + static_cast<float>(r * Gm::RS), a, b, cb, rel, cap, amin, gB);
         finish_geometry(gB, col, a, b);
       }
-      const bool anyA = __any_sync(0xffffffffu, cA), anyB = __any_sync(0xffffffffu, cB);
-      const float redA = anyA ? warp_reduce9(gA, lane) : 0.0f;
-      const float redB = anyB ? warp_reduce9(gB, lane) : 0.0f;
+      // listed splats nearly always contribute: reduce without a branch, so
+      // the two reductions and the pixel work form one block to schedule
+      (void)cA;
+      (void)cB;
+      const float redA = warp_reduce9(gA, lane);
+      const float redB = warp_reduce9(gB, lane);
       if (!(lane & 1) && my_slot >= 0) {
         if (redA != 0.0f) atomicAdd(&s_grad[jA * 9 + my_slot], redA);
         if (redB != 0.0f) atomicAdd(&s_grad[jB * 9 + my_slot], redB);
