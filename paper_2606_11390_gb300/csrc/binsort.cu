@@ -361,6 +361,10 @@ struct __align__(16) SortSmem {
   uint32_t tile;
 };
 
+// BITS: significant bits of this pass's digit (the last tile-id pass may
+// need fewer than 8; the higher digit bits are zero for every item there, so
+// their ballots would change nothing).
+template <int BITS>
 __global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) sort_pass_kernel(PassArgs a, int32_t* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SortSmem& sm = *reinterpret_cast<SortSmem*>(smem_raw);
@@ -400,7 +404,7 @@ __global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) sort_pass_ke
     const uint32_t d = (key[i] >> a.shift) & 0xffu;
     uint32_t peers = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
-    for (int bit = 0; bit < 8; ++bit) {
+    for (int bit = 0; bit < BITS; ++bit) {
       const uint32_t bal = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
       peers &= bal ^ (((d >> bit) & 1u) - 1u);  // bal where the bit is set, ~bal where not
     }
@@ -793,12 +797,17 @@ int sort_grid_cap(int64_t* cap) {
   static bool attr_set = false;
   static int ctas_per_sm = 0;
   if (!attr_set) {
-    if (cudaFuncSetAttribute(sort_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(sizeof(SortSmem))) != cudaSuccess ||
-        cudaFuncSetAttribute(sort_pass_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared) != cudaSuccess)
-      return GS_ERR_CUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, sort_pass_kernel, kSortThreads,
+    const void* fns[8] = {reinterpret_cast<const void*>(sort_pass_kernel<1>), reinterpret_cast<const void*>(sort_pass_kernel<2>),
+                          reinterpret_cast<const void*>(sort_pass_kernel<3>), reinterpret_cast<const void*>(sort_pass_kernel<4>),
+                          reinterpret_cast<const void*>(sort_pass_kernel<5>), reinterpret_cast<const void*>(sort_pass_kernel<6>),
+                          reinterpret_cast<const void*>(sort_pass_kernel<7>), reinterpret_cast<const void*>(sort_pass_kernel<8>)};
+    for (const void* f : fns)
+      if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sizeof(SortSmem))) !=
+              cudaSuccess ||
+          cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
+              cudaSuccess)
+        return GS_ERR_CUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, sort_pass_kernel<8>, kSortThreads,
                                                       sizeof(SortSmem)) != cudaSuccess ||
         ctas_per_sm < 1)
       ctas_per_sm = 1;
@@ -830,7 +839,7 @@ int run_u32_sort_passes(uint32_t* const keys[2], uint32_t* const vals[2], const 
     a.stall_tile = -1;
     a.spin_limit = kSpinLimit;
     a.lookback = lookback + static_cast<size_t>(p) * (tiles + 1) * kRadix;
-    sort_pass_kernel<<<grid, kSortThreads, sizeof(SortSmem), stream>>>(a, status);
+    sort_pass_kernel<8><<<grid, kSortThreads, sizeof(SortSmem), stream>>>(a, status);
   }
   return cuda_status(cudaGetLastError());
 }
@@ -901,7 +910,7 @@ int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* 
       a.stall_tile = (p == 0 && (cfg->flags & GS_FLAG_TEST_STALL_LOOKBACK)) ? 0 : -1;
       a.spin_limit = (cfg->flags & GS_FLAG_TEST_STALL_LOOKBACK) ? kTestSpinLimit : kSpinLimit;
       a.lookback = reinterpret_cast<uint64_t*>(ws + w.lb_depth) + static_cast<size_t>(p) * (w.n_depth_tiles + 1) * kRadix;
-      sort_pass_kernel<<<sort_grid(w.n_depth_tiles), kSortThreads, sizeof(SortSmem), stream>>>(a, status_dev);
+      sort_pass_kernel<8><<<sort_grid(w.n_depth_tiles), kSortThreads, sizeof(SortSmem), stream>>>(a, status_dev);
     }
   } else {
     // 1a'/1b'. P partitions of the records, each compacted and depth-sorted
@@ -984,7 +993,23 @@ int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* 
     a.stall_tile = -1;
     a.spin_limit = kSpinLimit;
     a.lookback = reinterpret_cast<uint64_t*>(ws + w.lb_tile) + static_cast<size_t>(p) * (w.n_tile_tiles + 1) * kRadix;
-    sort_pass_kernel<<<sort_grid(w.n_tile_tiles), kSortThreads, sizeof(SortSmem), stream>>>(a, status_dev);
+    int bits = 8;
+    if (p == TP - 1) {
+      bits = 0;
+      while ((int64_t(1) << bits) < L.n_tiles) ++bits;
+      bits -= 8 * (TP - 1);
+    }
+    const unsigned grid = sort_grid(w.n_tile_tiles);
+    switch (bits) {
+      case 1: sort_pass_kernel<1><<<grid, kSortThreads, sizeof(SortSmem), stream>>>(a, status_dev); break;
+      case 2: sort_pass_kernel<2><<<grid, kSortThreads, sizeof(SortSmem), stream>>>(a, status_dev); break;
+      case 3: sort_pass_kernel<3><<<grid, kSortThreads, sizeof(SortSmem), stream>>>(a, status_dev); break;
+      case 4: sort_pass_kernel<4><<<grid, kSortThreads, sizeof(SortSmem), stream>>>(a, status_dev); break;
+      case 5: sort_pass_kernel<5><<<grid, kSortThreads, sizeof(SortSmem), stream>>>(a, status_dev); break;
+      case 6: sort_pass_kernel<6><<<grid, kSortThreads, sizeof(SortSmem), stream>>>(a, status_dev); break;
+      case 7: sort_pass_kernel<7><<<grid, kSortThreads, sizeof(SortSmem), stream>>>(a, status_dev); break;
+      default: sort_pass_kernel<8><<<grid, kSortThreads, sizeof(SortSmem), stream>>>(a, status_dev); break;
+    }
   }
   const uint32_t* tkeys_final = tk[TP & 1];
   // 2c. tile ranges, optional 64-bit keys
