@@ -281,26 +281,32 @@ __global__ void __launch_bounds__(TW* TH / PPT) raster_fwd_kernel(const float4* 
     }
     __syncwarp();
     int q = 0;
-    // two splats per iteration: both exponents / alphas are independent of
-    // the pixel state and are issued first; the compositing then applies
-    // them in list order
-    for (; q + 1 < nl && !all_done; q += 2) {
-      const int jA = s_list[warp][q], jB = s_list[warp][q + 1];
-      const float4 aA = s_a[jA], bA = s_b[jA], aB = s_a[jB], bB = s_b[jB];
-      const float cA = s_c[jA], cB = s_c[jB];
-      const SplatCol colA = splat_column(px, aA), colB = splat_column(px, aB);
-      float eA[PPT], alA[PPT], eB[PPT], alB[PPT];
+#ifndef GS_FWD_GROUP
+#define GS_FWD_GROUP 3
+#endif
+    // GS_FWD_GROUP splats per iteration: their exponents / alphas are
+    // independent of the pixel state and are issued first; the compositing
+    // then applies them in list order
+    constexpr int GR = GS_FWD_GROUP;
+    for (; q + GR - 1 < nl && !all_done; q += GR) {
+      float e[GR][PPT], al[GR][PPT];
+      int js[GR];
 #pragma unroll
-      for (int r = 0; r < PPT; ++r) {
-        const float py = py0 + static_cast<float>(r * G::RS);
-        splat_alpha(colA, py, aA, bA, cap, eA[r], alA[r]);
-        splat_alpha(colB, py, aB, bB, cap, eB[r], alB[r]);
+      for (int u = 0; u < GR; ++u) {
+        js[u] = s_list[warp][q + u];
+        const float4 a = s_a[js[u]], b = s_b[js[u]];
+        const SplatCol col = splat_column(px, a);
+#pragma unroll
+        for (int r = 0; r < PPT; ++r) splat_alpha(col, py0 + static_cast<float>(r * G::RS), a, b, cap, e[u][r], al[u][r]);
       }
       all_done = true;
 #pragma unroll
       for (int r = 0; r < PPT; ++r) {
-        composite_apply(P[r], eA[r], alA[r], bA, cA, static_cast<uint32_t>(b0 + jA), tstop);
-        composite_apply(P[r], eB[r], alB[r], bB, cB, static_cast<uint32_t>(b0 + jB), tstop);
+#pragma unroll
+        for (int u = 0; u < GR; ++u) {
+          const float4 b = s_b[js[u]];
+          composite_apply(P[r], e[u][r], al[u][r], b, s_c[js[u]], static_cast<uint32_t>(b0 + js[u]), tstop);
+        }
         all_done = all_done && P[r].thr == kInf;
       }
     }
