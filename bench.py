@@ -386,6 +386,7 @@ def main():
                 extra["morton"] = morton_measure(step, scene, args, tile, ms)
         if not args.no_e2e:
             extra["e2e"] = e2e_measure(step, args, dist.world)
+            extra["e2e_params_streamed"] = e2e_measure(step, args, dist.world, stream_params=True)
         del step
         torch.cuda.empty_cache()
         if not args.no_compare and args.workload == "diff_4k":
@@ -701,42 +702,53 @@ def batched_vs_per_view(args, tile=None):
     return out
 
 
-def e2e_measure(step, args, world):
+def e2e_measure(step, args, world, stream_params=False):
     """Same metric through the public API with host buffers (HostFedStep):
-    per step, the parameters, cameras and target are copied in from pinned
-    host memory and the loss and the parameter gradients read back; the copies
+    per step, the camera and the target image are copied in from pinned host
+    memory and the loss read back, the Gaussians staying resident in device
+    memory as model state (like the weights of a network) and their gradients
+    there for an optimizer on the device. With stream_params the parameters
+    are copied in and the gradients read back as well, every step. The copies
     of neighbouring steps overlap the compute on two copy streams. Timed from
     an event before the first input copy to one after the last output copy."""
     import torch
 
     from paper_2606_11390_gb300 import renderer as R
 
-    host_params = torch.empty_like(step.params.flat, device="cpu").pin_memory()
-    host_params.copy_(step.params.flat)
+    host_params = host_grads = None
+    if stream_params:
+        host_params = torch.empty_like(step.params.flat, device="cpu").pin_memory()
+        host_params.copy_(step.params.flat)
+        host_grads = [torch.empty_like(step.grads.flat, device="cpu").pin_memory() for _ in range(2)]
     host_target = torch.empty_like(step.target, device="cpu").pin_memory()
     host_target.copy_(step.target)
     host_cams = torch.from_numpy(step.cams.host.copy()).pin_memory()
-    host_grads = [torch.empty_like(step.grads.flat, device="cpu").pin_memory() for _ in range(2)]
     host_loss = [torch.empty(1, dtype=torch.float64).pin_memory() for _ in range(2)]
-    fed = R.HostFedStep(step)
+    fed = R.HostFedStep(step, stream_params=stream_params)
     n = max(3, args.steps // 2)
+    grads_of = (lambda i: host_grads[i & 1]) if stream_params else (lambda i: None)  # noqa: E731
     for i in range(2):
-        fed.run(host_params, host_target, host_cams, host_grads[i & 1], host_loss[i & 1])
+        fed.run(host_params, host_target, host_cams, grads_of(i), host_loss[i & 1])
     fed.sync()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     a.record(fed.h2d)
     for i in range(n):
-        fed.run(host_params, host_target, host_cams, host_grads[i & 1], host_loss[i & 1])
+        fed.run(host_params, host_target, host_cams, grads_of(i), host_loss[i & 1])
     b.record(fed.d2h)
     fed.sync()
     wall = (time.perf_counter() - t0) / n
     ms = a.elapsed_time(b) / n
-    bi = host_params.numel() * 4 + host_target.numel() * 4 + host_cams.numel() * 4
-    bo = host_grads[0].numel() * 4 + 8
+    bi = host_target.numel() * 4 + host_cams.numel() * 4
+    bo = 8
+    if stream_params:
+        bi += host_params.numel() * 4
+        bo += host_grads[0].numel() * 4
+    moved = ("camera and target image in, loss out; Gaussians resident in device memory" if not stream_params else
+             "parameters, camera and target image in, gradients and loss out")
     return {"value": world * step.cams.n_pixels / (ms * 1e-3) / 1e6, "unit": "Mpix/s", "ms_per_step": ms,
-            "wall_ms_per_step": wall * 1e3, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+            "wall_ms_per_step": wall * 1e3, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "copies": moved,
             "overlap": "inputs of step k+1 and outputs of step k copied while step k computes (HostFedStep)"}
 
 

@@ -433,26 +433,32 @@ class TrainStep:
 
 
 class HostFedStep:
-    """Training steps fed from host memory: every step copies its parameters,
-    cameras and target in from (pinned) host buffers and its gradients and
-    loss back out. The copies run on two copy streams, double-buffered in
-    device staging buffers, so the inputs of step k+1 and the outputs of
-    step k move while step k computes; the link carries both directions at
-    once. Stream order keeps every hazard: a staging buffer is refilled only
-    after the step that used it has consumed it, and read out only after the
-    step that fills it is done.
+    """Training steps fed from host memory: every step copies its cameras and
+    target image in from (pinned) host buffers and its loss back out; with
+    stream_params=True it also copies the parameters in and the gradients
+    out (a caller that keeps the Gaussians in host memory), otherwise the
+    parameters stay resident in device memory as model state and the
+    gradients stay there for an optimizer on the device. The copies run on
+    two copy streams, double-buffered in device staging buffers, so the
+    inputs of step k+1 and the outputs of step k move while step k computes;
+    the link carries both directions at once. Stream order keeps every
+    hazard: a staging buffer is refilled only after the step that used it has
+    consumed it, and read out only after the step that fills it is done.
 
     run(...) enqueues one step and returns at once; the host buffers passed to
     a step must stay untouched until sync() (or until two later steps have
-    been enqueued and synced)."""
+    been enqueued and synced). host_params and host_grads are ignored (and
+    may be None) without stream_params."""
 
-    def __init__(self, step: TrainStep):
+    def __init__(self, step: TrainStep, stream_params: bool = True):
         self.step = step
+        self.stream_params = bool(stream_params)
         dev = step.params.flat.device
-        self.in_params = [torch.empty_like(step.params.flat) for _ in range(2)]
+        sp = self.stream_params
+        self.in_params = [torch.empty_like(step.params.flat) for _ in range(2)] if sp else None
         self.in_target = [torch.empty_like(step.target) for _ in range(2)]
         self.in_cams = [torch.empty_like(step.cams.dev) for _ in range(2)]
-        self.out_grads = [torch.empty_like(step.grads.flat) for _ in range(2)]
+        self.out_grads = [torch.empty_like(step.grads.flat) for _ in range(2)] if sp else None
         self.out_loss = [torch.empty_like(step.loss) for _ in range(2)]
         self.h2d = torch.cuda.Stream(device=dev)
         self.d2h = torch.cuda.Stream(device=dev)
@@ -465,25 +471,30 @@ class HostFedStep:
         comp = torch.cuda.current_stream()
         if self.k >= 2:
             self.h2d.wait_event(self.in_free[b])
+        sp = self.stream_params
         with torch.cuda.stream(self.h2d):
-            self.in_params[b].copy_(host_params, non_blocking=True)
+            if sp:
+                self.in_params[b].copy_(host_params, non_blocking=True)
             self.in_target[b].copy_(host_target, non_blocking=True)
             self.in_cams[b].copy_(host_cams, non_blocking=True)
             self.in_ready[b].record(self.h2d)
         comp.wait_event(self.in_ready[b])
-        st.params.flat.copy_(self.in_params[b])
+        if sp:
+            st.params.flat.copy_(self.in_params[b])
         st.target.copy_(self.in_target[b])
         st.cams.dev.copy_(self.in_cams[b])
         self.in_free[b].record(comp)
         st.run()
         if self.k >= 2:
             comp.wait_event(self.out_free[b])
-        self.out_grads[b].copy_(st.grads.flat)
+        if sp:
+            self.out_grads[b].copy_(st.grads.flat)
         self.out_loss[b].copy_(st.loss)
         self.out_ready[b].record(comp)
         self.d2h.wait_event(self.out_ready[b])
         with torch.cuda.stream(self.d2h):
-            host_grads.copy_(self.out_grads[b], non_blocking=True)
+            if sp:
+                host_grads.copy_(self.out_grads[b], non_blocking=True)
             host_loss.copy_(self.out_loss[b], non_blocking=True)
             self.out_free[b].record(self.d2h)
         self.k += 1

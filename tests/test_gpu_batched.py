@@ -124,3 +124,35 @@ def test_host_fed_steps_match_direct_steps(R):
         g, L = want[k & 1]
         grad_close(host_g[k].numpy(), g, rel=1e-4, name=f"step {k} grads")
         assert abs(host_l[k].item() - L) <= 1e-9 * abs(L)
+
+
+def test_host_fed_resident_params_match_direct_steps(R):
+    """HostFedStep without stream_params (camera and target copied in, loss
+    out, Gaussians resident): for alternating target images, each step's loss
+    is that of the same step run directly, and the gradients left on the
+    device are those of the last step."""
+    import torch
+
+    s = _scene()
+    st = R.TrainStep(s, mode="batched").prepare()
+    ta = st.target.clone()
+    tb = ta.clone()
+    tb.mul_(0.5).add_(0.25)
+    want = []
+    for t in (ta, tb):
+        st.target.copy_(t)
+        st.run()
+        torch.cuda.synchronize()
+        want.append((st.grads.flat.cpu().numpy().astype(np.float64), float(st.loss.item())))
+    host_t = [t.cpu().pin_memory() for t in (ta, tb)]
+    host_c = torch.from_numpy(st.cams.host.copy()).pin_memory()
+    host_l = [torch.empty(1, dtype=torch.float64).pin_memory() for _ in range(4)]
+    fed = R.HostFedStep(st, stream_params=False)
+    for k in range(4):
+        fed.run(None, host_t[k & 1], host_c, None, host_l[k])
+    fed.sync()
+    st.check()
+    for k in range(4):
+        L = want[k & 1][1]
+        assert abs(host_l[k].item() - L) <= 1e-9 * abs(L), (k, host_l[k].item(), L)
+    grad_close(st.grads.flat.cpu().numpy(), want[1][0], rel=1e-4, name="resident grads")
