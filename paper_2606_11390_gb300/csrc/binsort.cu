@@ -339,8 +339,10 @@ constexpr int kSortTile = kSortThreads * kSortItems;
 struct PassArgs {
   const uint32_t* keys_in;
   const uint32_t* vals_in;
-  uint32_t* keys_out;
+  uint32_t* keys_out;  // may be null: the keys are not written
   uint32_t* vals_out;
+  uint2* ranges;             // last tile-id pass: per-key (~first, last + 1) bounds, else null
+  uint32_t n_keys;           // ranges has n_keys entries
   const int64_t* n_total;   // items = min(*n_total, cap)
   int64_t cap;
   int shift;
@@ -486,8 +488,22 @@ __global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) sort_pass_ke
     const uint32_t k = sm.keys[idx];
     const uint32_t p = sm.base[(k >> a.shift) & 0xffu] + static_cast<uint32_t>(idx);
     if (p < n32) {
-      a.keys_out[p] = k;
+      if (a.keys_out) a.keys_out[p] = k;
       a.vals_out[p] = sm.vals[idx];
+      if (a.ranges) {
+        // Last pass: the input is sorted by the lower digits, so a key's
+        // items are contiguous in this tile's local order, and the key's
+        // runs from successive tiles are adjacent in the output. The run's
+        // first and last items bound the key's range: the start kept as
+        // ~position under atomicMax (zero-initialised), the end as
+        // position + 1.
+        if (k < a.n_keys) {
+          if (idx == 0 || sm.keys[idx - 1] != k) atomicMax(&a.ranges[k].x, ~p);
+          if (idx == n_valid - 1 || sm.keys[idx + 1] != k) atomicMax(&a.ranges[k].y, p + 1);
+        } else {
+          set_status(status, GS_STATUS_BOUNDS);
+        }
+      }
     } else {
       set_status(status, GS_STATUS_BOUNDS);
     }
@@ -698,6 +714,16 @@ __global__ void tile_ranges_kernel(const uint32_t* __restrict__ tkeys, const int
   }
 }
 
+// Ranges left by the last tile-id pass: a non-empty tile holds (~start, end);
+// empty tiles stay (0, 0).
+__global__ void ranges_fixup_kernel(uint2* __restrict__ ranges, int64_t n_tiles) {
+  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < n_tiles;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const uint2 r = ranges[t];
+    if (r.y) ranges[t].x = ~r.x;
+  }
+}
+
 // Optional 64-bit keys (tile << 32) | bits(depth) of the sorted list.
 __global__ void keys64_kernel(const uint32_t* __restrict__ tkeys, const uint32_t* __restrict__ vals,
                               const float* __restrict__ projected, const int64_t* n_total, int64_t capacity,
@@ -836,6 +862,7 @@ int run_u32_sort_passes(uint32_t* const keys[2], uint32_t* const vals[2], const 
     a.keys_in = keys[p & 1]; a.vals_in = vals[p & 1]; a.keys_out = keys[(p + 1) & 1]; a.vals_out = vals[(p + 1) & 1];
     a.n_total = n_dev; a.cap = cap; a.shift = 8 * p; a.digit_offsets = hist + p * kRadix;
     a.ticket = tickets + p;
+    a.ranges = nullptr; a.n_keys = 0;
     a.stall_tile = -1;
     a.spin_limit = kSpinLimit;
     a.lookback = lookback + static_cast<size_t>(p) * (tiles + 1) * kRadix;
@@ -907,6 +934,7 @@ int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* 
       a.keys_in = dk[p & 1]; a.vals_in = dv[p & 1]; a.keys_out = dk[(p + 1) & 1]; a.vals_out = dv[(p + 1) & 1];
       a.n_total = n_visible; a.cap = VN; a.shift = 8 * p; a.digit_offsets = hist_d + p * kRadix;
       a.ticket = tickets + 2 + p;
+      a.ranges = nullptr; a.n_keys = 0;
       a.stall_tile = (p == 0 && (cfg->flags & GS_FLAG_TEST_STALL_LOOKBACK)) ? 0 : -1;
       a.spin_limit = (cfg->flags & GS_FLAG_TEST_STALL_LOOKBACK) ? kTestSpinLimit : kSpinLimit;
       a.lookback = reinterpret_cast<uint64_t*>(ws + w.lb_depth) + static_cast<size_t>(p) * (w.n_depth_tiles + 1) * kRadix;
@@ -988,6 +1016,14 @@ int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* 
   for (int p = 0; p < TP; ++p) {
     PassArgs a;
     a.keys_in = tk[p & 1]; a.vals_in = tv[p & 1]; a.keys_out = tk[(p + 1) & 1]; a.vals_out = tv[(p + 1) & 1];
+    a.ranges = nullptr; a.n_keys = 0;
+    if (p == TP - 1) {
+      // the last pass bounds the tile ranges itself; it writes the ids only
+      // when the 64-bit keys are asked for
+      a.ranges = reinterpret_cast<uint2*>(tile_ranges);
+      a.n_keys = static_cast<uint32_t>(L.n_tiles);
+      if (!keys) a.keys_out = nullptr;
+    }
     a.n_total = n_isect_dev; a.cap = capacity; a.shift = 8 * p; a.digit_offsets = hist_t + p * kRadix;
     a.ticket = tickets + 6 + p;
     a.stall_tile = -1;
@@ -1012,10 +1048,15 @@ int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* 
     }
   }
   const uint32_t* tkeys_final = tk[TP & 1];
-  // 2c. tile ranges, optional 64-bit keys
-  tile_ranges_kernel<<<static_cast<unsigned>(4 * n_sm), 256, 0, stream>>>(
-      tkeys_final, n_isect_dev, capacity, static_cast<uint32_t>(L.n_tiles), reinterpret_cast<uint2*>(tile_ranges),
-      status_dev);
+  // 2c. tile ranges (from the ids themselves when there is no tile pass),
+  //     optional 64-bit keys
+  if (TP > 0)
+    ranges_fixup_kernel<<<static_cast<unsigned>((L.n_tiles + 255) / 256), 256, 0, stream>>>(
+        reinterpret_cast<uint2*>(tile_ranges), L.n_tiles);
+  else
+    tile_ranges_kernel<<<static_cast<unsigned>(4 * n_sm), 256, 0, stream>>>(
+        tkeys_final, n_isect_dev, capacity, static_cast<uint32_t>(L.n_tiles), reinterpret_cast<uint2*>(tile_ranges),
+        status_dev);
   if (keys)
     keys64_kernel<<<static_cast<unsigned>(4 * n_sm), 256, 0, stream>>>(tkeys_final, vals, projected, n_isect_dev,
                                                                         capacity, keys);
