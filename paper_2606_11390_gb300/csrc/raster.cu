@@ -24,8 +24,9 @@
 // largest `last` among its pixels, recovers T_k = T_{k+1} / (1 - alpha_k) from
 // the stored final T, sums a splat's 9 gradient values over the thread's
 // pixels (the geometric ones as dy-moments, the pixels sharing dx), reduces
-// them across the warp with a 12-shuffle reduce-scatter (instead of 9 x 5
-// butterfly shuffles), sums the warps of the CTA in shared memory and issues
+// them across the warp with a reduce-scatter (two splats' 18 values with 20
+// shuffles; a lone splat's 9 with 12, instead of 9 x 5 butterfly
+// shuffles), sums the warps of the CTA in shared memory and issues
 // one FP32 atomic per value per (tile, splat) to the per-record gradient
 // buffer.
 #include <cuda_runtime.h>
@@ -380,6 +381,41 @@ __device__ __forceinline__ int slot_of_lane(int lane) {
   return h1 ? u[1] : u[0];
 }
 
+// Reduce-scatter of the 18 values of two splats (a[9], then b[9]) over a warp
+// with 20 shuffles (instead of 2 x 12): on return, the lane holds the
+// warp-wide sum of value index slot18_of_lane(lane) (0..8: a, 9..17: b), or
+// 0 where that is -1. Every value lands in exactly one lane.
+__device__ __forceinline__ float warp_reduce18(const float a[9], const float b[9], int lane) {
+  const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4, h1 = lane & 2, h0 = lane & 1;
+  float s[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) s[i] = (h4 ? b[i] : a[i]) + __shfl_xor_sync(0xffffffffu, h4 ? a[i] : b[i], 16);
+  float t[5];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) t[i] = (h3 ? s[5 + i] : s[i]) + __shfl_xor_sync(0xffffffffu, h3 ? s[i] : s[5 + i], 8);
+  t[4] = (h3 ? 0.0f : s[4]) + __shfl_xor_sync(0xffffffffu, h3 ? s[4] : 0.0f, 8);
+  float u[3];
+  u[0] = (h2 ? t[3] : t[0]) + __shfl_xor_sync(0xffffffffu, h2 ? t[0] : t[3], 4);
+  u[1] = (h2 ? t[4] : t[1]) + __shfl_xor_sync(0xffffffffu, h2 ? t[1] : t[4], 4);
+  u[2] = (h2 ? 0.0f : t[2]) + __shfl_xor_sync(0xffffffffu, h2 ? t[2] : 0.0f, 4);
+  float w[2];
+  w[0] = (h1 ? u[2] : u[0]) + __shfl_xor_sync(0xffffffffu, h1 ? u[0] : u[2], 2);
+  w[1] = (h1 ? 0.0f : u[1]) + __shfl_xor_sync(0xffffffffu, h1 ? u[1] : 0.0f, 2);
+  return (h0 ? w[1] : w[0]) + __shfl_xor_sync(0xffffffffu, h0 ? w[0] : w[1], 1);
+}
+
+__device__ __forceinline__ int slot18_of_lane(int lane) {
+  const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4, h1 = lane & 2, h0 = lane & 1;
+  int s[9];
+  for (int i = 0; i < 9; ++i) s[i] = (h4 ? 9 : 0) + i;
+  int t[5];
+  for (int i = 0; i < 4; ++i) t[i] = h3 ? s[5 + i] : s[i];
+  t[4] = h3 ? -1 : s[4];
+  const int u[3] = {h2 ? t[3] : t[0], h2 ? t[4] : t[1], h2 ? -1 : t[2]};
+  const int w[2] = {h1 ? u[2] : u[0], h1 ? -1 : u[1]};
+  return h0 ? w[1] : w[0];
+}
+
 struct PixelBwd {
   float T, g0, g1, g2, gbg, ar0, ar1, ar2;
   uint32_t last;
@@ -411,7 +447,6 @@ __device__ __forceinline__ bool pixel_grad(PixelBwd& P, const SplatCol& col, flo
   // branch-free, like the forward step: decisions select, zeros add nothing
   float dy;
   const float e = splat_exponent(col, py, a, b.x, dy);
-  const float dx = col.dx;
   const float G = ex2_approx(e);
   const float oG = __fmul_rn(b.y, G);
   const float alpha = fminf(cap, oG);
@@ -494,6 +529,10 @@ __global__ void GS_RBWD_BOUNDS(TW* TH / PPT) raster_bwd_kernel(
     lmax = max(lmax, P[r].last);
   }
   const int my_slot = slot_of_lane(lane);
+  // the pair reduction: which splat of the pair and which of its 9 values
+  const int slot18 = slot18_of_lane(lane);
+  const bool pair_b = slot18 >= 9;
+  const int pair_slot = slot18 >= 9 ? slot18 - 9 : slot18;
   const uint32_t wmax = __reduce_max_sync(0xffffffffu, lmax);
   if (lane == 0) s_wmax[warp] = wmax;
   for (int i = tid; i < B * 9; i += NT) s_grad[i] = 0.0f;
@@ -584,12 +623,8 @@ __global__ void GS_RBWD_BOUNDS(TW* TH / PPT) raster_bwd_kernel(
       // the two reductions and the pixel work form one block to schedule
       (void)cA;
       (void)cB;
-      const float redA = warp_reduce9(gA, lane);
-      const float redB = warp_reduce9(gB, lane);
-      if (!(lane & 1) && my_slot >= 0) {
-        if (redA != 0.0f) atomicAdd(&s_grad[jA * 9 + my_slot], redA);
-        if (redB != 0.0f) atomicAdd(&s_grad[jB * 9 + my_slot], redB);
-      }
+      const float red = warp_reduce18(gA, gB, lane);
+      if (slot18 >= 0 && red != 0.0f) atomicAdd(&s_grad[(pair_b ? jB : jA) * 9 + pair_slot], red);
     }
     if (q < nl) {
       const int j = s_list[warp][q];
