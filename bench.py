@@ -199,6 +199,9 @@ def stage_times(step, iters=5):
     p, gr = step.params, step.grads
     for _ in range(iters):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
+        # keep the GPU busy while the host enqueues the stages, so that no
+        # stage's time includes the host's launch latency
+        torch.cuda._sleep(200_000)
         ev[0].record(stream)
         R.project(p, cams, fr)
         ev[1].record(stream)
