@@ -417,7 +417,10 @@ __device__ __forceinline__ int slot18_of_lane(int lane) {
 }
 
 struct PixelBwd {
-  float T, g0, g1, g2, gbg, ar0, ar1, ar2;
+  // S = (colour accumulated behind the current entry, normalised) . dL/dC:
+  // the alpha gradient needs the accumulated colour only through this dot
+  // product, so one scalar replaces the three channels
+  float T, g0, g1, g2, gbg, S;
   uint32_t last;
 };
 
@@ -458,13 +461,11 @@ __device__ __forceinline__ bool pixel_grad(PixelBwd& P, const SplatCol& col, flo
   gv[5] += w * P.g0;
   gv[6] += w * P.g1;
   gv[7] += w * P.g2;
-  const float d0 = b.z - P.ar0, d1 = b.w - P.ar1, d2 = cb - P.ar2;
+  // (c - accumulated) . dL/dC = c . dL/dC - S
+  const float dcs = fmaf(cb, P.g2, fmaf(b.w, P.g1, b.z * P.g0)) - P.S;
   // with a zero background (the default) the background term vanishes
-  const float dalpha = BG ? P.T * (d0 * P.g0 + d1 * P.g1 + d2 * P.g2) - P.gbg * inv
-                          : P.T * (d0 * P.g0 + d1 * P.g1 + d2 * P.g2);
-  P.ar0 += aok * d0;
-  P.ar1 += aok * d1;
-  P.ar2 += aok * d2;
+  const float dalpha = BG ? P.T * dcs - P.gbg * inv : P.T * dcs;
+  P.S = fmaf(aok, dcs, P.S);
   const float da = (ok && !(oG > cap)) ? dalpha : 0.0f;
   gv[8] += da * G;
   // The geometric sums need dpw = dalpha * alpha only through its moments in
@@ -515,7 +516,7 @@ __global__ void GS_RBWD_BOUNDS(TW* TH / PPT) raster_bwd_kernel(
   uint32_t lmax = 0;
 #pragma unroll
   for (int r = 0; r < PPT; ++r) {
-    P[r] = PixelBwd{1.0f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u};
+    P[r] = PixelBwd{1.0f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u};
     const int yy = y0 + r * Gm::RS;
     if (x < W && yy < H) {
       const size_t p = static_cast<size_t>(L.pix_base[v]) + static_cast<size_t>(yy) * W + x;
