@@ -15,6 +15,7 @@ barrier and a max-reduction of the timings only).
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import statistics
@@ -34,7 +35,9 @@ METRIC = "fwd+bwd ms/iter & Mpix/s @4M Gaussians 4K; batched vs per-view, same t
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 200 for this implementation, about 0.8 s at 4K so that the clock "
+                         "record holds several samples; 20 for the reference arm)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="diff_4k", choices=["diff_4k", "batch16", "train_1080p", "tiny", "street"])
@@ -53,7 +56,10 @@ def parse():
     ap.add_argument("--kernel", default="step", choices=["step", "ssim_loss"],
                     help="step: the training step (default); ssim_loss: the fused SSIM loss kernel alone on a "
                          "seeded image pair of the workload's view sizes")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 20 if args.impl == "reference" else 200
+    return args
 
 
 # ---------------------------------------------------------------------------
@@ -103,7 +109,7 @@ def max_over_ranks(values):
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------
 class ClockSampler:
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -126,7 +132,12 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
-    def stop(self):
+    def mark(self):
+        """Wall-clock time of a timed-region boundary (local time, as nvidia-smi stamps its samples)."""
+        return datetime.datetime.now()
+
+    def stop(self, t0=None, t1=None):
+        """Summary of the samples stamped within [t0, t1] (all samples when no window is given)."""
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -138,18 +149,22 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f")
+                clk, clk_max = float(f[2]), float(f[3])
             except ValueError:
                 continue
-            for n, val in zip(names, f[5:9]):
+            if (t0 is not None and ts < t0) or (t1 is not None and ts > t1):
+                continue
+            sm.append(clk)
+            mx.append(clk_max)
+            for n, val in zip(names, f[6:10]):
                 if val.lower().startswith("active"):
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "window": "samples stamped inside the timed region"}
 
 
 def measured_peaks():
@@ -358,13 +373,15 @@ def main():
     dist.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_start = clocks.mark()
     e0.record(stream)
     for _ in range(args.steps):
         step.run()
     e1.record(stream)
     torch.cuda.synchronize()
+    t_end = clocks.mark()
     dist.barrier()
-    clk = clocks.stop()
+    clk = clocks.stop(t_start, t_end)
     step.check()
     ms_local = e0.elapsed_time(e1) / args.steps
     ms = dist.max(ms_local)
