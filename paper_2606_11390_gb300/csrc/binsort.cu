@@ -335,6 +335,7 @@ constexpr int kSortItems = GS_SORT_ITEMS;
 #define GS_SORT_MIN_BLOCKS 4
 #endif
 constexpr int kSortTile = kSortThreads * kSortItems;
+static_assert(32 * kSortItems <= 1024, "a within-warp rank must fit the 10 bits it is packed in");
 
 struct PassArgs {
   const uint32_t* keys_in;
@@ -397,7 +398,9 @@ __global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) sort_pass_ke
   }
   // 2. stable rank within the warp, item by item: the lanes holding the same
   //    digit are found with one ballot per digit bit (cheaper than match_any)
-  uint32_t rank[kSortItems];
+  uint32_t rpk[(kSortItems + 2) / 3];  // ranks (< 32 x items <= 1024), 10 bits each, 3 per register
+#pragma unroll
+  for (int i = 0; i < (kSortItems + 2) / 3; ++i) rpk[i] = 0u;
   const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
@@ -413,7 +416,7 @@ __global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) sort_pass_ke
     // Every lane of a digit group reads the group's running count (a
     // broadcast) and writes the same new value: no leader, no divergence.
     const uint32_t before = sm.warp_hist[warp][d];
-    rank[i] = before + __popc(peers & lt_mask);
+    rpk[i / 3] |= (before + __popc(peers & lt_mask)) << (10 * (i % 3));
     __syncwarp();
     if (valid) sm.warp_hist[warp][d] = before + __popc(peers);
     __syncwarp();
@@ -474,7 +477,7 @@ __global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) sort_pass_ke
     const int li = warp_base + i * 32 + lane;
     if (li < n_valid) {
       const uint32_t dd = (key[i] >> a.shift) & 0xffu;
-      const uint32_t p = sm.local_start[dd] + sm.warp_hist[warp][dd] + rank[i];
+      const uint32_t p = sm.local_start[dd] + sm.warp_hist[warp][dd] + ((rpk[i / 3] >> (10 * (i % 3))) & 0x3ffu);
       sm.keys[p] = key[i];
       sm.vals[p] = val[i];
     }
