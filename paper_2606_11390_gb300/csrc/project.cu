@@ -11,7 +11,9 @@
 // views. A CTA of 128 Gaussians stages its contiguous parameter slices
 // (means, log-scales, quaternions, opacities, SH) into shared memory with TMA
 // bulk copies (cp.async.bulk + mbarrier), and writes its projected records
-// back through shared memory as coalesced 16-byte stores.
+// back through shared memory as coalesced 16-byte stores. With its own copies
+// it asks L2 to prefetch (cp.async.bulk.prefetch.L2) the slices of the CTA
+// one resident wave later, which then stages from L2 instead of DRAM.
 //
 // Bit-exact tile rectangles. Steps 1-8 of the projection (scale activation
 // through the tile rectangle) decide integers, so they are evaluated with
@@ -322,13 +324,19 @@ struct ExtraCopies {
   int n = 0;
   void* dst[2];
   const void* src[2];
+  const void* pf_src[2];  // the same arrays at the prefetched slice
   uint32_t bytes[2];
 };
+
+// Asks L2 to fetch [src, src + bytes) (16-byte aligned, a multiple of 16 bytes).
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 
 __device__ __forceinline__ void stage_params(ParamSmem& sm, const float* means, const float* log_scales,
                                              const float* quats, const float* opac, const float* sh, int64_t g0, int n,
                                              const gs_camera* cams, int V, bool use_bulk, int32_t* status,
-                                             const ExtraCopies& extra = ExtraCopies()) {
+                                             int64_t g_pf, const ExtraCopies& extra = ExtraCopies()) {
   const int tid = threadIdx.x;
   {
     const float* src = reinterpret_cast<const float*>(cams);
@@ -354,6 +362,16 @@ __device__ __forceinline__ void stage_params(ParamSmem& sm, const float* means, 
       bulk_g2s(sm.quats, quats + g0 * 4, b_quat, &sm.bar);
       bulk_g2s(sm.opac, opac + g0, b_op, &sm.bar);
       bulk_g2s(sm.sh, sh + g0 * 48, b_sh, &sm.bar);
+      // the slice of the CTA that will take this one's place: into L2 now,
+      // so that its staging copies find it there
+      if (g_pf >= 0) {
+        bulk_prefetch_l2(sh + g_pf * 48, b_sh);
+        bulk_prefetch_l2(means + g_pf * 3, b_means);
+        bulk_prefetch_l2(log_scales + g_pf * 3, b_means);
+        bulk_prefetch_l2(quats + g_pf * 4, b_quat);
+        bulk_prefetch_l2(opac + g_pf, b_op);
+        for (int i = 0; i < extra.n; ++i) bulk_prefetch_l2(extra.pf_src[i], extra.bytes[i]);
+      }
     }
     if (!mbar_wait(&sm.bar, 0)) {
       set_status(status, GS_STATUS_TIMEOUT);
@@ -386,12 +404,14 @@ __global__ void __launch_bounds__(kProjBlock) project_fwd_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ opac, const float* __restrict__ sh, int64_t N, const gs_camera* __restrict__ cams,
     const Layout L, const Consts K, float4* __restrict__ projected, short4* __restrict__ rects,
-    uint32_t* __restrict__ counts, int use_bulk, int32_t* status) {
+    uint32_t* __restrict__ counts, int use_bulk, int64_t ahead, int32_t* status) {
   __shared__ ProjFwdSmem sm;
   const int tid = threadIdx.x;
   const int64_t g0 = static_cast<int64_t>(blockIdx.x) * kProjBlock;
   const int n = static_cast<int>(N - g0 < kProjBlock ? N - g0 : kProjBlock);
-  stage_params(sm.p, means, log_scales, quats, opac, sh, g0, n, cams, L.V, use_bulk != 0, status);
+  const int64_t g_pf = (static_cast<int64_t>(blockIdx.x) + ahead) * kProjBlock;
+  stage_params(sm.p, means, log_scales, quats, opac, sh, g0, n, cams, L.V, use_bulk != 0, status,
+               ahead > 0 && g_pf + kProjBlock <= N ? g_pf : -1);
   const bool active = tid < n;
   constexpr int NB = (DEG + 1) * (DEG + 1);
   GaussLocal G;
@@ -453,7 +473,7 @@ __global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_ke
     const float* __restrict__ opac, const float* __restrict__ sh, int64_t N, const gs_camera* __restrict__ cams,
     const Layout L, const Consts K, const uint32_t* __restrict__ counts, const float* __restrict__ d_proj,
     float* __restrict__ d_means, float* __restrict__ d_log_scales, float* __restrict__ d_quats,
-    float* __restrict__ d_opac, float* __restrict__ d_sh, int use_bulk, int32_t* status) {
+    float* __restrict__ d_opac, float* __restrict__ d_sh, int use_bulk, int64_t ahead, int32_t* status) {
   constexpr int NB = (DEG + 1) * (DEG + 1);
   __shared__ ParamSmem sm_p;
   struct {
@@ -476,7 +496,13 @@ __global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_ke
     ex.src[1] = counts + g0;
     ex.bytes[1] = kProjBlock * 4;
   }
-  stage_params(sm.p, means, log_scales, quats, opac, sh, g0, n, cams, L.V, use_bulk != 0, status, ex);
+  const int64_t g_pf = (static_cast<int64_t>(blockIdx.x) + ahead) * kProjBlock;
+  const bool pf = ahead > 0 && g_pf + kProjBlock <= N;
+  if (staged) {
+    ex.pf_src[0] = d_proj + (pf ? g_pf : g0) * kDRecordFloats;
+    ex.pf_src[1] = counts + (pf ? g_pf : g0);
+  }
+  stage_params(sm.p, means, log_scales, quats, opac, sh, g0, n, cams, L.V, use_bulk != 0, status, pf ? g_pf : -1, ex);
   const bool active = tid < n;
   float gm[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, go = 0.f;
   float4* my_sh4 = &sm.p.sh[12 * tid];
@@ -629,6 +655,20 @@ __global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_ke
 
 }  // namespace
 
+// CTAs of `kernel` resident on the whole GPU at once (queried once per kernel).
+template <int Tag, class F>
+int64_t resident_ctas(F kernel) {
+  static int64_t cached = -1;
+  if (cached < 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kProjBlock, 0) != cudaSuccess)
+      return 0;
+    cached = static_cast<int64_t>(sms) * per_sm;
+  }
+  return cached;
+}
+
 int launch_project_bwd(const float* means, const float* log_scales, const float* quats, const float* opacity_logits,
                        const float* sh, int64_t N, const gs_camera* cams, const Layout& L, const Consts& K,
                        const uint32_t* counts, const float* d_projected, float* d_means, float* d_log_scales,
@@ -642,7 +682,8 @@ int launch_project_bwd(const float* means, const float* log_scales, const float*
 #define GS_PBWD(D)                                                                                              \
   project_bwd_kernel<D><<<blocks, kProjBlock, 0, stream>>>(means, log_scales, quats, opacity_logits, sh, N, cams, L, \
                                                            K, counts, d_projected, d_means, d_log_scales, d_quats,      \
-                                                           d_opacity_logits, d_sh, bulk_mode, status)
+                                                           d_opacity_logits, d_sh, bulk_mode,                     \
+                                                           resident_ctas<10 + D>(project_bwd_kernel<D>), status)
   switch (K.sh_degree) {
     case 0: GS_PBWD(0); break;
     case 1: GS_PBWD(1); break;
@@ -678,7 +719,7 @@ extern "C" int gs_project(const float* means, const float* log_scales, const flo
   project_fwd_kernel<D><<<blocks, kProjBlock, 0, st>>>(means, log_scales, quats, opacity_logits, sh, N, cams_dev, L, K, \
                                                        reinterpret_cast<float4*>(projected),                           \
                                                        reinterpret_cast<short4*>(rects), counts, bulk ? 1 : 0,          \
-                                                       status_dev)
+                                                       resident_ctas<D>(project_fwd_kernel<D>), status_dev)
   switch (cfg->sh_degree) {
     case 0: GS_PFWD(0); break;
     case 1: GS_PFWD(1); break;
