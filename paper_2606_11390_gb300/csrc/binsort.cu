@@ -384,6 +384,20 @@ __global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) sort_pass_ke
   const int64_t tile_start = static_cast<int64_t>(t) * kSortTile;
   if (tile_start >= n) return;  // past the data: publishes nothing, awaited by nobody
   const int n_valid = static_cast<int>(n - tile_start < kSortTile ? n - tile_start : kSortTile);
+  if (tid == 0) {
+    // the tile one grid ahead (taken by some CTA about one round later): into L2 now
+    const int64_t pf_start = tile_start + static_cast<int64_t>(gridDim.x) * kSortTile;
+    if (pf_start < n) {
+      const int64_t items = n - pf_start < kSortTile ? n - pf_start : kSortTile;
+      const uint32_t bytes = static_cast<uint32_t>(items * 4) & ~15u;
+      const uint32_t* kp = a.keys_in + pf_start;
+      const uint32_t* vp = a.vals_in + pf_start;
+      if (bytes && !(reinterpret_cast<uintptr_t>(kp) & 15u) && !(reinterpret_cast<uintptr_t>(vp) & 15u)) {
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(kp), "r"(bytes) : "memory");
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(vp), "r"(bytes) : "memory");
+      }
+    }
+  }
 
   // 1. load everything first (warp-striped), so the loads overlap
   uint32_t key[kSortItems], val[kSortItems];
