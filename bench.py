@@ -562,6 +562,7 @@ def partitioned_sort_measure(step, parts=(1, 2, 4, 8), iters=10):
         fr.projected.copy_(fr0.projected)
         fr.rects.copy_(fr0.rects)
         fr.counts.copy_(fr0.counts)
+        fr.depth_keys.copy_(fr0.depth_keys)
         for _ in range(2):
             R.bin_sort(fr)
         torch.cuda.synchronize()

@@ -157,12 +157,16 @@ GS_API int gs_layout_totals(const int32_t* sizes, int32_t V, const gs_config* cf
  *                 5 opacity   6 depth     7 radius   8 r  9 g  10 b  11 = 0
  *               (all zero for an invisible record);
  *               rects [V*N][4] int16 tile rectangle (x0, y0, x1, y1), half-open;
- *               counts [V*N] uint32 = (x1-x0)*(y1-y0), 0 if culled.
+ *               counts [V*N] uint32 = (x1-x0)*(y1-y0), 0 if culled;
+ *               depth_keys [V*N] uint32 (optional, NULL to skip): the float
+ *               bits of the depth (field 6) of a visible record, 0 for a
+ *               culled one. gs_bin_sort reads them instead of gathering the
+ *               depths from the 48-byte records.
  * N may be 0 (nothing enqueued). Errors: GS_ERR_ARG, GS_ERR_UNSUPPORTED, GS_ERR_CUDA. */
 GS_API int gs_project(const float* means, const float* log_scales, const float* quats, const float* opacity_logits,
                const float* sh, int64_t N, const gs_camera* cams_dev, const int32_t* sizes, int32_t V,
-               const gs_config* cfg, float* projected, int16_t* rects, uint32_t* counts, int32_t* status_dev,
-               gs_stream_t stream);
+               const gs_config* cfg, float* projected, int16_t* rects, uint32_t* counts, uint32_t* depth_keys,
+               int32_t* status_dev, gs_stream_t stream);
 
 /* Bytes of device workspace gs_bin_sort needs for N Gaussians, V views, a
  * key capacity and n_tiles tiles (from gs_layout_totals); 0 for invalid
@@ -182,7 +186,9 @@ GS_API size_t gs_bin_sort_workspace_bytes(int64_t N, int32_t V, int64_t capacity
  * followed by a stable sort of the emitted entries by tile id, which yields
  * the same order.
  *
- * in  (device): projected, rects, counts from gs_project.
+ * in  (device): projected, rects, counts from gs_project; depth_keys from
+ *               gs_project (optional: with NULL the depths are read from the
+ *               projected records; the result is the same).
  * in  (host)  : N, sizes [V][2], cfg, capacity (>= 0, < 2^32 - 1).
  * out (device): vals [capacity] uint32 (first n entries valid);
  *               keys [capacity] uint64 (optional: pass NULL to skip writing
@@ -197,8 +203,9 @@ GS_API size_t gs_bin_sort_workspace_bytes(int64_t N, int32_t V, int64_t capacity
  * and call again. A device wait that exceeds its iteration bound sets
  * GS_STATUS_TIMEOUT.
  * Errors: GS_ERR_ARG (also for a too-small workspace), GS_ERR_CUDA. */
-GS_API int gs_bin_sort(const float* projected, const int16_t* rects, const uint32_t* counts, int64_t N, const int32_t* sizes,
-                int32_t V, const gs_config* cfg, uint64_t* keys, uint32_t* vals, int64_t capacity,
+GS_API int gs_bin_sort(const float* projected, const int16_t* rects, const uint32_t* counts, const uint32_t* depth_keys,
+                int64_t N, const int32_t* sizes, int32_t V, const gs_config* cfg, uint64_t* keys, uint32_t* vals,
+                int64_t capacity,
                 uint32_t* tile_ranges, int64_t* n_isect_dev, void* workspace, size_t workspace_bytes,
                 int32_t* status_dev, gs_stream_t stream);
 
@@ -218,8 +225,9 @@ GS_API size_t gs_bin_sort_partitioned_workspace_bytes(int64_t N, int32_t V, int6
  * to gs_bin_sort's. Arguments as gs_bin_sort, plus partitions (a power of two
  * in [1, 64]) and a workspace of gs_bin_sort_partitioned_workspace_bytes.
  * Errors: as gs_bin_sort. */
-GS_API int gs_bin_sort_partitioned(const float* projected, const int16_t* rects, const uint32_t* counts, int64_t N,
-                                   const int32_t* sizes, int32_t V, const gs_config* cfg, uint64_t* keys,
+GS_API int gs_bin_sort_partitioned(const float* projected, const int16_t* rects, const uint32_t* counts,
+                                   const uint32_t* depth_keys, int64_t N, const int32_t* sizes, int32_t V,
+                                   const gs_config* cfg, uint64_t* keys,
                                    uint32_t* vals, int64_t capacity, uint32_t* tile_ranges, int64_t* n_isect_dev,
                                    int32_t partitions, void* workspace, size_t workspace_bytes, int32_t* status_dev,
                                    gs_stream_t stream);
@@ -233,7 +241,8 @@ GS_API int gs_bin_sort_partitioned(const float* projected, const int16_t* rects,
  * GS_STATIC_SCRATCH_BYTES (64 MiB) that each GPU loading this code holds
  * until the process exits.
  * Arguments, outputs and status bits are those of gs_bin_sort, minus the
- * workspace. Limit: gs_bin_sort_workspace_bytes(N, V, capacity, n_tiles)
+ * workspace and the optional depth keys (the depths are read from the
+ * projected records). Limit: gs_bin_sort_workspace_bytes(N, V, capacity, n_tiles)
  * must not exceed GS_STATIC_SCRATCH_BYTES (about 20 V N + 12 capacity bytes),
  * else GS_ERR_TOO_LARGE is returned and nothing is enqueued.
  * The first call on a device looks up the array's device address (with that

@@ -58,10 +58,10 @@ _SIGNATURES = {
     "gs_version": ([], ctypes.c_int),
     "gs_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "gs_layout_totals": ([_VP, _I32, _VP, _VP, _VP], ctypes.c_int),
-    "gs_project": ([_VP] * 5 + [_I64, _VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "gs_project": ([_VP] * 5 + [_I64, _VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "gs_bin_sort_workspace_bytes": ([_I64, _I32, _I64, _I64], ctypes.c_size_t),
-    "gs_bin_sort": ([_VP, _VP, _VP, _I64, _VP, _I32, _VP, _VP, _VP, _I64, _VP, _VP, _VP, ctypes.c_size_t, _VP, _VP],
-                    ctypes.c_int),
+    "gs_bin_sort": ([_VP, _VP, _VP, _VP, _I64, _VP, _I32, _VP, _VP, _VP, _I64, _VP, _VP, _VP, ctypes.c_size_t, _VP,
+                     _VP], ctypes.c_int),
     "gs_bin_sort_static": ([_VP, _VP, _VP, _I64, _VP, _I32, _VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP], ctypes.c_int),
     "gs_rasterize_fwd": ([_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "gs_rasterize_bwd": ([_VP] * 5 + [_I64, _VP, _VP, _I32, _VP] + [_VP] * 7 + [_VP] * 6 + [_VP, _VP], ctypes.c_int),
@@ -74,7 +74,7 @@ _SIGNATURES = {
     "gs_morton_order": ([_VP, _I64, _VP, _VP, _VP, ctypes.c_size_t, _VP, _VP], ctypes.c_int),
     "gs_gather_rows": ([_VP, _VP, _I64, _I32, _VP, _VP, _VP], ctypes.c_int),
     "gs_bin_sort_partitioned_workspace_bytes": ([_I64, _I32, _I64, _I64, _I32], ctypes.c_size_t),
-    "gs_bin_sort_partitioned": ([_VP, _VP, _VP, _I64, _VP, _I32, _VP, _VP, _VP, _I64, _VP, _VP, _I32, _VP,
+    "gs_bin_sort_partitioned": ([_VP, _VP, _VP, _VP, _I64, _VP, _I32, _VP, _VP, _VP, _I64, _VP, _VP, _I32, _VP,
                                  ctypes.c_size_t, _VP, _VP], ctypes.c_int),
     "gs_densify_stats": ([_VP, _VP, _VP, _I64, _VP, _I32, _VP, _VP, _VP, _VP], ctypes.c_int),
 }
@@ -154,12 +154,12 @@ def gs_layout_totals(sizes, cfg):
 
 
 def gs_project(means, log_scales, quats, opacity_logits, sh, cams, sizes, cfg, projected, rects, counts, status,
-               stream=None):
+               stream=None, depth_keys=None):
     sz = _sizes(sizes)
     c, cref = _cfg_ref(cfg)
     rc = load().gs_project(_ptr(means), _ptr(log_scales), _ptr(quats), _ptr(opacity_logits), _ptr(sh),
                            means.shape[0], _ptr(cams), _ptr(sz), sz.shape[0], cref, _ptr(projected), _ptr(rects),
-                           _ptr(counts), _ptr(status), _stream(stream))
+                           _ptr(counts), _ptr(depth_keys), _ptr(status), _stream(stream))
     _check(rc, "gs_project")
 
 
@@ -168,10 +168,11 @@ def gs_bin_sort_workspace_bytes(N, V, capacity, n_tiles) -> int:
 
 
 def gs_bin_sort(projected, rects, counts, N, sizes, cfg, keys, vals, capacity, tile_ranges, n_isect, workspace,
-                status, stream=None):
+                status, stream=None, depth_keys=None):
     sz = _sizes(sizes)
     c, cref = _cfg_ref(cfg)
-    rc = load().gs_bin_sort(_ptr(projected), _ptr(rects), _ptr(counts), int(N), _ptr(sz), sz.shape[0], cref,
+    rc = load().gs_bin_sort(_ptr(projected), _ptr(rects), _ptr(counts), _ptr(depth_keys), int(N), _ptr(sz),
+                            sz.shape[0], cref,
                             _ptr(keys), _ptr(vals), int(capacity), _ptr(tile_ranges), _ptr(n_isect), _ptr(workspace),
                             workspace.numel() * workspace.element_size(), _ptr(status), _stream(stream))
     _check(rc, "gs_bin_sort")
@@ -183,10 +184,11 @@ def gs_bin_sort_partitioned_workspace_bytes(N, V, capacity, n_tiles, partitions)
 
 
 def gs_bin_sort_partitioned(projected, rects, counts, N, sizes, cfg, keys, vals, capacity, tile_ranges, n_isect,
-                            partitions, workspace, status, stream=None):
+                            partitions, workspace, status, stream=None, depth_keys=None):
     sz = _sizes(sizes)
     c, cref = _cfg_ref(cfg)
-    rc = load().gs_bin_sort_partitioned(_ptr(projected), _ptr(rects), _ptr(counts), int(N), _ptr(sz), sz.shape[0],
+    rc = load().gs_bin_sort_partitioned(_ptr(projected), _ptr(rects), _ptr(counts), _ptr(depth_keys), int(N),
+                                        _ptr(sz), sz.shape[0],
                                         cref, _ptr(keys), _ptr(vals), int(capacity), _ptr(tile_ranges),
                                         _ptr(n_isect), int(partitions), _ptr(workspace),
                                         workspace.numel() * workspace.element_size(), _ptr(status), _stream(stream))

@@ -129,10 +129,14 @@ __device__ __forceinline__ uint64_t block_scan_lookback(uint64_t local, uint32_t
 // 1a. Compaction of visible records: (depth bits, record) pairs in record
 //     order, plus the digit histograms of the four depth passes.
 // ---------------------------------------------------------------------------
+// With depth_keys (float bits of each record's depth, 0 for a culled record,
+// as gs_project writes them) the kernel reads 4 coalesced bytes per record;
+// without, the tile counts and a gather of the depth from each 48-byte
+// projected record.
 __global__ void __launch_bounds__(kScanThreads) compact_visible_kernel(
-    const uint32_t* __restrict__ counts, const float* __restrict__ projected, int64_t n, uint32_t index_base,
-    ScanState st, uint32_t* __restrict__ dkeys, uint32_t* __restrict__ dvals, uint32_t* __restrict__ hist,
-    int64_t* n_visible, int32_t* status) {
+    const uint32_t* __restrict__ counts, const float* __restrict__ projected, const uint32_t* __restrict__ depth_keys,
+    int64_t n, uint32_t index_base, ScanState st, uint32_t* __restrict__ dkeys, uint32_t* __restrict__ dvals,
+    uint32_t* __restrict__ hist, int64_t* n_visible, int32_t* status) {
   __shared__ uint32_t s_tile;
   __shared__ uint64_t s_warp[kScanThreads / 32];
   __shared__ uint64_t s_prefix;
@@ -144,15 +148,26 @@ __global__ void __launch_bounds__(kScanThreads) compact_visible_kernel(
   const uint32_t t = s_tile;
   const int64_t base = static_cast<int64_t>(t) * kScanTile + static_cast<int64_t>(tid) * kScanItems;
   uint32_t vis = 0;  // bit i: item i visible
+  uint32_t dkey[kScanItems];
+  if (depth_keys) {
 #pragma unroll
-  for (int i = 0; i < kScanItems; ++i)
-    if (base + i < n && counts[base + i] > 0) vis |= 1u << i;
+    for (int i = 0; i < kScanItems; ++i) {
+      dkey[i] = base + i < n ? depth_keys[base + i] : 0u;
+      if (dkey[i] != 0u) vis |= 1u << i;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+      dkey[i] = 0u;
+      if (base + i < n && counts[base + i] > 0) vis |= 1u << i;
+    }
+  }
   const uint64_t pos0 = block_scan_lookback(__popc(vis), t, st, s_warp, &s_prefix, status);
   uint64_t pos = pos0;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     if (vis & (1u << i)) {
-      const uint32_t d = __float_as_uint(projected[(base + i) * kRecordFloats + 6]);
+      const uint32_t d = depth_keys ? dkey[i] : __float_as_uint(projected[(base + i) * kRecordFloats + 6]);
       dkeys[pos] = d;
       dvals[pos] = index_base + static_cast<uint32_t>(base + i);
 #pragma unroll
@@ -895,7 +910,8 @@ namespace {
 
 bool valid_partitions(int P) { return P >= 1 && P <= 64 && (P & (P - 1)) == 0; }
 
-int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* counts, int64_t N,
+int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* counts, const uint32_t* depth_keys,
+                  int64_t N,
                   const int32_t* sizes, int32_t V, const gs_config* cfg, uint64_t* keys, uint32_t* vals,
                   int64_t capacity, uint32_t* tile_ranges, int64_t* n_isect_dev, void* workspace,
                   size_t workspace_bytes, int32_t* status_dev, cudaStream_t stream, int P) {
@@ -942,8 +958,8 @@ int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* 
   if (P == 1) {
     ScanState st1{reinterpret_cast<uint64_t*>(ws + w.scan1), tickets + 0};
     uint32_t* hist_d = u32(w.hist_d);
-    compact_visible_kernel<<<scan_grid, kScanThreads, 0, stream>>>(counts, projected, VN, 0u, st1, dk[0], dv[0],
-                                                                     hist_d, n_visible, status_dev);
+    compact_visible_kernel<<<scan_grid, kScanThreads, 0, stream>>>(counts, projected, depth_keys, VN, 0u, st1, dk[0],
+                                                                     dv[0], hist_d, n_visible, status_dev);
     hist_scan_kernel<<<1, kRadix, 0, stream>>>(hist_d, kDepthPasses);
     // 1b. four depth passes (even count: the result is back in dk[0], dv[0])
     for (int p = 0; p < kDepthPasses; ++p) {
@@ -971,7 +987,8 @@ int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* 
       if (cnt <= 0) continue;  // an empty partition keeps part_n = 0
       ScanState stp{part_scan + static_cast<size_t>(p) * (w.part_scan_tiles + 1), part_tickets + p * kPartTickets};
       compact_visible_kernel<<<static_cast<unsigned>((cnt + kScanTile - 1) / kScanTile), kScanThreads, 0, stream>>>(
-          counts + lo, projected + lo * kRecordFloats, cnt, static_cast<uint32_t>(lo), stp, dk[0] + lo, dv[0] + lo,
+          counts + lo, projected + lo * kRecordFloats, depth_keys ? depth_keys + lo : nullptr, cnt,
+          static_cast<uint32_t>(lo), stp, dk[0] + lo, dv[0] + lo,
           part_hist + p * kDepthPasses * kRadix, part_n + p, status_dev);
     }
     hist_scan_kernel<<<1, kRadix, 0, stream>>>(part_hist, kDepthPasses * P);
@@ -1091,11 +1108,12 @@ extern "C" size_t gs_bin_sort_workspace_bytes(int64_t N, int32_t V, int64_t capa
   return gs::ws_layout(N, V, capacity, n_tiles).total;
 }
 
-extern "C" int gs_bin_sort(const float* projected, const int16_t* rects, const uint32_t* counts, int64_t N,
-                           const int32_t* sizes, int32_t V, const gs_config* cfg, uint64_t* keys, uint32_t* vals,
-                           int64_t capacity, uint32_t* tile_ranges, int64_t* n_isect_dev, void* workspace,
-                           size_t workspace_bytes, int32_t* status_dev, gs_stream_t stream) {
-  return gs::bin_sort_impl(projected, rects, counts, N, sizes, V, cfg, keys, vals, capacity, tile_ranges, n_isect_dev,
+extern "C" int gs_bin_sort(const float* projected, const int16_t* rects, const uint32_t* counts,
+                           const uint32_t* depth_keys, int64_t N, const int32_t* sizes, int32_t V, const gs_config* cfg,
+                           uint64_t* keys, uint32_t* vals, int64_t capacity, uint32_t* tile_ranges,
+                           int64_t* n_isect_dev, void* workspace, size_t workspace_bytes, int32_t* status_dev,
+                           gs_stream_t stream) {
+  return gs::bin_sort_impl(projected, rects, counts, depth_keys, N, sizes, V, cfg, keys, vals, capacity, tile_ranges, n_isect_dev,
                            workspace, workspace_bytes, status_dev, reinterpret_cast<cudaStream_t>(stream), 1);
 }
 
@@ -1105,11 +1123,12 @@ extern "C" size_t gs_bin_sort_partitioned_workspace_bytes(int64_t N, int32_t V, 
   return gs::ws_layout(N, V, capacity, n_tiles, partitions).total;
 }
 
-extern "C" int gs_bin_sort_partitioned(const float* projected, const int16_t* rects, const uint32_t* counts, int64_t N,
-                                       const int32_t* sizes, int32_t V, const gs_config* cfg, uint64_t* keys,
-                                       uint32_t* vals, int64_t capacity, uint32_t* tile_ranges, int64_t* n_isect_dev,
-                                       int32_t partitions, void* workspace, size_t workspace_bytes,
-                                       int32_t* status_dev, gs_stream_t stream) {
-  return gs::bin_sort_impl(projected, rects, counts, N, sizes, V, cfg, keys, vals, capacity, tile_ranges, n_isect_dev,
+extern "C" int gs_bin_sort_partitioned(const float* projected, const int16_t* rects, const uint32_t* counts,
+                                       const uint32_t* depth_keys, int64_t N, const int32_t* sizes, int32_t V,
+                                       const gs_config* cfg, uint64_t* keys, uint32_t* vals, int64_t capacity,
+                                       uint32_t* tile_ranges, int64_t* n_isect_dev, int32_t partitions,
+                                       void* workspace, size_t workspace_bytes, int32_t* status_dev,
+                                       gs_stream_t stream) {
+  return gs::bin_sort_impl(projected, rects, counts, depth_keys, N, sizes, V, cfg, keys, vals, capacity, tile_ranges, n_isect_dev,
                            workspace, workspace_bytes, status_dev, reinterpret_cast<cudaStream_t>(stream), partitions);
 }

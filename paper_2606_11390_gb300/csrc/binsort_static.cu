@@ -63,6 +63,6 @@ extern "C" int gs_bin_sort_static(const float* projected, const int16_t* rects, 
   if (arc != GS_OK) return arc;
   // gs_bin_sort clears the part of its workspace that must start at zero on
   // every call, so whatever an earlier call left in the array is harmless.
-  return gs_bin_sort(projected, rects, counts, N, sizes, V, cfg, keys, vals, capacity, tile_ranges, n_isect_dev,
+  return gs_bin_sort(projected, rects, counts, nullptr, N, sizes, V, cfg, keys, vals, capacity, tile_ranges, n_isect_dev,
                      scratch, static_cast<size_t>(GS_STATIC_SCRATCH_BYTES), status_dev, stream);
 }

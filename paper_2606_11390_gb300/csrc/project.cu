@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(kProjBlock) project_fwd_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ opac, const float* __restrict__ sh, int64_t N, const gs_camera* __restrict__ cams,
     const Layout L, const Consts K, float4* __restrict__ projected, short4* __restrict__ rects,
-    uint32_t* __restrict__ counts, int use_bulk, int64_t ahead, int32_t* status) {
+    uint32_t* __restrict__ counts, uint32_t* __restrict__ depth_keys, int use_bulk, int64_t ahead, int32_t* status) {
   __shared__ ProjFwdSmem sm;
   const int tid = threadIdx.x;
   const int64_t g0 = static_cast<int64_t>(blockIdx.x) * kProjBlock;
@@ -431,6 +431,7 @@ __global__ void __launch_bounds__(kProjBlock) project_fwd_kernel(
       const int64_t vg = static_cast<int64_t>(v) * N + g0 + tid;
       counts[vg] = P.count;
       rects[vg] = P.visible ? make_short4(P.x0, P.y0, P.x1, P.y1) : make_short4(0, 0, 0, 0);
+      if (depth_keys) depth_keys[vg] = P.visible ? __float_as_uint(P.t[2]) : 0u;
       if (P.visible) {
         float dvec[3], dnorm;
         view_dir(cam, G.mean, dvec, dnorm);
@@ -699,7 +700,7 @@ int launch_project_bwd(const float* means, const float* log_scales, const float*
 extern "C" int gs_project(const float* means, const float* log_scales, const float* quats,
                           const float* opacity_logits, const float* sh, int64_t N, const gs_camera* cams_dev,
                           const int32_t* sizes, int32_t V, const gs_config* cfg, float* projected, int16_t* rects,
-                          uint32_t* counts, int32_t* status_dev, gs_stream_t stream) {
+                          uint32_t* counts, uint32_t* depth_keys, int32_t* status_dev, gs_stream_t stream) {
   using namespace gs;
   if (N < 0 || !cfg || cfg->sh_degree < 0 || cfg->sh_degree > 3) return GS_ERR_ARG;
   Layout L;
@@ -718,8 +719,8 @@ extern "C" int gs_project(const float* means, const float* log_scales, const flo
 #define GS_PFWD(D)                                                                                               \
   project_fwd_kernel<D><<<blocks, kProjBlock, 0, st>>>(means, log_scales, quats, opacity_logits, sh, N, cams_dev, L, K, \
                                                        reinterpret_cast<float4*>(projected),                           \
-                                                       reinterpret_cast<short4*>(rects), counts, bulk ? 1 : 0,          \
-                                                       resident_ctas<D>(project_fwd_kernel<D>), status_dev)
+                                                       reinterpret_cast<short4*>(rects), counts, depth_keys,            \
+                                                       bulk ? 1 : 0, resident_ctas<D>(project_fwd_kernel<D>), status_dev)
   switch (cfg->sh_degree) {
     case 0: GS_PFWD(0); break;
     case 1: GS_PFWD(1); break;

@@ -100,6 +100,7 @@ class Frame:
         self.projected = torch.zeros(V * N * gs.RECORD_FLOATS, **f32)
         self.rects = torch.zeros(V * N * 4, dtype=torch.int16, device=device)
         self.counts = torch.zeros(V * N, **i32)
+        self.depth_keys = torch.zeros(V * N, **i32)  # depth bits of visible records, read by the sort
         order = bool(self.cfg.get("flags", 0) & gs.GS_FLAG_TILE_ORDER)
         self.tile_ranges = torch.zeros(self.n_tiles * (3 if order else 2), **i32)
         self.ranges = self.tile_ranges[:2 * self.n_tiles]  # [n_tiles][2] start, end
@@ -140,18 +141,20 @@ class Frame:
 
 def project(params: FlatParams, cams: Cameras, frame: Frame, stream=None):
     gs.gs_project(params["means"], params["log_scales"], params["quats"], params["opacity_logits"], params["sh"],
-                  cams.dev, cams.sizes, frame.cfg, frame.projected, frame.rects, frame.counts, frame.status, stream)
+                  cams.dev, cams.sizes, frame.cfg, frame.projected, frame.rects, frame.counts, frame.status, stream,
+                  depth_keys=frame.depth_keys)
 
 
 def bin_sort(frame: Frame, stream=None):
     if frame.partitions == 1:
         gs.gs_bin_sort(frame.projected, frame.rects, frame.counts, frame.N, frame.cams.sizes, frame.cfg, frame.keys,
                        frame.vals, frame.capacity, frame.tile_ranges, frame.n_isect, frame.workspace, frame.status,
-                       stream)
+                       stream, depth_keys=frame.depth_keys)
     else:
         gs.gs_bin_sort_partitioned(frame.projected, frame.rects, frame.counts, frame.N, frame.cams.sizes, frame.cfg,
                                    frame.keys, frame.vals, frame.capacity, frame.tile_ranges, frame.n_isect,
-                                   frame.partitions, frame.workspace, frame.status, stream)
+                                   frame.partitions, frame.workspace, frame.status, stream,
+                                   depth_keys=frame.depth_keys)
 
 
 def rasterize_fwd(frame: Frame, stream=None):
