@@ -170,7 +170,7 @@ GS_API int gs_project(const float* means, const float* log_scales, const float* 
 
 /* Bytes of device workspace gs_bin_sort needs for N Gaussians, V views, a
  * key capacity and n_tiles tiles (from gs_layout_totals); 0 for invalid
- * arguments. About 20 V N + 12 capacity bytes. */
+ * arguments. About 16 V N + 12 capacity bytes. */
 GS_API size_t gs_bin_sort_workspace_bytes(int64_t N, int32_t V, int64_t capacity, int64_t n_tiles);
 
 /* gs_bin_sort - tile keys and per-camera depth sort.
@@ -243,7 +243,7 @@ GS_API int gs_bin_sort_partitioned(const float* projected, const int16_t* rects,
  * Arguments, outputs and status bits are those of gs_bin_sort, minus the
  * workspace and the optional depth keys (the depths are read from the
  * projected records). Limit: gs_bin_sort_workspace_bytes(N, V, capacity, n_tiles)
- * must not exceed GS_STATIC_SCRATCH_BYTES (about 20 V N + 12 capacity bytes),
+ * must not exceed GS_STATIC_SCRATCH_BYTES (about 16 V N + 12 capacity bytes),
  * else GS_ERR_TOO_LARGE is returned and nothing is enqueued.
  * The first call on a device looks up the array's device address (with that
  * device current); make that first call before any stream capture.

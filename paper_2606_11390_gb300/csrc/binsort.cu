@@ -184,72 +184,79 @@ __global__ void __launch_bounds__(kScanThreads) compact_visible_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// 1c. Exclusive scan of the tile counts of the depth-sorted records.
+// 1c + 2a. Tile-count offsets in depth order and emission in one kernel.
+//     Each CTA takes a tile of 1024 depth-sorted records by ticket, scans
+//     their tile counts (block scan + decoupled look-back, clamped at the
+//     capacity), then expands them one warp per 32 records, load-balanced:
+//     the warp scans the records' counts, and lane l produces entries l,
+//     l + 32, ... of the warp's concatenated output, finding the record of
+//     each entry from the record starts of the round. All lanes stay busy
+//     whatever the record sizes, and each warp store writes 32 consecutive
+//     positions except at record boundaries. The tile-id digit histograms of
+//     the tile passes are gathered on the way with shared atomics.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kScanThreads) scan_sorted_counts_kernel(
-    const uint32_t* __restrict__ counts, const uint32_t* __restrict__ order, const int64_t* n_visible, ScanState st,
-    uint32_t* __restrict__ offsets, uint64_t capacity, int64_t* n_total, int32_t* status) {
+constexpr int kEmitThreads = 256;
+static_assert(kEmitThreads == kScanThreads, "the emission scans its records with the block scan");
+constexpr int kEmitItems = 4;                              // records per thread in the count scan
+constexpr int kEmitTile = kEmitThreads * kEmitItems;       // records per emission tile
+constexpr int kEmitGroups = kEmitTile / 32;                // 32-record groups per tile
+
+__global__ void __launch_bounds__(kEmitThreads) emit_tiles_kernel(
+    const uint32_t* __restrict__ order, const int64_t* n_visible, const uint32_t* __restrict__ counts,
+    const short4* __restrict__ rects, int64_t N, const Layout L, uint64_t capacity, int tile_passes, ScanState st,
+    uint32_t* __restrict__ tkeys, uint32_t* __restrict__ tvals, uint32_t* __restrict__ hist, int64_t* n_total,
+    int32_t* status) {
+  __shared__ uint32_t s_hist[kMaxTilePasses][kRadix];
+  __shared__ uint32_t s_vg[kEmitTile], s_cnt[kEmitTile], s_off[kEmitTile];
   __shared__ uint32_t s_tile;
   __shared__ uint64_t s_warp[kScanThreads / 32];
   __shared__ uint64_t s_prefix;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
   if (tid == 0) s_tile = atomicAdd(st.ticket, 1u);
+  for (int i = tid; i < kMaxTilePasses * kRadix; i += kEmitThreads) (&s_hist[0][0])[i] = 0;
   __syncthreads();
   const uint32_t t = s_tile;
   const int64_t n = *n_visible;
-  if (static_cast<int64_t>(t) * kScanTile >= n) return;  // past the data: publishes nothing, awaited by nobody
-  const int64_t base = static_cast<int64_t>(t) * kScanTile + static_cast<int64_t>(tid) * kScanItems;
-  uint32_t c[kScanItems];
+  const int64_t tile0 = static_cast<int64_t>(t) * kEmitTile;
+  if (tile0 >= n) return;  // past the data: publishes nothing, awaited by nobody
+  // 1. the tile's records (depth order) and their tile counts, scanned with
+  //    decoupled look-back: output offsets, clamped at the capacity
+  const int64_t base = tile0 + static_cast<int64_t>(tid) * kEmitItems;
+  uint32_t c[kEmitItems];
   uint64_t local = 0;
 #pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    c[i] = (base + i < n) ? counts[order[base + i]] : 0u;
+  for (int i = 0; i < kEmitItems; ++i) {
+    const uint32_t vg = base + i < n ? order[base + i] : 0u;
+    c[i] = base + i < n ? counts[vg] : 0u;
+    s_vg[tid * kEmitItems + i] = vg;
+    s_cnt[tid * kEmitItems + i] = c[i];
     local += c[i];
   }
   uint64_t run = block_scan_lookback(local, t, st, s_warp, &s_prefix, status);
 #pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    if (base + i < n) offsets[base + i] = static_cast<uint32_t>(run < capacity ? run : capacity);
+  for (int i = 0; i < kEmitItems; ++i) {
+    s_off[tid * kEmitItems + i] = static_cast<uint32_t>(run < capacity ? run : capacity);
     run += c[i];
   }
-  if (base <= n - 1 && n - 1 < base + kScanItems) {
+  if (base <= n - 1 && n - 1 < base + kEmitItems) {
     *n_total = static_cast<int64_t>(run);
     if (run > capacity) set_status(status, GS_STATUS_CAPACITY);
   }
-}
-
-// ---------------------------------------------------------------------------
-// 2a. Emission, one warp per 32 depth-sorted records, load-balanced: the
-//     warp scans the records' tile counts, and lane l produces entries
-//     l, l + 32, ... of the warp's concatenated output, finding the record of
-//     each entry by a 5-step shuffle search. All lanes stay busy whatever the
-//     record sizes, and each warp store writes 32 consecutive positions
-//     except at record boundaries. The tile-id digit histograms of the tile
-//     passes are gathered on the way with shared atomics.
-// ---------------------------------------------------------------------------
-constexpr int kEmitThreads = 256;
-
-__global__ void __launch_bounds__(kEmitThreads) emit_tiles_kernel(
-    const uint32_t* __restrict__ order, const uint32_t* __restrict__ offsets, const int64_t* n_visible,
-    const uint32_t* __restrict__ counts, const short4* __restrict__ rects, int64_t N, const Layout L,
-    uint64_t capacity, int tile_passes, uint32_t* __restrict__ tkeys, uint32_t* __restrict__ tvals,
-    uint32_t* __restrict__ hist) {
-  __shared__ uint32_t s_hist[kMaxTilePasses][kRadix];
-  const int tid = threadIdx.x, lane = tid & 31;
-  for (int i = tid; i < kMaxTilePasses * kRadix; i += kEmitThreads) (&s_hist[0][0])[i] = 0;
   __syncthreads();
-  const int64_t n = *n_visible;
+  // 2. emission, one warp per group of 32 records, load-balanced: the warp
+  //    scans the records' counts, and lane l produces entries l, l + 32, ...
+  //    of the group's concatenated output, finding the record of each entry
+  //    from the record starts of the round. The tile-id digit histograms of
+  //    the tile passes are gathered on the way with shared atomics.
   const float invN = 1.0f / static_cast<float>(N);
-  const int64_t warps_total = static_cast<int64_t>(gridDim.x) * (kEmitThreads / 32);
-  for (int64_t w = static_cast<int64_t>(blockIdx.x) * (kEmitThreads / 32) + (tid >> 5); w * 32 < n;
-       w += warps_total) {
-    const int64_t j = w * 32 + lane;
-    uint32_t vg = 0, cnt = 0, off = 0, tb = 0, xy = 0, wn = 1;
+  for (int g = tid >> 5; g < kEmitGroups && capacity > 0; g += kEmitThreads / 32) {
+    const int r = g * 32 + lane;
+    const int64_t j = tile0 + r;
+    uint32_t vg = 0, cnt = 0, tb = 0, xy = 0, wn = 1;
     if (j < n) {
-      vg = order[j];
-      cnt = counts[vg];
-      off = offsets[j];
-      const short4 r = rects[vg];
+      vg = s_vg[r];
+      cnt = s_cnt[r];
+      const short4 rc = rects[vg];
       // view index v = vg / N by float quotient and exact fix-up (one view: 0)
       int v = 0;
       if (L.V > 1) {
@@ -259,11 +266,11 @@ __global__ void __launch_bounds__(kEmitThreads) emit_tiles_kernel(
       }
       tb = L.tile_base[v];
       // packed record fields: (x0, y0) and (width, tiles per row), 16 bits each
-      xy = static_cast<uint32_t>(static_cast<uint16_t>(r.x)) | (static_cast<uint32_t>(static_cast<uint16_t>(r.y)) << 16);
-      wn = static_cast<uint32_t>(r.z - r.x) | (static_cast<uint32_t>(L.ntx[v]) << 16);
+      xy = static_cast<uint32_t>(static_cast<uint16_t>(rc.x)) | (static_cast<uint32_t>(static_cast<uint16_t>(rc.y)) << 16);
+      wn = static_cast<uint32_t>(rc.z - rc.x) | (static_cast<uint32_t>(L.ntx[v]) << 16);
     }
-    // exclusive prefix of the counts within the warp; the warp's entries are
-    // contiguous in the output from the first record's offset
+    // exclusive prefix of the counts within the group; the group's entries are
+    // contiguous in the output from its first record's offset
     uint32_t incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -272,18 +279,18 @@ __global__ void __launch_bounds__(kEmitThreads) emit_tiles_kernel(
     }
     const uint32_t excl = incl - cnt;
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-    const uint64_t out_base = __shfl_sync(0xffffffffu, off, 0);
+    const uint64_t out_base = s_off[g * 32];
     const uint32_t le_mask = 0xffffffffu >> (31 - lane);  // bits 0..lane
     uint32_t started = 0;  // records (lanes) whose entries start before this round
-    for (uint32_t base = 0; base < total; base += 32) {
-      // bit i: a record's first entry is entry base + i (records have count >= 1,
-      // so the starts are distinct); the record of entry base + lane is the
+    for (uint32_t eb = 0; eb < total; eb += 32) {
+      // bit i: a record's first entry is entry eb + i (records have count >= 1,
+      // so the starts are distinct); the record of entry eb + lane is the
       // last one started at or before it
-      const uint32_t st = (cnt > 0 && excl >= base && excl - base < 32u) ? (1u << (excl - base)) : 0u;
-      const uint32_t starts = __reduce_or_sync(0xffffffffu, st);
+      const uint32_t stb = (cnt > 0 && excl >= eb && excl - eb < 32u) ? (1u << (excl - eb)) : 0u;
+      const uint32_t starts = __reduce_or_sync(0xffffffffu, stb);
       const int src = static_cast<int>(started + __popc(starts & le_mask)) - 1;
       started += __popc(starts);
-      const uint32_t e = base + lane;
+      const uint32_t e = eb + lane;
       const uint32_t k = e - __shfl_sync(0xffffffffu, excl, src);
       const uint32_t r_vg = __shfl_sync(0xffffffffu, vg, src);
       const uint32_t r_xy = __shfl_sync(0xffffffffu, xy, src);
@@ -309,8 +316,8 @@ __global__ void __launch_bounds__(kEmitThreads) emit_tiles_kernel(
   }
   __syncthreads();
   for (int i = tid; i < tile_passes * kRadix; i += kEmitThreads) {
-    const uint32_t c = (&s_hist[0][0])[i];
-    if (c) atomicAdd(hist + i, c);
+    const uint32_t cc = (&s_hist[0][0])[i];
+    if (cc) atomicAdd(hist + i, cc);
   }
 }
 
@@ -781,10 +788,10 @@ int tile_passes_for(int64_t n_tiles) {
 }
 
 struct WsLayout {
-  size_t dkeys0, dvals0, dkeys1, dvals1, offsets, tkeys0, tkeys1, tvals_alt;
+  size_t dkeys0, dvals0, dkeys1, dvals1, tkeys0, tkeys1, tvals_alt;
   size_t zero_begin, scan1, scan2, hist_d, hist_t, tickets, n_visible, lb_depth, lb_tile;
   size_t part_scan, part_hist, part_tickets, part_n, part_lb, zero_end, total;
-  int64_t n_scan_tiles, n_depth_tiles, n_tile_tiles;
+  int64_t n_scan_tiles, n_emit_tiles, n_depth_tiles, n_tile_tiles;
   int64_t part_stride, part_scan_tiles, part_sort_tiles;
   int tile_passes;
 };
@@ -797,7 +804,7 @@ WsLayout ws_layout(int64_t N, int32_t V, int64_t capacity, int64_t n_tiles, int 
   const int64_t VN = N * V;
   w.part_stride = P > 1 ? (VN + P - 1) / P : VN;
   const int64_t depth_slots = P > 1 ? w.part_stride * P : VN;
-  const size_t vn = static_cast<size_t>(VN > 0 ? VN : 1), cap = static_cast<size_t>(capacity > 0 ? capacity : 1);
+  const size_t cap = static_cast<size_t>(capacity > 0 ? capacity : 1);
   const size_t ds = static_cast<size_t>(depth_slots > 0 ? depth_slots : 1);
   w.tile_passes = tile_passes_for(n_tiles);
   w.n_scan_tiles = (VN + kScanTile - 1) / kScanTile;
@@ -810,13 +817,13 @@ WsLayout ws_layout(int64_t N, int32_t V, int64_t capacity, int64_t n_tiles, int 
   w.dvals0 = o; o = align256(o + 4 * ds);
   w.dkeys1 = o; o = align256(o + 4 * ds);
   w.dvals1 = o; o = align256(o + 4 * ds);
-  w.offsets = o; o = align256(o + 4 * vn);
   w.tkeys0 = o; o = align256(o + 4 * cap);
   w.tkeys1 = o; o = align256(o + 4 * cap);
   w.tvals_alt = o; o = align256(o + 4 * cap);
   w.zero_begin = o;
   w.scan1 = o; o = align256(o + 8 * static_cast<size_t>(w.n_scan_tiles + 1));
-  w.scan2 = o; o = align256(o + 8 * static_cast<size_t>(w.n_scan_tiles + 1));
+  w.n_emit_tiles = (VN + kEmitTile - 1) / kEmitTile;
+  w.scan2 = o; o = align256(o + 8 * static_cast<size_t>(w.n_emit_tiles + 1));
   w.hist_d = o; o = align256(o + 4 * kDepthPasses * kRadix);
   w.hist_t = o; o = align256(o + 4 * kMaxTilePasses * kRadix);
   w.tickets = o; o = align256(o + 4 * 16);
@@ -1021,20 +1028,10 @@ int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* 
     }
     order = dv[src];
   }
-  // 1c. tile-count offsets in depth order
+  // 1c + 2a. tile-count offsets in depth order and emission, one kernel; the
+  //     buffers are chosen so that the last tile pass writes the values into
+  //     `vals`
   ScanState st2{reinterpret_cast<uint64_t*>(ws + w.scan2), tickets + 1};
-  uint32_t* offsets = u32(w.offsets);
-  scan_sorted_counts_kernel<<<scan_grid, kScanThreads, 0, stream>>>(counts, order, n_visible, st2, offsets,
-                                                                      static_cast<uint64_t>(capacity), n_isect_dev,
-                                                                      status_dev);
-  if (capacity == 0) {
-    if (cfg->flags & GS_FLAG_TILE_ORDER)
-      tile_order_kernel<<<1, kOrderThreads, 0, stream>>>(reinterpret_cast<const uint2*>(tile_ranges), L.n_tiles,
-                                                         tile_ranges + 2 * L.n_tiles);
-    return cuda_status(cudaGetLastError());
-  }
-  // 2a. emission in depth order; the buffers are chosen so that the last tile
-  //     pass writes the values into `vals`
   const int TP = w.tile_passes;
   uint32_t* tk[2] = {u32(w.tkeys0), u32(w.tkeys1)};
   uint32_t* tv[2];
@@ -1042,9 +1039,15 @@ int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* 
   tv[(TP + 1) & 1] = u32(w.tvals_alt);
   uint32_t* hist_t = u32(w.hist_t);
   const int n_sm = sm_count();
-  emit_tiles_kernel<<<static_cast<unsigned>(4 * n_sm), kEmitThreads, 0, stream>>>(
-      order, offsets, n_visible, counts, reinterpret_cast<const short4*>(rects), N, L,
-      static_cast<uint64_t>(capacity), TP, tk[0], tv[0], hist_t);
+  emit_tiles_kernel<<<static_cast<unsigned>(w.n_emit_tiles), kEmitThreads, 0, stream>>>(
+      order, n_visible, counts, reinterpret_cast<const short4*>(rects), N, L, static_cast<uint64_t>(capacity), TP, st2,
+      capacity > 0 ? tk[0] : nullptr, capacity > 0 ? tv[0] : nullptr, hist_t, n_isect_dev, status_dev);
+  if (capacity == 0) {
+    if (cfg->flags & GS_FLAG_TILE_ORDER)
+      tile_order_kernel<<<1, kOrderThreads, 0, stream>>>(reinterpret_cast<const uint2*>(tile_ranges), L.n_tiles,
+                                                         tile_ranges + 2 * L.n_tiles);
+    return cuda_status(cudaGetLastError());
+  }
   // 2b. stable tile-id passes
   if (TP > 0) hist_scan_kernel<<<1, kRadix, 0, stream>>>(hist_t, TP);
   for (int p = 0; p < TP; ++p) {
