@@ -275,6 +275,27 @@ GS_API int gs_rasterize_fwd(const float* projected, const uint32_t* vals, const 
                      int32_t V, const gs_config* cfg, float* image, float* final_T, uint32_t* last,
                      gs_stream_t stream);
 
+/* gs_rasterize_fwd_l1l2 - gs_rasterize_fwd with the L1 + L2 image loss of
+ * gs_image_loss computed in the same kernel, as each pixel's colour is final
+ * (the rendered image is not read back). Paper: §4, rasterisation and the
+ * per-camera image loss; the loss is the workloads' L = w_l1 mean|r| +
+ * w_l2 mean(r^2), r = image - target, means over n_values values.
+ * in  (device): as gs_rasterize_fwd; target [P][3] laid out like image.
+ * in  (host)  : as gs_rasterize_fwd; n_values (>= 3 P; the total over all
+ *               calls whose losses add up, e.g. all views rendered one call
+ *               per view); accumulate (0: loss_dev is zeroed first, else the
+ *               call adds to it).
+ * out (device): image, final_T, last as gs_rasterize_fwd; dL_dimage [P][3]
+ *               = (w_l1 sign(r) + 2 w_l2 r) / n_values, bit-identical to
+ *               gs_image_loss's; loss_dev [1] double += this call's sum of
+ *               (w_l1 |r| + w_l2 r^2) / n_values (atomic adds: the last bits
+ *               depend on their order).
+ * Errors: GS_ERR_ARG (also n_values < 3 P), GS_ERR_UNSUPPORTED, GS_ERR_CUDA. */
+GS_API int gs_rasterize_fwd_l1l2(const float* projected, const uint32_t* vals, const uint32_t* tile_ranges,
+                                 const int32_t* sizes, int32_t V, const gs_config* cfg, float* image, float* final_T,
+                                 uint32_t* last, const float* target, int64_t n_values, float w_l1, float w_l2,
+                                 int32_t accumulate, float* dL_dimage, double* loss_dev, gs_stream_t stream);
+
 /* gs_rasterize_bwd - backward of rasterisation, projection and SH colour.
  * Paper: §4, where the backward pass keeps the forward pass's partitioning
  * and sums gradients with atomics; here device-scope FP32 atomics on one

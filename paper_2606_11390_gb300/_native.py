@@ -64,6 +64,8 @@ _SIGNATURES = {
                      _VP], ctypes.c_int),
     "gs_bin_sort_static": ([_VP, _VP, _VP, _I64, _VP, _I32, _VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP], ctypes.c_int),
     "gs_rasterize_fwd": ([_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "gs_rasterize_fwd_l1l2": ([_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP, _I64, _F32, _F32, _I32, _VP, _VP,
+                               _VP], ctypes.c_int),
     "gs_rasterize_bwd": ([_VP] * 5 + [_I64, _VP, _VP, _I32, _VP] + [_VP] * 7 + [_VP] * 6 + [_VP, _VP], ctypes.c_int),
     "gs_rasterize_bwd_pixels": ([_VP, _VP, _VP, _VP, _I32, _VP, _I64, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "gs_project_bwd": ([_VP] * 5 + [_I64, _VP, _VP, _I32, _VP, _VP, _VP] + [_VP] * 5 + [_VP, _VP], ctypes.c_int),
@@ -213,6 +215,18 @@ def gs_rasterize_fwd(projected, vals, tile_ranges, sizes, cfg, image, final_T, l
     rc = load().gs_rasterize_fwd(_ptr(projected), _ptr(vals), _ptr(tile_ranges), _ptr(sz), sz.shape[0], cref,
                                  _ptr(image), _ptr(final_T), _ptr(last), _stream(stream))
     _check(rc, "gs_rasterize_fwd")
+
+
+def gs_rasterize_fwd_l1l2(projected, vals, tile_ranges, sizes, cfg, image, final_T, last, target, n_values, w_l1,
+                          w_l2, accumulate, dL_dimage, loss, stream=None):
+    """gs_rasterize_fwd with the L1 + L2 loss of gs_image_loss in the same kernel."""
+    sz = _sizes(sizes)
+    c, cref = _cfg_ref(cfg)
+    rc = load().gs_rasterize_fwd_l1l2(_ptr(projected), _ptr(vals), _ptr(tile_ranges), _ptr(sz), sz.shape[0], cref,
+                                      _ptr(image), _ptr(final_T), _ptr(last), _ptr(target), int(n_values),
+                                      float(w_l1), float(w_l2), int(bool(accumulate)), _ptr(dL_dimage), _ptr(loss),
+                                      _stream(stream))
+    _check(rc, "gs_rasterize_fwd_l1l2")
 
 
 def gs_rasterize_bwd(means, log_scales, quats, opacity_logits, sh, cams, sizes, cfg, projected, counts, vals,

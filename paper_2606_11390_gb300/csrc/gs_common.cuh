@@ -114,6 +114,14 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
+// dL/dr of L = (w1 |r| + w2 r^2) / n for one value r, every step a single
+// rounded operation, so that the loss kernel and the forward's fused loss
+// produce the same bits.
+__device__ __forceinline__ float l1l2_grad(float r, float w1, float w2, float inv_n) {
+  const float sg = r > 0.0f ? 1.0f : (r < 0.0f ? -1.0f : 0.0f);
+  return __fmul_rn(__fadd_rn(__fmul_rn(w1, sg), __fmul_rn(__fmul_rn(2.0f, w2), r)), inv_n);
+}
+
 constexpr int kRecordFloats = GS_RECORD_FLOATS;
 constexpr int kDRecordFloats = GS_DRECORD_FLOATS;
 

@@ -37,8 +37,7 @@ __global__ void __launch_bounds__(kLossThreads) image_loss_kernel(const float* _
     float part = 0.0f;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const float sg = r[k] > 0.0f ? 1.0f : (r[k] < 0.0f ? -1.0f : 0.0f);
-      g[k] = (w1 * sg + 2.0f * w2 * r[k]) * inv_n;
+      g[k] = l1l2_grad(r[k], w1, w2, inv_n);
       part += w1 * fabsf(r[k]) + w2 * r[k] * r[k];
     }
     g4[i] = make_float4(g[0], g[1], g[2], g[3]);
@@ -46,8 +45,7 @@ __global__ void __launch_bounds__(kLossThreads) image_loss_kernel(const float* _
   }
   for (int64_t i = 4 * n4 + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
     const float r = image[i] - target[i];
-    const float sg = r > 0.0f ? 1.0f : (r < 0.0f ? -1.0f : 0.0f);
-    grad[i] = (w1 * sg + 2.0f * w2 * r) * inv_n;
+    grad[i] = l1l2_grad(r, w1, w2, inv_n);
     acc += w1 * fabsf(r) + w2 * r * r;
   }
 #pragma unroll

@@ -218,6 +218,17 @@ __device__ __forceinline__ void composite_step(PixelFwd& P, const SplatCol& col,
   composite_apply(P, e, alpha, b, cb, rel, tstop);
 }
 
+// Optional L1 + L2 image loss computed in the forward's epilogue (target
+// null: none). grad and loss as gs_image_loss: dL/dimage = (w1 sign(r) +
+// 2 w2 r) / n, loss += sum(w1 |r| + w2 r^2) / n, r = image - target.
+struct ImageLoss {
+  const float* target;
+  float* grad;
+  double* loss;
+  float w1, w2, inv_n;
+  double inv_n_d;
+};
+
 // Compiled for 1024 resident threads per SM (8 CTAs of 128 at 32x16 tiles,
 // 64 registers, no spills): 0.5 % faster than 7 CTAs at 72 registers.
 template <int TW, int TH, int PPT>
@@ -227,7 +238,7 @@ __global__ void __launch_bounds__(TW* TH / PPT, 1024 / (TW * TH / PPT)) raster_f
                                                                    const uint32_t* __restrict__ order, const Layout L,
                                                                    const Consts K, float* __restrict__ image,
                                                                    float* __restrict__ final_T,
-                                                                   uint32_t* __restrict__ last) {
+                                                                   uint32_t* __restrict__ last, const ImageLoss IL) {
   using G = Geo<TW, TH, PPT>;
   constexpr int NT = G::NT, B = G::B;
   __shared__ float4 s_a[B];
@@ -331,16 +342,42 @@ __global__ void __launch_bounds__(TW* TH / PPT, 1024 / (TW * TH / PPT)) raster_f
     }
   }
   const size_t pb = L.pix_base[v];
+  const bool with_loss = IL.target != nullptr;
+  float part = 0.0f;
 #pragma unroll
   for (int r = 0; r < PPT; ++r) {
     const int yy = y0 + r * G::RS;
     if (x < W && yy < H) {
       const size_t p = pb + static_cast<size_t>(yy) * W + x;
-      image[3 * p] = P[r].c0 + P[r].T * K.bg[0];
-      image[3 * p + 1] = P[r].c1 + P[r].T * K.bg[1];
-      image[3 * p + 2] = P[r].c2 + P[r].T * K.bg[2];
+      const float c[3] = {P[r].c0 + P[r].T * K.bg[0], P[r].c1 + P[r].T * K.bg[1], P[r].c2 + P[r].T * K.bg[2]};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) image[3 * p + k] = c[k];
       final_T[p] = P[r].T;
       last[p] = P[r].last;
+      if (with_loss) {
+        // the L1 + L2 image loss of these values (same arithmetic as gs_image_loss)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float rr = c[k] - IL.target[3 * p + k];
+          IL.grad[3 * p + k] = l1l2_grad(rr, IL.w1, IL.w2, IL.inv_n);
+          part += IL.w1 * fabsf(rr) + IL.w2 * rr * rr;
+        }
+      }
+    }
+  }
+  if (with_loss) {
+    // CTA sum of the loss terms, one double atomic per CTA
+    __shared__ double s_loss[G::NW];
+    double acc = part;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) s_loss[warp] = acc;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < G::NW; ++w) t += s_loss[w];
+      atomicAdd(IL.loss, t * IL.inv_n_d);
     }
   }
 }
@@ -657,10 +694,10 @@ __global__ void GS_RBWD_BOUNDS(TW* TH / PPT) raster_bwd_kernel(
 
 template <int TW, int TH, int PPT>
 int launch_fwd(const float4* projected, const uint32_t* vals, const uint2* ranges, const Layout& L, const Consts& K,
-               float* image, float* final_T, uint32_t* last, cudaStream_t stream) {
+               float* image, float* final_T, uint32_t* last, const ImageLoss& IL, cudaStream_t stream) {
   const uint32_t* order = (K.flags & GS_FLAG_TILE_ORDER) ? reinterpret_cast<const uint32_t*>(ranges + L.n_tiles) : nullptr;
   raster_fwd_kernel<TW, TH, PPT><<<static_cast<unsigned>(L.n_tiles), TW * TH / PPT, 0, stream>>>(
-      projected, vals, ranges, order, L, K, image, final_T, last);
+      projected, vals, ranges, order, L, K, image, final_T, last, IL);
   return cuda_status(cudaGetLastError());
 }
 
@@ -689,11 +726,12 @@ inline int pixels_per_thread(const Layout& L, const Consts& K) {
 }  // namespace
 }  // namespace gs
 
-extern "C" int gs_rasterize_fwd(const float* projected, const uint32_t* vals, const uint32_t* tile_ranges,
-                                const int32_t* sizes, int32_t V, const gs_config* cfg, float* image, float* final_T,
-                                uint32_t* last, gs_stream_t stream_) {
-  using namespace gs;
-  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+namespace gs {
+namespace {
+
+int rasterize_fwd_impl(const float* projected, const uint32_t* vals, const uint32_t* tile_ranges, const int32_t* sizes,
+                       int32_t V, const gs_config* cfg, float* image, float* final_T, uint32_t* last,
+                       const ImageLoss& IL, cudaStream_t stream) {
   Layout L;
   int rc = build_layout(sizes, V, cfg, &L, nullptr);
   if (rc != GS_OK) return rc;
@@ -704,16 +742,52 @@ extern "C" int gs_rasterize_fwd(const float* projected, const uint32_t* vals, co
   const uint2* rg = reinterpret_cast<const uint2*>(tile_ranges);
   const int ppt = pixels_per_thread(L, K);
   if (L.tile_w == 16 && L.tile_h == 16)
-    return ppt == 4 ? launch_fwd<16, 16, 4>(pr, vals, rg, L, K, image, final_T, last, stream)
-                    : launch_fwd<16, 16, 2>(pr, vals, rg, L, K, image, final_T, last, stream);
-  if (L.tile_w == 8 && L.tile_h == 8) return launch_fwd<8, 8, 2>(pr, vals, rg, L, K, image, final_T, last, stream);
+    return ppt == 4 ? launch_fwd<16, 16, 4>(pr, vals, rg, L, K, image, final_T, last, IL, stream)
+                    : launch_fwd<16, 16, 2>(pr, vals, rg, L, K, image, final_T, last, IL, stream);
+  if (L.tile_w == 8 && L.tile_h == 8) return launch_fwd<8, 8, 2>(pr, vals, rg, L, K, image, final_T, last, IL, stream);
   if (L.tile_w == 32 && L.tile_h == 16)
-    return ppt == 4 ? launch_fwd<32, 16, 4>(pr, vals, rg, L, K, image, final_T, last, stream)
-                    : launch_fwd<32, 16, 2>(pr, vals, rg, L, K, image, final_T, last, stream);
+    return ppt == 4 ? launch_fwd<32, 16, 4>(pr, vals, rg, L, K, image, final_T, last, IL, stream)
+                    : launch_fwd<32, 16, 2>(pr, vals, rg, L, K, image, final_T, last, IL, stream);
   if (L.tile_w == 32 && L.tile_h == 32)
-    return ppt == 4 ? launch_fwd<32, 32, 4>(pr, vals, rg, L, K, image, final_T, last, stream)
-                    : launch_fwd<32, 32, 2>(pr, vals, rg, L, K, image, final_T, last, stream);
+    return ppt == 4 ? launch_fwd<32, 32, 4>(pr, vals, rg, L, K, image, final_T, last, IL, stream)
+                    : launch_fwd<32, 32, 2>(pr, vals, rg, L, K, image, final_T, last, IL, stream);
   return GS_ERR_UNSUPPORTED;
+}
+
+}  // namespace
+}  // namespace gs
+
+extern "C" int gs_rasterize_fwd(const float* projected, const uint32_t* vals, const uint32_t* tile_ranges,
+                                const int32_t* sizes, int32_t V, const gs_config* cfg, float* image, float* final_T,
+                                uint32_t* last, gs_stream_t stream) {
+  gs::ImageLoss none{};
+  return gs::rasterize_fwd_impl(projected, vals, tile_ranges, sizes, V, cfg, image, final_T, last, none,
+                                reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int gs_rasterize_fwd_l1l2(const float* projected, const uint32_t* vals, const uint32_t* tile_ranges,
+                                     const int32_t* sizes, int32_t V, const gs_config* cfg, float* image,
+                                     float* final_T, uint32_t* last, const float* target, int64_t n_values, float w_l1,
+                                     float w_l2, int32_t accumulate, float* dL_dimage, double* loss_dev,
+                                     gs_stream_t stream_) {
+  using namespace gs;
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  if (!target || !dL_dimage || !loss_dev || n_values <= 0) return GS_ERR_ARG;
+  int64_t n_pixels = 0;
+  int64_t n_tiles = 0;
+  const int rc = gs_layout_totals(sizes, V, cfg, &n_tiles, &n_pixels);
+  if (rc != GS_OK) return rc;
+  if (n_values < 3 * n_pixels) return GS_ERR_ARG;
+  if (!accumulate && cudaMemsetAsync(loss_dev, 0, sizeof(double), stream) != cudaSuccess) return GS_ERR_CUDA;
+  ImageLoss IL;
+  IL.target = target;
+  IL.grad = dL_dimage;
+  IL.loss = loss_dev;
+  IL.w1 = w_l1;
+  IL.w2 = w_l2;
+  IL.inv_n = 1.0f / static_cast<float>(n_values);
+  IL.inv_n_d = 1.0 / static_cast<double>(n_values);
+  return rasterize_fwd_impl(projected, vals, tile_ranges, sizes, V, cfg, image, final_T, last, IL, stream);
 }
 
 extern "C" int gs_rasterize_bwd_pixels(const float* projected, const uint32_t* vals, const uint32_t* tile_ranges,

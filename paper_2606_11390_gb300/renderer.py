@@ -162,6 +162,14 @@ def rasterize_fwd(frame: Frame, stream=None):
                         frame.final_T, frame.last, stream)
 
 
+def rasterize_fwd_l1l2(frame: Frame, target, n_values, w_l1, w_l2, accumulate, dL_dimage, loss, stream=None):
+    """rasterize_fwd with the L1 + L2 image loss computed in the same kernel
+    (target and dL_dimage laid out like frame.image)."""
+    gs.gs_rasterize_fwd_l1l2(frame.projected, frame.vals, frame.tile_ranges, frame.cams.sizes, frame.cfg,
+                             frame.image, frame.final_T, frame.last, target, n_values, w_l1, w_l2, accumulate,
+                             dL_dimage, loss, stream)
+
+
 def rasterize_bwd(params: FlatParams, cams: Cameras, frame: Frame, dL_dimage, grads: FlatParams, stream=None,
                   accumulate=False):
     flags = int(frame.cfg.get("flags", 0)) & ~gs.GS_FLAG_ACCUMULATE_GRADS
@@ -320,16 +328,24 @@ class TrainStep:
         """Enqueues one full step; returns the number of library kernels launched."""
         n = 0
         pv = self.mode == "per_view"
+        # the L1 + L2 loss is computed by the forward kernel itself (its value
+        # summed over the views); the SSIM loss needs whole windows and runs after
+        fused_loss = self.loss_kind == "l1l2"
         for v, (fr, cams) in enumerate(zip(self.frames, self.frame_cams)):
             project(self.params, cams, fr, stream)
             bin_sort(fr, stream)
             # the frame's image is its slice of the packed image
             a, b = int(self.cams.pix_base[v]) * 3, int(self.cams.pix_base[v + 1 if pv else -1]) * 3
             fr.image = self.image[a:b]
-            rasterize_fwd(fr, stream)
+            if fused_loss:
+                rasterize_fwd_l1l2(fr, self.target[a:b], self.image.numel(), self.w_l1, self.w_l2, v > 0,
+                                   self.dL_dimage[a:b], self.loss, stream)
+            else:
+                rasterize_fwd(fr, stream)
             n += 1 + self._sort_launches(fr) + 1  # project, sort, raster
-        self.enqueue_loss(stream)
-        n += 1
+        if not fused_loss:
+            self.enqueue_loss(stream)
+            n += 1
         for v, (fr, cams) in enumerate(zip(self.frames, self.frame_cams)):
             a, b = int(self.cams.pix_base[v]) * 3, int(self.cams.pix_base[v + 1 if pv else -1]) * 3
             rasterize_bwd(self.params, cams, fr, self.dL_dimage[a:b], self.grads, stream, accumulate=pv and v > 0)

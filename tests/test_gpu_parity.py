@@ -248,3 +248,63 @@ def test_tile_order_is_longest_first_permutation(oracle):
     # non-increasing up to the bucket width (a factor of 2 at most between neighbours out of order)
     assert np.all(nz[1:] <= 2 * nz[:-1])
     assert np.all(lens[len(nz):] == 0)
+
+
+@pytest.mark.parametrize("idx", [1, 2, 7])
+def test_forward_with_l1l2_loss(oracle, idx):
+    """gs_rasterize_fwd_l1l2 equals gs_rasterize_fwd followed by gs_image_loss:
+    image, final T, last and dL/dimage bit for bit, the loss up to the
+    rounding of its float partial sums (grouped differently by the two
+    kernels); one call for all views and one call per view (accumulated)."""
+    import torch
+
+    from paper_2606_11390_gb300 import _native
+    from paper_2606_11390_gb300 import renderer as R
+
+    name, s = SCENES[idx]
+    N = int(s["means"].shape[0])
+    params = R.FlatParams(N).load_from(s)
+    cams = R.Cameras(s["cams"], s["sizes"])
+    P = cams.n_pixels
+    rng = np.random.default_rng(7 + idx)
+    tgt = torch.from_numpy(rng.random(P * 3).astype(np.float32)).cuda()
+    w1, w2 = 1.0, 0.2
+    fa = R.Frame(N, cams, s["cfg"])
+    R.render(params, cams, fa)
+    dla = torch.zeros(P * 3, device="cuda")
+    la = torch.zeros(1, dtype=torch.float64, device="cuda")
+    _native.gs_image_loss(fa.image, tgt, w1, w2, dla, la)
+    # one call for all views
+    fb = R.Frame(N, cams, s["cfg"], capacity=fa.capacity)
+    R.project(params, cams, fb)
+    R.bin_sort(fb)
+    dlb = torch.full((P * 3,), 7.0, device="cuda")
+    lb = torch.full((1,), 5.0, dtype=torch.float64, device="cuda")
+    R.rasterize_fwd_l1l2(fb, tgt, P * 3, w1, w2, False, dlb, lb)
+    torch.cuda.synchronize()
+    assert fb.read_status() == 0
+    for a, b in ((fa.image, fb.image), (fa.final_T, fb.final_T), (fa.last, fb.last), (dla, dlb)):
+        np.testing.assert_array_equal(to_np(a), to_np(b))
+    assert lb.item() == pytest.approx(la.item(), rel=1e-6)
+    L_ref, _ = oracle.loss(to_np(fa.image), to_np(tgt), w1, w2)
+    assert lb.item() == pytest.approx(L_ref, rel=1e-6)
+    # one call per view, the loss accumulated over the views
+    dlc = torch.zeros(P * 3, device="cuda")
+    lc = torch.full((1,), 5.0, dtype=torch.float64, device="cuda")
+    img_c = torch.zeros(P * 3, device="cuda")
+    for v in range(cams.V):
+        cv = cams.view(v)
+        a, b = int(cams.pix_base[v]) * 3, int(cams.pix_base[v + 1]) * 3
+        fv = R.Frame(N, cv, s["cfg"], capacity=fa.capacity)
+        R.project(params, cv, fv)
+        R.bin_sort(fv)
+        fv.image = img_c[a:b]
+        R.rasterize_fwd_l1l2(fv, tgt[a:b], P * 3, w1, w2, v > 0, dlc[a:b], lc)
+        torch.cuda.synchronize()
+        assert fv.read_status() == 0
+    np.testing.assert_array_equal(to_np(img_c), to_np(fa.image))
+    np.testing.assert_array_equal(to_np(dlc), to_np(dla))
+    assert lc.item() == pytest.approx(la.item(), rel=1e-6)
+    # the mean must cover at least this call's values
+    with pytest.raises(_native.GSError):
+        R.rasterize_fwd_l1l2(fb, tgt, P * 3 - 1, w1, w2, False, dlb, lb)
