@@ -369,7 +369,8 @@ struct PassArgs {
   const int64_t* n_total;   // items = min(*n_total, cap)
   int64_t cap;
   int shift;
-  const uint32_t* digit_offsets;  // [256], exclusive
+  const uint32_t* digit_offsets;  // [256]: exclusive offsets, or the digit counts when scan_digits
+  int scan_digits;                // 1: each CTA scans the counts into offsets itself
   uint32_t* ticket;
   uint64_t* lookback;  // [sort tiles][256]
   int32_t stall_tile;   // test hook: this tile never publishes (-1: none)
@@ -383,6 +384,7 @@ struct __align__(16) SortSmem {
   uint32_t local_start[kRadix];
   uint32_t base[kRadix];  // output position of local index 0 of each digit, modulo 2^32
   uint32_t wsum[kSortWarps];
+  uint32_t doff[kRadix];  // exclusive output offset of each digit
   uint32_t tile;
 };
 
@@ -396,6 +398,25 @@ __global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) sort_pass_ke
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int64_t n = *a.n_total;
   if (n > a.cap) n = a.cap;
+  {
+    // the pass's digit offsets: given, or the exclusive scan of the digit
+    // counts (every CTA scans the 256 counts itself: no separate launch)
+    uint32_t c = a.digit_offsets[tid];  // kSortThreads == kRadix
+    if (a.scan_digits) {
+      uint32_t v = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t nb = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += nb;
+      }
+      if (lane == 31) sm.wsum[warp] = v;
+      __syncthreads();
+      uint32_t add = 0;
+      for (int w = 0; w < warp; ++w) add += sm.wsum[w];
+      c = v - c + add;
+    }
+    sm.doff[tid] = c;  // read after the loop's first barrier
+  }
   // Persistent CTA: take tiles in ticket order until the data is exhausted.
   // A tile only waits on tiles with smaller tickets, all held by running CTAs.
   for (;;) {
@@ -504,7 +525,7 @@ __global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) sort_pass_ke
     }
     if (publish) st_relaxed_u64(lb + static_cast<int64_t>(t) * kRadix + d, kFlagIncl | (prefix + total));
   }
-  sm.base[d] = a.digit_offsets[d] + static_cast<uint32_t>(prefix) - sm.local_start[d];
+  sm.base[d] = sm.doff[d] + static_cast<uint32_t>(prefix) - sm.local_start[d];
   __syncthreads();
 
   // 4. scatter into shared memory in local sorted order
@@ -566,15 +587,31 @@ __device__ __forceinline__ int order_bucket(uint32_t len) {
   return kOrderBuckets - 2 - (b < kOrderBuckets - 2 ? b : kOrderBuckets - 2);
 }
 
-__global__ void __launch_bounds__(kOrderThreads) tile_order_kernel(const uint2* __restrict__ ranges, int64_t n_tiles,
-                                                                   uint32_t* __restrict__ order) {
+// With fixup, the starts of the non-empty tiles come complemented from the
+// last tile-id pass and are restored here first (ranges_fixup_kernel's job).
+// Lanes of a warp with the same bucket are served by one shared atomic
+// (match.any + popcount): most tiles fall into a few buckets.
+__global__ void __launch_bounds__(kOrderThreads) tile_order_kernel(uint2* __restrict__ ranges, int64_t n_tiles,
+                                                                   uint32_t* __restrict__ order, int fixup) {
   __shared__ uint32_t s_cnt[kOrderBuckets];
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
   if (tid < kOrderBuckets) s_cnt[tid] = 0;
   __syncthreads();
-  for (int64_t t = tid; t < n_tiles; t += kOrderThreads) {
-    const uint2 r = ranges[t];
-    atomicAdd(&s_cnt[order_bucket(r.y - r.x)], 1u);
+  const uint32_t lt = (1u << lane) - 1u;
+  // the loops run in whole warps (t beyond the tiles: no bucket)
+  const int64_t n_round = (n_tiles + 31) & ~int64_t(31);
+  for (int64_t t = tid; t < n_round; t += kOrderThreads) {
+    int b = -1;
+    if (t < n_tiles) {
+      uint2 r = ranges[t];
+      if (fixup && r.y) {
+        r.x = ~r.x;
+        ranges[t].x = r.x;
+      }
+      b = order_bucket(r.y - r.x);
+    }
+    const uint32_t peers = __match_any_sync(0xffffffffu, b);
+    if (b >= 0 && (peers & lt) == 0) atomicAdd(&s_cnt[b], static_cast<uint32_t>(__popc(peers)));
   }
   __syncthreads();
   if (tid == 0) {
@@ -586,9 +623,18 @@ __global__ void __launch_bounds__(kOrderThreads) tile_order_kernel(const uint2* 
     }
   }
   __syncthreads();
-  for (int64_t t = tid; t < n_tiles; t += kOrderThreads) {
-    const uint2 r = ranges[t];
-    order[atomicAdd(&s_cnt[order_bucket(r.y - r.x)], 1u)] = static_cast<uint32_t>(t);
+  for (int64_t t = tid; t < n_round; t += kOrderThreads) {
+    int b = -1;
+    if (t < n_tiles) {
+      const uint2 r = ranges[t];
+      b = order_bucket(r.y - r.x);
+    }
+    const uint32_t peers = __match_any_sync(0xffffffffu, b);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (b >= 0 && lane == leader) base = atomicAdd(&s_cnt[b], static_cast<uint32_t>(__popc(peers)));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (b >= 0) order[base + __popc(peers & lt)] = static_cast<uint32_t>(t);
   }
 }
 
@@ -899,7 +945,7 @@ int run_u32_sort_passes(uint32_t* const keys[2], uint32_t* const vals[2], const 
   for (int p = 0; p < passes; ++p) {
     PassArgs a;
     a.keys_in = keys[p & 1]; a.vals_in = vals[p & 1]; a.keys_out = keys[(p + 1) & 1]; a.vals_out = vals[(p + 1) & 1];
-    a.n_total = n_dev; a.cap = cap; a.shift = 8 * p; a.digit_offsets = hist + p * kRadix;
+    a.n_total = n_dev; a.cap = cap; a.shift = 8 * p; a.digit_offsets = hist + p * kRadix; a.scan_digits = 0;
     a.ticket = tickets + p;
     a.ranges = nullptr; a.n_keys = 0;
     a.stall_tile = -1;
@@ -946,8 +992,8 @@ int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* 
   const int64_t VN = N * V;
   if (VN == 0) {
     if (cfg->flags & GS_FLAG_TILE_ORDER)
-      tile_order_kernel<<<1, kOrderThreads, 0, stream>>>(reinterpret_cast<const uint2*>(tile_ranges), L.n_tiles,
-                                                         tile_ranges + 2 * L.n_tiles);
+      tile_order_kernel<<<1, kOrderThreads, 0, stream>>>(reinterpret_cast<uint2*>(tile_ranges), L.n_tiles,
+                                                         tile_ranges + 2 * L.n_tiles, 0);
     return cuda_status(cudaGetLastError());
   }
   int64_t sort_grid_cap = 0;
@@ -967,12 +1013,12 @@ int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* 
     uint32_t* hist_d = u32(w.hist_d);
     compact_visible_kernel<<<scan_grid, kScanThreads, 0, stream>>>(counts, projected, depth_keys, VN, 0u, st1, dk[0],
                                                                      dv[0], hist_d, n_visible, status_dev);
-    hist_scan_kernel<<<1, kRadix, 0, stream>>>(hist_d, kDepthPasses);
     // 1b. four depth passes (even count: the result is back in dk[0], dv[0])
     for (int p = 0; p < kDepthPasses; ++p) {
       PassArgs a;
       a.keys_in = dk[p & 1]; a.vals_in = dv[p & 1]; a.keys_out = dk[(p + 1) & 1]; a.vals_out = dv[(p + 1) & 1];
       a.n_total = n_visible; a.cap = VN; a.shift = 8 * p; a.digit_offsets = hist_d + p * kRadix;
+      a.scan_digits = 1;  // the counts gathered by the compaction
       a.ticket = tickets + 2 + p;
       a.ranges = nullptr; a.n_keys = 0;
       a.stall_tile = (p == 0 && (cfg->flags & GS_FLAG_TEST_STALL_LOOKBACK)) ? 0 : -1;
@@ -1044,12 +1090,11 @@ int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* 
       capacity > 0 ? tk[0] : nullptr, capacity > 0 ? tv[0] : nullptr, hist_t, n_isect_dev, status_dev);
   if (capacity == 0) {
     if (cfg->flags & GS_FLAG_TILE_ORDER)
-      tile_order_kernel<<<1, kOrderThreads, 0, stream>>>(reinterpret_cast<const uint2*>(tile_ranges), L.n_tiles,
-                                                         tile_ranges + 2 * L.n_tiles);
+      tile_order_kernel<<<1, kOrderThreads, 0, stream>>>(reinterpret_cast<uint2*>(tile_ranges), L.n_tiles,
+                                                         tile_ranges + 2 * L.n_tiles, 0);
     return cuda_status(cudaGetLastError());
   }
   // 2b. stable tile-id passes
-  if (TP > 0) hist_scan_kernel<<<1, kRadix, 0, stream>>>(hist_t, TP);
   for (int p = 0; p < TP; ++p) {
     PassArgs a;
     a.keys_in = tk[p & 1]; a.vals_in = tv[p & 1]; a.keys_out = tk[(p + 1) & 1]; a.vals_out = tv[(p + 1) & 1];
@@ -1062,6 +1107,7 @@ int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* 
       if (!keys) a.keys_out = nullptr;
     }
     a.n_total = n_isect_dev; a.cap = capacity; a.shift = 8 * p; a.digit_offsets = hist_t + p * kRadix;
+    a.scan_digits = 1;  // the counts gathered by the emission
     a.ticket = tickets + 6 + p;
     a.stall_tile = -1;
     a.spin_limit = kSpinLimit;
@@ -1087,19 +1133,21 @@ int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* 
   const uint32_t* tkeys_final = tk[TP & 1];
   // 2c. tile ranges (from the ids themselves when there is no tile pass),
   //     optional 64-bit keys
-  if (TP > 0)
+  // (with a tile order the order kernel restores the starts itself)
+  const bool ordered = (cfg->flags & GS_FLAG_TILE_ORDER) != 0;
+  if (TP > 0 && !ordered)
     ranges_fixup_kernel<<<static_cast<unsigned>((L.n_tiles + 255) / 256), 256, 0, stream>>>(
         reinterpret_cast<uint2*>(tile_ranges), L.n_tiles);
-  else
+  else if (TP == 0)
     tile_ranges_kernel<<<static_cast<unsigned>(4 * n_sm), 256, 0, stream>>>(
         tkeys_final, n_isect_dev, capacity, static_cast<uint32_t>(L.n_tiles), reinterpret_cast<uint2*>(tile_ranges),
         status_dev);
   if (keys)
     keys64_kernel<<<static_cast<unsigned>(4 * n_sm), 256, 0, stream>>>(tkeys_final, vals, projected, n_isect_dev,
                                                                         capacity, keys);
-  if (cfg->flags & GS_FLAG_TILE_ORDER)
-    tile_order_kernel<<<1, kOrderThreads, 0, stream>>>(reinterpret_cast<const uint2*>(tile_ranges), L.n_tiles,
-                                                       tile_ranges + 2 * L.n_tiles);
+  if (ordered)
+    tile_order_kernel<<<1, kOrderThreads, 0, stream>>>(reinterpret_cast<uint2*>(tile_ranges), L.n_tiles,
+                                                       tile_ranges + 2 * L.n_tiles, TP > 0 ? 1 : 0);
   return cuda_status(cudaGetLastError());
 }
 

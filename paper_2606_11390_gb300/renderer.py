@@ -370,16 +370,18 @@ class TrainStep:
 
     @staticmethod
     def _sort_launches(fr: Frame) -> int:
-        """Kernels gs_bin_sort launches: compaction, histogram scan, 4 depth
-        passes, count scan with emission, histogram scan, the tile-id passes,
-        ranges (and the optional 64-bit keys and tile order)."""
+        """Kernels gs_bin_sort launches: compaction, 4 depth passes, count
+        scan with emission, the tile-id passes (each pass scans its digit
+        counts itself), the ranges fix-up (done by the tile-order kernel when
+        there is one; the ranges kernel when there is no tile pass), the
+        optional 64-bit keys and the tile order."""
         bits = 0
         while (1 << bits) < fr.n_tiles:
             bits += 1
         tile_passes = (bits + 7) // 8
         order = 1 if fr.cfg.get("flags", 0) & gs.GS_FLAG_TILE_ORDER else 0
-        return (1 + 1 + 4 + 1 + (1 if tile_passes else 0) + tile_passes + 1 + (1 if fr.keep_keys else 0)
-                + order)
+        ranges = 0 if (tile_passes and order) else 1
+        return 1 + 4 + 1 + tile_passes + ranges + (1 if fr.keep_keys else 0) + order
 
     def prepare(self, warmup_checks=2):
         """Sizes the key capacity from an eager run, then (batched mode)
