@@ -409,20 +409,39 @@ class TrainStep:
         self.launches_per_step = self._enqueue()  # counted on an eager step
         torch.cuda.synchronize()
         if self.graph_on:
-            s = torch.cuda.Stream()
-            s.wait_stream(torch.cuda.current_stream())
-            with torch.cuda.stream(s):
-                self._enqueue(s)  # warm the capture stream
-            torch.cuda.current_stream().wait_stream(s)
-            torch.cuda.synchronize()
-            self.graph = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(self.graph):
-                self._enqueue(torch.cuda.current_stream())
-            torch.cuda.synchronize()
+            self.graph = self._capture()
         if self.densify_on:  # the sizing and capture steps do not count
             self.reset_densify_stats()
             torch.cuda.synchronize()
         return self
+
+    def _capture(self):
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self._enqueue(s)  # warm the capture stream
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            self._enqueue(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        return graph
+
+    def capture_fed(self, target, cams_dev):
+        """One more graph of the (batched, captured) step that reads its target
+        image and cameras from the given device buffers instead of self.target
+        and self.cams.dev, so that a host-fed step needs no device copy of its
+        inputs. The capture runs the step once on those buffers (an optimizer
+        or densification statistics in the step advance with it)."""
+        if self.graph is None or self.mode != "batched":
+            raise ValueError("capture_fed needs a prepared batched step with a CUDA graph")
+        old_t, old_c = self.target, self.cams.dev
+        self.target, self.cams.dev = target, cams_dev
+        try:
+            return self._capture()
+        finally:
+            self.target, self.cams.dev = old_t, old_c
 
     def reset_densify_stats(self):
         """Starts a new densification-statistics window."""
@@ -486,6 +505,16 @@ class HostFedStep:
         ev = lambda: [torch.cuda.Event() for _ in range(2)]  # noqa: E731
         self.in_ready, self.in_free, self.out_ready, self.out_free = ev(), ev(), ev(), ev()
         self.k = 0
+        # a captured step gets one graph per staging buffer, reading the
+        # target image and cameras where they land (no device-to-device copy);
+        # not with an optimizer or densification statistics in the step, whose
+        # state the capture's own run would advance
+        self.graphs = None
+        if step.graph is not None and not step.adam_on and not step.densify_on:
+            for b in range(2):  # valid contents for the capture's own run
+                self.in_target[b].copy_(step.target)
+                self.in_cams[b].copy_(step.cams.dev)
+            self.graphs = [step.capture_fed(self.in_target[b], self.in_cams[b]) for b in range(2)]
 
     def run(self, host_params, host_target, host_cams, host_grads, host_loss):
         st, b = self.step, self.k & 1
@@ -502,10 +531,14 @@ class HostFedStep:
         comp.wait_event(self.in_ready[b])
         if sp:
             st.params.flat.copy_(self.in_params[b])
-        st.target.copy_(self.in_target[b])
-        st.cams.dev.copy_(self.in_cams[b])
-        self.in_free[b].record(comp)
-        st.run()
+        if self.graphs is not None:
+            self.graphs[b].replay()
+            self.in_free[b].record(comp)  # the step has read its inputs
+        else:
+            st.target.copy_(self.in_target[b])
+            st.cams.dev.copy_(self.in_cams[b])
+            self.in_free[b].record(comp)
+            st.run()
         if self.k >= 2:
             comp.wait_event(self.out_free[b])
         if sp:
