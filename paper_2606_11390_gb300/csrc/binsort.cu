@@ -589,29 +589,19 @@ __device__ __forceinline__ int order_bucket(uint32_t len) {
 
 // With fixup, the starts of the non-empty tiles come complemented from the
 // last tile-id pass and are restored here first (ranges_fixup_kernel's job).
-// Lanes of a warp with the same bucket are served by one shared atomic
-// (match.any + popcount): most tiles fall into a few buckets.
 __global__ void __launch_bounds__(kOrderThreads) tile_order_kernel(uint2* __restrict__ ranges, int64_t n_tiles,
                                                                    uint32_t* __restrict__ order, int fixup) {
   __shared__ uint32_t s_cnt[kOrderBuckets];
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x;
   if (tid < kOrderBuckets) s_cnt[tid] = 0;
   __syncthreads();
-  const uint32_t lt = (1u << lane) - 1u;
-  // the loops run in whole warps (t beyond the tiles: no bucket)
-  const int64_t n_round = (n_tiles + 31) & ~int64_t(31);
-  for (int64_t t = tid; t < n_round; t += kOrderThreads) {
-    int b = -1;
-    if (t < n_tiles) {
-      uint2 r = ranges[t];
-      if (fixup && r.y) {
-        r.x = ~r.x;
-        ranges[t].x = r.x;
-      }
-      b = order_bucket(r.y - r.x);
+  for (int64_t t = tid; t < n_tiles; t += kOrderThreads) {
+    uint2 r = ranges[t];
+    if (fixup && r.y) {
+      r.x = ~r.x;
+      ranges[t].x = r.x;
     }
-    const uint32_t peers = __match_any_sync(0xffffffffu, b);
-    if (b >= 0 && (peers & lt) == 0) atomicAdd(&s_cnt[b], static_cast<uint32_t>(__popc(peers)));
+    atomicAdd(&s_cnt[order_bucket(r.y - r.x)], 1u);
   }
   __syncthreads();
   if (tid == 0) {
@@ -623,18 +613,9 @@ __global__ void __launch_bounds__(kOrderThreads) tile_order_kernel(uint2* __rest
     }
   }
   __syncthreads();
-  for (int64_t t = tid; t < n_round; t += kOrderThreads) {
-    int b = -1;
-    if (t < n_tiles) {
-      const uint2 r = ranges[t];
-      b = order_bucket(r.y - r.x);
-    }
-    const uint32_t peers = __match_any_sync(0xffffffffu, b);
-    const int leader = __ffs(peers) - 1;
-    uint32_t base = 0;
-    if (b >= 0 && lane == leader) base = atomicAdd(&s_cnt[b], static_cast<uint32_t>(__popc(peers)));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (b >= 0) order[base + __popc(peers & lt)] = static_cast<uint32_t>(t);
+  for (int64_t t = tid; t < n_tiles; t += kOrderThreads) {
+    const uint2 r = ranges[t];
+    order[atomicAdd(&s_cnt[order_bucket(r.y - r.x)], 1u)] = static_cast<uint32_t>(t);
   }
 }
 

@@ -32,6 +32,7 @@ def run_gpu(scene, dL_dimage=None, capacity=None, tile=None, graph=False, partit
         "projected": to_np(frame.projected).reshape(-1, 12),
         "rects": to_np(frame.rects).reshape(-1, 4),
         "counts": to_np(frame.counts, np.uint32),
+        "depth_keys": to_np(frame.depth_keys, np.uint32),
         "n_isect": int(frame.n_isect.item()),
         "status": frame.read_status(),
         "capacity": frame.capacity,

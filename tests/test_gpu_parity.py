@@ -61,6 +61,9 @@ def _check_forward(s, g, o_proj, o_bins, o_ras):
     np.testing.assert_allclose(g["projected"][vis, 5], o_proj["projected"][vis, 5], rtol=2e-6, err_msg="opacity")
     np.testing.assert_allclose(g["projected"][vis, 8:11], o_proj["projected"][vis, 8:11], atol=2e-6, err_msg="rgb")
     assert not g["projected"][~vis].any()
+    # the depth keys gs_project writes for the sort: the depth's float bits where visible, 0 where culled
+    np.testing.assert_array_equal(g["depth_keys"][vis], o_proj["projected"][vis, 6].astype(np.float32).view(np.uint32))
+    assert not g["depth_keys"][~vis].any()
     # keys / values / ranges: bit-exact
     assert g["n_isect"] == o_bins["n_isect"]
     if g["keys"] is not None:
