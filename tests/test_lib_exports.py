@@ -68,3 +68,24 @@ def test_workspace_grows_with_capacity(lib):
     b = _native.gs_bin_sort_workspace_bytes(1000, 2, 20000, 100)
     assert 0 < a < b
     assert a % 256 == 0
+
+
+def _declared_arity():
+    """Parameter count of every GS_API function in include/gs.h."""
+    with open(os.path.join(ROOT, "include", "gs.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for m in re.finditer(r"GS_API\s+[\w\s\*]+?\b(gs_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", text):
+        params = m.group(2).strip()
+        out[m.group(1)] = 0 if params in ("", "void") else len(params.split(","))
+    return out
+
+
+def test_binding_signatures_match_the_header():
+    # the ctypes argument lists must follow every C-ABI change of the header
+    declared = _declared_arity()
+    assert len(declared) >= 20
+    for name, (args, _res) in _native._SIGNATURES.items():
+        assert name in declared, name
+        assert len(args) == declared[name], (name, len(args), declared[name])
