@@ -138,6 +138,54 @@ class Frame:
     def clear_status(self):
         self.status.zero_()
 
+    def hand_over(self) -> "FrameState":
+        """Moves what a backward of the last render reads out of this frame
+        into a FrameState (no copy) and gives the frame fresh buffers in their
+        place, so that a later render on this frame cannot overwrite them:
+        the projected records, tile counts, sorted list and tile ranges, and
+        per pixel the image, final transmittance and last-contributor count.
+        The camera records are copied (V x 80 bytes), since the caller may
+        refill them."""
+        st = FrameState(self)
+        self.projected = torch.zeros_like(self.projected)
+        self.counts = torch.zeros_like(self.counts)
+        self.vals = torch.zeros_like(self.vals)
+        self.tile_ranges = torch.zeros_like(self.tile_ranges)
+        self.ranges = self.tile_ranges[:2 * self.n_tiles]
+        self.image = torch.zeros_like(self.image)
+        self.final_T = torch.zeros_like(self.final_T)
+        self.last = torch.zeros_like(self.last)
+        return st
+
+
+class FrameState:
+    """The buffers of one rendered frame that its backward reads (see
+    Frame.hand_over), with the attribute names rasterize_bwd uses; the
+    backward's own scratch (d_projected, status) is allocated on demand."""
+
+    def __init__(self, frame: Frame):
+        c = frame.cams
+        self.cams = Cameras.__new__(Cameras)
+        self.cams.sizes, self.cams.V, self.cams.host = c.sizes.copy(), c.V, c.host.copy()
+        self.cams.dev = c.dev.clone()
+        self.cams.n_pixels, self.cams.pix_base = c.n_pixels, c.pix_base.copy()
+        self.N, self.cfg, self.n_tiles = frame.N, dict(frame.cfg), frame.n_tiles
+        self.projected, self.counts, self.vals = frame.projected, frame.counts, frame.vals
+        self.tile_ranges, self.image = frame.tile_ranges, frame.image
+        self.final_T, self.last = frame.final_T, frame.last
+        self.d_projected = None
+        self.status = None
+
+    def alloc_scratch(self):
+        if self.d_projected is None:
+            dev = self.projected.device
+            self.d_projected = torch.empty(self.cams.V * self.N * gs.DRECORD_FLOATS, dtype=torch.float32, device=dev)
+            self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+        return self
+
+    def read_status(self) -> int:
+        return int(self.status.item()) if self.status is not None else 0
+
 
 def project(params: FlatParams, cams: Cameras, frame: Frame, stream=None):
     gs.gs_project(params["means"], params["log_scales"], params["quats"], params["opacity_logits"], params["sh"],
@@ -229,33 +277,39 @@ class GaussianRasterize(torch.autograd.Function):
 
     The forward keeps only what the backward needs: the projected records, the
     sorted list and tile ranges, and per pixel the final transmittance and the
-    last-contributor count (no per-pixel lists). The backward calls
-    gs_rasterize_bwd, which recomputes transmittance in reverse."""
+    last-contributor count (no per-pixel lists). It takes these buffers over
+    from the frame (Frame.hand_over), so the frame can render again before
+    this backward runs, in any order of forwards and backwards. The backward
+    calls gs_rasterize_bwd, which recomputes transmittance in reverse from the
+    final T and the last-contributor count."""
 
     @staticmethod
     def forward(ctx, means, log_scales, quats, opacity_logits, sh, cams: Cameras, frame: Frame):
         N = means.shape[0]
         params = _PackedView(means, log_scales, quats, opacity_logits, sh, N)
         render(params, cams, frame)
-        ctx.frame, ctx.cams = frame, cams
+        ctx.state = frame.hand_over()
         ctx.save_for_backward(means, log_scales, quats, opacity_logits, sh)
-        return frame.image.view(-1, 3).clone()
+        return ctx.state.image.view(-1, 3)
 
     @staticmethod
     def backward(ctx, grad_image):
         means, log_scales, quats, opacity_logits, sh = ctx.saved_tensors
-        frame, cams = ctx.frame, ctx.cams
+        st = ctx.state.alloc_scratch()
         N = means.shape[0]
         params = _PackedView(means, log_scales, quats, opacity_logits, sh, N)
         grads = FlatParams(N, means.device)
-        rasterize_bwd(params, cams, frame, grad_image.contiguous().view(-1), grads)
-        return (grads["means"], grads["log_scales"], grads["quats"], grads["opacity_logits"], grads["sh"], None,
-                None)
+        rasterize_bwd(params, st.cams, st, grad_image.contiguous().view(-1), grads)
+        ins = (means, log_scales, quats, opacity_logits, sh)
+        out = tuple(grads[k].view(t.shape) if need else None
+                    for k, t, need in zip(PARAM_NAMES, ins, ctx.needs_input_grad[:5]))
+        return out + (None, None)
 
 
 class _PackedView:
     """Parameter tensors in the form the binding functions index by name;
-    each must be contiguous float32 on the device."""
+    each must be a contiguous float32 CUDA tensor with N rows of its width
+    (sh as [N, 16, 3] or [N, 48], opacity_logits as [N] or [N, 1])."""
 
     def __init__(self, means, log_scales, quats, opacity_logits, sh, N):
         self.N = N
@@ -263,6 +317,9 @@ class _PackedView:
         for name, t in zip(PARAM_NAMES, (means, log_scales, quats, opacity_logits, sh)):
             if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
                 raise ValueError(f"{name}: expected a contiguous float32 CUDA tensor")
+            if t.dim() == 0 or t.shape[0] != N or t.numel() != N * PARAM_WIDTH[name]:
+                raise ValueError(f"{name}: expected {N} rows of {PARAM_WIDTH[name]} floats, got shape "
+                                 f"{tuple(t.shape)}")
             self.views[name] = t.detach()
 
     def __getitem__(self, k):

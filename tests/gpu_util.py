@@ -71,3 +71,12 @@ def grad_close(got, ref, rel=1e-3, mask=None, name=""):
     assert not bad.any(), (f"{name}: {bad.sum()} of {bad.size} entries out of tolerance; worst "
                            f"{(d / tol).max():.3g}x tol at {np.unravel_index(np.argmax(d / tol), d.shape)}")
     assert rel_norm <= rel, f"{name}: relative norm error {rel_norm:.3g}"
+
+
+def norm_close(got, ref, rel=1e-3, name=""):
+    """||got - ref||_2 <= rel * ||ref||_2 over all entries."""
+    got = np.asarray(got, np.float64).reshape(-1)
+    ref = np.asarray(ref, np.float64).reshape(-1)
+    nrm = np.linalg.norm(ref)
+    err = np.linalg.norm(got - ref)
+    assert err <= rel * nrm + 1e-12, f"{name}: relative norm error {err / max(nrm, 1e-300):.3g}"

@@ -22,6 +22,7 @@ def test_densify_stats_match_oracle(oracle):
     P = s["target"].shape[0]
     dl = (rng.standard_normal((P, 3)) / P).astype(np.float32)
     o_proj, o_bins, o_ras = oracle.forward(s, "f32")
+    dl[o_ras["marginal_pix"].astype(bool)] = 0  # no near-threshold decision reaches a gradient
     o_dproj, _ = oracle.backward(s, o_proj, o_bins, dl.astype(np.float64), "f32")
     g = run_gpu(s, dL_dimage=dl)
     assert g["status"] == 0
@@ -39,8 +40,8 @@ def test_densify_stats_match_oracle(oracle):
     ga, dn, mr = (d.cpu().numpy() for d in dev)
     np.testing.assert_array_equal(dn, want[1])
     np.testing.assert_array_equal(mr, want[2])
-    ok_g = (o_ras["marginal_vg"] == 0).reshape(V, N).all(axis=0)
-    grad_close(ga, want[0], mask=ok_g, name="grad_accum")
+    grad_close(ga, want[0], name="grad_accum")
+    assert V == 3
 
 
 def test_train_step_gathers_densify_stats():

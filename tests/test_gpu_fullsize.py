@@ -8,8 +8,8 @@ tile shape).
 - for sampled tiles, the sorted list (exact) against a brute-force list built
   from the oracle's rectangles and depths, and the rendered pixels;
 - for sampled Gaussians whose tiles are all included, the complete parameter
-  gradients under a seeded upstream gradient, with the oracle compositing
-  those tiles from its own lists.
+  gradients under a seeded upstream gradient (zero on near-threshold pixels),
+  with the oracle compositing those tiles from its own lists.
 """
 import numpy as np
 import pytest
@@ -114,14 +114,17 @@ def test_full_size_4k_sampled(oracle):
 
     P = W * H
     dl = (rng.standard_normal((P, 3)) / P).astype(np.float32)
+    # near-threshold pixels of the sampled tiles get a zero upstream gradient
+    # (each pixel composites on its own, so no other contribution changes)
+    dl[pix[marg]] = 0
     grads = st.params.like()
     R.rasterize_bwd(st.params, st.cams, fr, torch.from_numpy(dl).cuda().view(-1), grads)
     torch.cuda.synchronize()
     assert fr.read_status() == 0
     d_o = oracle.raster_bwd(s, o_proj, bins_o, dl.astype(np.float64), "f32", tiles=all_tiles)
-    ok = ras["marginal_vg"][gsel] == 0
-    assert ok.mean() > 0.8
-    grad_close(to_np(fr.d_projected).reshape(-1, 9)[gsel], d_o[gsel], mask=ok, name="d_projected")
+    print(f"near-threshold pixels {marg.mean():.4f}, sampled records touched by one "
+          f"{(ras['marginal_vg'][gsel] != 0).mean():.4f}")
+    grad_close(to_np(fr.d_projected).reshape(-1, 9)[gsel], d_o[gsel], name="d_projected")
     o_g = oracle.project_bwd(s, d_o, "f32", gaussians=gsel)
     for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
-        grad_close(to_np(grads[k])[gsel], o_g[k], mask=ok, name=k)
+        grad_close(to_np(grads[k])[gsel], o_g[k], name=k)

@@ -5,14 +5,15 @@ ranges; images within 1e-5 absolute; gradients within 1e-3 relative (see
 gpu_util.grad_close). Pixels whose compositing involved a decision within
 1e-4 (relative) of a threshold (alpha cutoff, alpha cap, transmittance stop)
 can legitimately go either way between two correct float implementations;
-the oracle flags them, they are checked at 1e-2 and their share is bounded.
+the oracle flags them, they are checked at 1e-2 and their share is bounded;
+gradients are compared element-wise with their upstream gradient set to zero.
 """
 import numpy as np
 import pytest
 
 from paper_2606_11390_gb300 import scenes
 
-from gpu_util import grad_close, run_gpu, to_np
+from gpu_util import grad_close, norm_close, run_gpu, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -99,21 +100,34 @@ def test_forward_parity_without_keys(oracle, name, s):
 
 @pytest.mark.parametrize("name,s", SCENES, ids=IDS)
 def test_backward_parity(oracle, name, s):
+    """Element-wise on every record, with the upstream gradient of the
+    near-threshold pixels set to zero: a pixel composites on its own, so this
+    removes exactly the contributions that depend on a decision two correct
+    float implementations may take differently. With the full upstream
+    gradient, the relative-norm bound holds over all records."""
     rng = np.random.default_rng(7)
     P = s["target"].shape[0]
     dl = (rng.standard_normal((P, 3)) / P).astype(np.float32)
     o_proj, o_bins, o_ras = oracle.forward(s, "f32")
+    marg = o_ras["marginal_pix"].astype(bool)
+    print(f"{name}: near-threshold pixels {marg.mean():.4f}, records touched by one "
+          f"{(o_ras['marginal_vg'] != 0).mean():.4f}")
+    N = s["means"].shape[0]
+    dl_m = dl.copy()
+    dl_m[marg] = 0
+    o_dproj, o_grads = oracle.backward(s, o_proj, o_bins, dl_m.astype(np.float64), "f32")
+    g = run_gpu(s, dL_dimage=dl_m)
+    assert g["status"] == 0
+    grad_close(g["d_projected"], o_dproj, name="d_projected")
+    for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        grad_close(g["grads"][k], o_grads[k], name=k)
     o_dproj, o_grads = oracle.backward(s, o_proj, o_bins, dl.astype(np.float64), "f32")
     g = run_gpu(s, dL_dimage=dl)
     assert g["status"] == 0
-    N = s["means"].shape[0]
-    V = s["sizes"].shape[0]
-    ok_vg = o_ras["marginal_vg"] == 0
-    assert ok_vg.mean() > 0.9, ok_vg.mean()
-    grad_close(g["d_projected"], o_dproj, mask=ok_vg, name="d_projected")
-    ok_g = ok_vg.reshape(V, N).all(axis=0)
+    norm_close(g["d_projected"], o_dproj, name="d_projected (full upstream)")
     for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
-        grad_close(g["grads"][k], o_grads[k], mask=ok_g, name=k)
+        norm_close(g["grads"][k], o_grads[k], name=f"{k} (full upstream)")
+    assert N > 0
 
 
 def test_capacity_overflow_sets_status_and_recovers(oracle):
