@@ -113,8 +113,9 @@ class ClockSampler:
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, period_ms: int = 50):
         self.gpu = gpu_index
+        self.period_ms = int(period_ms)
         self.proc = None
         self.lines = []
 
@@ -122,7 +123,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.period_ms)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except (OSError, FileNotFoundError):
@@ -137,7 +138,8 @@ class ClockSampler:
         return datetime.datetime.now()
 
     def stop(self, t0=None, t1=None):
-        """Summary of the samples stamped within [t0, t1] (all samples when no window is given)."""
+        """Stops sampling; summary of the samples stamped within [t0, t1] (all
+        samples when no window is given)."""
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -145,9 +147,15 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        return self.summary(t0, t1)
+
+    def summary(self, t0=None, t1=None):
+        """Summary of the samples so far stamped within [t0, t1]."""
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in list(self.lines):
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 10:
                 continue
@@ -165,6 +173,31 @@ class ClockSampler:
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm), "window": "samples stamped inside the timed region"}
+
+
+def clock_record(clocks, step, t_start, t_end, min_samples=3, extend_s=1.0):
+    """The clock summary of the timed region. When the region is shorter than
+    a few sampling periods (e.g. 20 steps of 3.7 ms), the same step keeps
+    running, untimed, for extend_s more seconds and the summary covers the
+    timed region plus that continuation, said so in `window`."""
+    import torch
+
+    time.sleep(2 * clocks.period_ms / 1000.0)  # let the sampler deliver the last in-region sample
+    clk = clocks.summary(t_start, t_end)
+    if (clk.get("samples") or 0) >= min_samples:
+        clocks.stop()
+        return clk
+    t1 = time.perf_counter() + extend_s
+    while time.perf_counter() < t1:
+        for _ in range(8):
+            step.run()
+        torch.cuda.synchronize()
+    t_ext = clocks.mark()
+    clk = clocks.stop(t_start, t_ext)
+    clk["window"] = (f"timed region ({(t_end - t_start).total_seconds() * 1e3:.0f} ms) and the same step replayed "
+                     f"untimed for {extend_s:.1f} s right after it")
+    clk["samples_in_timed_region"] = clocks.summary(t_start, t_end).get("samples", 0)
+    return clk
 
 
 def measured_peaks():
@@ -249,51 +282,114 @@ def stage_times(step, iters=5):
 
 
 def pair_counts(step):
-    """Evaluated (pixel, splat) pairs implied by the outputs: the backward
-    visits, per pixel, its `last` entries (sum of last); the forward visits at
-    least those."""
+    """Pixel-splat pair counts of the rasteriser on the step's own frame,
+    from the pair-counting variants of the forward and backward kernels (the
+    same cull and decisions as the timed kernels, run once outside the timed
+    region): per kernel, pairs executed, evaluated and composited; plus
+    sum(last), the pairs up to each pixel's last contributor."""
     import torch
 
-    last = step.frames[0].last
-    return int(last.to(torch.int64).sum().item())
+    from paper_2606_11390_gb300 import _native as gs
+
+    fr, cams = step.frames[0], step.frame_cams[0]
+    img, fT, last = torch.empty_like(fr.image), torch.empty_like(fr.final_T), torch.empty_like(fr.last)
+    cf = torch.zeros(3, dtype=torch.int64, device=fr.image.device)
+    cb = torch.zeros_like(cf)
+    dp = torch.empty_like(fr.d_projected)
+    gs.gs_rasterize_fwd_counted(fr.projected, fr.vals, fr.tile_ranges, cams.sizes, fr.cfg, img, fT, last, cf)
+    gs.gs_rasterize_bwd_pixels_counted(fr.projected, fr.vals, fr.tile_ranges, cams.sizes, fr.cfg, fr.N, fT, last,
+                                       step.dL_dimage, dp, cb)
+    torch.cuda.synchronize()
+    names = ("executed", "evaluated", "composited")
+    return {"raster_fwd": dict(zip(names, (int(x) for x in cf.cpu()))),
+            "raster_bwd": dict(zip(names, (int(x) for x in cb.cpu()))),
+            "sum_last": int(last.to(torch.int64).sum().item())}
 
 
 # ---------------------------------------------------------------------------
 # CPU oracle baseline
 # ---------------------------------------------------------------------------
-def cpu_sample(scene, window=(512, 256)):
-    """Times the oracle on the workload: per-Gaussian stages (projection and
-    its backward) over all Gaussians for the full view, per-pixel stages (key
-    sort, compositing and its backward) on a centred window, then
-    extrapolates the per-pixel stages to the full image."""
+def host_cpu():
+    """Host CPU description: logical CPUs available to this process and the
+    model name (lscpu, else /proc/cpuinfo)."""
+    ncpu = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Vendor ID") and ":" in ln:
+                model = (model + " / " if model else "") + ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for ln in f:
+                    if ln.lower().startswith(("model name", "cpu part")):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"nproc": ncpu, "model": model or "unknown"}
+
+
+def _cpu_timed(scene, window, threads):
+    """One timing of the oracle on the workload (see cpu_sample)."""
+    import contextlib
+
     from oracle import oracle as O
     from paper_2606_11390_gb300 import scenes
 
     W, H = int(scene["sizes"][0, 0]), int(scene["sizes"][0, 1])
     ww, wh = window
     x0, y0 = (W - ww) // 2 // 16 * 16, (H - wh) // 2 // 16 * 16
-    t0 = time.perf_counter()
-    proj = O.project(scene)
-    t_proj = time.perf_counter() - t0
-    d0 = np.zeros((proj["counts"].shape[0], 9))
-    t0 = time.perf_counter()
-    O.project_bwd(scene, d0)
-    t_pbwd = time.perf_counter() - t0
-    crop = scenes.crop_view(scene, x0, y0, ww, wh)
-    cproj = O.project(crop)
-    t0 = time.perf_counter()
-    bins = O.bin_sort(crop, cproj)
-    ras = O.raster_fwd(crop, cproj, bins)
-    L, g = O.loss(ras["image"].astype(np.float32), crop["target"], *crop["loss"])
-    O.raster_bwd(crop, cproj, bins, g)
-    t_pix = time.perf_counter() - t0
+    ctx = O.parallel(threads) if threads > 1 else contextlib.nullcontext(1)
+    with ctx as used:
+        t0 = time.perf_counter()
+        proj = O.project(scene)
+        t_proj = time.perf_counter() - t0
+        d0 = np.zeros((proj["counts"].shape[0], 9))
+        t0 = time.perf_counter()
+        O.project_bwd(scene, d0)
+        t_pbwd = time.perf_counter() - t0
+        crop = scenes.crop_view(scene, x0, y0, ww, wh)
+        cproj = O.project(crop)
+        t0 = time.perf_counter()
+        bins = O.bin_sort(crop, cproj)
+        ras = O.raster_fwd(crop, cproj, bins)
+        L, g = O.loss(ras["image"].astype(np.float32), crop["target"], *crop["loss"])
+        O.raster_bwd(crop, cproj, bins, g)
+        t_pix = time.perf_counter() - t0
     P = W * H
     total = t_proj + t_pbwd + t_pix * P / (ww * wh)
-    return {"value": P / total / 1e6, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
-            "sample": (f"single-threaded C++ oracle: projection fwd+bwd over all {scene['means'].shape[0]} "
-                       f"Gaussians for the full {W}x{H} view ({t_proj + t_pbwd:.1f} s), sort+composite+backward on "
-                       f"a {ww}x{wh} window ({t_pix:.1f} s) extrapolated x{P / (ww * wh):.1f} to the full image"),
-            "seconds_measured": round(t_proj + t_pbwd + t_pix, 2)}
+    return {"value": P / total / 1e6, "threads": int(used), "t_gauss": t_proj + t_pbwd, "t_pix": t_pix,
+            "extrapolation": P / (ww * wh), "seconds_measured": round(t_proj + t_pbwd + t_pix, 2)}
+
+
+def cpu_sample(scene, window=(512, 256)):
+    """Times the oracle on the workload, single-threaded and with OpenMP on
+    every host core: per-Gaussian stages (projection and its backward) over
+    all Gaussians for the full view, per-pixel stages (key sort, compositing
+    and its backward) on a centred window, then extrapolates the per-pixel
+    stages to the full image. The key sort (std::stable_sort) stays serial in
+    both builds."""
+    host = host_cpu()
+    W, H = int(scene["sizes"][0, 0]), int(scene["sizes"][0, 1])
+    one = _cpu_timed(scene, window, 1)
+    par = _cpu_timed(scene, window, host["nproc"])
+    ww, wh = window
+
+    def sample(r, what):
+        return (f"{what} C++ oracle: projection fwd+bwd over all {scene['means'].shape[0]} Gaussians for the full "
+                f"{W}x{H} view ({r['t_gauss']:.1f} s), sort+composite+backward on a {ww}x{wh} window "
+                f"({r['t_pix']:.1f} s) extrapolated x{r['extrapolation']:.1f} to the full image")
+
+    return {"value": par["value"], "unit": "Mpix/s", "cores": par["threads"], "kind": "oracle",
+            "sample": sample(par, f"OpenMP ({par['threads']} threads)"),
+            "seconds_measured": par["seconds_measured"], "host": host,
+            "single_thread": {"value": one["value"], "unit": "Mpix/s", "cores": 1,
+                              "sample": sample(one, "single-threaded"),
+                              "seconds_measured": one["seconds_measured"]}}
 
 
 def reference_arm(args, dist):
@@ -332,7 +428,8 @@ def reference_arm(args, dist):
             "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "reference",
             "config": {"workload": scene["name"], "sample": f"{ww}x{wh} window", "gaussians": int(scene["means"].shape[0])},
-            "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": 1, "kind": "oracle", "sample": sample,
+                             "host": host_cpu()},
             "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -365,7 +462,8 @@ def main():
         scene["cfg"] = dict(scene["cfg"], flags=gs.GS_FLAG_RASTER_2PX)
     tile = tuple(int(x) for x in args.tile.split("x")) if args.tile else (scene["cfg"]["tile_w"], scene["cfg"]["tile_h"])
     adam = scene["name"] == "street"  # the street workload's step includes the fused Adam update
-    step = R.TrainStep(scene, mode=args.mode, graph=not args.no_graph, tile=tile, adam=adam, loss=args.loss).prepare()
+    step = R.TrainStep(scene, mode=args.mode, graph=False if args.no_graph else None, tile=tile, adam=adam,
+                       loss=args.loss).prepare()
     P = step.cams.n_pixels
     launches = step.launches_per_step
     stream = torch.cuda.current_stream()
@@ -388,8 +486,8 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     t_end = clocks.mark()
+    clk = clock_record(clocks, step, t_start, t_end)
     dist.barrier()
-    clk = clocks.stop(t_start, t_end)
     step.check()
     ms_local = e0.elapsed_time(e1) / args.steps
     ms = dist.max(ms_local)
@@ -402,10 +500,15 @@ def main():
             st = stage_times(step)
             extra["stage_ms"] = {k: round(v, 4) for k, v in st.items()}
             extra["n_isect"] = step.n_isect()
-            extra["pairs_to_last"] = pair_counts(step)
+            pc = pair_counts(step)
+            extra["raster_pairs"] = pc
             dom = max(st, key=st.get)
             peaks, src = measured_peaks()
-            extra["roofline"] = roofline_for(dom, st[dom], step, peaks, src, scene["name"])
+            extra["roofline"] = roofline_for(dom, st[dom], step, peaks, src, scene["name"], pc)
+            extra["stage_roofline"] = {k: roofline_for(k, v, step, peaks, src, scene["name"], pc)
+                                       for k, v in st.items() if k in ROOFLINE_STAGES}
+            if step.adam_on:
+                extra["adam"] = adam_measure(step, peaks, src)
             extra["ssim_loss"] = ssim_kernel_measure(step.image, step.target, step.cams.sizes, peaks, src)
             extra["densify_stats"] = densify_measure(step, peaks, src)
             if not args.no_partitioned and scene["name"] != "street":
@@ -435,17 +538,28 @@ def main():
 
 
 # Algorithmic FP32 work of the method per (pixel, splat) pair, mul and add
-# counted separately. Forward 24: offsets and power 9, exp 2, alpha 2
-# (opacity product, cap), transmittance 2, colour 7 (weight alpha T, three
-# multiply-adds), threshold tests 2. Backward 60: alpha recomputation 17
-# (offsets, power, exp, alpha and the skip tests), transmittance recovery 2,
-# colour gradient 7, alpha gradient and running colour sum 10, 2D-mean, conic
-# and opacity gradients 15, accumulation into the splat's nine sums 9.
-FLOP_PER_PAIR = {"raster_fwd": 24, "raster_bwd": 60}
+# counted separately, by what the compositing rule does with the pair.
+# Forward, composited 24: offsets and power 9, exp 2, alpha 2 (opacity
+# product, cap), threshold tests 2, transmittance 2, colour 7 (weight
+# alpha T, three multiply-adds); evaluated and skipped (power < 0, alpha <
+# alpha_min, or the stopping entry) 15: the first four groups only.
+# Backward, composited 60: alpha recomputation 17 (offsets, power, exp,
+# alpha, the skip tests and the cap test), transmittance recovery 2, colour
+# gradient 7, alpha gradient and running colour sum 10, 2D-mean, conic and
+# opacity gradients 15, accumulation into the splat's nine sums 9; evaluated
+# and not composited 17 (the alpha recomputation that finds it skipped).
+# Pairs the per-warp cull drops are work the kernel provably does not need
+# and are not charged; pairs a lane executes for a pixel that has stopped or
+# lies outside the image are waste, not work.
+FLOP_PER_PAIR = {"raster_fwd": {"composited": 24, "skipped": 15},
+                 "raster_bwd": {"composited": 60, "skipped": 17}}
+ROOFLINE_STAGES = ("project", "bin_sort", "raster_fwd", "raster_bwd", "project_bwd")
 
 
 # CUDA sources that make up each timed stage (plus the shared headers).
-KERNEL_SOURCES = {"raster_fwd": ["raster.cu"], "raster_bwd": ["raster.cu"], "project": ["project.cu"],
+RASTER_SOURCES = ["raster.cu", "raster_kernels.cuh", "raster_launch.h", "raster_inst_fwd.cu", "raster_inst_bwd.cu",
+                  "raster_inst_aux.cu"]
+KERNEL_SOURCES = {"raster_fwd": RASTER_SOURCES, "raster_bwd": RASTER_SOURCES, "project": ["project.cu"],
                   "project_bwd": ["project.cu"], "bin_sort": ["binsort.cu"], "loss": ["loss_adam.cu"],
                   "ssim_loss": ["ssim.cu"]}
 COMMON_SOURCES = ["gs_common.cuh", "gs_internal.h"]
@@ -480,26 +594,41 @@ def recorded_traffic(kernel, workload):
     return e.get("bytes_per_launch")
 
 
-def roofline_for(stage, ms, step, peaks, src, workload):
-    """Achieved vs peak for the dominant stage. The rasteriser is bound by
-    FP32 issue: algorithmic FLOPs = (pixel, splat) pairs up to each pixel's
-    last contributor x FLOPs per pair of the method; peak = SMs x 128 FP32
-    lanes x 2 (FMA) x max SM clock. The other stages are HBM-bound with the
-    algorithmic bytes of their inputs and outputs."""
+def raster_work(stage, pc):
+    """Algorithmic FLOPs of one rasteriser launch from its pair counts, with
+    the charge of each class."""
+    c = pc[stage]
+    f = FLOP_PER_PAIR[stage]
+    comp, skipped = c["composited"], c["evaluated"] - c["composited"]
+    flops = comp * f["composited"] + skipped * f["skipped"]
+    return flops, {"composited": {"pairs": comp, "flop_per_pair": f["composited"]},
+                   "evaluated_not_composited": {"pairs": skipped, "flop_per_pair": f["skipped"]},
+                   "executed_lane_pairs": c["executed"], "sum_last": pc["sum_last"],
+                   "lane_efficiency": c["evaluated"] / max(c["executed"], 1)}
+
+
+def roofline_for(stage, ms, step, peaks, src, workload, pc=None):
+    """Achieved vs peak of one stage. The rasteriser is bound by FP32 issue:
+    algorithmic FLOPs = the pairs it evaluates, charged by class (composited
+    or skipped; see FLOP_PER_PAIR), counted by the kernels' pair-counting
+    variants; peak = SMs x 128 FP32 lanes x 2 (FMA) x max SM clock. The other
+    stages are HBM-bound with the algorithmic bytes of their inputs and
+    outputs."""
     import torch
 
     N, V, I, P = step.N, step.cams.V, step.n_isect(), step.cams.n_pixels
     traffic = recorded_traffic(stage, workload)
     if stage in FLOP_PER_PAIR:
-        pairs = pair_counts(step)
+        pc = pc if pc is not None else pair_counts(step)
+        flops, work = raster_work(stage, pc)
         sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
         n_sm = torch.cuda.get_device_properties(0).multi_processor_count
         peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
-        achieved = pairs * FLOP_PER_PAIR[stage] / (ms * 1e-3) / 1e12
+        achieved = flops / (ms * 1e-3) / 1e12
         return {"kernel": stage, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz ({src} max SM clock; no measured FP32 peak)",
-                "work": f"{pairs} pixel-splat pairs x {FLOP_PER_PAIR[stage]} FLOP", "ms": ms}
+                "work": work, "flop": flops, "ms": ms}
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     if stage == "project":
         bytes_ = N * 236 + V * N * (48 + 8 + 4)
@@ -593,6 +722,44 @@ def partitioned_sort_measure(step, parts=(1, 2, 4, 8), iters=10):
     return {"bin_sort_ms_by_partitions": out}
 
 
+def adam_measure(step, peaks, src, iters=10):
+    """gs_adam_step (the fused Adam update of the step's optimiser) alone on
+    the step's parameters, gradients and moments (CUDA events on the
+    launching stream; at 64M Gaussians each array is 15 GB, far beyond L2).
+    HBM-bound: per scalar p, g, m, v read and p, m, v written, 28 B. The
+    extra updates move the parameters by iters x lr, after every timed step."""
+    import torch
+
+    from paper_2606_11390_gb300 import _native as gs
+
+    stream = torch.cuda.current_stream()
+    p, g = step.params.flat, step.grads.flat
+    b1, b2 = step.betas
+
+    def one():
+        step.step_count.add_(1)
+        gs.gs_adam_step(p, g, step.exp_avg, step.exp_avg_sq, step.lr, b1, b2, step.eps, step.step_count)
+
+    one()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(iters)]
+    for a, b in ev:
+        step.step_count.add_(1)
+        a.record(stream)
+        gs.gs_adam_step(p, g, step.exp_avg, step.exp_avg_sq, step.lr, b1, b2, step.eps, step.step_count)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / iters
+    n = p.numel()
+    bytes_ = 28 * n
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    gbs = bytes_ / (ms * 1e-3) / 1e9
+    return {"ms": ms, "scalars": n, "launches": 1,
+            "roofline": {"kernel": "adam", "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                         "frac": gbs / hbm, "traffic": None, "work": f"{n} scalars x 28 B",
+                         "peak_source": f"{src} hbm_gbs"}}
+
+
 def densify_measure(step, peaks, src, iters=20):
     """gs_densify_stats alone on the step's backward buffers (one launch per
     step when TrainStep(densify_stats=True)); HBM-bound: per (view, Gaussian)
@@ -645,7 +812,8 @@ def morton_measure(step, scene, args, tile, ms_input_order):
     if status.item() != 0:
         raise RuntimeError(f"morton status {status.item()}")
     order_ms, gather_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
-    st = R.TrainStep(scene, mode=args.mode, graph=not args.no_graph, tile=tile, params=out, loss=args.loss).prepare()
+    st = R.TrainStep(scene, mode=args.mode, graph=False if args.no_graph else None, tile=tile, params=out,
+                     loss=args.loss).prepare()
     for _ in range(args.warmup):
         st.run()
     torch.cuda.synchronize()
@@ -705,16 +873,23 @@ def batched_vs_per_view(args, tile=None):
 
     scene = make_scene("batch16")
     if tile is None:
-        tile, tune = autotune.best_tile(scene, steps=2)
+        best, tune = autotune.best_config(scene, steps=2)
     else:
-        tune = {}
+        best, tune = {"tile": tuple(tile), "ppt": 4, "batch_fwd": 0, "batch_bwd": 0}, {}
+    kw = autotune.step_kwargs(best)
     out = {"workload": "batch16", "gaussians": int(scene["means"].shape[0]), "views": 16,
-           "tile": f"{tile[0]}x{tile[1]}", "autotune_ms": {f"{t[0]}x{t[1]}": round(v, 3) for t, v in tune.items()}}
+           "tile": f"{best['tile'][0]}x{best['tile'][1]}", "raster_config": autotune.name(best),
+           "autotune_ms": {k: round(v, 3) for k, v in tune.items()}}
     n = max(3, args.steps // 4)
     res = {}
     params = None
-    for mode in ("batched", "per_view"):
-        step = R.TrainStep(scene, mode=mode, tile=tile, params=params).prepare()
+    # batched: one launch per stage for all views, captured; per_view: one
+    # launch per stage and view, eager (the plain per-camera loop);
+    # per_view_graph: the same per-view launches captured in a graph, which
+    # separates the gain of batching from that of graph capture
+    for label, mode, graph in (("batched", "batched", True), ("per_view", "per_view", False),
+                               ("per_view_graph", "per_view", True)):
+        step = R.TrainStep(scene, mode=mode, graph=graph, params=params, **kw).prepare()
         params = step.params
         for _ in range(2):
             step.run()
@@ -727,12 +902,13 @@ def batched_vs_per_view(args, tile=None):
         torch.cuda.synchronize()
         step.check()
         ms = a.elapsed_time(b) / n
-        res[mode] = {"ms_per_step": ms, "Mpix_s": step.cams.n_pixels / (ms * 1e-3) / 1e6,
-                     "launches_per_step": step.launches_per_step, "n_isect": step.n_isect()}
+        res[label] = {"ms_per_step": ms, "Mpix_s": step.cams.n_pixels / (ms * 1e-3) / 1e6,
+                      "launches_per_step": step.launches_per_step, "n_isect": step.n_isect()}
         del step
         torch.cuda.empty_cache()
     out.update(res)
     out["batched_speedup"] = res["per_view"]["ms_per_step"] / res["batched"]["ms_per_step"]
+    out["batched_speedup_vs_per_view_graph"] = res["per_view_graph"]["ms_per_step"] / res["batched"]["ms_per_step"]
     return out
 
 

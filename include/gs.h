@@ -89,16 +89,24 @@ typedef struct gs_camera {
   float fx, fy, cx, cy;
 } gs_camera;
 
-/* Rendering constants, 52 bytes. tile_w x tile_h must be one of 8x8, 16x16,
+/* Rendering constants, 60 bytes. tile_w x tile_h must be one of 8x8, 16x16,
  * 32x16, 32x32. sh_degree in 0..3. flags: GS_FLAG_* bits. Culling: near_plane < depth < far_plane. eps2d is
  * added to the diagonal of every 2D covariance. Compositing: alpha =
  * min(alpha_cap, opacity * exp(-power)); entries with alpha < alpha_min are
  * skipped; compositing stops before the entry that would take the
- * transmittance below t_stop. bg is added with the final transmittance. */
+ * transmittance below t_stop. bg is added with the final transmittance.
+ * raster_batch_fwd / raster_batch_bwd: splats the rasteriser stages per
+ * shared-memory batch in the forward / backward, 0 for the default
+ * (forward: max(threads per tile, 128); backward: threads per tile, clamped
+ * to [64, 256]) or one of 64, 128, 256 (GS_ERR_UNSUPPORTED otherwise); a
+ * performance choice only, results are the same (with a non-zero bg the
+ * backward keeps its default). Threads per tile = tile_w * tile_h / pixels
+ * per thread (see GS_FLAG_RASTER_2PX). */
 typedef struct gs_config {
   int32_t tile_w, tile_h, sh_degree, flags;
   float near_plane, far_plane, eps2d, alpha_cap, alpha_min, t_stop;
   float bg[3];
+  int32_t raster_batch_fwd, raster_batch_bwd;
 } gs_config;
 
 /* gs_config.flags: gs_rasterize_bwd adds the parameter gradients to the
@@ -275,6 +283,24 @@ GS_API int gs_rasterize_fwd(const float* projected, const uint32_t* vals, const 
                      int32_t V, const gs_config* cfg, float* image, float* final_T, uint32_t* last,
                      gs_stream_t stream);
 
+/* gs_rasterize_fwd_counted - gs_rasterize_fwd (same outputs) that also counts
+ * the pixel-splat pairs of its work, for measuring the rasteriser against its
+ * arithmetic roofline (paper §4 names rasterisation the cost centre of the
+ * step). A separately compiled variant of the kernel: the normal entry points
+ * count nothing.
+ * out (device): pair_counts_dev [3] uint64, added to (the caller zeroes it):
+ *   [0] pairs executed: for every splat a warp takes from its tile's list
+ *       after its per-warp cull, one pair per pixel of each thread that runs
+ *       the step (pixels that have stopped or lie outside the image included);
+ *   [1] pairs evaluated: those of [0] whose pixel is still compositing;
+ *   [2] pairs composited: those of [1] with power >= 0, alpha >= alpha_min
+ *       and T (1 - alpha) >= t_stop.
+ * Errors: as gs_rasterize_fwd; GS_ERR_ARG for a null or misaligned
+ * pair_counts_dev. */
+GS_API int gs_rasterize_fwd_counted(const float* projected, const uint32_t* vals, const uint32_t* tile_ranges,
+                                    const int32_t* sizes, int32_t V, const gs_config* cfg, float* image,
+                                    float* final_T, uint32_t* last, uint64_t* pair_counts_dev, gs_stream_t stream);
+
 /* gs_rasterize_fwd_l1l2 - gs_rasterize_fwd with the L1 + L2 image loss of
  * gs_image_loss computed in the same kernel, as each pixel's colour is final
  * (the rendered image is not read back). Paper: §4, rasterisation and the
@@ -337,6 +363,22 @@ GS_API int gs_rasterize_bwd_pixels(const float* projected, const uint32_t* vals,
                                    const int32_t* sizes, int32_t V, const gs_config* cfg, int64_t N,
                                    const float* final_T, const uint32_t* last, const float* dL_dimage,
                                    float* d_projected, gs_stream_t stream);
+
+/* gs_rasterize_bwd_pixels_counted - gs_rasterize_bwd_pixels (same outputs)
+ * that also counts the pixel-splat pairs of its work (paper §4, the backward
+ * of rasterisation), like gs_rasterize_fwd_counted:
+ * out (device): pair_counts_dev [3] uint64, added to (the caller zeroes it):
+ *   [0] pairs executed (listed splats x pixels of each thread running the
+ *       step), [1] pairs evaluated: those of [0] whose entry lies before the
+ *       pixel's last contributor, [2] pairs composited in the forward among
+ *       [1] (the ones that receive a gradient).
+ * Errors: as gs_rasterize_bwd_pixels; GS_ERR_ARG for a null or misaligned
+ * pair_counts_dev. */
+GS_API int gs_rasterize_bwd_pixels_counted(const float* projected, const uint32_t* vals,
+                                           const uint32_t* tile_ranges, const int32_t* sizes, int32_t V,
+                                           const gs_config* cfg, int64_t N, const float* final_T,
+                                           const uint32_t* last, const float* dL_dimage, float* d_projected,
+                                           uint64_t* pair_counts_dev, gs_stream_t stream);
 
 /* gs_project_bwd - second half of gs_rasterize_bwd: chains d_projected
  * (from gs_rasterize_bwd_pixels) through SH colour and projection to the

@@ -34,6 +34,9 @@
 // untiled renderer, python's sort on (tile, depth, index), central finite
 // differences in double for every parameter gradient, textbook Adam.
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -438,6 +441,9 @@ void project_all(const R* means, const R* log_scales, const R* quats, const R* o
                  const std::vector<OCam>& cams, const OConfig& cfg, R* projected, int16_t* rects, uint32_t* counts) {
   const int V = (int)cams.size();
   for (int v = 0; v < V; ++v) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
     for (int64_t g = 0; g < N; ++g) {
       Proj<R> P;
       project_one<R>(means + 3 * g, log_scales + 3 * g, quats + 4 * g, opac[g], sh + 48 * g, cfg.sh_degree, cams[v], cfg,
@@ -503,6 +509,18 @@ inline double rel_margin(double value, double threshold) {
 }
 const double kMarginal = 1e-4;
 
+// Writes shared between pixels: a flag set to 1 and a gradient sum. In the
+// OpenMP build (used only to time the oracle on all host cores) pixels run
+// in parallel, so these become atomic; the serial build does plain stores and
+// adds in the same order as always.
+inline void flag_set(uint8_t* p) { __atomic_store_n(p, (uint8_t)1, __ATOMIC_RELAXED); }
+inline void acc(double* p, double v) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+  *p += v;
+}
+
 // Composite one pixel. `hits` (may be null) receives, for each composited
 // entry, 2*k + (1 if the alpha cap was active).
 // Optionally flags marginal decisions per (view, Gaussian) and per pixel.
@@ -511,8 +529,9 @@ const double kMarginal = 1e-4;
 template <class R>
 void composite_pixel(const R* projected, const uint32_t* vals, uint32_t start, uint32_t end, R px, R py, const OConfig& cfg,
                      R out[3], R& T_final, uint32_t& last, std::vector<int64_t>* hits, uint8_t* marg_vg, bool* marg_pix,
-                     uint64_t* sig = nullptr) {
+                     uint64_t* sig = nullptr, uint32_t* ncomp = nullptr) {
   if (sig) *sig = 0;
+  if (ncomp) *ncomp = 0;
   R T = R(1);
   R Cacc[3] = {R(0), R(0), R(0)};
   last = 0;
@@ -525,7 +544,7 @@ void composite_pixel(const R* projected, const uint32_t* vals, uint32_t start, u
     bool marg = false;
     if (power < R(0)) {
       if (std::fabs((double)power) < 1e-5) marg = true;
-      if (marg && marg_vg) { marg_vg[vg] = 1; if (marg_pix) *marg_pix = true; }
+      if (marg && marg_vg) { flag_set(marg_vg + vg); if (marg_pix) *marg_pix = true; }
       continue;
     }
     const R G = std::exp(-power);
@@ -533,11 +552,11 @@ void composite_pixel(const R* projected, const uint32_t* vals, uint32_t start, u
     const R alpha = std::min(cap, oG);
     if (rel_margin((double)oG, (double)cap) < kMarginal) marg = true;
     if (rel_margin((double)alpha, (double)amin) < kMarginal) marg = true;
-    if (marg && marg_vg) { marg_vg[vg] = 1; if (marg_pix) *marg_pix = true; }
+    if (marg && marg_vg) { flag_set(marg_vg + vg); if (marg_pix) *marg_pix = true; }
     if (alpha < amin) continue;
     const R Tn = T * (R(1) - alpha);
     if (rel_margin((double)Tn, (double)tstop) < kMarginal) {
-      if (marg_vg) marg_vg[vg] = 1;
+      if (marg_vg) flag_set(marg_vg + vg);
       if (marg_pix) *marg_pix = true;
     }
     if (Tn < tstop) break;
@@ -546,6 +565,7 @@ void composite_pixel(const R* projected, const uint32_t* vals, uint32_t start, u
     last = k - start + 1;
     if (hits) hits->push_back(2 * (int64_t)k + (oG > cap ? 1 : 0));
     if (sig) *sig += ((uint64_t)(k - start) + 1) * 0x9E3779B97F4A7C15ull + (oG > cap ? 1 : 0);
+    if (ncomp) ++*ncomp;
   }
   for (int ch = 0; ch < 3; ++ch) out[ch] = Cacc[ch] + T * R(cfg.bg[ch]);
   T_final = T;
@@ -561,9 +581,12 @@ inline int view_of_tile(const TileLayout& L, int64_t tile) {
 template <class R>
 void raster_fwd(const R* projected, const uint32_t* vals, const uint32_t* ranges, const std::vector<OCam>& cams,
                 const OConfig& cfg, const int64_t* tiles, int64_t n_sel, R* image, R* final_T, uint32_t* last,
-                uint8_t* marg_vg, uint8_t* marg_pix, uint64_t* hitsig) {
+                uint8_t* marg_vg, uint8_t* marg_pix, uint64_t* hitsig, uint32_t* ncomp) {
   const TileLayout L = make_layout(cams, cfg);
   const int64_t nt = tiles ? n_sel : L.n_tiles;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
   for (int64_t ti = 0; ti < nt; ++ti) {
     const int64_t tile = tiles ? tiles[ti] : ti;
     const int v = view_of_tile(L, tile);
@@ -576,7 +599,8 @@ void raster_fwd(const R* projected, const uint32_t* vals, const uint32_t* ranges
         R out[3];
         bool mp = false;
         composite_pixel<R>(projected, vals, ranges[2 * tile], ranges[2 * tile + 1], R(i) + R(0.5), R(j) + R(0.5), cfg, out,
-                           final_T[p], last[p], nullptr, marg_vg, &mp, hitsig ? hitsig + p : nullptr);
+                           final_T[p], last[p], nullptr, marg_vg, &mp, hitsig ? hitsig + p : nullptr,
+                           ncomp ? ncomp + p : nullptr);
         for (int ch = 0; ch < 3; ++ch) image[3 * p + ch] = out[ch];
         if (marg_pix) marg_pix[p] = mp ? 1 : 0;
       }
@@ -622,21 +646,21 @@ void composite_pixel_bwd(const R* projected, const uint32_t* vals, uint32_t star
     double dalpha = 0.0;
     for (int ch = 0; ch < 3; ++ch) {
       const double c = (double)rec[8 + ch];
-      g[5 + ch] += w * dout[ch];
+      acc(g + 5 + ch, w * dout[ch]);
       dalpha += dout[ch] * (c * Tk[ii] - S[ch] / (1.0 - alpha[ii]) - Tfin * (double)cfg.bg[ch] / (1.0 - alpha[ii]));
     }
     for (int ch = 0; ch < 3; ++ch) S[ch] += (double)rec[8 + ch] * w;
     if (!capped[ii]) {
       // alpha = o * exp(-power)
-      g[8] += dalpha * G[ii];
+      acc(g + 8, dalpha * G[ii]);
       const double dpower = -dalpha * alpha[ii];
       const double A = rec[2], B = rec[3], C = rec[4];
       // power = 0.5 (A dx^2 + C dy^2) + B dx dy, dx = px - mean.x
-      g[0] += dpower * (-(A * dx[ii] + B * dy[ii]));
-      g[1] += dpower * (-(B * dx[ii] + C * dy[ii]));
-      g[2] += dpower * 0.5 * dx[ii] * dx[ii];
-      g[3] += dpower * dx[ii] * dy[ii];
-      g[4] += dpower * 0.5 * dy[ii] * dy[ii];
+      acc(g + 0, dpower * (-(A * dx[ii] + B * dy[ii])));
+      acc(g + 1, dpower * (-(B * dx[ii] + C * dy[ii])));
+      acc(g + 2, dpower * 0.5 * dx[ii] * dx[ii]);
+      acc(g + 3, dpower * dx[ii] * dy[ii]);
+      acc(g + 4, dpower * 0.5 * dy[ii] * dy[ii]);
     }
   }
 }
@@ -646,6 +670,9 @@ void raster_bwd(const R* projected, const uint32_t* vals, const uint32_t* ranges
                 const OConfig& cfg, const int64_t* tiles, int64_t n_sel, const double* dL_dimage, double* d_proj) {
   const TileLayout L = make_layout(cams, cfg);
   const int64_t nt = tiles ? n_sel : L.n_tiles;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
   for (int64_t ti = 0; ti < nt; ++ti) {
     const int64_t tile = tiles ? tiles[ti] : ti;
     const int v = view_of_tile(L, tile);
@@ -798,6 +825,9 @@ void project_bwd(const R* means, const R* log_scales, const R* quats, const R* o
                  const std::vector<OCam>& cams, const OConfig& cfg, const double* d_proj, const int64_t* gsel, int64_t n_sel,
                  double* gm, double* gls, double* gq, double* go, double* gsh) {
   const int64_t n = gsel ? n_sel : N;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
   for (int64_t i = 0; i < n; ++i) {
     const int64_t g = gsel ? gsel[i] : i;
     project_bwd_one<R>(means, log_scales, quats, opac, sh, N, g, cams, cfg, d_proj, gm + 3 * i, gls + 3 * i, gq + 4 * i,
@@ -881,9 +911,9 @@ int64_t oracle_num_tiles(const int32_t* sizes, int32_t V, const OConfig* cfg) {
   void oracle_raster_fwd_##SUF(const R* projected, const uint32_t* vals, const uint32_t* ranges, const float* cams,         \
                                const int32_t* sizes, int32_t V, const OConfig* cfg, const int64_t* tiles, int64_t n_sel,   \
                                R* image, R* final_T, uint32_t* last, uint8_t* marg_vg, uint8_t* marg_pix,                  \
-                               uint64_t* hitsig) {                                                                         \
+                               uint64_t* hitsig, uint32_t* ncomp) {                                                        \
     raster_fwd<R>(projected, vals, ranges, load_cams(cams, sizes, V), *cfg, tiles, n_sel, image, final_T, last, marg_vg,    \
-                  marg_pix, hitsig);                                                                                       \
+                  marg_pix, hitsig, ncomp);                                                                                \
   }                                                                                                                        \
   void oracle_raster_bwd_##SUF(const R* projected, const uint32_t* vals, const uint32_t* ranges, const float* cams,         \
                                const int32_t* sizes, int32_t V, const OConfig* cfg, const int64_t* tiles, int64_t n_sel,   \
@@ -920,6 +950,22 @@ double oracle_loss(const float* image, const float* target, int64_t n, double w1
 }
 
 // Adam (Kingma & Ba 2015, Algorithm 1) for step t >= 1, in double.
+// Host threads the OpenMP build uses (1 in the serial build).
+int oracle_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 void oracle_adam(double* param, const double* grad, double* m, double* v, int64_t n, double lr, double beta1, double beta2,
                  double eps, int32_t t) {
   const double bc1 = 1.0 - std::pow(beta1, t), bc2 = 1.0 - std::pow(beta2, t);

@@ -10,9 +10,17 @@ no code with the CUDA library.
 Precision: functions take ``precision="f32"`` (decisions and forward values in
 float, the precision of the GPU kernels) or ``"f64"`` (everything in double,
 used by the finite-difference pins). Gradients are always returned in double.
+
+Threads: the oracle is built twice from the same source, serial (what the
+tests use) and with OpenMP over Gaussians (projection and its backward) and
+over tiles (compositing and its backward). Inside ``with parallel(n):`` the
+functions run the OpenMP build on n host threads; it exists to time the
+oracle on all cores of a host, and its gradient sums may differ from the
+serial build's in the last bits (atomic adds in thread order).
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -24,20 +32,51 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gs_oracle.cpp")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libgs_oracle.so")
+_OMP_PATH = os.path.join(_BUILD, "libgs_oracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
+_use_omp = False
 
 CXXFLAGS = ["-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
 
 
+def _build_one(path, extra, force):
+    if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+        tmp = path + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", *CXXFLAGS, *extra, "-o", tmp, _SRC])
+        os.replace(tmp, path)
+    return path
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle into oracle/_build/libgs_oracle.so (host compiler only)."""
+    """Compile the oracle into oracle/_build/libgs_oracle.so (serial) and
+    libgs_oracle_omp.so (OpenMP), host compiler only; returns the serial one."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["g++", *CXXFLAGS, "-o", tmp, _SRC])
-        os.replace(tmp, _LIB_PATH)
+    _build_one(_LIB_PATH, [], force)
+    try:
+        _build_one(_OMP_PATH, ["-fopenmp"], force)
+    except (subprocess.CalledProcessError, OSError):
+        pass  # no OpenMP runtime: parallel() then raises
     return _LIB_PATH
+
+
+@contextlib.contextmanager
+def parallel(threads: int | None = None):
+    """Runs the oracle's OpenMP build inside the block, on `threads` host
+    threads (default: all the runtime offers). Yields the thread count."""
+    global _use_omp
+    build()
+    if not os.path.exists(_OMP_PATH):
+        raise RuntimeError("the OpenMP build of the oracle is not available (g++ -fopenmp failed)")
+    L = _load(_OMP_PATH)
+    if threads:
+        L.oracle_set_threads(int(threads))
+    old = _use_omp
+    _use_omp = True
+    try:
+        yield int(L.oracle_max_threads())
+    finally:
+        _use_omp = old
 
 
 class OConfig(ctypes.Structure):
@@ -69,11 +108,17 @@ _I32 = ctypes.c_int32
 
 
 def lib():
-    global _lib
+    """The serial build, or the OpenMP build inside parallel()."""
+    if _use_omp:
+        return _load(_OMP_PATH)
+    return _load(build())
+
+
+def _load(path):
     with _lock:
-        if _lib is None:
-            _lib = ctypes.CDLL(build())
-            L = _lib
+        if path not in _libs:
+            L = ctypes.CDLL(path)
+            _libs[path] = L
             L.oracle_exp_cody_waite.restype = ctypes.c_float
             L.oracle_exp_cody_waite.argtypes = [ctypes.c_float]
             L.oracle_sh_basis.argtypes = [_VP, _I64, _VP]
@@ -85,7 +130,7 @@ def lib():
                 f.restype = _I64
                 f.argtypes = [_VP, _VP, _VP, _I64, _VP, _VP, _I32, _VP, _VP, _VP, _I64, _VP]
                 getattr(L, f"oracle_raster_fwd_{suf}").argtypes = [_VP, _VP, _VP, _VP, _VP, _I32, _VP, _VP, _I64,
-                                                                    _VP, _VP, _VP, _VP, _VP, _VP]
+                                                                    _VP, _VP, _VP, _VP, _VP, _VP, _VP]
                 getattr(L, f"oracle_raster_bwd_{suf}").argtypes = [_VP, _VP, _VP, _VP, _VP, _I32, _VP, _VP, _I64,
                                                                     _VP, _VP]
                 getattr(L, f"oracle_project_bwd_{suf}").argtypes = [_VP] * 5 + [_I64, _VP, _VP, _I32, _VP, _VP, _VP,
@@ -96,7 +141,10 @@ def lib():
             L.oracle_loss.argtypes = [_VP, _VP, _I64, ctypes.c_double, ctypes.c_double, _VP]
             L.oracle_adam.argtypes = [_VP, _VP, _VP, _VP, _I64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, _I32]
-    return _lib
+            L.oracle_max_threads.restype = ctypes.c_int
+            L.oracle_max_threads.argtypes = []
+            L.oracle_set_threads.argtypes = [ctypes.c_int]
+    return _libs[path]
 
 
 def _dt(precision):
@@ -171,8 +219,9 @@ def bin_sort(scene, proj, precision="f32"):
 
 def raster_fwd(scene, proj, bins, precision="f32", tiles=None):
     """Image [P,3], final transmittance [P], last-contributor count [P],
-    marginal-decision flags per (view, Gaussian) [V*N] and per pixel [P], and a
-    per-pixel signature of the set of composited list entries [P]."""
+    marginal-decision flags per (view, Gaussian) [V*N] and per pixel [P], a
+    per-pixel signature of the set of composited list entries [P] and the
+    number of entries composited per pixel [P]."""
     dt = _dt(precision)
     cams, sizes = _cams(scene)
     V = cams.shape[0]
@@ -185,13 +234,14 @@ def raster_fwd(scene, proj, bins, precision="f32", tiles=None):
     marg_vg = np.zeros(V * N, np.uint8)
     marg_pix = np.zeros(P, np.uint8)
     hitsig = np.zeros(P, np.uint64)
+    ncomp = np.zeros(P, np.uint32)
     t = None if tiles is None else _c(tiles, np.int64)
     getattr(lib(), f"oracle_raster_fwd_{precision}")(
         _p(_c(proj["projected"], dt)), _p(_c(bins["vals"], np.uint32)), _p(_c(bins["ranges"], np.uint32)), _p(cams),
         _p(sizes), V, ctypes.byref(cfg), _p(t), 0 if t is None else t.shape[0], _p(image), _p(final_T), _p(last),
-        _p(marg_vg), _p(marg_pix), _p(hitsig))
+        _p(marg_vg), _p(marg_pix), _p(hitsig), _p(ncomp))
     return {"image": image, "final_T": final_T, "last": last, "marginal_vg": marg_vg, "marginal_pix": marg_pix,
-            "hit_signature": hitsig}
+            "hit_signature": hitsig, "composited": ncomp}
 
 
 def raster_bwd(scene, proj, bins, dL_dimage, precision="f32", tiles=None):

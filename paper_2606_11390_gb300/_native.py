@@ -35,6 +35,7 @@ class GSConfig(ctypes.Structure):
         ("near_plane", ctypes.c_float), ("far_plane", ctypes.c_float), ("eps2d", ctypes.c_float),
         ("alpha_cap", ctypes.c_float), ("alpha_min", ctypes.c_float), ("t_stop", ctypes.c_float),
         ("bg", ctypes.c_float * 3),
+        ("raster_batch_fwd", ctypes.c_int32), ("raster_batch_bwd", ctypes.c_int32),
     ]
 
 
@@ -46,6 +47,8 @@ def make_config(cfg: dict) -> GSConfig:
     c.alpha_cap, c.alpha_min, c.t_stop = cfg["alpha_cap"], cfg["alpha_min"], cfg["t_stop"]
     for i in range(3):
         c.bg[i] = cfg["bg"][i]
+    c.raster_batch_fwd = int(cfg.get("raster_batch_fwd", 0))
+    c.raster_batch_bwd = int(cfg.get("raster_batch_bwd", 0))
     return c
 
 
@@ -64,10 +67,13 @@ _SIGNATURES = {
                      _VP], ctypes.c_int),
     "gs_bin_sort_static": ([_VP, _VP, _VP, _I64, _VP, _I32, _VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP], ctypes.c_int),
     "gs_rasterize_fwd": ([_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "gs_rasterize_fwd_counted": ([_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "gs_rasterize_fwd_l1l2": ([_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP, _I64, _F32, _F32, _I32, _VP, _VP,
                                _VP], ctypes.c_int),
     "gs_rasterize_bwd": ([_VP] * 5 + [_I64, _VP, _VP, _I32, _VP] + [_VP] * 7 + [_VP] * 6 + [_VP, _VP], ctypes.c_int),
     "gs_rasterize_bwd_pixels": ([_VP, _VP, _VP, _VP, _I32, _VP, _I64, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "gs_rasterize_bwd_pixels_counted": ([_VP, _VP, _VP, _VP, _I32, _VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP],
+                                        ctypes.c_int),
     "gs_project_bwd": ([_VP] * 5 + [_I64, _VP, _VP, _I32, _VP, _VP, _VP] + [_VP] * 5 + [_VP, _VP], ctypes.c_int),
     "gs_image_loss": ([_VP, _VP, _I64, _F32, _F32, _VP, _VP, _VP], ctypes.c_int),
     "gs_adam_step": ([_VP, _VP, _VP, _VP, _I64, _F32, _F32, _F32, _F32, _VP, _VP], ctypes.c_int),
@@ -217,6 +223,17 @@ def gs_rasterize_fwd(projected, vals, tile_ranges, sizes, cfg, image, final_T, l
     _check(rc, "gs_rasterize_fwd")
 
 
+def gs_rasterize_fwd_counted(projected, vals, tile_ranges, sizes, cfg, image, final_T, last, pair_counts,
+                             stream=None):
+    """gs_rasterize_fwd that also adds its (executed, evaluated, composited)
+    pixel-splat pair counts into pair_counts (int64 [3] on the device)."""
+    sz = _sizes(sizes)
+    c, cref = _cfg_ref(cfg)
+    rc = load().gs_rasterize_fwd_counted(_ptr(projected), _ptr(vals), _ptr(tile_ranges), _ptr(sz), sz.shape[0], cref,
+                                         _ptr(image), _ptr(final_T), _ptr(last), _ptr(pair_counts), _stream(stream))
+    _check(rc, "gs_rasterize_fwd_counted")
+
+
 def gs_rasterize_fwd_l1l2(projected, vals, tile_ranges, sizes, cfg, image, final_T, last, target, n_values, w_l1,
                           w_l2, accumulate, dL_dimage, loss, stream=None):
     """gs_rasterize_fwd with the L1 + L2 loss of gs_image_loss in the same kernel."""
@@ -250,6 +267,19 @@ def gs_rasterize_bwd_pixels(projected, vals, tile_ranges, sizes, cfg, N, final_T
                                         int(N), _ptr(final_T), _ptr(last), _ptr(dL_dimage), _ptr(d_projected),
                                         _stream(stream))
     _check(rc, "gs_rasterize_bwd_pixels")
+
+
+def gs_rasterize_bwd_pixels_counted(projected, vals, tile_ranges, sizes, cfg, N, final_T, last, dL_dimage,
+                                    d_projected, pair_counts, stream=None):
+    """gs_rasterize_bwd_pixels that also adds its (executed, evaluated,
+    composited) pixel-splat pair counts into pair_counts (int64 [3])."""
+    sz = _sizes(sizes)
+    c, cref = _cfg_ref(cfg)
+    rc = load().gs_rasterize_bwd_pixels_counted(_ptr(projected), _ptr(vals), _ptr(tile_ranges), _ptr(sz),
+                                                sz.shape[0], cref, int(N), _ptr(final_T), _ptr(last),
+                                                _ptr(dL_dimage), _ptr(d_projected), _ptr(pair_counts),
+                                                _stream(stream))
+    _check(rc, "gs_rasterize_bwd_pixels_counted")
 
 
 def gs_project_bwd(means, log_scales, quats, opacity_logits, sh, cams, sizes, cfg, counts, d_projected, d_means,

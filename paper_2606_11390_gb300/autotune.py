@@ -1,9 +1,23 @@
-"""Tile-size autotuner for the batched step.
+"""Rasteriser autotuner for the training step.
 
-For a workload (Gaussian count, view sizes, SH degree) it times the captured
-training step with each supported tile shape (8x8, 16x16, 32x16, 32x32) and
-keeps the fastest. Results are cached per GPU name and workload signature in a JSON file
-(default ~/.cache/gs_gb300/autotune.json, override with GS_AUTOTUNE_CACHE).
+For a workload (Gaussian count, view sizes, SH degree) it searches the
+rasteriser's launch configuration:
+- tile shape (8x8, 16x16, 32x16, 32x32) together with the pixels each thread
+  owns (2 or 4, so threads per tile = tile area / pixels per thread; 8x8 tiles
+  take 2 only);
+- splats staged per shared-memory batch in the forward (64, 128, 256);
+- splats staged per shared-memory batch in the backward (64, 128, 256).
+The search is coordinate descent: every tile shape and pixels per thread at
+the default batch sizes, then the forward batch at the best of those, then
+the backward batch; 13 timed configurations instead of the 63 of the full
+product. Each is timed as the whole captured training step. Every
+configuration produces the same image (tests/test_gpu_raster_variants.py),
+so the choice is about time only.
+
+Results are cached in a JSON file (default ~/.cache/gs_gb300/autotune.json,
+override with GS_AUTOTUNE_CACHE) under the GPU name, the workload signature,
+the step mode and a digest of the library's sources, so a rebuilt kernel is
+tuned afresh.
 """
 from __future__ import annotations
 
@@ -14,6 +28,7 @@ import os
 import numpy as np
 
 TILES = ((16, 16), (8, 8), (32, 16), (32, 32))
+BATCHES = (64, 128, 256)
 
 
 def _cache_path():
@@ -25,6 +40,13 @@ def signature(scene) -> str:
     sizes = np.asarray(scene["sizes"]).reshape(-1, 2)
     key = f"N={int(scene['means'].shape[0])};views={sizes.tolist()};deg={scene['cfg']['sh_degree']}"
     return hashlib.sha1(key.encode()).hexdigest()[:16]
+
+
+def library_digest() -> str:
+    """Digest of the CUDA library's sources and build flags."""
+    from . import build
+
+    return build._digest()[:16]
 
 
 def _load():
@@ -47,37 +69,88 @@ def _store(d):
         pass
 
 
-def best_tile(scene, steps=3, use_cache=True, candidates=TILES, mode="batched"):
-    """Returns ((tw, th), {tile: ms}) for the fastest tile shape."""
+def name(c: dict) -> str:
+    """Short label of a configuration, e.g. 32x16/4px/f128/b0 (0: default batch)."""
+    return f"{c['tile'][0]}x{c['tile'][1]}/{c['ppt']}px/f{c['batch_fwd']}/b{c['batch_bwd']}"
+
+
+def tile_candidates(tiles=TILES):
+    """(tile, pixels per thread) pairs at the default batch sizes."""
+    out = []
+    for t in tiles:
+        for ppt in ((2,) if t == (8, 8) else (4, 2)):
+            out.append({"tile": tuple(t), "ppt": ppt, "batch_fwd": 0, "batch_bwd": 0})
+    return out
+
+
+def search(measure, tiles=TILES, batches=BATCHES):
+    """Coordinate descent over the configuration space with measure(config) ->
+    ms; returns (best config, {label: ms} of every configuration timed)."""
+    times = {}
+
+    def timed(c):
+        k = name(c)
+        if k not in times:
+            times[k] = float(measure(c))
+        return times[k]
+
+    best = min(tile_candidates(tiles), key=timed)
+    for dim in ("batch_fwd", "batch_bwd"):
+        cands = [best] + [dict(best, **{dim: b}) for b in batches]
+        best = min(cands, key=timed)
+    return best, times
+
+
+def step_kwargs(c: dict) -> dict:
+    """TrainStep keyword arguments of a configuration."""
+    return {"tile": tuple(c["tile"]), "raster_px": int(c["ppt"]), "raster_batch": (int(c["batch_fwd"]),
+                                                                                   int(c["batch_bwd"]))}
+
+
+def _time_step(scene, c, steps, mode, params):
     import torch
 
     from . import renderer as R
 
-    gpu = torch.cuda.get_device_name()
-    key = f"{gpu}|{signature(scene)}|{mode}"
+    step = R.TrainStep(scene, mode=mode, params=params, **step_kwargs(c)).prepare()
+    for _ in range(2):
+        step.run()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        step.run()
+    b.record()
+    torch.cuda.synchronize()
+    step.check()
+    ms = a.elapsed_time(b) / steps
+    return ms, step.params
+
+
+def best_config(scene, steps=3, use_cache=True, mode="batched", measure=None, gpu=None, digest=None):
+    """Returns (config, {label: ms}) of the fastest rasteriser configuration
+    for the workload. `measure`, `gpu` and `digest` default to timing the
+    captured step on the current GPU with the built library."""
+    if gpu is None:
+        import torch
+
+        gpu = torch.cuda.get_device_name()
+    digest = digest if digest is not None else library_digest()
+    key = f"{gpu}|{signature(scene)}|{mode}|{digest}"
     cache = _load() if use_cache else {}
     if key in cache:
-        t = tuple(cache[key]["tile"])
-        return t, {tuple(map(int, k.split("x"))): v for k, v in cache[key]["ms"].items()}
-    times = {}
-    params = None
-    for tile in candidates:
-        step = R.TrainStep(scene, mode=mode, tile=tile, params=params).prepare()
-        params = step.params
-        for _ in range(2):
-            step.run()
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        for _ in range(steps):
-            step.run()
-        b.record()
-        torch.cuda.synchronize()
-        step.check()
-        times[tile] = a.elapsed_time(b) / steps
-        del step
-    best = min(times, key=times.get)
-    cache[key] = {"tile": list(best), "ms": {f"{t[0]}x{t[1]}": v for t, v in times.items()}}
+        e = cache[key]
+        c = dict(e["config"], tile=tuple(e["config"]["tile"]))
+        return c, dict(e["ms"])
+    if measure is None:
+        state = {"params": None}
+
+        def measure(c):
+            ms, state["params"] = _time_step(scene, c, steps, mode, state["params"])
+            return ms
+    best, times = search(measure)
     if use_cache:
+        cache = _load()
+        cache[key] = {"config": dict(best, tile=list(best["tile"])), "ms": times}
         _store(cache)
     return best, times

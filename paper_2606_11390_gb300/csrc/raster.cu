@@ -1,757 +1,136 @@
-// Tile rasterisation: front-to-back alpha compositing (forward) and its
-// reverse-order backward.
+// Tile rasterisation entry points of the C ABI: argument checks and the
+// dispatch over tile shape, pixels per thread and splats per shared-memory
+// batch to the kernel variants of raster_kernels.cuh (instantiated by the
+// raster_inst_*.cu units).
 //
 // Paper: arXiv 2606.11390 §4 - rasterisation is partitioned per camera (or per
 // image tile), and its backward keeps the forward partitioning and sums the
 // per-Gaussian gradients with atomics (device scope suffices on one GPU).
-// Compositing rule of 3D Gaussian Splatting (Kerbl et al. 2023): per pixel,
-// for the tile's depth-sorted entries, alpha = min(cap, o exp(-power)),
-// skip alpha < alpha_min, stop before T(1 - alpha) < t_stop, C += c alpha T.
-//
-// GB300 design. One CTA per (view, tile); each thread owns PPT pixels of one
-// column (4 by default: a warp covers a 16x8 block; 2 for 8x8 tiles or on
-// request: 8x8 blocks). The tile's splats are staged into shared memory 128 at
-// a time; while staging, each splat gets a bitmask of the warps whose block
-// meets the ellipse on which its alpha can reach alpha_min (exact
-// ellipse-rectangle test with a safety margin), so a warp skips splats that
-// cannot touch its pixels. Skipped pairs are pairs the compositing rule would
-// skip anyway, so the result is unchanged. The per-pixel step has no
-// branches: every lane evaluates the splat and the decisions select, so a
-// thread's pixels interleave. The per-pair arithmetic is written with
-// explicitly rounded operations and a fixed ex2.approx so that the backward
-// recomputes bit-identical alphas and takes exactly the forward's skip / stop
-// decisions. The backward walks the list in reverse, each warp from the
-// largest `last` among its pixels, recovers T_k = T_{k+1} / (1 - alpha_k) from
-// the stored final T, sums a splat's 9 gradient values over the thread's
-// pixels (the geometric ones as dy-moments, the pixels sharing dx), reduces
-// them across the warp with a reduce-scatter (two splats' 18 values with 20
-// shuffles; a lone splat's 9 with 12, instead of 9 x 5 butterfly
-// shuffles), sums the warps of the CTA in shared memory and issues
-// one FP32 atomic per value per (tile, splat) to the per-record gradient
-// buffer.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "gs_common.cuh"
 #include "gs_internal.h"
+#include "raster_launch.h"
 
 namespace gs {
 namespace {
 
-constexpr float kLog2e = 1.4426950408889634f;
+using rast::BwdArgs;
+using rast::FwdArgs;
 
-// Splat data staged in shared memory, with the conic pre-scaled so that
-// e = (A' dx + B' dy) dx + C' dy dy = -power * log2(e).
-struct SplatS {
-  float4 a;  // mean.x, mean.y, A' = -0.5 A log2e, B' = -B log2e
-  float4 b;  // C' = -0.5 C log2e, opacity, r, g
-  float c;   // b
-};
-
-__device__ __forceinline__ void load_splat(const float4* __restrict__ projected, uint32_t vg, float4& a, float4& b,
-                                           float& c) {
-  const float4 r0 = __ldg(projected + 3 * static_cast<size_t>(vg));
-  const float4 r1 = __ldg(projected + 3 * static_cast<size_t>(vg) + 1);
-  const float4 r2 = __ldg(projected + 3 * static_cast<size_t>(vg) + 2);
-  a = make_float4(r0.x, r0.y, -0.5f * kLog2e * r0.z, -kLog2e * r0.w);
-  b = make_float4(-0.5f * kLog2e * r1.x, r1.y, r2.x, r2.y);
-  c = r2.z;
-}
-
-// e = -power*log2(e) = A' dx^2 + B' dx dy + C' dy^2 for pixel centre
-// (px, py), dx = px - mean.x, dy = py - mean.y. A thread's pixels share a
-// column, so the dx terms are formed once per splat (SplatCol) and each pixel
-// adds dy * (C' dy + B' dx) to A' dx^2: one subtraction and two FMAs. Every
-// operation is explicitly rounded so the forward and the backward compute
-// the same bits.
-struct SplatCol {
-  float dx, adx2, bdx;
-};
-
-__device__ __forceinline__ SplatCol splat_column(float px, const float4& a) {
-  SplatCol c;
-  c.dx = __fsub_rn(px, a.x);
-  c.adx2 = __fmul_rn(__fmul_rn(a.z, c.dx), c.dx);
-  c.bdx = __fmul_rn(a.w, c.dx);
-  return c;
-}
-
-__device__ __forceinline__ float splat_exponent(const SplatCol& c, float py, const float4& a, float Cp, float& dy) {
-  dy = __fsub_rn(py, a.y);
-  return __fmaf_rn(dy, __fmaf_rn(Cp, dy, c.bdx), c.adx2);
-}
-
-// Splats staged per shared-memory batch (at least one per thread): the
-// forward takes 128 (at 4K 3 % faster than 256: warps wait less at the
-// batch barrier); the backward, which flushes a batch's gradients between
-// two barriers, runs best with small batches: one splat per thread (at 4K 8 %
-// faster than 256; on the 16-view workload with 16x16 tiles 64 beats 128;
-// 64 with 128 threads is 5 % slower at 4K).
-constexpr int kBatch = 128;
-constexpr int kBatchBwd = 64;
-
-// Resident warps per SM the backward kernel is compiled for (0: no register
-// cap); the cap trades registers for latency hiding.
-#ifndef GS_RBWD_TARGET_WARPS
-#define GS_RBWD_TARGET_WARPS 0
-#endif
-#if GS_RBWD_TARGET_WARPS > 0
-#define GS_RBWD_BOUNDS(NT) __launch_bounds__(NT, GS_RBWD_TARGET_WARPS / ((NT) / 32))
-#else
-#define GS_RBWD_BOUNDS(NT) __launch_bounds__(NT)
-#endif
-
-// Thread / pixel geometry. With PPT pixels per thread a warp covers a block
-// of WB = 4 PPT columns by 8 rows: lane l owns column l % WB and rows
-// l / WB + r * (32 / WB), r < PPT. The warps of a TW x TH tile tile it in
-// TW / WB columns and TH / 8 rows of blocks.
-template <int TW, int TH, int PPT>
-struct Geo {
-  static constexpr int WB = 4 * PPT;
-  static constexpr int RS = 32 / WB;
-  static constexpr int NT = TW * TH / PPT;
-  static constexpr int NW = NT / 32;
-  static constexpr int WXN = TW / WB;
-  static constexpr int B = NT > kBatch ? NT : kBatch;
-  static_assert(TW % WB == 0 && TH % 8 == 0 && PPT * RS == 8, "unsupported tile / pixels-per-thread");
-  static_assert(NW <= 32, "at most 32 warps");
-  __device__ static void pixel_of(int tid, int& x, int& y0) {
-    const int w = tid >> 5, l = tid & 31;
-    x = WB * (w % WXN) + (l % WB);
-    y0 = 8 * (w / WXN) + (l / WB);
-  }
-};
-
-// Minimum over y in [y0, y1] of q(x, y) = m00 x^2 + 2 m01 x y + m11 y^2 for
-// fixed x (the quadratic in y is minimised at y = -m01 x / m11, clamped).
-__device__ __forceinline__ float edge_min_y(float x, float y0, float y1, float m00, float m01, float m11) {
-  const float y = fminf(fmaxf(-m01 * x / m11, y0), y1);
-  return m00 * x * x + 2.0f * m01 * x * y + m11 * y * y;
-}
-
-// Bitmask of the warps of the tile at (tx0, ty0) whose pixel block can hold a
-// pixel with alpha >= alpha_min. With the scaled conic
-// M = [[-2A', -B'], [-B', -2C']] (so e = -d^T M d / 2) that set is the
-// ellipse d^T M d <= 2 ts, ts = log2(o / alpha_min). A block is kept if its
-// rectangle of pixel centres meets the ellipse: the minimum of d^T M d over
-// the rectangle is 0 when the centre lies inside, else the smallest of the
-// four edge minima. ts and the rectangle are widened (x1.001 + margins), far
-// beyond the rounding of the per-pixel evaluation, so no pixel of a dropped
-// block can pass the alpha test.
-template <class G>
-__device__ __forceinline__ uint32_t warp_cull_mask(const float4& a, const float4& b, float tx0, float ty0,
-                                                    float amin) {
-  constexpr uint32_t kAll = (G::NW >= 32) ? 0xffffffffu : ((1u << G::NW) - 1u);
-  const float o = b.y;
-  if (!(o > amin)) return 0u;
-  const float m00 = -2.0f * a.z, m01 = -a.w, m11 = -2.0f * b.x;
-  const float det = m00 * m11 - m01 * m01;
-  if (!(det > 0.0f) || !(m00 > 0.0f) || !(m11 > 0.0f)) return kAll;
-  const float ts = (__log2f(o) - __log2f(amin)) * 1.001f + 0.01f;
-  const float lim = 2.0f * ts;
-  const float hx = sqrtf(lim * m11 / det) * 1.001f + 0.05f;
-  const float hy = sqrtf(lim * m00 / det) * 1.001f + 0.05f;
-  if (!(hx < 1e30f) || !(hy < 1e30f)) return kAll;
-  uint32_t mask = 0;
-#pragma unroll
-  for (int w = 0; w < G::NW; ++w) {
-    // rectangle of the block's pixel centres relative to the mean, widened
-    const float x0 = tx0 + static_cast<float>(G::WB * (w % G::WXN)) + 0.45f - a.x;
-    const float x1 = x0 + static_cast<float>(G::WB - 1) + 0.1f;
-    const float y0 = ty0 + static_cast<float>(8 * (w / G::WXN)) + 0.45f - a.y;
-    const float y1 = y0 + 7.1f;
-    if (x1 < -hx || x0 > hx || y1 < -hy || y0 > hy) continue;  // outside the bounding box
-    if (x0 <= 0.0f && x1 >= 0.0f && y0 <= 0.0f && y1 >= 0.0f) {
-      mask |= 1u << w;  // the centre lies in the block
-      continue;
-    }
-    float qmin = fminf(edge_min_y(x0, y0, y1, m00, m01, m11), edge_min_y(x1, y0, y1, m00, m01, m11));
-    qmin = fminf(qmin, edge_min_y(y0, x0, x1, m11, m01, m00));
-    qmin = fminf(qmin, edge_min_y(y1, x0, x1, m11, m01, m00));
-    if (qmin <= lim * 1.001f + 0.01f) mask |= 1u << w;
-  }
-  return mask;
-}
-
-struct PixelFwd {
-  float T, c0, c1, c2;
-  float thr;      // alpha threshold: alpha_min while compositing, +inf once stopped or outside the image
-  uint32_t last;
-};
-
-// One compositing step of one pixel (forward rule), without branches: every
-// lane evaluates the splat and the decisions select what changes, so the
-// compiler can interleave the independent pixels of a thread (a branch only
-// saves issue slots when all 32 lanes agree, which a partly covered block
-// rarely does). Adding w = 0 leaves the colour unchanged bit for bit. A pixel
-// that has stopped (or lies outside the image) carries an infinite alpha
-// threshold, so no later splat passes its test.
-// The splat's exponent and alpha at one pixel (independent of the pixel state).
-__device__ __forceinline__ void splat_alpha(const SplatCol& col, float py, const float4& a, const float4& b, float cap,
-                                            float& e, float& alpha) {
-  float dy;
-  e = splat_exponent(col, py, a, b.x, dy);
-  alpha = fminf(cap, __fmul_rn(b.y, ex2_approx(e)));
-}
-
-// The compositing decisions and update of one pixel for a splat with
-// exponent e and alpha.
-__device__ __forceinline__ void composite_apply(PixelFwd& P, float e, float alpha, const float4& b, float cb,
-                                                uint32_t rel, float tstop) {
-  const float Tn = __fmul_rn(P.T, __fsub_rn(1.0f, alpha));
-  const bool ok = !(e > 0.0f) && !(alpha < P.thr);
-  const bool stop = ok && Tn < tstop;
-  const bool take = ok && !stop;
-  const float w = take ? __fmul_rn(alpha, P.T) : 0.0f;
-  P.c0 = __fmaf_rn(b.z, w, P.c0);
-  P.c1 = __fmaf_rn(b.w, w, P.c1);
-  P.c2 = __fmaf_rn(cb, w, P.c2);
-  P.T = take ? Tn : P.T;
-  P.last = take ? rel + 1 : P.last;
-  P.thr = stop ? __int_as_float(0x7f800000) : P.thr;
-}
-
-__device__ __forceinline__ void composite_step(PixelFwd& P, const SplatCol& col, float py, const float4& a,
-                                               const float4& b, float cb, uint32_t rel, float cap, float tstop) {
-  float e, alpha;
-  splat_alpha(col, py, a, b, cap, e, alpha);
-  composite_apply(P, e, alpha, b, cb, rel, tstop);
-}
-
-// Optional L1 + L2 image loss computed in the forward's epilogue (target
-// null: none). grad and loss as gs_image_loss: dL/dimage = (w1 sign(r) +
-// 2 w2 r) / n, loss += sum(w1 |r| + w2 r^2) / n, r = image - target.
-struct ImageLoss {
-  const float* target;
-  float* grad;
-  double* loss;
-  float w1, w2, inv_n;
-  double inv_n_d;
-};
-
-// Compiled for 1024 resident threads per SM (8 CTAs of 128 at 32x16 tiles,
-// 64 registers, no spills): 0.5 % faster than 7 CTAs at 72 registers.
-template <int TW, int TH, int PPT>
-__global__ void __launch_bounds__(TW* TH / PPT, 1024 / (TW * TH / PPT)) raster_fwd_kernel(const float4* __restrict__ projected,
-                                                                   const uint32_t* __restrict__ vals,
-                                                                   const uint2* __restrict__ ranges,
-                                                                   const uint32_t* __restrict__ order, const Layout L,
-                                                                   const Consts K, float* __restrict__ image,
-                                                                   float* __restrict__ final_T,
-                                                                   uint32_t* __restrict__ last, const ImageLoss IL) {
-  using G = Geo<TW, TH, PPT>;
-  constexpr int NT = G::NT, B = G::B;
-  __shared__ float4 s_a[B];
-  __shared__ float4 s_b[B];
-  __shared__ float s_c[B];
-  __shared__ uint32_t s_m[B];
-  __shared__ uint16_t s_list[G::NW][B];  // per warp: the staged splats that can touch its block
-  // CTA i takes tile order[i] (longest lists first) when an order is given
-  const uint32_t tile = order ? order[blockIdx.x] : blockIdx.x;
-  if (tile >= L.n_tiles) return;
-  const int v = view_of_tile(L, tile);
-  const uint32_t local = tile - L.tile_base[v];
-  const int ntx = L.ntx[v];
-  const int tx = static_cast<int>(local % ntx), ty = static_cast<int>(local / ntx);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t wbit = 1u << warp;
-  int lx, ly;
-  G::pixel_of(tid, lx, ly);
-  const int W = L.width[v], H = L.height[v];
-  const int x = tx * TW + lx, y0 = ty * TH + ly;
-  const float px = static_cast<float>(x) + 0.5f, py0 = static_cast<float>(y0) + 0.5f;
-  const uint2 range = ranges[tile];
-  const int n = static_cast<int>(range.y - range.x);
-  const float cap = K.alpha_cap, amin = K.alpha_min, tstop = K.t_stop;
-  const float tx0 = static_cast<float>(tx * TW), ty0 = static_cast<float>(ty * TH);
-  const float kInf = __int_as_float(0x7f800000);
-  PixelFwd P[PPT];
-  bool all_done = true;
-#pragma unroll
-  for (int r = 0; r < PPT; ++r) {
-    const bool inside = x < W && y0 + r * G::RS < H;
-    P[r] = PixelFwd{1.0f, 0.0f, 0.0f, 0.0f, inside ? amin : kInf, 0u};
-    all_done = all_done && !inside;
-  }
-  for (int b0 = 0; b0 < n; b0 += B) {
-    if (__syncthreads_count(all_done) == NT) break;
-    for (int k = tid; k < B && b0 + k < n; k += NT) {
-      float4 a, b;
-      float c;
-      load_splat(projected, vals[range.x + b0 + k], a, b, c);
-      s_a[k] = a;
-      s_b[k] = b;
-      s_c[k] = c;
-      s_m[k] = warp_cull_mask<G>(a, b, tx0, ty0, amin);
-    }
-    __syncthreads();
-    const int cnt = min(B, n - b0);
-    // the warp's list of staged splats that can touch its block
-    int nl = 0;
-    for (int jb = 0; jb < cnt; jb += 32) {
-      const int j = jb + lane;
-      const bool keep = j < cnt && (s_m[j] & wbit);
-      const uint32_t bal = __ballot_sync(0xffffffffu, keep);
-      if (keep) s_list[warp][nl + __popc(bal & ((1u << lane) - 1u))] = static_cast<uint16_t>(j);
-      nl += __popc(bal);
-    }
-    __syncwarp();
-    int q = 0;
-#ifndef GS_FWD_GROUP
-#define GS_FWD_GROUP 3
-#endif
-    // GS_FWD_GROUP splats per iteration: their exponents / alphas are
-    // independent of the pixel state and are issued first; the compositing
-    // then applies them in list order
-    constexpr int GR = GS_FWD_GROUP;
-    for (; q + GR - 1 < nl && !all_done; q += GR) {
-      float e[GR][PPT], al[GR][PPT];
-      int js[GR];
-#pragma unroll
-      for (int u = 0; u < GR; ++u) {
-        js[u] = s_list[warp][q + u];
-        const float4 a = s_a[js[u]], b = s_b[js[u]];
-        const SplatCol col = splat_column(px, a);
-#pragma unroll
-        for (int r = 0; r < PPT; ++r) splat_alpha(col, py0 + static_cast<float>(r * G::RS), a, b, cap, e[u][r], al[u][r]);
-      }
-      all_done = true;
-#pragma unroll
-      for (int r = 0; r < PPT; ++r) {
-#pragma unroll
-        for (int u = 0; u < GR; ++u) {
-          const float4 b = s_b[js[u]];
-          composite_apply(P[r], e[u][r], al[u][r], b, s_c[js[u]], static_cast<uint32_t>(b0 + js[u]), tstop);
-        }
-        all_done = all_done && P[r].thr == kInf;
-      }
-    }
-    for (; q < nl && !all_done; ++q) {
-      const int j = s_list[warp][q];
-      const float4 a = s_a[j];
-      const float4 b = s_b[j];
-      const float cb = s_c[j];
-      const uint32_t rel = static_cast<uint32_t>(b0 + j);
-      const SplatCol col = splat_column(px, a);
-      all_done = true;
-#pragma unroll
-      for (int r = 0; r < PPT; ++r) {
-        composite_step(P[r], col, py0 + static_cast<float>(r * G::RS), a, b, cb, rel, cap, tstop);
-        all_done = all_done && P[r].thr == kInf;
-      }
-    }
-  }
-  const size_t pb = L.pix_base[v];
-  const bool with_loss = IL.target != nullptr;
-  float part = 0.0f;
-#pragma unroll
-  for (int r = 0; r < PPT; ++r) {
-    const int yy = y0 + r * G::RS;
-    if (x < W && yy < H) {
-      const size_t p = pb + static_cast<size_t>(yy) * W + x;
-      const float c[3] = {P[r].c0 + P[r].T * K.bg[0], P[r].c1 + P[r].T * K.bg[1], P[r].c2 + P[r].T * K.bg[2]};
-#pragma unroll
-      for (int k = 0; k < 3; ++k) image[3 * p + k] = c[k];
-      final_T[p] = P[r].T;
-      last[p] = P[r].last;
-      if (with_loss) {
-        // the L1 + L2 image loss of these values (same arithmetic as gs_image_loss)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const float rr = c[k] - IL.target[3 * p + k];
-          IL.grad[3 * p + k] = l1l2_grad(rr, IL.w1, IL.w2, IL.inv_n);
-          part += IL.w1 * fabsf(rr) + IL.w2 * rr * rr;
-        }
-      }
-    }
-  }
-  if (with_loss) {
-    // CTA sum of the loss terms, one double atomic per CTA
-    __shared__ double s_loss[G::NW];
-    double acc = part;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) s_loss[warp] = acc;
-    __syncthreads();
-    if (tid == 0) {
-      double t = 0.0;
-#pragma unroll
-      for (int w = 0; w < G::NW; ++w) t += s_loss[w];
-      atomicAdd(IL.loss, t * IL.inv_n_d);
-    }
-  }
-}
-
-// Reduce-scatter of 9 values over a warp with 12 shuffles. On return, the
-// lane holds the warp-wide sum of value index slot_of_lane(lane) (or 0 where
-// that is -1); lanes 2k and 2k+1 hold the same slot.
-__device__ __forceinline__ float warp_reduce9(const float v[9], int lane) {
-  const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4, h1 = lane & 2;
-  float s[5];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const float send = h4 ? v[i] : v[5 + i];
-    s[i] = (h4 ? v[5 + i] : v[i]) + __shfl_xor_sync(0xffffffffu, send, 16);
-  }
-  {
-    const float send = h4 ? v[4] : 0.0f;
-    const float r = __shfl_xor_sync(0xffffffffu, send, 16);
-    s[4] = h4 ? 0.0f : v[4] + r;
-  }
-  float t[3];
-  t[0] = (h3 ? s[3] : s[0]) + __shfl_xor_sync(0xffffffffu, h3 ? s[0] : s[3], 8);
-  t[1] = (h3 ? s[4] : s[1]) + __shfl_xor_sync(0xffffffffu, h3 ? s[1] : s[4], 8);
-  t[2] = (h3 ? 0.0f : s[2]) + __shfl_xor_sync(0xffffffffu, h3 ? s[2] : 0.0f, 8);
-  float u[2];
-  u[0] = (h2 ? t[2] : t[0]) + __shfl_xor_sync(0xffffffffu, h2 ? t[0] : t[2], 4);
-  u[1] = (h2 ? 0.0f : t[1]) + __shfl_xor_sync(0xffffffffu, h2 ? t[1] : 0.0f, 4);
-  float w = (h1 ? u[1] : u[0]) + __shfl_xor_sync(0xffffffffu, h1 ? u[0] : u[1], 2);
-  w += __shfl_xor_sync(0xffffffffu, w, 1);
-  return w;
-}
-
-__device__ __forceinline__ int slot_of_lane(int lane) {
-  const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4, h1 = lane & 2;
-  int s[5];
-  for (int i = 0; i < 4; ++i) s[i] = h4 ? 5 + i : i;
-  s[4] = h4 ? -1 : 4;
-  int t[3] = {h3 ? s[3] : s[0], h3 ? s[4] : s[1], h3 ? -1 : s[2]};
-  int u[2] = {h2 ? t[2] : t[0], h2 ? -1 : t[1]};
-  return h1 ? u[1] : u[0];
-}
-
-// Reduce-scatter of the 18 values of two splats (a[9], then b[9]) over a warp
-// with 20 shuffles (instead of 2 x 12): on return, the lane holds the
-// warp-wide sum of value index slot18_of_lane(lane) (0..8: a, 9..17: b), or
-// 0 where that is -1. Every value lands in exactly one lane.
-__device__ __forceinline__ float warp_reduce18(const float a[9], const float b[9], int lane) {
-  const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4, h1 = lane & 2, h0 = lane & 1;
-  float s[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) s[i] = (h4 ? b[i] : a[i]) + __shfl_xor_sync(0xffffffffu, h4 ? a[i] : b[i], 16);
-  float t[5];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) t[i] = (h3 ? s[5 + i] : s[i]) + __shfl_xor_sync(0xffffffffu, h3 ? s[i] : s[5 + i], 8);
-  t[4] = (h3 ? 0.0f : s[4]) + __shfl_xor_sync(0xffffffffu, h3 ? s[4] : 0.0f, 8);
-  float u[3];
-  u[0] = (h2 ? t[3] : t[0]) + __shfl_xor_sync(0xffffffffu, h2 ? t[0] : t[3], 4);
-  u[1] = (h2 ? t[4] : t[1]) + __shfl_xor_sync(0xffffffffu, h2 ? t[1] : t[4], 4);
-  u[2] = (h2 ? 0.0f : t[2]) + __shfl_xor_sync(0xffffffffu, h2 ? t[2] : 0.0f, 4);
-  float w[2];
-  w[0] = (h1 ? u[2] : u[0]) + __shfl_xor_sync(0xffffffffu, h1 ? u[0] : u[2], 2);
-  w[1] = (h1 ? 0.0f : u[1]) + __shfl_xor_sync(0xffffffffu, h1 ? u[1] : 0.0f, 2);
-  return (h0 ? w[1] : w[0]) + __shfl_xor_sync(0xffffffffu, h0 ? w[0] : w[1], 1);
-}
-
-__device__ __forceinline__ int slot18_of_lane(int lane) {
-  const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4, h1 = lane & 2, h0 = lane & 1;
-  int s[9];
-  for (int i = 0; i < 9; ++i) s[i] = (h4 ? 9 : 0) + i;
-  int t[5];
-  for (int i = 0; i < 4; ++i) t[i] = h3 ? s[5 + i] : s[i];
-  t[4] = h3 ? -1 : s[4];
-  const int u[3] = {h2 ? t[3] : t[0], h2 ? t[4] : t[1], h2 ? -1 : t[2]};
-  const int w[2] = {h1 ? u[2] : u[0], h1 ? -1 : u[1]};
-  return h0 ? w[1] : w[0];
-}
-
-struct PixelBwd {
-  // S = (colour accumulated behind the current entry, normalised) . dL/dC:
-  // the alpha gradient needs the accumulated colour only through this dot
-  // product, so one scalar replaces the three channels
-  float T, g0, g1, g2, gbg, S;
-  uint32_t last;
-};
-
-// Backward contribution of splat (a, b, cb) at relative position `rel` to one
-// pixel, added into gv[9]; returns whether the pixel took part. Constant
-// factors are applied once per splat when the sums are flushed:
-//   gv[0..1] = sum dalpha*alpha*(2A'dx + B'dy, B'dx + 2C'dy)  -> dmean = -gv/log2e
-//   gv[2..4] = sum dalpha*alpha*(dx^2, dx dy, dy^2)          -> dconic = -(gv2/2, gv3, gv4/2)
-//   gv[5..7] = sum alpha T dL/dC, gv[8] = sum dalpha G          (as is)
-// From the moments m0 = sum dpw, m1 = sum dpw dy, m2 = sum dpw dy^2 of a
-// thread's pixels (common dx) to
-//   gv[0..1] = sum dpw (2A'dx + B'dy, B'dx + 2C'dy),
-//   gv[2..4] = sum dpw (dx^2, dx dy, dy^2).
-__device__ __forceinline__ void finish_geometry(float gv[9], const SplatCol& col, const float4& a, const float4& b) {
-  const float m0 = gv[0], m1 = gv[1], m2 = gv[2], dx = col.dx;
-  gv[0] = fmaf(2.0f * a.z * dx, m0, a.w * m1);
-  gv[1] = fmaf(col.bdx, m0, 2.0f * b.x * m1);
-  gv[2] = dx * dx * m0;
-  gv[3] = dx * m1;
-  gv[4] = m2;
-}
-
-template <bool BG>
-__device__ __forceinline__ bool pixel_grad(PixelBwd& P, const SplatCol& col, float py, const float4& a,
-                                           const float4& b, float cb, uint32_t rel, float cap, float amin,
-                                           float gv[9]) {
-  // branch-free, like the forward step: decisions select, zeros add nothing
-  float dy;
-  const float e = splat_exponent(col, py, a, b.x, dy);
-  const float G = ex2_approx(e);
-  const float oG = __fmul_rn(b.y, G);
-  const float alpha = fminf(cap, oG);
-  const bool ok = rel < P.last && !(e > 0.0f) && !(alpha < amin);
-  const float inv = rcp_approx(__fsub_rn(1.0f, alpha));
-  P.T = ok ? P.T * inv : P.T;  // transmittance in front of this entry
-  const float aok = ok ? alpha : 0.0f;
-  const float w = aok * P.T;
-  gv[5] += w * P.g0;
-  gv[6] += w * P.g1;
-  gv[7] += w * P.g2;
-  // (c - accumulated) . dL/dC = c . dL/dC - S
-  const float dcs = fmaf(cb, P.g2, fmaf(b.w, P.g1, b.z * P.g0)) - P.S;
-  // with a zero background (the default) the background term vanishes
-  const float dalpha = BG ? P.T * dcs - P.gbg * inv : P.T * dcs;
-  P.S = fmaf(aok, dcs, P.S);
-  const float da = (ok && !(oG > cap)) ? dalpha : 0.0f;
-  gv[8] += da * G;
-  // The geometric sums need dpw = dalpha * alpha only through its moments in
-  // dy (the thread's pixels share dx): gv[0..2] collect sum dpw, sum dpw dy,
-  // sum dpw dy^2 here and finish_geometry turns them into the five sums.
-  const float dpw = da * alpha;
-  const float dpy = dpw * dy;
-  gv[0] += dpw;
-  gv[1] += dpy;
-  gv[2] += dpy * dy;
-  return ok;
-}
-
-template <int TW, int TH, int PPT, bool BG>
-__global__ void GS_RBWD_BOUNDS(TW* TH / PPT) raster_bwd_kernel(
-    const float4* __restrict__ projected, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
-    const uint32_t* __restrict__ order, const Layout L, const Consts K, const float* __restrict__ final_T,
-    const uint32_t* __restrict__ last, const float* __restrict__ dL_dimage, float* __restrict__ d_proj) {
-  using Gm = Geo<TW, TH, PPT>;
-  constexpr int NT = Gm::NT, NW = Gm::NW;
-  constexpr int B = NT > kBatchBwd ? NT : kBatchBwd;
-  __shared__ float4 s_a[B];
-  __shared__ float4 s_b[B];
-  __shared__ float s_c[B];
-  __shared__ uint32_t s_m[B];
-  __shared__ uint32_t s_vg[B];
-  __shared__ float s_grad[B * 9];
-  __shared__ uint32_t s_wmax[NW];
-  __shared__ uint16_t s_list[NW][B];  // per warp: the staged splats that can touch its block
-  // CTA i takes tile order[i] (longest lists first) when an order is given
-  const uint32_t tile = order ? order[blockIdx.x] : blockIdx.x;
-  if (tile >= L.n_tiles) return;
-  const int v = view_of_tile(L, tile);
-  const uint32_t local = tile - L.tile_base[v];
-  const int ntx = L.ntx[v];
-  const int tx = static_cast<int>(local % ntx), ty = static_cast<int>(local / ntx);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t wbit = 1u << warp;
-  int lx, ly;
-  Gm::pixel_of(tid, lx, ly);
-  const int W = L.width[v], H = L.height[v];
-  const int x = tx * TW + lx, y0 = ty * TH + ly;
-  const float px = static_cast<float>(x) + 0.5f, py0 = static_cast<float>(y0) + 0.5f;
-  const uint2 range = ranges[tile];
-  const float cap = K.alpha_cap, amin = K.alpha_min;
-  const float tx0 = static_cast<float>(tx * TW), ty0 = static_cast<float>(ty * TH);
-  PixelBwd P[PPT];
-  uint32_t lmax = 0;
-#pragma unroll
-  for (int r = 0; r < PPT; ++r) {
-    P[r] = PixelBwd{1.0f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u};
-    const int yy = y0 + r * Gm::RS;
-    if (x < W && yy < H) {
-      const size_t p = static_cast<size_t>(L.pix_base[v]) + static_cast<size_t>(yy) * W + x;
-      P[r].T = final_T[p];
-      P[r].last = last[p];
-      P[r].g0 = dL_dimage[3 * p];
-      P[r].g1 = dL_dimage[3 * p + 1];
-      P[r].g2 = dL_dimage[3 * p + 2];
-      P[r].gbg = P[r].T * (P[r].g0 * K.bg[0] + P[r].g1 * K.bg[1] + P[r].g2 * K.bg[2]);
-    }
-    lmax = max(lmax, P[r].last);
-  }
-  const int my_slot = slot_of_lane(lane);
-  // the pair reduction: which splat of the pair and which of its 9 values
-  const int slot18 = slot18_of_lane(lane);
-  const bool pair_b = slot18 >= 9;
-  const int pair_slot = slot18 >= 9 ? slot18 - 9 : slot18;
-  const uint32_t wmax = __reduce_max_sync(0xffffffffu, lmax);
-  if (lane == 0) s_wmax[warp] = wmax;
-  for (int i = tid; i < B * 9; i += NT) s_grad[i] = 0.0f;
-  __syncthreads();
-  uint32_t max_last = 0;
-#pragma unroll
-  for (int w = 0; w < NW; ++w) max_last = max(max_last, s_wmax[w]);
-
-  // Adds the gradients gathered in slot k (one splat of the batch) to its
-  // record with one atomic per non-zero value, and clears the slot.
-  auto flush_slot = [&](int k) {
-    float* dst = d_proj + static_cast<size_t>(s_vg[k]) * kDRecordFloats;
-    constexpr float kScale[9] = {-1.0f / kLog2e, -1.0f / kLog2e, -0.5f, -1.0f, -0.5f, 1.0f, 1.0f, 1.0f, 1.0f};
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const float gval = s_grad[k * 9 + i];
-      if (gval != 0.0f) {
-        atomicAdd(dst + i, gval * kScale[i]);
-        s_grad[k * 9 + i] = 0.0f;
-      }
-    }
-  };
-  int prev_cnt = 0;
-  for (int b_end = static_cast<int>(max_last); b_end > 0; b_end -= B) {
-    const int cnt = min(B, b_end);
-    // each thread flushes the slots it staged for the previous batch, then
-    // stages the same slots for this one: no other thread touches them in
-    // between, so one barrier covers both
-    for (int k = tid; k < B; k += NT) {
-      if (k < prev_cnt) flush_slot(k);
-      if (k >= cnt) continue;
-      const uint32_t vg = vals[range.x + b_end - 1 - k];
-      float4 a, b;
-      float c;
-      load_splat(projected, vg, a, b, c);
-      s_a[k] = a;
-      s_b[k] = b;
-      s_c[k] = c;
-      s_vg[k] = vg;
-      s_m[k] = warp_cull_mask<Gm>(a, b, tx0, ty0, amin);
-    }
-    __syncthreads();
-    // entries j hold relative position b_end-1-j; this warp needs rel < wmax.
-    // The warp first lists the staged splats that can touch its block, then
-    // takes them in pairs: the second splat's pixel work is issued before the
-    // first one's warp reduction, so the reduction's shuffle latency overlaps
-    // independent arithmetic (the pixel state still advances splat by splat).
-    const int j0 = max(0, b_end - static_cast<int>(wmax));
-    int nl = 0;
-    for (int jb = j0; jb < cnt; jb += 32) {
-      const int j = jb + lane;
-      const bool keep = j < cnt && (s_m[j] & wbit);
-      const uint32_t bal = __ballot_sync(0xffffffffu, keep);
-      if (keep) s_list[warp][nl + __popc(bal & ((1u << lane) - 1u))] = static_cast<uint16_t>(j);
-      nl += __popc(bal);
-    }
-    __syncwarp();
-    int q = 0;
-    for (; q + 1 < nl; q += 2) {
-      const int jA = s_list[warp][q], jB = s_list[warp][q + 1];
-      float gA[9], gB[9];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) gA[i] = gB[i] = 0.0f;
-      bool cA = false, cB = false;
-      {
-        const float4 a = s_a[jA];
-        const float4 b = s_b[jA];
-        const float cb = s_c[jA];
-        const uint32_t rel = static_cast<uint32_t>(b_end - 1 - jA);
-        const SplatCol col = splat_column(px, a);
-#pragma unroll
-        for (int r = 0; r < PPT; ++r)
-          cA |= pixel_grad<BG>(P[r], col, py0 + static_cast<float>(r * Gm::RS), a, b, cb, rel, cap, amin, gA);
-        finish_geometry(gA, col, a, b);
-      }
-      {
-        const float4 a = s_a[jB];
-        const float4 b = s_b[jB];
-        const float cb = s_c[jB];
-        const uint32_t rel = static_cast<uint32_t>(b_end - 1 - jB);
-        const SplatCol col = splat_column(px, a);
-#pragma unroll
-        for (int r = 0; r < PPT; ++r)
-          cB |= pixel_grad<BG>(P[r], col, py0 + static_cast<float>(r * Gm::RS), a, b, cb, rel, cap, amin, gB);
-        finish_geometry(gB, col, a, b);
-      }
-      // listed splats nearly always contribute: reduce without a branch, so
-      // the two reductions and the pixel work form one block to schedule
-      (void)cA;
-      (void)cB;
-      const float red = warp_reduce18(gA, gB, lane);
-      if (slot18 >= 0 && red != 0.0f) atomicAdd(&s_grad[(pair_b ? jB : jA) * 9 + pair_slot], red);
-    }
-    if (q < nl) {
-      const int j = s_list[warp][q];
-      const float4 a = s_a[j];
-      const float4 b = s_b[j];
-      const float cb = s_c[j];
-      const uint32_t rel = static_cast<uint32_t>(b_end - 1 - j);
-      float gv[9];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) gv[i] = 0.0f;
-      bool contrib = false;
-      const SplatCol col = splat_column(px, a);
-#pragma unroll
-      for (int r = 0; r < PPT; ++r)
-        contrib |= pixel_grad<BG>(P[r], col, py0 + static_cast<float>(r * Gm::RS), a, b, cb, rel, cap, amin, gv);
-      finish_geometry(gv, col, a, b);
-      if (__any_sync(0xffffffffu, contrib)) {
-        const float red = warp_reduce9(gv, lane);
-        if (!(lane & 1) && my_slot >= 0 && red != 0.0f) atomicAdd(&s_grad[j * 9 + my_slot], red);
-      }
-    }
-    __syncthreads();
-    prev_cnt = cnt;
-  }
-  for (int k = tid; k < prev_cnt; k += NT) flush_slot(k);
-}
-
-template <int TW, int TH, int PPT>
-int launch_fwd(const float4* projected, const uint32_t* vals, const uint2* ranges, const Layout& L, const Consts& K,
-               float* image, float* final_T, uint32_t* last, const ImageLoss& IL, cudaStream_t stream) {
-  const uint32_t* order = (K.flags & GS_FLAG_TILE_ORDER) ? reinterpret_cast<const uint32_t*>(ranges + L.n_tiles) : nullptr;
-  raster_fwd_kernel<TW, TH, PPT><<<static_cast<unsigned>(L.n_tiles), TW * TH / PPT, 0, stream>>>(
-      projected, vals, ranges, order, L, K, image, final_T, last, IL);
-  return cuda_status(cudaGetLastError());
-}
-
-template <int TW, int TH, int PPT>
-int launch_bwd(const float4* projected, const uint32_t* vals, const uint2* ranges, const Layout& L, const Consts& K,
-               const float* final_T, const uint32_t* last, const float* dL_dimage, float* d_proj,
-               cudaStream_t stream) {
-  const bool bg = K.bg[0] != 0.0f || K.bg[1] != 0.0f || K.bg[2] != 0.0f;
-  const uint32_t* order = (K.flags & GS_FLAG_TILE_ORDER) ? reinterpret_cast<const uint32_t*>(ranges + L.n_tiles) : nullptr;
-  if (bg)
-    raster_bwd_kernel<TW, TH, PPT, true><<<static_cast<unsigned>(L.n_tiles), TW * TH / PPT, 0, stream>>>(
-        projected, vals, ranges, order, L, K, final_T, last, dL_dimage, d_proj);
-  else
-    raster_bwd_kernel<TW, TH, PPT, false><<<static_cast<unsigned>(L.n_tiles), TW * TH / PPT, 0, stream>>>(
-        projected, vals, ranges, order, L, K, final_T, last, dL_dimage, d_proj);
-  return cuda_status(cudaGetLastError());
-}
-
-// Pixels per thread: 4 for 16x16 and 32x16 tiles unless the configuration asks
-// for 2 (GS_FLAG_RASTER_2PX); 8x8 tiles always use 2.
+// Pixels per thread: 4 for 16x16, 32x16 and 32x32 tiles unless the
+// configuration asks for 2 (GS_FLAG_RASTER_2PX); 8x8 tiles always use 2.
 inline int pixels_per_thread(const Layout& L, const Consts& K) {
   if (L.tile_w == 8) return 2;
   return (K.flags & GS_FLAG_RASTER_2PX) ? 2 : 4;
 }
 
-}  // namespace
-}  // namespace gs
+// 0 (the default) or a batch size the kernels are instantiated for.
+inline bool valid_batch(int32_t b) { return b == 0 || b == 64 || b == 128 || b == 256; }
 
-namespace gs {
-namespace {
+template <int TW, int TH, int PPT>
+int fwd_variant(int32_t batch, bool count, const FwdArgs& a, cudaStream_t s) {
+  constexpr int BD = rast::default_batch_fwd<TW * TH / PPT>();
+  if (count) return rast::launch_fwd<TW, TH, PPT, BD, true>(a, s);
+  const int b = batch ? batch : BD;
+  if (b == BD) return rast::launch_fwd<TW, TH, PPT, BD, false>(a, s);
+  if (b == 64) return rast::launch_fwd<TW, TH, PPT, 64, false>(a, s);
+  if (b == 128) return rast::launch_fwd<TW, TH, PPT, 128, false>(a, s);
+  if (b == 256) return rast::launch_fwd<TW, TH, PPT, 256, false>(a, s);
+  return GS_ERR_UNSUPPORTED;
+}
+
+// With a non-zero background the backward runs its default batch (the tuned
+// sizes are compiled without the background term); results are the same.
+template <int TW, int TH, int PPT>
+int bwd_variant(int32_t batch, bool bg, bool count, const BwdArgs& a, cudaStream_t s) {
+  constexpr int BD = rast::default_batch_bwd<TW * TH / PPT>();
+  if (count) return rast::launch_bwd<TW, TH, PPT, BD, true, true>(a, s);
+  if (bg) return rast::launch_bwd<TW, TH, PPT, BD, true, false>(a, s);
+  const int b = batch ? batch : BD;
+  if (b == 64) return rast::launch_bwd<TW, TH, PPT, 64, false, false>(a, s);
+  if (b == 128) return rast::launch_bwd<TW, TH, PPT, 128, false, false>(a, s);
+  if (b == 256) return rast::launch_bwd<TW, TH, PPT, 256, false, false>(a, s);
+  return GS_ERR_UNSUPPORTED;
+}
+
+int dispatch_fwd(int ppt, int32_t batch, bool count, const FwdArgs& a, cudaStream_t s) {
+  const int tw = a.L.tile_w, th = a.L.tile_h;
+  if (tw == 8 && th == 8) return fwd_variant<8, 8, 2>(batch, count, a, s);
+  if (tw == 16 && th == 16)
+    return ppt == 4 ? fwd_variant<16, 16, 4>(batch, count, a, s) : fwd_variant<16, 16, 2>(batch, count, a, s);
+  if (tw == 32 && th == 16)
+    return ppt == 4 ? fwd_variant<32, 16, 4>(batch, count, a, s) : fwd_variant<32, 16, 2>(batch, count, a, s);
+  if (tw == 32 && th == 32)
+    return ppt == 4 ? fwd_variant<32, 32, 4>(batch, count, a, s) : fwd_variant<32, 32, 2>(batch, count, a, s);
+  return GS_ERR_UNSUPPORTED;
+}
+
+int dispatch_bwd(int ppt, int32_t batch, bool bg, bool count, const BwdArgs& a, cudaStream_t s) {
+  const int tw = a.L.tile_w, th = a.L.tile_h;
+  if (tw == 8 && th == 8) return bwd_variant<8, 8, 2>(batch, bg, count, a, s);
+  if (tw == 16 && th == 16)
+    return ppt == 4 ? bwd_variant<16, 16, 4>(batch, bg, count, a, s) : bwd_variant<16, 16, 2>(batch, bg, count, a, s);
+  if (tw == 32 && th == 16)
+    return ppt == 4 ? bwd_variant<32, 16, 4>(batch, bg, count, a, s) : bwd_variant<32, 16, 2>(batch, bg, count, a, s);
+  if (tw == 32 && th == 32)
+    return ppt == 4 ? bwd_variant<32, 32, 4>(batch, bg, count, a, s) : bwd_variant<32, 32, 2>(batch, bg, count, a, s);
+  return GS_ERR_UNSUPPORTED;
+}
 
 int rasterize_fwd_impl(const float* projected, const uint32_t* vals, const uint32_t* tile_ranges, const int32_t* sizes,
                        int32_t V, const gs_config* cfg, float* image, float* final_T, uint32_t* last,
-                       const ImageLoss& IL, cudaStream_t stream) {
-  Layout L;
-  int rc = build_layout(sizes, V, cfg, &L, nullptr);
+                       const rast::ImageLoss& IL, unsigned long long* counts, cudaStream_t stream) {
+  FwdArgs a;
+  int rc = build_layout(sizes, V, cfg, &a.L, nullptr);
   if (rc != GS_OK) return rc;
   if (!projected || !tile_ranges || !image || !final_T || !last) return GS_ERR_ARG;
   if (!aligned16(projected) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7u)) return GS_ERR_ARG;
-  const Consts K = make_consts(*cfg);
-  const float4* pr = reinterpret_cast<const float4*>(projected);
-  const uint2* rg = reinterpret_cast<const uint2*>(tile_ranges);
-  const int ppt = pixels_per_thread(L, K);
-  if (L.tile_w == 16 && L.tile_h == 16)
-    return ppt == 4 ? launch_fwd<16, 16, 4>(pr, vals, rg, L, K, image, final_T, last, IL, stream)
-                    : launch_fwd<16, 16, 2>(pr, vals, rg, L, K, image, final_T, last, IL, stream);
-  if (L.tile_w == 8 && L.tile_h == 8) return launch_fwd<8, 8, 2>(pr, vals, rg, L, K, image, final_T, last, IL, stream);
-  if (L.tile_w == 32 && L.tile_h == 16)
-    return ppt == 4 ? launch_fwd<32, 16, 4>(pr, vals, rg, L, K, image, final_T, last, IL, stream)
-                    : launch_fwd<32, 16, 2>(pr, vals, rg, L, K, image, final_T, last, IL, stream);
-  if (L.tile_w == 32 && L.tile_h == 32)
-    return ppt == 4 ? launch_fwd<32, 32, 4>(pr, vals, rg, L, K, image, final_T, last, IL, stream)
-                    : launch_fwd<32, 32, 2>(pr, vals, rg, L, K, image, final_T, last, IL, stream);
-  return GS_ERR_UNSUPPORTED;
+  if (counts && (reinterpret_cast<uintptr_t>(counts) & 7u)) return GS_ERR_ARG;
+  if (!valid_batch(cfg->raster_batch_fwd)) return GS_ERR_UNSUPPORTED;
+  a.K = make_consts(*cfg);
+  a.projected = reinterpret_cast<const float4*>(projected);
+  a.vals = vals;
+  a.ranges = reinterpret_cast<const uint2*>(tile_ranges);
+  a.order = (a.K.flags & GS_FLAG_TILE_ORDER) ? tile_ranges + 2 * static_cast<size_t>(a.L.n_tiles) : nullptr;
+  a.image = image;
+  a.final_T = final_T;
+  a.last = last;
+  a.IL = IL;
+  a.counts = counts;
+  return dispatch_fwd(pixels_per_thread(a.L, a.K), cfg->raster_batch_fwd, counts != nullptr, a, stream);
+}
+
+int rasterize_bwd_pixels_impl(const float* projected, const uint32_t* vals, const uint32_t* tile_ranges,
+                              const int32_t* sizes, int32_t V, const gs_config* cfg, int64_t N, const float* final_T,
+                              const uint32_t* last, const float* dL_dimage, float* d_projected,
+                              unsigned long long* counts, cudaStream_t stream) {
+  BwdArgs a;
+  int rc = build_layout(sizes, V, cfg, &a.L, nullptr);
+  if (rc != GS_OK) return rc;
+  if (N < 0) return GS_ERR_ARG;
+  if (N == 0) return GS_OK;
+  if (N * static_cast<int64_t>(V) >= (int64_t(1) << 32)) return GS_ERR_ARG;
+  if (!projected || !tile_ranges || !final_T || !last || !dL_dimage || !d_projected) return GS_ERR_ARG;
+  if (!aligned16(projected) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7u)) return GS_ERR_ARG;
+  if (counts && (reinterpret_cast<uintptr_t>(counts) & 7u)) return GS_ERR_ARG;
+  if (!valid_batch(cfg->raster_batch_bwd)) return GS_ERR_UNSUPPORTED;
+  a.K = make_consts(*cfg);
+  if (cudaMemsetAsync(d_projected, 0, sizeof(float) * kDRecordFloats * static_cast<size_t>(N) * V, stream) !=
+      cudaSuccess)
+    return GS_ERR_CUDA;
+  a.projected = reinterpret_cast<const float4*>(projected);
+  a.vals = vals;
+  a.ranges = reinterpret_cast<const uint2*>(tile_ranges);
+  a.order = (a.K.flags & GS_FLAG_TILE_ORDER) ? tile_ranges + 2 * static_cast<size_t>(a.L.n_tiles) : nullptr;
+  a.final_T = final_T;
+  a.last = last;
+  a.dL_dimage = dL_dimage;
+  a.d_proj = d_projected;
+  a.counts = counts;
+  const bool bg = a.K.bg[0] != 0.0f || a.K.bg[1] != 0.0f || a.K.bg[2] != 0.0f;
+  return dispatch_bwd(pixels_per_thread(a.L, a.K), cfg->raster_batch_bwd, bg, counts != nullptr, a, stream);
 }
 
 }  // namespace
@@ -760,8 +139,19 @@ int rasterize_fwd_impl(const float* projected, const uint32_t* vals, const uint3
 extern "C" int gs_rasterize_fwd(const float* projected, const uint32_t* vals, const uint32_t* tile_ranges,
                                 const int32_t* sizes, int32_t V, const gs_config* cfg, float* image, float* final_T,
                                 uint32_t* last, gs_stream_t stream) {
-  gs::ImageLoss none{};
+  gs::rast::ImageLoss none{};
+  return gs::rasterize_fwd_impl(projected, vals, tile_ranges, sizes, V, cfg, image, final_T, last, none, nullptr,
+                                reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int gs_rasterize_fwd_counted(const float* projected, const uint32_t* vals, const uint32_t* tile_ranges,
+                                        const int32_t* sizes, int32_t V, const gs_config* cfg, float* image,
+                                        float* final_T, uint32_t* last, uint64_t* pair_counts_dev,
+                                        gs_stream_t stream) {
+  if (!pair_counts_dev) return GS_ERR_ARG;
+  gs::rast::ImageLoss none{};
   return gs::rasterize_fwd_impl(projected, vals, tile_ranges, sizes, V, cfg, image, final_T, last, none,
+                                reinterpret_cast<unsigned long long*>(pair_counts_dev),
                                 reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -778,8 +168,9 @@ extern "C" int gs_rasterize_fwd_l1l2(const float* projected, const uint32_t* val
   const int rc = gs_layout_totals(sizes, V, cfg, &n_tiles, &n_pixels);
   if (rc != GS_OK) return rc;
   if (n_values < 3 * n_pixels) return GS_ERR_ARG;
+  if (!valid_batch(cfg->raster_batch_fwd)) return GS_ERR_UNSUPPORTED;
   if (!accumulate && cudaMemsetAsync(loss_dev, 0, sizeof(double), stream) != cudaSuccess) return GS_ERR_CUDA;
-  ImageLoss IL;
+  rast::ImageLoss IL;
   IL.target = target;
   IL.grad = dL_dimage;
   IL.loss = loss_dev;
@@ -787,42 +178,26 @@ extern "C" int gs_rasterize_fwd_l1l2(const float* projected, const uint32_t* val
   IL.w2 = w_l2;
   IL.inv_n = 1.0f / static_cast<float>(n_values);
   IL.inv_n_d = 1.0 / static_cast<double>(n_values);
-  return rasterize_fwd_impl(projected, vals, tile_ranges, sizes, V, cfg, image, final_T, last, IL, stream);
+  return rasterize_fwd_impl(projected, vals, tile_ranges, sizes, V, cfg, image, final_T, last, IL, nullptr, stream);
 }
 
 extern "C" int gs_rasterize_bwd_pixels(const float* projected, const uint32_t* vals, const uint32_t* tile_ranges,
                                        const int32_t* sizes, int32_t V, const gs_config* cfg, int64_t N,
                                        const float* final_T, const uint32_t* last, const float* dL_dimage,
-                                       float* d_projected, gs_stream_t stream_) {
-  using namespace gs;
-  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-  Layout L;
-  int rc = build_layout(sizes, V, cfg, &L, nullptr);
-  if (rc != GS_OK) return rc;
-  if (N < 0) return GS_ERR_ARG;
-  if (N == 0) return GS_OK;
-  if (N * static_cast<int64_t>(V) >= (int64_t(1) << 32)) return GS_ERR_ARG;
-  if (!projected || !tile_ranges || !final_T || !last || !dL_dimage || !d_projected) return GS_ERR_ARG;
-  if (!aligned16(projected) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7u)) return GS_ERR_ARG;
-  const Consts K = make_consts(*cfg);
-  if (cudaMemsetAsync(d_projected, 0, sizeof(float) * kDRecordFloats * static_cast<size_t>(N) * V, stream) !=
-      cudaSuccess)
-    return GS_ERR_CUDA;
-  const float4* pr = reinterpret_cast<const float4*>(projected);
-  const uint2* rg = reinterpret_cast<const uint2*>(tile_ranges);
-  const int ppt = pixels_per_thread(L, K);
-  if (L.tile_w == 16 && L.tile_h == 16)
-    return ppt == 4 ? launch_bwd<16, 16, 4>(pr, vals, rg, L, K, final_T, last, dL_dimage, d_projected, stream)
-                    : launch_bwd<16, 16, 2>(pr, vals, rg, L, K, final_T, last, dL_dimage, d_projected, stream);
-  if (L.tile_w == 8 && L.tile_h == 8)
-    return launch_bwd<8, 8, 2>(pr, vals, rg, L, K, final_T, last, dL_dimage, d_projected, stream);
-  if (L.tile_w == 32 && L.tile_h == 16)
-    return ppt == 4 ? launch_bwd<32, 16, 4>(pr, vals, rg, L, K, final_T, last, dL_dimage, d_projected, stream)
-                    : launch_bwd<32, 16, 2>(pr, vals, rg, L, K, final_T, last, dL_dimage, d_projected, stream);
-  if (L.tile_w == 32 && L.tile_h == 32)
-    return ppt == 4 ? launch_bwd<32, 32, 4>(pr, vals, rg, L, K, final_T, last, dL_dimage, d_projected, stream)
-                    : launch_bwd<32, 32, 2>(pr, vals, rg, L, K, final_T, last, dL_dimage, d_projected, stream);
-  return GS_ERR_UNSUPPORTED;
+                                       float* d_projected, gs_stream_t stream) {
+  return gs::rasterize_bwd_pixels_impl(projected, vals, tile_ranges, sizes, V, cfg, N, final_T, last, dL_dimage,
+                                       d_projected, nullptr, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int gs_rasterize_bwd_pixels_counted(const float* projected, const uint32_t* vals,
+                                               const uint32_t* tile_ranges, const int32_t* sizes, int32_t V,
+                                               const gs_config* cfg, int64_t N, const float* final_T,
+                                               const uint32_t* last, const float* dL_dimage, float* d_projected,
+                                               uint64_t* pair_counts_dev, gs_stream_t stream) {
+  if (!pair_counts_dev) return GS_ERR_ARG;
+  return gs::rasterize_bwd_pixels_impl(projected, vals, tile_ranges, sizes, V, cfg, N, final_T, last, dL_dimage,
+                                       d_projected, reinterpret_cast<unsigned long long*>(pair_counts_dev),
+                                       reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" int gs_rasterize_bwd(const float* means, const float* log_scales, const float* quats,

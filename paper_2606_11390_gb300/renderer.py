@@ -341,19 +341,33 @@ class TrainStep:
     a per-camera training loop would take), without graph capture.
     loss="l1l2": the scene's w_l1 mean|r| + w_l2 mean(r^2); loss="ssim": the
     fused SSIM loss (1 - ssim_lambda) mean|r| + ssim_lambda (1 - mean SSIM).
+    Rasteriser launch configuration (see autotune.py): tile=(tw, th),
+    raster_px (pixels per thread, 2 or 4; None keeps the scene's setting) and
+    raster_batch=(forward, backward) splats per shared-memory batch (0: the
+    default). graph: capture the step in a CUDA graph (default: batched mode
+    only).
     """
 
     def __init__(self, scene: dict, mode="batched", adam=False, lr=1e-3, betas=(0.9, 0.999), eps=1e-15,
-                 tile=None, device="cuda", graph=True, params: FlatParams | None = None, loss="l1l2",
-                 ssim_lambda=0.2, densify_stats=False):
+                 tile=None, device="cuda", graph=None, params: FlatParams | None = None, loss="l1l2",
+                 ssim_lambda=0.2, densify_stats=False, raster_px=None, raster_batch=(0, 0)):
         if loss not in ("l1l2", "ssim"):
             raise ValueError(f"unknown loss {loss!r}")
         self.loss_kind, self.ssim_lambda = loss, float(ssim_lambda)
-        self.mode, self.adam_on, self.graph_on = mode, adam, graph and mode == "batched"
+        # by default the batched step is captured and the per-view step (the
+        # plain per-camera loop) is not; graph=True captures either
+        self.mode, self.adam_on = mode, adam
+        self.graph_on = (mode == "batched") if graph is None else bool(graph)
         self.lr, self.betas, self.eps = lr, betas, eps
         self.cfg = dict(scene["cfg"])
         if tile is not None:
             self.cfg["tile_w"], self.cfg["tile_h"] = tile
+        if raster_px is not None:
+            if raster_px not in (2, 4):
+                raise ValueError("raster_px must be 2 or 4")
+            fl = int(self.cfg.get("flags", 0)) & ~gs.GS_FLAG_RASTER_2PX
+            self.cfg["flags"] = fl | (gs.GS_FLAG_RASTER_2PX if raster_px == 2 else 0)
+        self.cfg["raster_batch_fwd"], self.cfg["raster_batch_bwd"] = (int(b) for b in raster_batch)
         self.N = int(scene["means"].shape[0])
         self.params = params if params is not None else FlatParams(self.N, device).load_from(scene)
         self.grads = self.params.like()

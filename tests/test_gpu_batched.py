@@ -77,6 +77,52 @@ def test_graph_replay_equals_eager(R):
         grad_close(g.grads[k].cpu().numpy(), e.grads[k].cpu().numpy().astype(np.float64), rel=1e-3, name=k)
 
 
+def test_per_view_captured_equals_per_view_eager(R):
+    """The per-view loop (one launch per stage and view) captured in a graph:
+    the same image and loss as launching it eagerly."""
+    s = _scene()
+    g = _run(R, s, "per_view", graph=True, steps=2)
+    e = _run(R, s, "per_view", graph=False, steps=2)
+    assert g.graph is not None and e.graph is None
+    np.testing.assert_array_equal(g.image.cpu().numpy(), e.image.cpu().numpy())
+    assert abs(g.loss.item() - e.loss.item()) <= 1e-12 * max(1.0, abs(e.loss.item()))
+    for k in ("means", "sh"):
+        grad_close(g.grads[k].cpu().numpy(), e.grads[k].cpu().numpy().astype(np.float64), rel=1e-3, name=k)
+
+
+@pytest.mark.parametrize("px,batch", [(2, (64, 256)), (4, (256, 128)), (2, (0, 64))])
+def test_tuned_step_equals_default(R, px, batch):
+    """A step with another rasteriser configuration (pixels per thread,
+    splats per batch) renders the default step's image bit for bit."""
+    import torch
+
+    s = _scene()
+    d = _run(R, s, "batched")
+    st = R.TrainStep(s, mode="batched", raster_px=px, raster_batch=batch).prepare()
+    st.run()
+    torch.cuda.synchronize()
+    st.check()
+    np.testing.assert_array_equal(st.image.cpu().numpy(), d.image.cpu().numpy())
+    for k in ("means", "sh"):
+        grad_close(st.grads[k].cpu().numpy(), d.grads[k].cpu().numpy().astype(np.float64), rel=1e-3, name=k)
+
+
+def test_autotuner_on_the_gpu(R, tmp_path, monkeypatch):
+    """best_config times its 13 configurations, returns one of them and
+    caches it under the library digest; a second call reads the cache."""
+    from paper_2606_11390_gb300 import autotune
+
+    monkeypatch.setenv("GS_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    s = _scene()
+    best, times = autotune.best_config(s, steps=1)
+    assert len(times) == 13 and autotune.name(best) in times
+    assert times[autotune.name(best)] == min(times.values())
+    again, times2 = autotune.best_config(s, steps=1)
+    assert again == best and times2 == times
+    st = R.TrainStep(s, mode="batched", **autotune.step_kwargs(best)).prepare()
+    st.run()
+
+
 def test_adam_step_in_graph_moves_parameters(R, oracle):
     import torch
 
