@@ -26,6 +26,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "gs_common.cuh"
 #include "gs_internal.h"
 
@@ -868,27 +870,39 @@ WsLayout ws_layout(int64_t N, int32_t V, int64_t capacity, int64_t n_tiles, int 
   return w;
 }
 
-int sm_count() {
-  static int cached[64] = {0};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) return 148;
-  if (!cached[dev]) {
-    int n = 0;
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    cached[dev] = n > 0 ? n : 148;
-  }
-  return cached[dev];
+// Per-device launch facts, filled on the first call made on each device
+// (with that device current) under one lock, so that threads making their
+// first calls at once, or on different devices, see complete entries.
+struct DeviceFacts {
+  std::mutex m;
+  int sms[kMaxDevices] = {};
+  int sort_ctas_per_sm[kMaxDevices] = {};  // 0: the digit pass's attributes are not set yet
+};
+DeviceFacts& device_facts() {
+  static DeviceFacts f;
+  return f;
 }
 
-}  // namespace
+int query_sm_count(int dev) {
+  int n = 0;
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 148;
+}
 
-// Occupancy-derived persistent grid for the digit passes; sets the kernel's
-// shared-memory attributes on first use.
-int sort_grid_cap(int64_t* cap) {
-  static bool attr_set = false;
-  static int ctas_per_sm = 0;
-  if (!attr_set) {
+int sm_count() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+  if (dev < 0 || dev >= kMaxDevices) return query_sm_count(dev);
+  DeviceFacts& f = device_facts();
+  std::lock_guard<std::mutex> lock(f.m);
+  if (!f.sms[dev]) f.sms[dev] = query_sm_count(dev);
+  return f.sms[dev];
+}
+
+// Sets the digit pass's shared-memory attributes on the current device and
+// returns its resident CTAs per SM (0 on a CUDA error).
+int setup_sort_pass() {
+  {
     const void* fns[8] = {reinterpret_cast<const void*>(sort_pass_kernel<1>), reinterpret_cast<const void*>(sort_pass_kernel<2>),
                           reinterpret_cast<const void*>(sort_pass_kernel<3>), reinterpret_cast<const void*>(sort_pass_kernel<4>),
                           reinterpret_cast<const void*>(sort_pass_kernel<5>), reinterpret_cast<const void*>(sort_pass_kernel<6>),
@@ -898,14 +912,34 @@ int sort_grid_cap(int64_t* cap) {
               cudaSuccess ||
           cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
               cudaSuccess)
-        return GS_ERR_CUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, sort_pass_kernel<8>, kSortThreads,
-                                                      sizeof(SortSmem)) != cudaSuccess ||
-        ctas_per_sm < 1)
-      ctas_per_sm = 1;
-    attr_set = true;
+        return 0;
   }
-  *cap = static_cast<int64_t>(sm_count()) * ctas_per_sm;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sort_pass_kernel<8>, kSortThreads, sizeof(SortSmem)) !=
+          cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return per_sm;
+}
+
+}  // namespace
+
+// Occupancy-derived persistent grid for the digit passes; sets the kernel's
+// shared-memory attributes on the first call made on each device.
+int sort_grid_cap(int64_t* cap) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GS_ERR_CUDA;
+  int per_sm = 0;
+  if (dev < 0 || dev >= kMaxDevices) {
+    per_sm = setup_sort_pass();
+  } else {
+    DeviceFacts& f = device_facts();
+    std::lock_guard<std::mutex> lock(f.m);
+    if (!f.sort_ctas_per_sm[dev]) f.sort_ctas_per_sm[dev] = setup_sort_pass();
+    per_sm = f.sort_ctas_per_sm[dev];
+  }
+  if (per_sm < 1) return GS_ERR_CUDA;
+  *cap = static_cast<int64_t>(sm_count()) * per_sm;
   return GS_OK;
 }
 

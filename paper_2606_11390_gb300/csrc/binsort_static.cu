@@ -26,7 +26,6 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_static_scratch[GS_STATIC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 void* g_scratch_ptr[kMaxDevices] = {};
 
@@ -52,10 +51,13 @@ extern "C" int gs_bin_sort_static(const float* projected, const int16_t* rects, 
                                   const int32_t* sizes, int32_t V, const gs_config* cfg, uint64_t* keys,
                                   uint32_t* vals, int64_t capacity, uint32_t* tile_ranges, int64_t* n_isect_dev,
                                   int32_t* status_dev, gs_stream_t stream) {
-  if (N < 0 || V < 1 || capacity < 0) return GS_ERR_ARG;
   int64_t n_tiles = 0;
   const int rc = gs_layout_totals(sizes, V, cfg, &n_tiles, nullptr);
   if (rc != GS_OK) return rc;
+  // the argument checks of gs_bin_sort come first, so both return the same
+  // code for an invalid argument (sizes that no workspace could serve)
+  if (N < 0 || capacity < 0 || capacity >= (int64_t(1) << 32) - 1) return GS_ERR_ARG;
+  if (N * static_cast<int64_t>(V) >= (int64_t(1) << 32) - 1) return GS_ERR_ARG;
   const size_t need = gs_bin_sort_workspace_bytes(N, V, capacity, n_tiles);
   if (need == 0 || need > static_cast<size_t>(GS_STATIC_SCRATCH_BYTES)) return GS_ERR_TOO_LARGE;
   void* scratch = nullptr;

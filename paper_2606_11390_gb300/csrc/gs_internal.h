@@ -12,6 +12,10 @@ int build_layout(const int32_t* sizes, int32_t V, const gs_config* cfg, Layout* 
 
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// Device ordinals that the host-side per-device caches (launch geometry,
+// kernel attributes, the static scratch address) keep a slot for.
+constexpr int kMaxDevices = 64;
+
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? GS_OK : GS_ERR_CUDA; }
 
 // Launch of the per-Gaussian backward (defined in project.cu, used by

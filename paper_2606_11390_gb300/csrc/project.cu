@@ -26,6 +26,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "gs_common.cuh"
 #include "gs_internal.h"
 
@@ -658,18 +660,28 @@ __global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_ke
 
 }  // namespace
 
-// CTAs of `kernel` resident on the whole GPU at once (queried once per kernel).
+// CTAs of `kernel` resident on the whole current GPU at once (queried once
+// per kernel and device, under a lock).
 template <int Tag, class F>
 int64_t resident_ctas(F kernel) {
-  static int64_t cached = -1;
-  if (cached < 0) {
-    int dev = 0, sms = 0, per_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kProjBlock, 0) != cudaSuccess)
-      return 0;
-    cached = static_cast<int64_t>(sms) * per_sm;
+  static std::mutex m;
+  static int64_t cached[kMaxDevices] = {};
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  const bool slot = dev >= 0 && dev < kMaxDevices;
+  if (slot) {
+    std::lock_guard<std::mutex> lock(m);
+    if (cached[dev] > 0) return cached[dev];
   }
-  return cached;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kProjBlock, 0) != cudaSuccess)
+    return 0;
+  const int64_t n = static_cast<int64_t>(sms) * per_sm;
+  if (slot) {
+    std::lock_guard<std::mutex> lock(m);
+    cached[dev] = n;
+  }
+  return n;
 }
 
 int launch_project_bwd(const float* means, const float* log_scales, const float* quats, const float* opacity_logits,
