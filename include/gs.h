@@ -178,7 +178,7 @@ GS_API int gs_project(const float* means, const float* log_scales, const float* 
 
 /* Bytes of device workspace gs_bin_sort needs for N Gaussians, V views, a
  * key capacity and n_tiles tiles (from gs_layout_totals); 0 for invalid
- * arguments. About 16 V N + 12 capacity bytes. */
+ * arguments. About 16 V N + 18 capacity + 276 n_tiles bytes. */
 GS_API size_t gs_bin_sort_workspace_bytes(int64_t N, int32_t V, int64_t capacity, int64_t n_tiles);
 
 /* gs_bin_sort - tile keys and per-camera depth sort.
@@ -190,9 +190,10 @@ GS_API size_t gs_bin_sort_workspace_bytes(int64_t N, int32_t V, int64_t capacity
  *   key = (global tile id << 32) | float bits of depth,  val = vg,
  * stably sorted by key, so equal keys stay in record-index order; and
  * tile_ranges[t] = [start, end) of tile t's entries in the sorted list
- * ([0, 0) for an empty tile). Computed as a depth sort of the visible records
- * followed by a stable sort of the emitted entries by tile id, which yields
- * the same order.
+ * ([0, 0) for an empty tile). Computed as a depth sort of the visible records,
+ * a stable binning of them into super-tiles of 8 x 8 tiles, and a placement
+ * of each record in the lists of the tiles it covers in that order, which
+ * yields the same order.
  *
  * in  (device): projected, rects, counts from gs_project; depth_keys from
  *               gs_project (optional: with NULL the depths are read from the
@@ -205,10 +206,10 @@ GS_API size_t gs_bin_sort_workspace_bytes(int64_t N, int32_t V, int64_t capacity
  *               n_isect_dev [1] int64 = total number of intersections.
  * workspace (device, caller-owned, >= gs_bin_sort_workspace_bytes, 256-byte
  *   aligned): scratch, contents undefined on return.
- * If the total exceeds `capacity`, only the first `capacity` pairs in
- * depth-sorted emission order are kept, GS_STATUS_CAPACITY is set and
- * keys, vals and ranges must not be used: grow the buffers to *n_isect_dev
- * and call again. A device wait that exceeds its iteration bound sets
+ * If the total exceeds `capacity`, GS_STATUS_CAPACITY is set, no write goes
+ * past `capacity`, and keys, vals and ranges are incomplete and must not be
+ * used: grow the buffers to *n_isect_dev (always the exact total) and call
+ * again. A device wait that exceeds its iteration bound sets
  * GS_STATUS_TIMEOUT.
  * Errors: GS_ERR_ARG (also for a too-small workspace), GS_ERR_CUDA. */
 GS_API int gs_bin_sort(const float* projected, const int16_t* rects, const uint32_t* counts, const uint32_t* depth_keys,
@@ -251,7 +252,7 @@ GS_API int gs_bin_sort_partitioned(const float* projected, const int16_t* rects,
  * Arguments, outputs and status bits are those of gs_bin_sort, minus the
  * workspace and the optional depth keys (the depths are read from the
  * projected records). Limit: gs_bin_sort_workspace_bytes(N, V, capacity, n_tiles)
- * must not exceed GS_STATIC_SCRATCH_BYTES (about 16 V N + 12 capacity bytes),
+ * must not exceed GS_STATIC_SCRATCH_BYTES (about 16 V N + 18 capacity + 276 n_tiles bytes),
  * else GS_ERR_TOO_LARGE is returned and nothing is enqueued.
  * The first call on a device looks up the array's device address (with that
  * device current); make that first call before any stream capture.

@@ -1,5 +1,5 @@
-// Tile keys and depth sort: CUB-free onesweep radix sorts producing, per
-// image tile, the list of intersecting splats in (depth, index) order.
+// Tile keys and depth sort: per image tile, the list of intersecting splats
+// in (depth, index) order, with CUB-free onesweep radix passes.
 //
 // Paper: arXiv 2606.11390 §4 (each camera's Gaussians are depth-sorted before
 // rasterisation; the multi-GPU merge sort of §4 is not needed on one GPU) and
@@ -13,16 +13,21 @@
 //
 // The sorted order is that of the stable sort of the 64-bit keys
 // (tile << 32) | bits(depth) emitted in (view, Gaussian, row-major tile)
-// order. It is reached in two smaller sorts:
+// order. It is reached in three steps:
 //   1. compact the visible records and sort them by depth bits (4 passes over
 //      32-bit keys; stability keeps equal depths in record-index order);
-//   2. emit one (tile id, record) pair per covered tile, records in depth
-//      order, and stably sort the pairs by tile id (ceil(log2 tiles / 8)
-//      passes over 32-bit keys).
+//   2. bin the records, in depth order, into super-tiles of 8 x 8 tiles (one
+//      entry per super-tile a rectangle meets, about 1.3 per record) and sort
+//      the entries stably by super-tile id (1-2 passes);
+//   3. per chunk of 256 records of a super-tile's list, place each record in
+//      the lists of the tiles it covers: a 64-bit coverage mask per record,
+//      one warp ballot per tile for the ranks, per-chunk tile counts scanned
+//      over the super-tile's chunks and over all tiles; every intersection is
+//      written once, at its final position.
 // Within a tile the entries then run in (depth, record) order, exactly the
 // order of the 64-bit key sort, while the large list (one entry per tile
-// intersection) goes through 2 passes of 16 bytes per entry instead of 6
-// passes of 24 bytes.
+// intersection) is written once, 4 bytes per entry, instead of going through
+// 64-bit key passes.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -41,7 +46,6 @@ constexpr int kRadix = 256;
 constexpr int kDepthPasses = 4;
 // Wait bound used with GS_FLAG_TEST_STALL_LOOKBACK (milliseconds, not seconds).
 constexpr uint32_t kTestSpinLimit = 1u << 12;
-constexpr int kMaxTilePasses = 4;
 
 __device__ __forceinline__ uint64_t warp_incl_scan_u64(uint64_t v) {
   const int lane = threadIdx.x & 31;
@@ -182,144 +186,6 @@ __global__ void __launch_bounds__(kScanThreads) compact_visible_kernel(
   for (int i = tid; i < kDepthPasses * kRadix; i += kScanThreads) {
     const uint32_t c = (&s_hist[0][0])[i];
     if (c) atomicAdd(hist + i, c);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// 1c + 2a. Tile-count offsets in depth order and emission in one kernel.
-//     Each CTA takes a tile of 1024 depth-sorted records by ticket, scans
-//     their tile counts (block scan + decoupled look-back, clamped at the
-//     capacity), then expands them one warp per 32 records, load-balanced:
-//     the warp scans the records' counts, and lane l produces entries l,
-//     l + 32, ... of the warp's concatenated output, finding the record of
-//     each entry from the record starts of the round. All lanes stay busy
-//     whatever the record sizes, and each warp store writes 32 consecutive
-//     positions except at record boundaries. The tile-id digit histograms of
-//     the tile passes are gathered on the way with shared atomics.
-// ---------------------------------------------------------------------------
-constexpr int kEmitThreads = 256;
-static_assert(kEmitThreads == kScanThreads, "the emission scans its records with the block scan");
-constexpr int kEmitItems = 4;                              // records per thread in the count scan
-constexpr int kEmitTile = kEmitThreads * kEmitItems;       // records per emission tile
-constexpr int kEmitGroups = kEmitTile / 32;                // 32-record groups per tile
-
-__global__ void __launch_bounds__(kEmitThreads) emit_tiles_kernel(
-    const uint32_t* __restrict__ order, const int64_t* n_visible, const uint32_t* __restrict__ counts,
-    const short4* __restrict__ rects, int64_t N, const Layout L, uint64_t capacity, int tile_passes, ScanState st,
-    uint32_t* __restrict__ tkeys, uint32_t* __restrict__ tvals, uint32_t* __restrict__ hist, int64_t* n_total,
-    int32_t* status) {
-  __shared__ uint32_t s_hist[kMaxTilePasses][kRadix];
-  __shared__ uint32_t s_vg[kEmitTile], s_cnt[kEmitTile], s_off[kEmitTile];
-  __shared__ uint32_t s_tile;
-  __shared__ uint64_t s_warp[kScanThreads / 32];
-  __shared__ uint64_t s_prefix;
-  const int tid = threadIdx.x, lane = tid & 31;
-  if (tid == 0) s_tile = atomicAdd(st.ticket, 1u);
-  for (int i = tid; i < kMaxTilePasses * kRadix; i += kEmitThreads) (&s_hist[0][0])[i] = 0;
-  __syncthreads();
-  const uint32_t t = s_tile;
-  const int64_t n = *n_visible;
-  const int64_t tile0 = static_cast<int64_t>(t) * kEmitTile;
-  if (tile0 >= n) return;  // past the data: publishes nothing, awaited by nobody
-  // 1. the tile's records (depth order) and their tile counts, scanned with
-  //    decoupled look-back: output offsets, clamped at the capacity
-  const int64_t base = tile0 + static_cast<int64_t>(tid) * kEmitItems;
-  uint32_t c[kEmitItems];
-  uint64_t local = 0;
-#pragma unroll
-  for (int i = 0; i < kEmitItems; ++i) {
-    const uint32_t vg = base + i < n ? order[base + i] : 0u;
-    c[i] = base + i < n ? counts[vg] : 0u;
-    s_vg[tid * kEmitItems + i] = vg;
-    s_cnt[tid * kEmitItems + i] = c[i];
-    local += c[i];
-  }
-  uint64_t run = block_scan_lookback(local, t, st, s_warp, &s_prefix, status);
-#pragma unroll
-  for (int i = 0; i < kEmitItems; ++i) {
-    s_off[tid * kEmitItems + i] = static_cast<uint32_t>(run < capacity ? run : capacity);
-    run += c[i];
-  }
-  if (base <= n - 1 && n - 1 < base + kEmitItems) {
-    *n_total = static_cast<int64_t>(run);
-    if (run > capacity) set_status(status, GS_STATUS_CAPACITY);
-  }
-  __syncthreads();
-  // 2. emission, one warp per group of 32 records, load-balanced: the warp
-  //    scans the records' counts, and lane l produces entries l, l + 32, ...
-  //    of the group's concatenated output, finding the record of each entry
-  //    from the record starts of the round. The tile-id digit histograms of
-  //    the tile passes are gathered on the way with shared atomics.
-  const float invN = 1.0f / static_cast<float>(N);
-  for (int g = tid >> 5; g < kEmitGroups && capacity > 0; g += kEmitThreads / 32) {
-    const int r = g * 32 + lane;
-    const int64_t j = tile0 + r;
-    uint32_t vg = 0, cnt = 0, tb = 0, xy = 0, wn = 1;
-    if (j < n) {
-      vg = s_vg[r];
-      cnt = s_cnt[r];
-      const short4 rc = rects[vg];
-      // view index v = vg / N by float quotient and exact fix-up (one view: 0)
-      int v = 0;
-      if (L.V > 1) {
-        v = __float2int_rz(static_cast<float>(vg) * invN);
-        while (v > 0 && static_cast<int64_t>(v) * N > static_cast<int64_t>(vg)) --v;
-        while (static_cast<int64_t>(v + 1) * N <= static_cast<int64_t>(vg)) ++v;
-      }
-      tb = L.tile_base[v];
-      // packed record fields: (x0, y0) and (width, tiles per row), 16 bits each
-      xy = static_cast<uint32_t>(static_cast<uint16_t>(rc.x)) | (static_cast<uint32_t>(static_cast<uint16_t>(rc.y)) << 16);
-      wn = static_cast<uint32_t>(rc.z - rc.x) | (static_cast<uint32_t>(L.ntx[v]) << 16);
-    }
-    // exclusive prefix of the counts within the group; the group's entries are
-    // contiguous in the output from its first record's offset
-    uint32_t incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t nb = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += nb;
-    }
-    const uint32_t excl = incl - cnt;
-    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-    const uint64_t out_base = s_off[g * 32];
-    const uint32_t le_mask = 0xffffffffu >> (31 - lane);  // bits 0..lane
-    uint32_t started = 0;  // records (lanes) whose entries start before this round
-    for (uint32_t eb = 0; eb < total; eb += 32) {
-      // bit i: a record's first entry is entry eb + i (records have count >= 1,
-      // so the starts are distinct); the record of entry eb + lane is the
-      // last one started at or before it
-      const uint32_t stb = (cnt > 0 && excl >= eb && excl - eb < 32u) ? (1u << (excl - eb)) : 0u;
-      const uint32_t starts = __reduce_or_sync(0xffffffffu, stb);
-      const int src = static_cast<int>(started + __popc(starts & le_mask)) - 1;
-      started += __popc(starts);
-      const uint32_t e = eb + lane;
-      const uint32_t k = e - __shfl_sync(0xffffffffu, excl, src);
-      const uint32_t r_vg = __shfl_sync(0xffffffffu, vg, src);
-      const uint32_t r_xy = __shfl_sync(0xffffffffu, xy, src);
-      const uint32_t r_wn = __shfl_sync(0xffffffffu, wn, src);
-      const uint32_t r_tb = L.V > 1 ? __shfl_sync(0xffffffffu, tb, src) : tb;
-      const uint64_t pos = out_base + e;
-      if (e < total && pos < capacity) {
-        const int r_w = static_cast<int>(r_wn & 0xffffu);
-        const uint32_t r_ntx = r_wn >> 16;
-        const int r_x0 = static_cast<int16_t>(r_xy & 0xffffu), r_y0 = static_cast<int16_t>(r_xy >> 16);
-        // k = row * w + col: quotient from the approximate reciprocal, then an
-        // exact fix-up (the estimate is off by at most one)
-        int row = __float2int_rz(static_cast<float>(k) * rcp_approx(static_cast<float>(r_w)));
-        int col = static_cast<int>(k) - row * r_w;
-        if (col < 0) { --row; col += r_w; }
-        if (col >= r_w) { ++row; col -= r_w; }
-        const uint32_t tile = r_tb + static_cast<uint32_t>(r_y0 + row) * r_ntx + static_cast<uint32_t>(r_x0 + col);
-        tkeys[pos] = tile;
-        tvals[pos] = r_vg;
-        for (int p = 0; p < tile_passes; ++p) atomicAdd(&s_hist[p][(tile >> (8 * p)) & 0xffu], 1u);
-      }
-    }
-  }
-  __syncthreads();
-  for (int i = tid; i < tile_passes * kRadix; i += kEmitThreads) {
-    const uint32_t cc = (&s_hist[0][0])[i];
-    if (cc) atomicAdd(hist + i, cc);
   }
 }
 
@@ -589,20 +455,14 @@ __device__ __forceinline__ int order_bucket(uint32_t len) {
   return kOrderBuckets - 2 - (b < kOrderBuckets - 2 ? b : kOrderBuckets - 2);
 }
 
-// With fixup, the starts of the non-empty tiles come complemented from the
-// last tile-id pass and are restored here first (ranges_fixup_kernel's job).
-__global__ void __launch_bounds__(kOrderThreads) tile_order_kernel(uint2* __restrict__ ranges, int64_t n_tiles,
-                                                                   uint32_t* __restrict__ order, int fixup) {
+__global__ void __launch_bounds__(kOrderThreads) tile_order_kernel(const uint2* __restrict__ ranges, int64_t n_tiles,
+                                                                   uint32_t* __restrict__ order) {
   __shared__ uint32_t s_cnt[kOrderBuckets];
   const int tid = threadIdx.x;
   if (tid < kOrderBuckets) s_cnt[tid] = 0;
   __syncthreads();
   for (int64_t t = tid; t < n_tiles; t += kOrderThreads) {
-    uint2 r = ranges[t];
-    if (fixup && r.y) {
-      r.x = ~r.x;
-      ranges[t].x = r.x;
-    }
+    const uint2 r = ranges[t];
     atomicAdd(&s_cnt[order_bucket(r.y - r.x)], 1u);
   }
   __syncthreads();
@@ -745,63 +605,549 @@ __global__ void __launch_bounds__(kMergeThreads) merge_runs_kernel(MergeArgs m) 
   }
 }
 
-// Tile ranges from the sorted tile ids (ranges zeroed beforehand): four ids
-// per thread from one 16-byte load; a range starts where the id differs from
-// its predecessor and ends where it differs from its successor.
-__global__ void tile_ranges_kernel(const uint32_t* __restrict__ tkeys, const int64_t* n_total, int64_t capacity,
-                                   uint32_t n_tiles, uint2* __restrict__ ranges, int32_t* status) {
-  int64_t n = *n_total;
-  if (n > capacity) n = capacity;
-  const int64_t n4 = (n + 3) / 4;
-  for (int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < n4;
-       q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t i0 = 4 * q;
-    uint32_t k[4];
-    if (i0 + 3 < n) {
-      const uint4 v = reinterpret_cast<const uint4*>(tkeys)[q];
-      k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
-    } else {
-      for (int j = 0; j < 4; ++j) k[j] = i0 + j < n ? tkeys[i0 + j] : 0xffffffffu;
+// ---------------------------------------------------------------------------
+// 2. Tile lists through super-tiles.
+//    The visible records are in depth order (1a, 1b). Each is binned into the
+//    super-tiles (blocks of 8 x 8 tiles of its view) that its rectangle
+//    meets: emission in depth order and 1-2 stable digit passes by super-tile
+//    id, over about 1.3 entries per record instead of one per tile. A
+//    super-tile's list is then cut into chunks of 256 records. Within a
+//    chunk, each record's coverage of the super-tile's 64 tiles is a 64-bit
+//    mask, and the rank of a record in one tile's list is the population
+//    count of one warp ballot per tile, below the lane. Counting per (chunk,
+//    tile), a scan over each super-tile's chunks, a scan over all tiles in
+//    tile-id order (the tile ranges) and a scatter then write every tile
+//    entry once, 4 bytes, at its final position; the order within a tile is
+//    the record order of the super-tile's list, i.e. (depth, record).
+// ---------------------------------------------------------------------------
+constexpr int kSuperLog = 3;
+constexpr int kSuperDim = 1 << kSuperLog;           // tiles per super-tile side
+constexpr int kSuperTiles = kSuperDim * kSuperDim;  // 64: one bit each in a record's mask
+constexpr int kChunk = 256;                         // records per chunk
+constexpr int kChunkThreads = kChunk;               // one record per thread
+constexpr int kChunkWarps = kChunkThreads / 32;
+constexpr int kMaxSuperPasses = 4;
+
+// Super-tile grid of a call: view v has stx[v] x ceil(nty_v / 8) super-tiles,
+// with ids from sbase[v] in row-major order.
+struct SuperLayout {
+  int32_t n_super;
+  int32_t stx[kMaxViews];
+  uint32_t sbase[kMaxViews + 1];
+};
+
+SuperLayout make_super_layout(const Layout& L) {
+  SuperLayout S;
+  uint32_t base = 0;
+  for (int v = 0; v < kMaxViews; ++v) {
+    S.sbase[v] = base;
+    S.stx[v] = 0;
+    if (v < L.V) {
+      S.stx[v] = (L.ntx[v] + kSuperDim - 1) >> kSuperLog;
+      base += static_cast<uint32_t>(S.stx[v]) * static_cast<uint32_t>((L.nty[v] + kSuperDim - 1) >> kSuperLog);
     }
-    uint32_t prev = i0 > 0 ? tkeys[i0 - 1] : 0xffffffffu;
-    const uint32_t next = i0 + 4 < n ? tkeys[i0 + 4] : 0xffffffffu;
+  }
+  S.sbase[kMaxViews] = base;
+  S.n_super = static_cast<int32_t>(base);
+  return S;
+}
+
+__device__ __forceinline__ int view_of_super(const SuperLayout& S, int V, uint32_t s) {
+  int v = 0;
+  while (v + 1 < V && s >= S.sbase[v + 1]) ++v;
+  return v;
+}
+
+// View index of record vg = v * N + g (float quotient and exact fix-up).
+__device__ __forceinline__ int view_of_record(uint32_t vg, int64_t N, int V, float invN) {
+  if (V == 1) return 0;
+  int v = __float2int_rz(static_cast<float>(vg) * invN);
+  while (v > 0 && static_cast<int64_t>(v) * N > static_cast<int64_t>(vg)) --v;
+  while (static_cast<int64_t>(v + 1) * N <= static_cast<int64_t>(vg)) ++v;
+  return v;
+}
+
+// 2a. Super-tile emission. Each CTA takes a tile of 1024 depth-sorted
+//     records by ticket, scans their super-tile counts (block scan with
+//     decoupled look-back, clamped at the capacity), then expands them one
+//     warp per 32 records, load-balanced: the warp scans the records' counts
+//     and lane l produces entries l, l + 32, ... of the warp's concatenated
+//     output. It also adds the records' tile counts into *n_isect (the exact
+//     intersection count) and gathers the digit histograms of the super-tile
+//     passes.
+constexpr int kEmitThreads = 256;
+static_assert(kEmitThreads == kScanThreads, "the emission scans its records with the block scan");
+constexpr int kEmitItems = 4;                         // records per thread in the count scan
+constexpr int kEmitTile = kEmitThreads * kEmitItems;  // records per emission tile
+constexpr int kEmitGroups = kEmitTile / 32;           // 32-record groups per tile
+
+__device__ __forceinline__ uint32_t super_count(short4 rc) {
+  const int sx0 = rc.x >> kSuperLog, sx1 = ((rc.z - 1) >> kSuperLog) + 1;
+  const int sy0 = rc.y >> kSuperLog, sy1 = ((rc.w - 1) >> kSuperLog) + 1;
+  return static_cast<uint32_t>((sx1 - sx0) * (sy1 - sy0));
+}
+
+__global__ void __launch_bounds__(kEmitThreads) emit_super_kernel(
+    const uint32_t* __restrict__ order, const int64_t* n_visible, const short4* __restrict__ rects, int64_t N,
+    const Layout L, const SuperLayout S, uint64_t capacity, int passes, ScanState st, uint32_t* __restrict__ skeys,
+    uint32_t* __restrict__ svals, uint32_t* __restrict__ hist, int64_t* n_super_total,
+    unsigned long long* __restrict__ n_isect, int32_t* status) {
+  __shared__ uint32_t s_hist[kMaxSuperPasses][kRadix];
+  __shared__ uint32_t s_vg[kEmitTile], s_cnt[kEmitTile], s_off[kEmitTile];
+  __shared__ uint32_t s_tile;
+  __shared__ uint64_t s_warp[kScanThreads / 32];
+  __shared__ uint64_t s_prefix;
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid == 0) s_tile = atomicAdd(st.ticket, 1u);
+  for (int i = tid; i < kMaxSuperPasses * kRadix; i += kEmitThreads) (&s_hist[0][0])[i] = 0;
+  __syncthreads();
+  const uint32_t t = s_tile;
+  const int64_t n = *n_visible;
+  const int64_t tile0 = static_cast<int64_t>(t) * kEmitTile;
+  if (tile0 >= n) return;  // past the data: publishes nothing, awaited by nobody
+  // 1. the records (depth order), their super-tile counts, scanned with
+  //    decoupled look-back into output offsets (clamped at the capacity),
+  //    and their tile counts, summed into the intersection count
+  const int64_t base = tile0 + static_cast<int64_t>(tid) * kEmitItems;
+  uint32_t c[kEmitItems];
+  uint64_t local = 0;
+  uint64_t tiles = 0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int64_t i = i0 + j;
-      if (i >= n) break;
-      const uint32_t t = k[j];
-      const uint32_t nx = j < 3 ? (i + 1 < n ? k[j + 1] : 0xffffffffu) : next;
-      if (t >= n_tiles) {
-        set_status(status, GS_STATUS_BOUNDS);
-      } else {
-        if (t != prev) ranges[t].x = static_cast<uint32_t>(i);
-        if (t != nx) ranges[t].y = static_cast<uint32_t>(i + 1);
-      }
-      prev = t;
+  for (int i = 0; i < kEmitItems; ++i) {
+    const bool ok = base + i < n;
+    const uint32_t vg = ok ? order[base + i] : 0u;
+    c[i] = 0u;
+    if (ok) {
+      const short4 rc = rects[vg];
+      c[i] = super_count(rc);
+      tiles += static_cast<uint64_t>(rc.z - rc.x) * static_cast<uint64_t>(rc.w - rc.y);
     }
+    s_vg[tid * kEmitItems + i] = vg;
+    s_cnt[tid * kEmitItems + i] = c[i];
+    local += c[i];
+  }
+  {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tiles += __shfl_xor_sync(0xffffffffu, tiles, o);
+    if (lane == 0 && tiles) atomicAdd(n_isect, static_cast<unsigned long long>(tiles));
+  }
+  uint64_t run = block_scan_lookback(local, t, st, s_warp, &s_prefix, status);
+#pragma unroll
+  for (int i = 0; i < kEmitItems; ++i) {
+    s_off[tid * kEmitItems + i] = static_cast<uint32_t>(run < capacity ? run : capacity);
+    run += c[i];
+  }
+  if (base <= n - 1 && n - 1 < base + kEmitItems) *n_super_total = static_cast<int64_t>(run);
+  __syncthreads();
+  // 2. emission of (super-tile id, record) pairs, one warp per 32 records,
+  //    load-balanced as in the count scan's order
+  const float invN = 1.0f / static_cast<float>(N);
+  for (int g = tid >> 5; g < kEmitGroups && capacity > 0; g += kEmitThreads / 32) {
+    const int r = g * 32 + lane;
+    const int64_t j = tile0 + r;
+    uint32_t vg = 0, cnt = 0, sb = 0, xy = 0, wn = 1;
+    if (j < n) {
+      vg = s_vg[r];
+      cnt = s_cnt[r];
+      const short4 rc = rects[vg];
+      const int v = view_of_record(vg, N, L.V, invN);
+      sb = S.sbase[v];
+      const int sx0 = rc.x >> kSuperLog, sx1 = ((rc.z - 1) >> kSuperLog) + 1, sy0 = rc.y >> kSuperLog;
+      // packed super-rectangle fields: (x0, y0) and (width, super-tiles per row), 16 bits each
+      xy = static_cast<uint32_t>(sx0) | (static_cast<uint32_t>(sy0) << 16);
+      wn = static_cast<uint32_t>(sx1 - sx0) | (static_cast<uint32_t>(S.stx[v]) << 16);
+    }
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t nb = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += nb;
+    }
+    const uint32_t excl = incl - cnt;
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    const uint64_t out_base = s_off[g * 32];
+    const uint32_t le_mask = 0xffffffffu >> (31 - lane);  // bits 0..lane
+    uint32_t started = 0;  // records (lanes) whose entries start before this round
+    for (uint32_t eb = 0; eb < total; eb += 32) {
+      // bit i: a record's first entry is entry eb + i (counts are >= 1, so
+      // the starts are distinct); the record of entry eb + lane is the last
+      // one started at or before it
+      const uint32_t stb = (cnt > 0 && excl >= eb && excl - eb < 32u) ? (1u << (excl - eb)) : 0u;
+      const uint32_t starts = __reduce_or_sync(0xffffffffu, stb);
+      const int src = static_cast<int>(started + __popc(starts & le_mask)) - 1;
+      started += __popc(starts);
+      const uint32_t e = eb + lane;
+      const uint32_t k = e - __shfl_sync(0xffffffffu, excl, src);
+      const uint32_t r_vg = __shfl_sync(0xffffffffu, vg, src);
+      const uint32_t r_xy = __shfl_sync(0xffffffffu, xy, src);
+      const uint32_t r_wn = __shfl_sync(0xffffffffu, wn, src);
+      const uint32_t r_sb = L.V > 1 ? __shfl_sync(0xffffffffu, sb, src) : sb;
+      const uint64_t pos = out_base + e;
+      if (e < total && pos < capacity) {
+        const uint32_t r_w = r_wn & 0xffffu, r_stx = r_wn >> 16;
+        const uint32_t row = k / r_w, col = k - row * r_w;
+        const uint32_t s = r_sb + ((r_xy >> 16) + row) * r_stx + (r_xy & 0xffffu) + col;
+        skeys[pos] = s;
+        svals[pos] = r_vg;
+        for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p][(s >> (8 * p)) & 0xffu], 1u);
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < passes * kRadix; i += kEmitThreads) {
+    const uint32_t cc = (&s_hist[0][0])[i];
+    if (cc) atomicAdd(hist + i, cc);
   }
 }
 
-// Ranges left by the last tile-id pass: a non-empty tile holds (~start, end);
-// empty tiles stay (0, 0).
-__global__ void ranges_fixup_kernel(uint2* __restrict__ ranges, int64_t n_tiles) {
-  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < n_tiles;
-       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const uint2 r = ranges[t];
-    if (r.y) ranges[t].x = ~r.x;
+// 2c. Super-tile ranges and the chunk table (one CTA): restores the starts
+//     the last super-tile pass left complemented (with no pass, the one
+//     super-tile holds the whole list), turns each super-tile's length into
+//     chunks of kChunk records (chunk_base: exclusive offsets, chunk_base
+//     [n_super] the total) and lists the super-tile of every chunk.
+constexpr int kChunkTableThreads = 1024;
+
+__global__ void __launch_bounds__(kChunkTableThreads) super_chunks_kernel(
+    uint2* __restrict__ sranges, int32_t n_super, int passes, const int64_t* n_super_total, int64_t capacity,
+    uint32_t* __restrict__ chunk_base, uint32_t* __restrict__ chunk_super) {
+  __shared__ uint32_t s_w[kChunkTableThreads / 32];
+  __shared__ uint32_t s_run;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_run = 0;
+  __syncthreads();
+  for (int s0 = 0; s0 < n_super; s0 += kChunkTableThreads) {
+    const int s = s0 + tid;
+    uint32_t nc = 0;
+    if (s < n_super) {
+      uint2 r = sranges[s];
+      if (passes == 0) {
+        const int64_t n = *n_super_total < capacity ? *n_super_total : capacity;
+        r = make_uint2(0u, static_cast<uint32_t>(n));
+        sranges[s] = r;
+      } else if (r.y) {
+        r.x = ~r.x;
+        sranges[s] = r;
+      }
+      nc = (r.y - r.x + kChunk - 1) / kChunk;
+    }
+    uint32_t v = nc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t nb = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += nb;
+    }
+    if (lane == 31) s_w[warp] = v;
+    __syncthreads();
+    uint32_t add = s_run;
+    for (int w = 0; w < warp; ++w) add += s_w[w];
+    if (s < n_super) chunk_base[s] = add + v - nc;
+    __syncthreads();
+    if (tid == kChunkTableThreads - 1) s_run = add + v;
+    __syncthreads();
+  }
+  if (tid == 0) chunk_base[n_super] = s_run;
+  __syncthreads();
+  for (int s = tid; s < n_super; s += kChunkTableThreads) {
+    const uint32_t c0 = chunk_base[s], c1 = chunk_base[s + 1];
+    for (uint32_t c = c0; c < c1; ++c) chunk_super[c] = static_cast<uint32_t>(s);
+  }
+}
+
+// A chunk of a super-tile's list as a CTA sees it: its records, one per
+// thread, and each record's coverage of the super-tile's 64 tiles.
+struct ChunkArgs {
+  const uint32_t* svals;        // super-tile lists (records), depth order within each
+  const uint2* sranges;         // [n_super] [start, end) in svals
+  const uint32_t* chunk_base;   // [n_super + 1]
+  const uint32_t* chunk_super;  // [chunks] super-tile of each chunk
+  const short4* rects;
+  uint32_t* chunk_cnt;          // [chunks][64]: tile counts, then their exclusive prefix within the super-tile
+  const uint2* ranges;          // [n_tiles] tile ranges (scatter)
+  uint32_t* vals;               // [capacity] output (scatter)
+  uint64_t capacity;
+};
+
+struct ChunkView {
+  uint32_t s, sx, sy;  // super-tile and its position in its view's super grid
+  int v;               // view
+  uint32_t first, len;  // records [first, first + len) of svals
+};
+
+__device__ __forceinline__ ChunkView chunk_view(const ChunkArgs& a, const Layout& L, const SuperLayout& S, uint32_t c) {
+  ChunkView cv;
+  cv.s = a.chunk_super[c];
+  cv.v = view_of_super(S, L.V, cv.s);
+  const uint32_t local = cv.s - S.sbase[cv.v];
+  const uint32_t stx = static_cast<uint32_t>(S.stx[cv.v]);
+  cv.sy = local / stx;
+  cv.sx = local - cv.sy * stx;
+  const uint2 r = a.sranges[cv.s];
+  cv.first = r.x + (c - a.chunk_base[cv.s]) * kChunk;
+  cv.len = min(static_cast<uint32_t>(kChunk), r.y - cv.first);
+  return cv;
+}
+
+// Bit ly * 8 + lx: the record's rectangle covers local tile (lx, ly).
+__device__ __forceinline__ uint64_t coverage_mask(short4 rc, const ChunkView& cv) {
+  const int ox = static_cast<int>(cv.sx) << kSuperLog, oy = static_cast<int>(cv.sy) << kSuperLog;
+  const int lx0 = max(rc.x - ox, 0), lx1 = min(rc.z - ox, kSuperDim);
+  const int ly0 = max(rc.y - oy, 0), ly1 = min(rc.w - oy, kSuperDim);
+  if (lx0 >= lx1 || ly0 >= ly1) return 0ull;
+  const uint64_t row = ((1ull << (lx1 - lx0)) - 1ull) << lx0;  // < 256
+  // one byte per covered row: the multiplication places copies without carries
+  const uint64_t rows = (0x0101010101010101ull >> (8 * (kSuperDim - (ly1 - ly0)))) << (8 * ly0);
+  return row * rows;
+}
+
+// Global tile id of local tile t of the chunk's super-tile, or -1 if it lies
+// beyond the view's tile grid (a partial super-tile at the right or bottom).
+__device__ __forceinline__ int64_t tile_of(const Layout& L, const ChunkView& cv, int t) {
+  const int tx = (static_cast<int>(cv.sx) << kSuperLog) + (t & (kSuperDim - 1));
+  const int ty = (static_cast<int>(cv.sy) << kSuperLog) + (t >> kSuperLog);
+  if (tx >= L.ntx[cv.v] || ty >= L.nty[cv.v]) return -1;
+  return static_cast<int64_t>(L.tile_base[cv.v]) + static_cast<int64_t>(ty) * L.ntx[cv.v] + tx;
+}
+
+// 32 x 32 bit transpose across a warp: on entry lane l holds row l, on exit
+// lane l holds column l (bit i of the result = bit l of lane i's row). Stage
+// j swaps bit j of the row index (the lane) with bit j of the column index
+// (the bit position); the five swaps together exchange the two indices.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t masks[5] = {0x55555555u, 0x33333333u, 0x0f0f0f0fu, 0x00ff00ffu, 0x0000ffffu};
+#pragma unroll
+  for (int k = 4; k >= 0; --k) {
+    const int j = 1 << k;
+    const uint32_t m = masks[k];  // bit positions whose bit j is 0
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+    x = (lane & j) ? ((x & ~m) | ((y & ~m) >> j)) : ((x & m) | ((y & m) << j));
+  }
+  return x;
+}
+
+// For the warp's 32 coverage masks: in lane l, the lanes covering tile l
+// (lo) and tile l + 32 (hi), as 32-bit lane sets.
+__device__ __forceinline__ void warp_tile_lanes(uint64_t m, uint32_t& lo, uint32_t& hi) {
+  lo = warp_transpose32(static_cast<uint32_t>(m));
+  hi = warp_transpose32(static_cast<uint32_t>(m >> 32));
+}
+
+// 2d. Tile counts per chunk.
+__global__ void __launch_bounds__(kChunkThreads) chunk_count_kernel(const ChunkArgs a, const Layout L,
+                                                                     const SuperLayout S) {
+  __shared__ uint32_t s_cnt[kChunkWarps][kSuperTiles];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t n_chunks = a.chunk_base[S.n_super];
+  for (uint32_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+    const ChunkView cv = chunk_view(a, L, S, c);
+    uint64_t m = 0;
+    if (static_cast<uint32_t>(tid) < cv.len) m = coverage_mask(a.rects[a.svals[cv.first + tid]], cv);
+    uint32_t lo, hi;
+    warp_tile_lanes(m, lo, hi);
+    s_cnt[warp][lane] = __popc(lo);
+    s_cnt[warp][lane + 32] = __popc(hi);
+    __syncthreads();
+    if (tid < kSuperTiles) {
+      uint32_t sum = 0;
+#pragma unroll
+      for (int w = 0; w < kChunkWarps; ++w) sum += s_cnt[w][tid];
+      a.chunk_cnt[static_cast<size_t>(c) * kSuperTiles + tid] = sum;
+    }
+    __syncthreads();
+  }
+}
+
+// 2e. Per super-tile (one CTA each): the exclusive prefix of every tile's
+//     counts over the super-tile's chunks (in place) and the tile totals.
+constexpr int kSuperScanThreads = 256;
+constexpr int kSuperScanGroups = kSuperScanThreads / kSuperTiles;
+
+__global__ void __launch_bounds__(kSuperScanThreads) super_scan_kernel(uint32_t* __restrict__ chunk_cnt,
+                                                                       const uint32_t* __restrict__ chunk_base,
+                                                                       const Layout L, const SuperLayout S,
+                                                                       uint32_t* __restrict__ tile_cnt) {
+  __shared__ uint32_t s_part[kSuperScanGroups][kSuperTiles];
+  const uint32_t s = blockIdx.x;
+  const int t = threadIdx.x % kSuperTiles, g = threadIdx.x / kSuperTiles;
+  const uint32_t c0 = chunk_base[s], nc = chunk_base[s + 1] - c0;
+  const uint32_t per = (nc + kSuperScanGroups - 1) / kSuperScanGroups;
+  const uint32_t j0 = min(nc, g * per), j1 = min(nc, j0 + per);
+  uint32_t* col = chunk_cnt + static_cast<size_t>(c0) * kSuperTiles + t;
+  uint32_t sum = 0;
+  for (uint32_t j = j0; j < j1; ++j) sum += col[static_cast<size_t>(j) * kSuperTiles];
+  s_part[g][t] = sum;
+  __syncthreads();
+  uint32_t run = 0, total = 0;
+#pragma unroll
+  for (int h = 0; h < kSuperScanGroups; ++h) {
+    const uint32_t p = s_part[h][t];
+    if (h < g) run += p;
+    total += p;
+  }
+  for (uint32_t j = j0; j < j1; ++j) {
+    const uint32_t x = col[static_cast<size_t>(j) * kSuperTiles];
+    col[static_cast<size_t>(j) * kSuperTiles] = run;
+    run += x;
+  }
+  if (g == 0) {
+    ChunkView cv;
+    cv.s = s;
+    cv.v = view_of_super(S, L.V, s);
+    const uint32_t local = s - S.sbase[cv.v], stx = static_cast<uint32_t>(S.stx[cv.v]);
+    cv.sy = local / stx;
+    cv.sx = local - cv.sy * stx;
+    const int64_t tile = tile_of(L, cv, t);
+    if (tile >= 0) tile_cnt[tile] = total;
+  }
+}
+
+// 2f. Tile ranges: exclusive scan of the tile counts in tile-id order (block
+//     scan with decoupled look-back); flags a capacity overflow. The ranges
+//     are clamped at the capacity, so that even after an overflow (flagged,
+//     results unusable) a rasteriser reading them stays inside `vals`.
+__global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(const uint32_t* __restrict__ tile_cnt,
+                                                                 int64_t n_tiles, ScanState st,
+                                                                 uint2* __restrict__ ranges,
+                                                                 const int64_t* n_isect, int64_t capacity,
+                                                                 int32_t* status) {
+  __shared__ uint32_t s_tile;
+  __shared__ uint64_t s_warp[kScanThreads / 32];
+  __shared__ uint64_t s_prefix;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_tile = atomicAdd(st.ticket, 1u);
+  __syncthreads();
+  const uint32_t t = s_tile;
+  if (t == 0 && tid == 0 && *n_isect > capacity) set_status(status, GS_STATUS_CAPACITY);
+  const int64_t base = static_cast<int64_t>(t) * kScanTile + static_cast<int64_t>(tid) * kScanItems;
+  uint32_t cnt[kScanItems];
+  uint64_t local = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    cnt[i] = base + i < n_tiles ? tile_cnt[base + i] : 0u;
+    local += cnt[i];
+  }
+  uint64_t run = block_scan_lookback(local, t, st, s_warp, &s_prefix, status);
+  const uint64_t cap = static_cast<uint64_t>(capacity);
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    if (base + i < n_tiles) {
+      const uint64_t end = run + cnt[i];
+      ranges[base + i] = make_uint2(static_cast<uint32_t>(run < cap ? run : cap), static_cast<uint32_t>(end < cap ? end : cap));
+    }
+    run += cnt[i];
+  }
+}
+
+// 2g. Scatter. A record's entry in covered tile t goes to (tile start + the
+//     chunk's prefix for t + the warps before it + the lanes below it that
+//     cover t). After the transpose, lane l of a warp holds the lanes that
+//     cover tiles l and l + 32, so it writes those two tiles' entries in lane
+//     order: the work per lane is the entries of two neighbouring tiles,
+//     which vary much less than the tiles per record. The entries are staged
+//     in shared memory tile by tile (the chunk's runs in tile order) and the
+//     CTA then writes each tile's run with consecutive threads on consecutive
+//     positions. A chunk with more entries than the staging holds writes
+//     them directly.
+constexpr int kStage = 4096;
+
+__global__ void __launch_bounds__(kChunkThreads) scatter_kernel(const ChunkArgs a, const Layout L,
+                                                                 const SuperLayout S) {
+  __shared__ uint32_t s_vg[kChunkWarps][32];            // record of each lane
+  __shared__ uint32_t s_pre[kChunkWarps][kSuperTiles];  // counts, then the chunk-local prefix per tile
+  __shared__ uint32_t s_gbase[kSuperTiles];             // global position of the chunk's first entry in t
+  __shared__ uint32_t s_tloc[kSuperTiles + 1];          // start of tile t's run in the staging
+  __shared__ uint32_t s_out[kStage];
+  __shared__ uint8_t s_outt[kStage];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t n_chunks = a.chunk_base[S.n_super];
+  for (uint32_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+    const ChunkView cv = chunk_view(a, L, S, c);
+    uint64_t m = 0;
+    uint32_t vg = 0;
+    if (static_cast<uint32_t>(tid) < cv.len) {
+      vg = a.svals[cv.first + tid];
+      m = coverage_mask(a.rects[vg], cv);
+    }
+    uint32_t lo, hi;
+    warp_tile_lanes(m, lo, hi);
+    s_vg[warp][lane] = vg;
+    s_pre[warp][lane] = __popc(lo);
+    s_pre[warp][lane + 32] = __popc(hi);
+    __syncthreads();
+    uint32_t tot = 0;
+    if (tid < kSuperTiles) {
+      const int64_t tile = tile_of(L, cv, tid);
+      s_gbase[tid] =
+          tile >= 0 ? a.ranges[tile].x + a.chunk_cnt[static_cast<size_t>(c) * kSuperTiles + tid] : 0u;
+#pragma unroll
+      for (int w = 0; w < kChunkWarps; ++w) {
+        const uint32_t x = s_pre[w][tid];
+        s_pre[w][tid] = tot;
+        tot += x;
+      }
+      // staging layout: exclusive scan of the 64 tile totals (warps 0 and 1)
+      uint32_t v = tot;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t nb = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += nb;
+      }
+      s_tloc[tid + 1] = v;  // inclusive within the warp; the second warp adds the first's total below
+    }
+    __syncthreads();
+    if (tid >= 32 && tid < kSuperTiles) s_tloc[tid + 1] += s_tloc[32];
+    if (tid == 0) s_tloc[0] = 0;
+    __syncthreads();
+    const uint32_t total = s_tloc[kSuperTiles];
+    const bool staged = total <= static_cast<uint32_t>(kStage);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int t = lane + 32 * h;
+      uint32_t set = h ? hi : lo;
+      uint32_t k = s_pre[warp][t];
+      if (staged) {
+        uint32_t i = s_tloc[t] + k;
+        while (set) {
+          const int r = __ffs(set) - 1;
+          set &= set - 1;
+          s_out[i] = s_vg[warp][r];
+          s_outt[i] = static_cast<uint8_t>(t);
+          ++i;
+        }
+      } else {
+        const uint64_t g = s_gbase[t];
+        while (set) {
+          const int r = __ffs(set) - 1;
+          set &= set - 1;
+          if (g + k < a.capacity) a.vals[g + k] = s_vg[warp][r];
+          ++k;
+        }
+      }
+    }
+    __syncthreads();
+    if (staged) {
+      for (uint32_t i = tid; i < total; i += kChunkThreads) {
+        const int t = s_outt[i];
+        const uint64_t pos = static_cast<uint64_t>(s_gbase[t]) + (i - s_tloc[t]);
+        if (pos < a.capacity) a.vals[pos] = s_out[i];
+      }
+    }
+    __syncthreads();
   }
 }
 
 // Optional 64-bit keys (tile << 32) | bits(depth) of the sorted list.
-__global__ void keys64_kernel(const uint32_t* __restrict__ tkeys, const uint32_t* __restrict__ vals,
-                              const float* __restrict__ projected, const int64_t* n_total, int64_t capacity,
-                              uint64_t* __restrict__ keys) {
-  int64_t n = *n_total;
-  if (n > capacity) n = capacity;
-  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const uint32_t d = __float_as_uint(projected[static_cast<int64_t>(vals[i]) * kRecordFloats + 6]);
-    keys[i] = (static_cast<uint64_t>(tkeys[i]) << 32) | d;
+__global__ void keys64_kernel(const uint2* __restrict__ ranges, int64_t n_tiles, const uint32_t* __restrict__ vals,
+                              const float* __restrict__ projected, const uint32_t* __restrict__ depth_keys,
+                              int64_t capacity, uint64_t* __restrict__ keys) {
+  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const uint2 r = ranges[t];
+    for (int64_t p = static_cast<int64_t>(r.x) + threadIdx.x; p < r.y && p < capacity; p += blockDim.x) {
+      const uint32_t vg = vals[p];
+      const uint32_t d =
+          depth_keys ? depth_keys[vg] : __float_as_uint(projected[static_cast<int64_t>(vg) * kRecordFloats + 6]);
+      keys[p] = (static_cast<uint64_t>(t) << 32) | d;
+    }
   }
 }
 
@@ -810,19 +1156,24 @@ __global__ void keys64_kernel(const uint32_t* __restrict__ tkeys, const uint32_t
 // ---------------------------------------------------------------------------
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-int tile_passes_for(int64_t n_tiles) {
+// Digit passes (8 bits each) that sort keys below n_keys.
+int passes_for(int64_t n_keys) {
   int bits = 0;
-  while ((int64_t(1) << bits) < n_tiles) ++bits;
+  while ((int64_t(1) << bits) < n_keys) ++bits;
   return (bits + 7) / 8;
 }
 
+// Super-tile ids never exceed the tile count (a super-tile holds at least one
+// tile), so the super-tile buffers are sized from n_tiles.
 struct WsLayout {
-  size_t dkeys0, dvals0, dkeys1, dvals1, tkeys0, tkeys1, tvals_alt;
-  size_t zero_begin, scan1, scan2, hist_d, hist_t, tickets, n_visible, lb_depth, lb_tile;
+  size_t dkeys0, dvals0, dkeys1, dvals1, skeys0, skeys1, svals0, svals1;
+  size_t chunk_cnt, chunk_super, chunk_base, tile_cnt;
+  size_t zero_begin, scan1, scan_s, scan_t, hist_d, hist_s, tickets, n_visible, n_super_total, sranges, lb_depth,
+      lb_super;
   size_t part_scan, part_hist, part_tickets, part_n, part_lb, zero_end, total;
-  int64_t n_scan_tiles, n_emit_tiles, n_depth_tiles, n_tile_tiles;
+  int64_t n_scan_tiles, n_emit_tiles, n_depth_tiles, n_super_sort_tiles, n_tile_scan_tiles, max_chunks;
   int64_t part_stride, part_scan_tiles, part_sort_tiles;
-  int tile_passes;
+  int super_passes;
 };
 
 constexpr int kPartTickets = 8;  // per partition: compaction + 4 depth passes
@@ -835,30 +1186,43 @@ WsLayout ws_layout(int64_t N, int32_t V, int64_t capacity, int64_t n_tiles, int 
   const int64_t depth_slots = P > 1 ? w.part_stride * P : VN;
   const size_t cap = static_cast<size_t>(capacity > 0 ? capacity : 1);
   const size_t ds = static_cast<size_t>(depth_slots > 0 ? depth_slots : 1);
-  w.tile_passes = tile_passes_for(n_tiles);
+  const size_t nt = static_cast<size_t>(n_tiles > 0 ? n_tiles : 1);
+  w.super_passes = passes_for(n_tiles);
   w.n_scan_tiles = (VN + kScanTile - 1) / kScanTile;
+  w.n_emit_tiles = (VN + kEmitTile - 1) / kEmitTile;
   w.n_depth_tiles = (VN + kSortTile - 1) / kSortTile;
-  w.n_tile_tiles = (capacity + kSortTile - 1) / kSortTile;
+  w.n_super_sort_tiles = (capacity + kSortTile - 1) / kSortTile;
+  w.n_tile_scan_tiles = (n_tiles + kScanTile - 1) / kScanTile;
+  w.max_chunks = static_cast<int64_t>((cap + kChunk - 1) / kChunk + nt);
   w.part_scan_tiles = (w.part_stride + kScanTile - 1) / kScanTile;
   w.part_sort_tiles = (w.part_stride + kSortTile - 1) / kSortTile;
+  const size_t mc = static_cast<size_t>(w.max_chunks);
   size_t o = 0;
   w.dkeys0 = o; o = align256(o + 4 * ds);
   w.dvals0 = o; o = align256(o + 4 * ds);
   w.dkeys1 = o; o = align256(o + 4 * ds);
   w.dvals1 = o; o = align256(o + 4 * ds);
-  w.tkeys0 = o; o = align256(o + 4 * cap);
-  w.tkeys1 = o; o = align256(o + 4 * cap);
-  w.tvals_alt = o; o = align256(o + 4 * cap);
+  w.skeys0 = o; o = align256(o + 4 * cap);
+  w.skeys1 = o; o = align256(o + 4 * cap);
+  w.svals0 = o; o = align256(o + 4 * cap);
+  w.svals1 = o; o = align256(o + 4 * cap);
+  w.chunk_cnt = o; o = align256(o + 4 * kSuperTiles * mc);
+  w.chunk_super = o; o = align256(o + 4 * mc);
+  w.chunk_base = o; o = align256(o + 4 * (nt + 1));
+  w.tile_cnt = o; o = align256(o + 4 * nt);
   w.zero_begin = o;
   w.scan1 = o; o = align256(o + 8 * static_cast<size_t>(w.n_scan_tiles + 1));
-  w.n_emit_tiles = (VN + kEmitTile - 1) / kEmitTile;
-  w.scan2 = o; o = align256(o + 8 * static_cast<size_t>(w.n_emit_tiles + 1));
+  w.scan_s = o; o = align256(o + 8 * static_cast<size_t>(w.n_emit_tiles + 1));
+  w.scan_t = o; o = align256(o + 8 * static_cast<size_t>(w.n_tile_scan_tiles + 1));
   w.hist_d = o; o = align256(o + 4 * kDepthPasses * kRadix);
-  w.hist_t = o; o = align256(o + 4 * kMaxTilePasses * kRadix);
+  w.hist_s = o; o = align256(o + 4 * kMaxSuperPasses * kRadix);
   w.tickets = o; o = align256(o + 4 * 16);
   w.n_visible = o; o = align256(o + 8);
+  w.n_super_total = o; o = align256(o + 8);
+  w.sranges = o; o = align256(o + 8 * nt);
   w.lb_depth = o; o = align256(o + 8 * kRadix * kDepthPasses * static_cast<size_t>(w.n_depth_tiles + 1));
-  w.lb_tile = o; o = align256(o + 8 * kRadix * static_cast<size_t>(w.tile_passes) * static_cast<size_t>(w.n_tile_tiles + 1));
+  w.lb_super = o;
+  o = align256(o + 8 * kRadix * static_cast<size_t>(w.super_passes) * static_cast<size_t>(w.n_super_sort_tiles + 1));
   const size_t np = static_cast<size_t>(P > 1 ? P : 0);
   w.part_scan = o; o = align256(o + 8 * np * static_cast<size_t>(w.part_scan_tiles + 1));
   w.part_hist = o; o = align256(o + 4 * np * kDepthPasses * kRadix);
@@ -1007,8 +1371,8 @@ int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* 
   const int64_t VN = N * V;
   if (VN == 0) {
     if (cfg->flags & GS_FLAG_TILE_ORDER)
-      tile_order_kernel<<<1, kOrderThreads, 0, stream>>>(reinterpret_cast<uint2*>(tile_ranges), L.n_tiles,
-                                                         tile_ranges + 2 * L.n_tiles, 0);
+      tile_order_kernel<<<1, kOrderThreads, 0, stream>>>(reinterpret_cast<const uint2*>(tile_ranges), L.n_tiles,
+                                                         tile_ranges + 2 * L.n_tiles);
     return cuda_status(cudaGetLastError());
   }
   int64_t sort_grid_cap = 0;
@@ -1089,51 +1453,43 @@ int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* 
     }
     order = dv[src];
   }
-  // 1c + 2a. tile-count offsets in depth order and emission, one kernel; the
-  //     buffers are chosen so that the last tile pass writes the values into
-  //     `vals`
-  ScanState st2{reinterpret_cast<uint64_t*>(ws + w.scan2), tickets + 1};
-  const int TP = w.tile_passes;
-  uint32_t* tk[2] = {u32(w.tkeys0), u32(w.tkeys1)};
-  uint32_t* tv[2];
-  tv[TP & 1] = vals;
-  tv[(TP + 1) & 1] = u32(w.tvals_alt);
-  uint32_t* hist_t = u32(w.hist_t);
-  const int n_sm = sm_count();
-  emit_tiles_kernel<<<static_cast<unsigned>(w.n_emit_tiles), kEmitThreads, 0, stream>>>(
-      order, n_visible, counts, reinterpret_cast<const short4*>(rects), N, L, static_cast<uint64_t>(capacity), TP, st2,
-      capacity > 0 ? tk[0] : nullptr, capacity > 0 ? tv[0] : nullptr, hist_t, n_isect_dev, status_dev);
-  if (capacity == 0) {
-    if (cfg->flags & GS_FLAG_TILE_ORDER)
-      tile_order_kernel<<<1, kOrderThreads, 0, stream>>>(reinterpret_cast<uint2*>(tile_ranges), L.n_tiles,
-                                                         tile_ranges + 2 * L.n_tiles, 0);
-    return cuda_status(cudaGetLastError());
-  }
-  // 2b. stable tile-id passes
-  for (int p = 0; p < TP; ++p) {
+  // 2a. super-tile emission in depth order (and the exact intersection count)
+  const SuperLayout S = make_super_layout(L);
+  const int SP = passes_for(S.n_super);
+  uint32_t* sk[2] = {u32(w.skeys0), u32(w.skeys1)};
+  uint32_t* sv[2] = {u32(w.svals0), u32(w.svals1)};
+  uint32_t* hist_s = u32(w.hist_s);
+  int64_t* n_super_total = reinterpret_cast<int64_t*>(ws + w.n_super_total);
+  uint2* sranges = reinterpret_cast<uint2*>(ws + w.sranges);
+  uint2* ranges = reinterpret_cast<uint2*>(tile_ranges);
+  ScanState st2{reinterpret_cast<uint64_t*>(ws + w.scan_s), tickets + 1};
+  emit_super_kernel<<<static_cast<unsigned>(w.n_emit_tiles), kEmitThreads, 0, stream>>>(
+      order, n_visible, reinterpret_cast<const short4*>(rects), N, L, S, static_cast<uint64_t>(capacity), SP, st2,
+      sk[0], sv[0], hist_s, n_super_total, reinterpret_cast<unsigned long long*>(n_isect_dev), status_dev);
+  // 2b. stable super-tile passes; the last one bounds the super-tile ranges
+  for (int p = 0; p < SP; ++p) {
     PassArgs a;
-    a.keys_in = tk[p & 1]; a.vals_in = tv[p & 1]; a.keys_out = tk[(p + 1) & 1]; a.vals_out = tv[(p + 1) & 1];
+    a.keys_in = sk[p & 1]; a.vals_in = sv[p & 1]; a.keys_out = sk[(p + 1) & 1]; a.vals_out = sv[(p + 1) & 1];
     a.ranges = nullptr; a.n_keys = 0;
-    if (p == TP - 1) {
-      // the last pass bounds the tile ranges itself; it writes the ids only
-      // when the 64-bit keys are asked for
-      a.ranges = reinterpret_cast<uint2*>(tile_ranges);
-      a.n_keys = static_cast<uint32_t>(L.n_tiles);
-      if (!keys) a.keys_out = nullptr;
+    if (p == SP - 1) {
+      a.ranges = sranges;
+      a.n_keys = static_cast<uint32_t>(S.n_super);
+      a.keys_out = nullptr;
     }
-    a.n_total = n_isect_dev; a.cap = capacity; a.shift = 8 * p; a.digit_offsets = hist_t + p * kRadix;
+    a.n_total = n_super_total; a.cap = capacity; a.shift = 8 * p; a.digit_offsets = hist_s + p * kRadix;
     a.scan_digits = 1;  // the counts gathered by the emission
     a.ticket = tickets + 6 + p;
     a.stall_tile = -1;
     a.spin_limit = kSpinLimit;
-    a.lookback = reinterpret_cast<uint64_t*>(ws + w.lb_tile) + static_cast<size_t>(p) * (w.n_tile_tiles + 1) * kRadix;
+    a.lookback = reinterpret_cast<uint64_t*>(ws + w.lb_super) +
+                 static_cast<size_t>(p) * (w.n_super_sort_tiles + 1) * kRadix;
     int bits = 8;
-    if (p == TP - 1) {
+    if (p == SP - 1) {
       bits = 0;
-      while ((int64_t(1) << bits) < L.n_tiles) ++bits;
-      bits -= 8 * (TP - 1);
+      while ((int64_t(1) << bits) < S.n_super) ++bits;
+      bits -= 8 * (SP - 1);
     }
-    const unsigned grid = sort_grid(w.n_tile_tiles);
+    const unsigned grid = sort_grid(w.n_super_sort_tiles);
     switch (bits) {
       case 1: sort_pass_kernel<1><<<grid, kSortThreads, sizeof(SortSmem), stream>>>(a, status_dev); break;
       case 2: sort_pass_kernel<2><<<grid, kSortThreads, sizeof(SortSmem), stream>>>(a, status_dev); break;
@@ -1145,24 +1501,39 @@ int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* 
       default: sort_pass_kernel<8><<<grid, kSortThreads, sizeof(SortSmem), stream>>>(a, status_dev); break;
     }
   }
-  const uint32_t* tkeys_final = tk[TP & 1];
-  // 2c. tile ranges (from the ids themselves when there is no tile pass),
-  //     optional 64-bit keys
-  // (with a tile order the order kernel restores the starts itself)
-  const bool ordered = (cfg->flags & GS_FLAG_TILE_ORDER) != 0;
-  if (TP > 0 && !ordered)
-    ranges_fixup_kernel<<<static_cast<unsigned>((L.n_tiles + 255) / 256), 256, 0, stream>>>(
-        reinterpret_cast<uint2*>(tile_ranges), L.n_tiles);
-  else if (TP == 0)
-    tile_ranges_kernel<<<static_cast<unsigned>(4 * n_sm), 256, 0, stream>>>(
-        tkeys_final, n_isect_dev, capacity, static_cast<uint32_t>(L.n_tiles), reinterpret_cast<uint2*>(tile_ranges),
-        status_dev);
-  if (keys)
-    keys64_kernel<<<static_cast<unsigned>(4 * n_sm), 256, 0, stream>>>(tkeys_final, vals, projected, n_isect_dev,
-                                                                        capacity, keys);
-  if (ordered)
-    tile_order_kernel<<<1, kOrderThreads, 0, stream>>>(reinterpret_cast<uint2*>(tile_ranges), L.n_tiles,
-                                                       tile_ranges + 2 * L.n_tiles, TP > 0 ? 1 : 0);
+  // 2c-2g. chunk table, tile counts per chunk, per super-tile prefixes, tile
+  //        ranges, scatter into `vals`
+  uint32_t* chunk_base = u32(w.chunk_base);
+  uint32_t* chunk_super = u32(w.chunk_super);
+  super_chunks_kernel<<<1, kChunkTableThreads, 0, stream>>>(sranges, S.n_super, SP, n_super_total, capacity, chunk_base,
+                                                           chunk_super);
+  ChunkArgs ca;
+  ca.svals = sv[SP & 1];
+  ca.sranges = sranges;
+  ca.chunk_base = chunk_base;
+  ca.chunk_super = chunk_super;
+  ca.rects = reinterpret_cast<const short4*>(rects);
+  ca.chunk_cnt = u32(w.chunk_cnt);
+  ca.ranges = ranges;
+  ca.vals = vals;
+  ca.capacity = static_cast<uint64_t>(capacity);
+  const int n_sm = sm_count();
+  // persistent grids: every CTA loops over chunks, none waits on another
+  const unsigned chunk_grid = static_cast<unsigned>(
+      w.max_chunks < 8 * static_cast<int64_t>(n_sm) ? (w.max_chunks > 0 ? w.max_chunks : 1) : 8 * n_sm);
+  chunk_count_kernel<<<chunk_grid, kChunkThreads, 0, stream>>>(ca, L, S);
+  super_scan_kernel<<<static_cast<unsigned>(S.n_super), kSuperScanThreads, 0, stream>>>(ca.chunk_cnt, chunk_base, L, S,
+                                                                                        u32(w.tile_cnt));
+  ScanState st3{reinterpret_cast<uint64_t*>(ws + w.scan_t), tickets + 10};
+  tile_scan_kernel<<<static_cast<unsigned>(w.n_tile_scan_tiles), kScanThreads, 0, stream>>>(
+      u32(w.tile_cnt), L.n_tiles, st3, ranges, n_isect_dev, capacity, status_dev);
+  if (capacity > 0) scatter_kernel<<<chunk_grid, kChunkThreads, 0, stream>>>(ca, L, S);
+  // 2h. optional 64-bit keys, tile order
+  if (keys && capacity > 0)
+    keys64_kernel<<<static_cast<unsigned>(4 * n_sm), 256, 0, stream>>>(ranges, L.n_tiles, vals, projected, depth_keys,
+                                                                       capacity, keys);
+  if (cfg->flags & GS_FLAG_TILE_ORDER)
+    tile_order_kernel<<<1, kOrderThreads, 0, stream>>>(ranges, L.n_tiles, tile_ranges + 2 * L.n_tiles);
   return cuda_status(cudaGetLastError());
 }
 

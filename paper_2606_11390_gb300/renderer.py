@@ -441,18 +441,22 @@ class TrainStep:
 
     @staticmethod
     def _sort_launches(fr: Frame) -> int:
-        """Kernels gs_bin_sort launches: compaction, 4 depth passes, count
-        scan with emission, the tile-id passes (each pass scans its digit
-        counts itself), the ranges fix-up (done by the tile-order kernel when
-        there is one; the ranges kernel when there is no tile pass), the
-        optional 64-bit keys and the tile order."""
+        """Kernels gs_bin_sort launches: compaction, 4 depth passes, the
+        super-tile emission, the super-tile passes (each scans its digit counts
+        itself), the chunk table, the chunk counts, the per-super-tile scan,
+        the tile scan and the scatter, then the optional 64-bit keys and tile
+        order."""
+        tw, th = int(fr.cfg["tile_w"]), int(fr.cfg["tile_h"])
+        n_super = 0
+        for W, H in fr.cams.sizes:
+            ntx, nty = -(-int(W) // tw), -(-int(H) // th)
+            n_super += (-(-ntx // 8)) * (-(-nty // 8))
         bits = 0
-        while (1 << bits) < fr.n_tiles:
+        while (1 << bits) < n_super:
             bits += 1
-        tile_passes = (bits + 7) // 8
+        super_passes = (bits + 7) // 8
         order = 1 if fr.cfg.get("flags", 0) & gs.GS_FLAG_TILE_ORDER else 0
-        ranges = 0 if (tile_passes and order) else 1
-        return 1 + 4 + 1 + tile_passes + ranges + (1 if fr.keep_keys else 0) + order
+        return 1 + 4 + 1 + super_passes + 4 + 1 + (1 if fr.keep_keys else 0) + order
 
     def prepare(self, warmup_checks=2):
         """Sizes the key capacity from an eager run, then (batched mode)

@@ -138,6 +138,32 @@ def test_capacity_overflow_sets_status_and_recovers(oracle):
     np.testing.assert_array_equal(g["keys"], o_bins["keys"])
 
 
+@pytest.mark.parametrize("order", [False, True])
+def test_overflowed_sort_keeps_ranges_inside_the_capacity(oracle, order):
+    """After an overflow the lists are unusable (GS_STATUS_CAPACITY), but a
+    consumer that reads them before checking the status (a captured step's
+    rasteriser) must stay inside `vals`: every range lies in [0, capacity]."""
+    import torch
+
+    from paper_2606_11390_gb300 import _native as gs
+    from paper_2606_11390_gb300 import renderer as R
+
+    s = scenes.random_small(201, N=3000, width=120, height=90, n_views=4, spread=1.5, tile=8)
+    o_proj, o_bins, _ = oracle.forward(s, "f32")
+    N = s["means"].shape[0]
+    params = R.FlatParams(N).load_from(s)
+    cams = R.Cameras(s["cams"], s["sizes"])
+    for cap in (1, 1000, o_bins["n_isect"] // 2):
+        fr = R.Frame(N, cams, s["cfg"], capacity=cap, keep_keys=True, tile_order=order)
+        R.project(params, cams, fr)
+        R.bin_sort(fr)
+        torch.cuda.synchronize()
+        assert fr.read_status() & gs.GS_STATUS_CAPACITY
+        assert int(fr.n_isect.item()) == o_bins["n_isect"]  # the exact total, even when clipped
+        rg = to_np(fr.ranges, np.uint32).reshape(-1, 2)
+        assert (rg[:, 0] <= rg[:, 1]).all() and rg.max() <= cap
+
+
 def test_empty_and_fully_culled(oracle):
     s = scenes.random_small(106, N=50, width=40, height=30)
     s["means"][:, 2] = -3.0
