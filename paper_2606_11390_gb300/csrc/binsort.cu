@@ -804,12 +804,13 @@ __global__ void __launch_bounds__(kEmitThreads) emit_super_kernel(
 //     the last super-tile pass left complemented (with no pass, the one
 //     super-tile holds the whole list), turns each super-tile's length into
 //     chunks of kChunk records (chunk_base: exclusive offsets, chunk_base
-//     [n_super] the total) and lists the super-tile of every chunk.
+//     [n_super] the total) and describes every chunk (first record, length,
+//     super-tile), one warp per super-tile.
 constexpr int kChunkTableThreads = 1024;
 
 __global__ void __launch_bounds__(kChunkTableThreads) super_chunks_kernel(
     uint2* __restrict__ sranges, int32_t n_super, int passes, const int64_t* n_super_total, int64_t capacity,
-    uint32_t* __restrict__ chunk_base, uint32_t* __restrict__ chunk_super) {
+    uint32_t* __restrict__ chunk_base, uint4* __restrict__ chunk_info) {
   __shared__ uint32_t s_w[kChunkTableThreads / 32];
   __shared__ uint32_t s_run;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -847,9 +848,13 @@ __global__ void __launch_bounds__(kChunkTableThreads) super_chunks_kernel(
   }
   if (tid == 0) chunk_base[n_super] = s_run;
   __syncthreads();
-  for (int s = tid; s < n_super; s += kChunkTableThreads) {
-    const uint32_t c0 = chunk_base[s], c1 = chunk_base[s + 1];
-    for (uint32_t c = c0; c < c1; ++c) chunk_super[c] = static_cast<uint32_t>(s);
+  for (int s = warp; s < n_super; s += kChunkTableThreads / 32) {
+    const uint2 r = sranges[s];
+    const uint32_t c0 = chunk_base[s], nc = chunk_base[s + 1] - c0;
+    for (uint32_t j = lane; j < nc; j += 32) {
+      const uint32_t first = r.x + j * kChunk;
+      chunk_info[c0 + j] = make_uint4(first, min(static_cast<uint32_t>(kChunk), r.y - first), static_cast<uint32_t>(s), 0u);
+    }
   }
 }
 
@@ -859,7 +864,7 @@ struct ChunkArgs {
   const uint32_t* svals;        // super-tile lists (records), depth order within each
   const uint2* sranges;         // [n_super] [start, end) in svals
   const uint32_t* chunk_base;   // [n_super + 1]
-  const uint32_t* chunk_super;  // [chunks] super-tile of each chunk
+  const uint4* chunk_info;      // [chunks] first record, length, super-tile
   const short4* rects;
   uint32_t* chunk_cnt;          // [chunks][64]: tile counts, then their exclusive prefix within the super-tile
   const uint2* ranges;          // [n_tiles] tile ranges (scatter)
@@ -875,15 +880,15 @@ struct ChunkView {
 
 __device__ __forceinline__ ChunkView chunk_view(const ChunkArgs& a, const Layout& L, const SuperLayout& S, uint32_t c) {
   ChunkView cv;
-  cv.s = a.chunk_super[c];
+  const uint4 info = a.chunk_info[c];
+  cv.first = info.x;
+  cv.len = info.y;
+  cv.s = info.z;
   cv.v = view_of_super(S, L.V, cv.s);
   const uint32_t local = cv.s - S.sbase[cv.v];
   const uint32_t stx = static_cast<uint32_t>(S.stx[cv.v]);
   cv.sy = local / stx;
   cv.sx = local - cv.sy * stx;
-  const uint2 r = a.sranges[cv.s];
-  cv.first = r.x + (c - a.chunk_base[cv.s]) * kChunk;
-  cv.len = min(static_cast<uint32_t>(kChunk), r.y - cv.first);
   return cv;
 }
 
@@ -1041,27 +1046,33 @@ __global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(const uint32_t*
 // 2g. Scatter. A record's entry in covered tile t goes to (tile start + the
 //     chunk's prefix for t + the warps before it + the lanes below it that
 //     cover t). After the transpose, lane l of a warp holds the lanes that
-//     cover tiles l and l + 32, so it writes those two tiles' entries in lane
-//     order: the work per lane is the entries of two neighbouring tiles,
-//     which vary much less than the tiles per record. The entries are staged
-//     in shared memory tile by tile (the chunk's runs in tile order) and the
-//     CTA then writes each tile's run with consecutive threads on consecutive
-//     positions. A chunk with more entries than the staging holds writes
-//     them directly.
-constexpr int kStage = 4096;
+//     cover tiles l and l + 32, so it produces those two tiles' entries in
+//     lane order: the work per lane is the entries of two neighbouring tiles,
+//     which vary much less than the tiles per record. Each entry is staged
+//     in shared memory as 16 bits (tile, record within the chunk), tile by
+//     tile (the chunk's runs in tile order), and the CTA then writes the runs
+//     with consecutive threads on consecutive positions. A chunk with more
+//     entries than the staging holds (at 4K the largest has 5963) writes them
+//     directly.
+constexpr int kStage = 8192;
 
 __global__ void __launch_bounds__(kChunkThreads) scatter_kernel(const ChunkArgs a, const Layout L,
                                                                  const SuperLayout S) {
-  __shared__ uint32_t s_vg[kChunkWarps][32];            // record of each lane
+  __shared__ uint32_t s_vg[kChunkThreads];              // record of each thread
   __shared__ uint32_t s_pre[kChunkWarps][kSuperTiles];  // counts, then the chunk-local prefix per tile
   __shared__ uint32_t s_gbase[kSuperTiles];             // global position of the chunk's first entry in t
   __shared__ uint32_t s_tloc[kSuperTiles + 1];          // start of tile t's run in the staging
-  __shared__ uint32_t s_out[kStage];
-  __shared__ uint8_t s_outt[kStage];
+  __shared__ uint16_t s_stage[kStage];                  // tile << 8 | record within the chunk
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t n_chunks = a.chunk_base[S.n_super];
   for (uint32_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
     const ChunkView cv = chunk_view(a, L, S, c);
+    // the tile bases do not depend on the records: their loads go out first
+    uint32_t gb = 0;
+    if (tid < kSuperTiles) {
+      const int64_t tile = tile_of(L, cv, tid);
+      if (tile >= 0) gb = a.ranges[tile].x + a.chunk_cnt[static_cast<size_t>(c) * kSuperTiles + tid];
+    }
     uint64_t m = 0;
     uint32_t vg = 0;
     if (static_cast<uint32_t>(tid) < cv.len) {
@@ -1070,15 +1081,13 @@ __global__ void __launch_bounds__(kChunkThreads) scatter_kernel(const ChunkArgs 
     }
     uint32_t lo, hi;
     warp_tile_lanes(m, lo, hi);
-    s_vg[warp][lane] = vg;
+    s_vg[tid] = vg;
     s_pre[warp][lane] = __popc(lo);
     s_pre[warp][lane + 32] = __popc(hi);
     __syncthreads();
-    uint32_t tot = 0;
     if (tid < kSuperTiles) {
-      const int64_t tile = tile_of(L, cv, tid);
-      s_gbase[tid] =
-          tile >= 0 ? a.ranges[tile].x + a.chunk_cnt[static_cast<size_t>(c) * kSuperTiles + tid] : 0u;
+      s_gbase[tid] = gb;
+      uint32_t tot = 0;
 #pragma unroll
       for (int w = 0; w < kChunkWarps; ++w) {
         const uint32_t x = s_pre[w][tid];
@@ -1100,36 +1109,36 @@ __global__ void __launch_bounds__(kChunkThreads) scatter_kernel(const ChunkArgs 
     __syncthreads();
     const uint32_t total = s_tloc[kSuperTiles];
     const bool staged = total <= static_cast<uint32_t>(kStage);
+    const uint32_t wbase = static_cast<uint32_t>(warp) * 32u;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int t = lane + 32 * h;
       uint32_t set = h ? hi : lo;
-      uint32_t k = s_pre[warp][t];
+      const uint32_t k0 = s_pre[warp][t];
       if (staged) {
-        uint32_t i = s_tloc[t] + k;
+        uint32_t i = s_tloc[t] + k0;
+        const uint32_t tag = static_cast<uint32_t>(t) << 8;
         while (set) {
-          const int r = __ffs(set) - 1;
+          const uint32_t r = static_cast<uint32_t>(__ffs(set) - 1);
           set &= set - 1;
-          s_out[i] = s_vg[warp][r];
-          s_outt[i] = static_cast<uint8_t>(t);
-          ++i;
+          s_stage[i++] = static_cast<uint16_t>(tag | (wbase + r));
         }
       } else {
-        const uint64_t g = s_gbase[t];
-        while (set) {
-          const int r = __ffs(set) - 1;
+        const uint32_t g = s_gbase[t] + k0;
+        for (uint32_t k = 0; set; ++k) {
+          const uint32_t r = static_cast<uint32_t>(__ffs(set) - 1);
           set &= set - 1;
-          if (g + k < a.capacity) a.vals[g + k] = s_vg[warp][r];
-          ++k;
+          if (static_cast<uint64_t>(g) + k < a.capacity) a.vals[g + k] = s_vg[wbase + r];
         }
       }
     }
     __syncthreads();
     if (staged) {
       for (uint32_t i = tid; i < total; i += kChunkThreads) {
-        const int t = s_outt[i];
+        const uint32_t e = s_stage[i];
+        const uint32_t t = e >> 8;
         const uint64_t pos = static_cast<uint64_t>(s_gbase[t]) + (i - s_tloc[t]);
-        if (pos < a.capacity) a.vals[pos] = s_out[i];
+        if (pos < a.capacity) a.vals[pos] = s_vg[e & 0xffu];
       }
     }
     __syncthreads();
@@ -1167,7 +1176,7 @@ int passes_for(int64_t n_keys) {
 // tile), so the super-tile buffers are sized from n_tiles.
 struct WsLayout {
   size_t dkeys0, dvals0, dkeys1, dvals1, skeys0, skeys1, svals0, svals1;
-  size_t chunk_cnt, chunk_super, chunk_base, tile_cnt;
+  size_t chunk_cnt, chunk_info, chunk_base, tile_cnt;
   size_t zero_begin, scan1, scan_s, scan_t, hist_d, hist_s, tickets, n_visible, n_super_total, sranges, lb_depth,
       lb_super;
   size_t part_scan, part_hist, part_tickets, part_n, part_lb, zero_end, total;
@@ -1207,7 +1216,7 @@ WsLayout ws_layout(int64_t N, int32_t V, int64_t capacity, int64_t n_tiles, int 
   w.svals0 = o; o = align256(o + 4 * cap);
   w.svals1 = o; o = align256(o + 4 * cap);
   w.chunk_cnt = o; o = align256(o + 4 * kSuperTiles * mc);
-  w.chunk_super = o; o = align256(o + 4 * mc);
+  w.chunk_info = o; o = align256(o + 16 * mc);
   w.chunk_base = o; o = align256(o + 4 * (nt + 1));
   w.tile_cnt = o; o = align256(o + 4 * nt);
   w.zero_begin = o;
@@ -1504,14 +1513,14 @@ int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* 
   // 2c-2g. chunk table, tile counts per chunk, per super-tile prefixes, tile
   //        ranges, scatter into `vals`
   uint32_t* chunk_base = u32(w.chunk_base);
-  uint32_t* chunk_super = u32(w.chunk_super);
+  uint4* chunk_info = reinterpret_cast<uint4*>(ws + w.chunk_info);
   super_chunks_kernel<<<1, kChunkTableThreads, 0, stream>>>(sranges, S.n_super, SP, n_super_total, capacity, chunk_base,
-                                                           chunk_super);
+                                                           chunk_info);
   ChunkArgs ca;
   ca.svals = sv[SP & 1];
   ca.sranges = sranges;
   ca.chunk_base = chunk_base;
-  ca.chunk_super = chunk_super;
+  ca.chunk_info = chunk_info;
   ca.rects = reinterpret_cast<const short4*>(rects);
   ca.chunk_cnt = u32(w.chunk_cnt);
   ca.ranges = ranges;
