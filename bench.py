@@ -635,7 +635,11 @@ def roofline_for(stage, ms, step, peaks, src, workload, pc=None):
     elif stage == "project_bwd":
         bytes_ = N * 236 * 2 + V * N * 40
     elif stage == "bin_sort":
-        bytes_ = V * N * 8 + I * (8 + 16 * 2 + 4)
+        # the stage's minimal data movement: per record its depth key and tile
+        # count read, per visible record its rectangle, per intersection its
+        # 4-byte list entry written, per tile its range
+        n_vis = int((step.frames[0].counts != 0).sum().item())
+        bytes_ = V * N * 8 + n_vis * 8 + I * 4 + int(step.frames[0].n_tiles) * 8
     else:
         bytes_ = P * 3 * 4 * 3
     achieved = bytes_ / (ms * 1e-3) / 1e9
