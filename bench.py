@@ -46,7 +46,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the per-view comparison leg")
-    ap.add_argument("--tile", default=None, help="WxH tile override, e.g. 16x16")
+    ap.add_argument("--tile", default=None, help="WxH tile override, e.g. 16x16 (skips the autotuner)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="use the workload's tile shape and the default rasteriser configuration instead of the "
+                         "autotuner's choice")
     ap.add_argument("--gaussians", type=int, default=None, help="override the workload's Gaussian count")
     ap.add_argument("--raster-px", type=int, default=4, choices=[2, 4], help="pixels per thread in the rasteriser")
     ap.add_argument("--loss", default="l1l2", choices=["l1l2", "ssim"],
@@ -461,9 +464,20 @@ def main():
     if args.raster_px == 2:
         scene["cfg"] = dict(scene["cfg"], flags=gs.GS_FLAG_RASTER_2PX)
     tile = tuple(int(x) for x in args.tile.split("x")) if args.tile else (scene["cfg"]["tile_w"], scene["cfg"]["tile_h"])
+    raster_kw = {"tile": tile}
+    tune = None
+    if not args.no_tune and not args.tile and args.raster_px == 4:
+        # the rasteriser configuration (tile shape, pixels per thread, splats
+        # per batch) from the autotuner, timed on this GPU for this workload
+        from paper_2606_11390_gb300 import autotune
+
+        best, tune_ms = autotune.best_config(scene, steps=5, mode=args.mode)
+        raster_kw = autotune.step_kwargs(best)
+        tile = raster_kw["tile"]
+        tune = {"choice": autotune.name(best), "ms": {k: round(v, 4) for k, v in tune_ms.items()}}
     adam = scene["name"] == "street"  # the street workload's step includes the fused Adam update
-    step = R.TrainStep(scene, mode=args.mode, graph=False if args.no_graph else None, tile=tile, adam=adam,
-                       loss=args.loss).prepare()
+    step = R.TrainStep(scene, mode=args.mode, graph=False if args.no_graph else None, adam=adam, loss=args.loss,
+                       **raster_kw).prepare()
     P = step.cams.n_pixels
     launches = step.launches_per_step
     stream = torch.cuda.current_stream()
@@ -514,7 +528,7 @@ def main():
             if not args.no_partitioned and scene["name"] != "street":
                 extra["partitioned_sort"] = partitioned_sort_measure(step)
             if not args.no_morton and scene["name"] != "street":
-                extra["morton"] = morton_measure(step, scene, args, tile, ms)
+                extra["morton"] = morton_measure(step, scene, args, raster_kw, ms)
         if not args.no_e2e:
             extra["e2e"] = e2e_measure(step, args, dist.world)
             extra["e2e_params_streamed"] = e2e_measure(step, args, dist.world, stream_params=True)
@@ -531,6 +545,9 @@ def main():
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": workload_config(scene, args, tile), "clocks": clk,
                 "gpu_launches": launches * args.steps}
+        if tune is not None:
+            line["config"]["raster"] = tune["choice"]
+            line["autotune"] = tune
         line.update(extra)
         print(json.dumps(line), flush=True)
     dist.close()
@@ -795,7 +812,7 @@ def densify_measure(step, peaks, src, iters=20):
                                                   "peak_source": f"{src} hbm_gbs"}}
 
 
-def morton_measure(step, scene, args, tile, ms_input_order):
+def morton_measure(step, scene, args, raster_kw, ms_input_order):
     """The same step after reordering the Gaussians along a 3D Morton curve
     (gs_morton_order + gs_gather_rows, timed separately), as the paper does at
     densification; the input order of the synthetic scenes is random."""
@@ -816,7 +833,7 @@ def morton_measure(step, scene, args, tile, ms_input_order):
     if status.item() != 0:
         raise RuntimeError(f"morton status {status.item()}")
     order_ms, gather_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
-    st = R.TrainStep(scene, mode=args.mode, graph=False if args.no_graph else None, tile=tile, params=out,
+    st = R.TrainStep(scene, mode=args.mode, graph=False if args.no_graph else None, params=out, **raster_kw,
                      loss=args.loss).prepare()
     for _ in range(args.warmup):
         st.run()
