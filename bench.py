@@ -272,7 +272,7 @@ def stage_times(step, iters=5):
             step.enqueue_loss()
         ev[4].record(stream)
         gs.gs_rasterize_bwd_pixels(fr.projected, fr.vals, fr.tile_ranges, cams.sizes, fr.cfg, fr.N, fr.final_T,
-                                   fr.last, step.dL_dimage, fr.d_projected)
+                                   fr.last, step.dL_dimage, fr.d_projected, cull_masks=fr.cull)
         ev[5].record(stream)
         gs.gs_project_bwd(p["means"], p["log_scales"], p["quats"], p["opacity_logits"], p["sh"], cams.dev,
                           cams.sizes, fr.cfg, fr.counts, fr.d_projected, gr["means"], gr["log_scales"],

@@ -279,10 +279,19 @@ GS_API int gs_bin_sort_static(const float* projected, const int16_t* rects, cons
  * out (device): image [P][3], final_T [P] (transmittance after the last
  *               composited entry), last [P] uint32 (1 + position, within its
  *               tile's range, of the last composited entry; 0 if none).
+ * cull_masks (device, optional, [capacity] uint16 like vals, 2-byte aligned;
+ *               NULL for none): for every list entry the kernel stages, the
+ *               warps of its tile whose pixel block the splat can reach,
+ *               tagged with the warp layout (tile shape, pixels per thread),
+ *               for gs_rasterize_bwd / gs_rasterize_bwd_pixels on the same
+ *               lists to reuse instead of recomputing; other entries are left
+ *               as they were. Not written for 32x32 tiles at 2 pixels per
+ *               thread. A performance aid only: the backward's results are
+ *               the same with or without it.
  * Errors: GS_ERR_ARG, GS_ERR_UNSUPPORTED, GS_ERR_CUDA. */
 GS_API int gs_rasterize_fwd(const float* projected, const uint32_t* vals, const uint32_t* tile_ranges, const int32_t* sizes,
                      int32_t V, const gs_config* cfg, float* image, float* final_T, uint32_t* last,
-                     gs_stream_t stream);
+                     uint16_t* cull_masks, gs_stream_t stream);
 
 /* gs_rasterize_fwd_counted - gs_rasterize_fwd (same outputs) that also counts
  * the pixel-splat pairs of its work, for measuring the rasteriser against its
@@ -300,7 +309,8 @@ GS_API int gs_rasterize_fwd(const float* projected, const uint32_t* vals, const 
  * pair_counts_dev. */
 GS_API int gs_rasterize_fwd_counted(const float* projected, const uint32_t* vals, const uint32_t* tile_ranges,
                                     const int32_t* sizes, int32_t V, const gs_config* cfg, float* image,
-                                    float* final_T, uint32_t* last, uint64_t* pair_counts_dev, gs_stream_t stream);
+                                    float* final_T, uint32_t* last, uint64_t* pair_counts_dev, uint16_t* cull_masks,
+                                    gs_stream_t stream);
 
 /* gs_rasterize_fwd_l1l2 - gs_rasterize_fwd with the L1 + L2 image loss of
  * gs_image_loss computed in the same kernel, as each pixel's colour is final
@@ -316,12 +326,13 @@ GS_API int gs_rasterize_fwd_counted(const float* projected, const uint32_t* vals
  *               = (w_l1 sign(r) + 2 w_l2 r) / n_values, bit-identical to
  *               gs_image_loss's; loss_dev [1] double += this call's sum of
  *               (w_l1 |r| + w_l2 r^2) / n_values (atomic adds: the last bits
- *               depend on their order).
+ *               depend on their order); cull_masks as gs_rasterize_fwd.
  * Errors: GS_ERR_ARG (also n_values < 3 P), GS_ERR_UNSUPPORTED, GS_ERR_CUDA. */
 GS_API int gs_rasterize_fwd_l1l2(const float* projected, const uint32_t* vals, const uint32_t* tile_ranges,
                                  const int32_t* sizes, int32_t V, const gs_config* cfg, float* image, float* final_T,
                                  uint32_t* last, const float* target, int64_t n_values, float w_l1, float w_l2,
-                                 int32_t accumulate, float* dL_dimage, double* loss_dev, gs_stream_t stream);
+                                 int32_t accumulate, float* dL_dimage, double* loss_dev, uint16_t* cull_masks,
+                                 gs_stream_t stream);
 
 /* gs_rasterize_bwd - backward of rasterisation, projection and SH colour.
  * Paper: §4, where the backward pass keeps the forward pass's partitioning
@@ -347,13 +358,16 @@ GS_API int gs_rasterize_fwd_l1l2(const float* projected, const uint32_t* vals, c
  *               d_opacity_logits [N], d_sh [N][16][3]: overwritten, or added
  *               to when cfg->flags has GS_FLAG_ACCUMULATE_GRADS; d_sh
  *               coefficients beyond the degree receive 0.
+ * in  (device, optional): cull_masks written by the forward on the same lists
+ *               (NULL: the backward computes the cull itself; an entry whose
+ *               tag does not match this call's warp layout is recomputed).
  * Errors: GS_ERR_ARG, GS_ERR_UNSUPPORTED, GS_ERR_CUDA. */
 GS_API int gs_rasterize_bwd(const float* means, const float* log_scales, const float* quats, const float* opacity_logits,
                      const float* sh, int64_t N, const gs_camera* cams_dev, const int32_t* sizes, int32_t V,
                      const gs_config* cfg, const float* projected, const uint32_t* counts, const uint32_t* vals,
                      const uint32_t* tile_ranges, const float* final_T, const uint32_t* last, const float* dL_dimage,
                      float* d_projected, float* d_means, float* d_log_scales, float* d_quats, float* d_opacity_logits,
-                     float* d_sh, int32_t* status_dev, gs_stream_t stream);
+                     float* d_sh, const uint16_t* cull_masks, int32_t* status_dev, gs_stream_t stream);
 
 /* gs_rasterize_bwd_pixels - first half of gs_rasterize_bwd: the per-pixel
  * reverse compositing only. Zeroes d_projected [V*N][9] (device) and
@@ -363,7 +377,7 @@ GS_API int gs_rasterize_bwd(const float* means, const float* log_scales, const f
 GS_API int gs_rasterize_bwd_pixels(const float* projected, const uint32_t* vals, const uint32_t* tile_ranges,
                                    const int32_t* sizes, int32_t V, const gs_config* cfg, int64_t N,
                                    const float* final_T, const uint32_t* last, const float* dL_dimage,
-                                   float* d_projected, gs_stream_t stream);
+                                   float* d_projected, const uint16_t* cull_masks, gs_stream_t stream);
 
 /* gs_rasterize_bwd_pixels_counted - gs_rasterize_bwd_pixels (same outputs)
  * that also counts the pixel-splat pairs of its work (paper §4, the backward
@@ -379,7 +393,8 @@ GS_API int gs_rasterize_bwd_pixels_counted(const float* projected, const uint32_
                                            const uint32_t* tile_ranges, const int32_t* sizes, int32_t V,
                                            const gs_config* cfg, int64_t N, const float* final_T,
                                            const uint32_t* last, const float* dL_dimage, float* d_projected,
-                                           uint64_t* pair_counts_dev, gs_stream_t stream);
+                                           uint64_t* pair_counts_dev, const uint16_t* cull_masks,
+                                           gs_stream_t stream);
 
 /* gs_project_bwd - second half of gs_rasterize_bwd: chains d_projected
  * (from gs_rasterize_bwd_pixels) through SH colour and projection to the

@@ -66,13 +66,14 @@ _SIGNATURES = {
     "gs_bin_sort": ([_VP, _VP, _VP, _VP, _I64, _VP, _I32, _VP, _VP, _VP, _I64, _VP, _VP, _VP, ctypes.c_size_t, _VP,
                      _VP], ctypes.c_int),
     "gs_bin_sort_static": ([_VP, _VP, _VP, _I64, _VP, _I32, _VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP], ctypes.c_int),
-    "gs_rasterize_fwd": ([_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
-    "gs_rasterize_fwd_counted": ([_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "gs_rasterize_fwd": ([_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "gs_rasterize_fwd_counted": ([_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "gs_rasterize_fwd_l1l2": ([_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP, _I64, _F32, _F32, _I32, _VP, _VP,
-                               _VP], ctypes.c_int),
-    "gs_rasterize_bwd": ([_VP] * 5 + [_I64, _VP, _VP, _I32, _VP] + [_VP] * 7 + [_VP] * 6 + [_VP, _VP], ctypes.c_int),
-    "gs_rasterize_bwd_pixels": ([_VP, _VP, _VP, _VP, _I32, _VP, _I64, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
-    "gs_rasterize_bwd_pixels_counted": ([_VP, _VP, _VP, _VP, _I32, _VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP],
+                               _VP, _VP], ctypes.c_int),
+    "gs_rasterize_bwd": ([_VP] * 5 + [_I64, _VP, _VP, _I32, _VP] + [_VP] * 7 + [_VP] * 6 + [_VP, _VP, _VP],
+                         ctypes.c_int),
+    "gs_rasterize_bwd_pixels": ([_VP, _VP, _VP, _VP, _I32, _VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "gs_rasterize_bwd_pixels_counted": ([_VP, _VP, _VP, _VP, _I32, _VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
                                         ctypes.c_int),
     "gs_project_bwd": ([_VP] * 5 + [_I64, _VP, _VP, _I32, _VP, _VP, _VP] + [_VP] * 5 + [_VP, _VP], ctypes.c_int),
     "gs_image_loss": ([_VP, _VP, _I64, _F32, _F32, _VP, _VP, _VP], ctypes.c_int),
@@ -215,62 +216,63 @@ def gs_bin_sort_static(projected, rects, counts, N, sizes, cfg, keys, vals, capa
     _check(rc, "gs_bin_sort_static")
 
 
-def gs_rasterize_fwd(projected, vals, tile_ranges, sizes, cfg, image, final_T, last, stream=None):
+def gs_rasterize_fwd(projected, vals, tile_ranges, sizes, cfg, image, final_T, last, stream=None, cull_masks=None):
     sz = _sizes(sizes)
     c, cref = _cfg_ref(cfg)
     rc = load().gs_rasterize_fwd(_ptr(projected), _ptr(vals), _ptr(tile_ranges), _ptr(sz), sz.shape[0], cref,
-                                 _ptr(image), _ptr(final_T), _ptr(last), _stream(stream))
+                                 _ptr(image), _ptr(final_T), _ptr(last), _ptr(cull_masks), _stream(stream))
     _check(rc, "gs_rasterize_fwd")
 
 
 def gs_rasterize_fwd_counted(projected, vals, tile_ranges, sizes, cfg, image, final_T, last, pair_counts,
-                             stream=None):
+                             stream=None, cull_masks=None):
     """gs_rasterize_fwd that also adds its (executed, evaluated, composited)
     pixel-splat pair counts into pair_counts (int64 [3] on the device)."""
     sz = _sizes(sizes)
     c, cref = _cfg_ref(cfg)
     rc = load().gs_rasterize_fwd_counted(_ptr(projected), _ptr(vals), _ptr(tile_ranges), _ptr(sz), sz.shape[0], cref,
-                                         _ptr(image), _ptr(final_T), _ptr(last), _ptr(pair_counts), _stream(stream))
+                                         _ptr(image), _ptr(final_T), _ptr(last), _ptr(pair_counts), _ptr(cull_masks),
+                                         _stream(stream))
     _check(rc, "gs_rasterize_fwd_counted")
 
 
 def gs_rasterize_fwd_l1l2(projected, vals, tile_ranges, sizes, cfg, image, final_T, last, target, n_values, w_l1,
-                          w_l2, accumulate, dL_dimage, loss, stream=None):
+                          w_l2, accumulate, dL_dimage, loss, stream=None, cull_masks=None):
     """gs_rasterize_fwd with the L1 + L2 loss of gs_image_loss in the same kernel."""
     sz = _sizes(sizes)
     c, cref = _cfg_ref(cfg)
     rc = load().gs_rasterize_fwd_l1l2(_ptr(projected), _ptr(vals), _ptr(tile_ranges), _ptr(sz), sz.shape[0], cref,
                                       _ptr(image), _ptr(final_T), _ptr(last), _ptr(target), int(n_values),
                                       float(w_l1), float(w_l2), int(bool(accumulate)), _ptr(dL_dimage), _ptr(loss),
-                                      _stream(stream))
+                                      _ptr(cull_masks), _stream(stream))
     _check(rc, "gs_rasterize_fwd_l1l2")
 
 
 def gs_rasterize_bwd(means, log_scales, quats, opacity_logits, sh, cams, sizes, cfg, projected, counts, vals,
                      tile_ranges, final_T, last, dL_dimage, d_projected, d_means, d_log_scales, d_quats,
-                     d_opacity_logits, d_sh, status, stream=None):
+                     d_opacity_logits, d_sh, status, stream=None, cull_masks=None):
     sz = _sizes(sizes)
     c, cref = _cfg_ref(cfg)
     rc = load().gs_rasterize_bwd(_ptr(means), _ptr(log_scales), _ptr(quats), _ptr(opacity_logits), _ptr(sh),
                                  means.shape[0], _ptr(cams), _ptr(sz), sz.shape[0], cref, _ptr(projected),
                                  _ptr(counts), _ptr(vals), _ptr(tile_ranges), _ptr(final_T), _ptr(last),
                                  _ptr(dL_dimage), _ptr(d_projected), _ptr(d_means), _ptr(d_log_scales), _ptr(d_quats),
-                                 _ptr(d_opacity_logits), _ptr(d_sh), _ptr(status), _stream(stream))
+                                 _ptr(d_opacity_logits), _ptr(d_sh), _ptr(cull_masks), _ptr(status), _stream(stream))
     _check(rc, "gs_rasterize_bwd")
 
 
 def gs_rasterize_bwd_pixels(projected, vals, tile_ranges, sizes, cfg, N, final_T, last, dL_dimage, d_projected,
-                            stream=None):
+                            stream=None, cull_masks=None):
     sz = _sizes(sizes)
     c, cref = _cfg_ref(cfg)
     rc = load().gs_rasterize_bwd_pixels(_ptr(projected), _ptr(vals), _ptr(tile_ranges), _ptr(sz), sz.shape[0], cref,
                                         int(N), _ptr(final_T), _ptr(last), _ptr(dL_dimage), _ptr(d_projected),
-                                        _stream(stream))
+                                        _ptr(cull_masks), _stream(stream))
     _check(rc, "gs_rasterize_bwd_pixels")
 
 
 def gs_rasterize_bwd_pixels_counted(projected, vals, tile_ranges, sizes, cfg, N, final_T, last, dL_dimage,
-                                    d_projected, pair_counts, stream=None):
+                                    d_projected, pair_counts, stream=None, cull_masks=None):
     """gs_rasterize_bwd_pixels that also adds its (executed, evaluated,
     composited) pixel-splat pair counts into pair_counts (int64 [3])."""
     sz = _sizes(sizes)
@@ -278,7 +280,7 @@ def gs_rasterize_bwd_pixels_counted(projected, vals, tile_ranges, sizes, cfg, N,
     rc = load().gs_rasterize_bwd_pixels_counted(_ptr(projected), _ptr(vals), _ptr(tile_ranges), _ptr(sz),
                                                 sz.shape[0], cref, int(N), _ptr(final_T), _ptr(last),
                                                 _ptr(dL_dimage), _ptr(d_projected), _ptr(pair_counts),
-                                                _stream(stream))
+                                                _ptr(cull_masks), _stream(stream))
     _check(rc, "gs_rasterize_bwd_pixels_counted")
 
 

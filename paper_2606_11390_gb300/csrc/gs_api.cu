@@ -46,7 +46,7 @@ int build_layout(const int32_t* sizes, int32_t V, const gs_config* cfg, Layout* 
 
 }  // namespace gs
 
-extern "C" int gs_version(void) { return 300; }  // 0.3.0: raster batch sizes in gs_config, pair-counting raster entry points
+extern "C" int gs_version(void) { return 400; }  // 0.4.0: cull masks handed from the raster forward to its backward
 
 extern "C" const char* gs_status_string(int code) {
   switch (code) {

@@ -81,13 +81,14 @@ int dispatch_bwd(int ppt, int32_t batch, bool bg, bool count, const BwdArgs& a, 
 
 int rasterize_fwd_impl(const float* projected, const uint32_t* vals, const uint32_t* tile_ranges, const int32_t* sizes,
                        int32_t V, const gs_config* cfg, float* image, float* final_T, uint32_t* last,
-                       const rast::ImageLoss& IL, unsigned long long* counts, cudaStream_t stream) {
+                       const rast::ImageLoss& IL, unsigned long long* counts, uint16_t* cull, cudaStream_t stream) {
   FwdArgs a;
   int rc = build_layout(sizes, V, cfg, &a.L, nullptr);
   if (rc != GS_OK) return rc;
   if (!projected || !tile_ranges || !image || !final_T || !last) return GS_ERR_ARG;
   if (!aligned16(projected) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7u)) return GS_ERR_ARG;
   if (counts && (reinterpret_cast<uintptr_t>(counts) & 7u)) return GS_ERR_ARG;
+  if (cull && (reinterpret_cast<uintptr_t>(cull) & 1u)) return GS_ERR_ARG;
   if (!valid_batch(cfg->raster_batch_fwd)) return GS_ERR_UNSUPPORTED;
   a.K = make_consts(*cfg);
   a.projected = reinterpret_cast<const float4*>(projected);
@@ -99,13 +100,14 @@ int rasterize_fwd_impl(const float* projected, const uint32_t* vals, const uint3
   a.last = last;
   a.IL = IL;
   a.counts = counts;
+  a.cull = cull;
   return dispatch_fwd(pixels_per_thread(a.L, a.K), cfg->raster_batch_fwd, counts != nullptr, a, stream);
 }
 
 int rasterize_bwd_pixels_impl(const float* projected, const uint32_t* vals, const uint32_t* tile_ranges,
                               const int32_t* sizes, int32_t V, const gs_config* cfg, int64_t N, const float* final_T,
                               const uint32_t* last, const float* dL_dimage, float* d_projected,
-                              unsigned long long* counts, cudaStream_t stream) {
+                              unsigned long long* counts, const uint16_t* cull, cudaStream_t stream) {
   BwdArgs a;
   int rc = build_layout(sizes, V, cfg, &a.L, nullptr);
   if (rc != GS_OK) return rc;
@@ -115,6 +117,7 @@ int rasterize_bwd_pixels_impl(const float* projected, const uint32_t* vals, cons
   if (!projected || !tile_ranges || !final_T || !last || !dL_dimage || !d_projected) return GS_ERR_ARG;
   if (!aligned16(projected) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7u)) return GS_ERR_ARG;
   if (counts && (reinterpret_cast<uintptr_t>(counts) & 7u)) return GS_ERR_ARG;
+  if (cull && (reinterpret_cast<uintptr_t>(cull) & 1u)) return GS_ERR_ARG;
   if (!valid_batch(cfg->raster_batch_bwd)) return GS_ERR_UNSUPPORTED;
   a.K = make_consts(*cfg);
   if (cudaMemsetAsync(d_projected, 0, sizeof(float) * kDRecordFloats * static_cast<size_t>(N) * V, stream) !=
@@ -129,6 +132,7 @@ int rasterize_bwd_pixels_impl(const float* projected, const uint32_t* vals, cons
   a.dL_dimage = dL_dimage;
   a.d_proj = d_projected;
   a.counts = counts;
+  a.cull = cull;
   const bool bg = a.K.bg[0] != 0.0f || a.K.bg[1] != 0.0f || a.K.bg[2] != 0.0f;
   return dispatch_bwd(pixels_per_thread(a.L, a.K), cfg->raster_batch_bwd, bg, counts != nullptr, a, stream);
 }
@@ -138,20 +142,20 @@ int rasterize_bwd_pixels_impl(const float* projected, const uint32_t* vals, cons
 
 extern "C" int gs_rasterize_fwd(const float* projected, const uint32_t* vals, const uint32_t* tile_ranges,
                                 const int32_t* sizes, int32_t V, const gs_config* cfg, float* image, float* final_T,
-                                uint32_t* last, gs_stream_t stream) {
+                                uint32_t* last, uint16_t* cull_masks, gs_stream_t stream) {
   gs::rast::ImageLoss none{};
   return gs::rasterize_fwd_impl(projected, vals, tile_ranges, sizes, V, cfg, image, final_T, last, none, nullptr,
-                                reinterpret_cast<cudaStream_t>(stream));
+                                cull_masks, reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" int gs_rasterize_fwd_counted(const float* projected, const uint32_t* vals, const uint32_t* tile_ranges,
                                         const int32_t* sizes, int32_t V, const gs_config* cfg, float* image,
                                         float* final_T, uint32_t* last, uint64_t* pair_counts_dev,
-                                        gs_stream_t stream) {
+                                        uint16_t* cull_masks, gs_stream_t stream) {
   if (!pair_counts_dev) return GS_ERR_ARG;
   gs::rast::ImageLoss none{};
   return gs::rasterize_fwd_impl(projected, vals, tile_ranges, sizes, V, cfg, image, final_T, last, none,
-                                reinterpret_cast<unsigned long long*>(pair_counts_dev),
+                                reinterpret_cast<unsigned long long*>(pair_counts_dev), cull_masks,
                                 reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -159,7 +163,7 @@ extern "C" int gs_rasterize_fwd_l1l2(const float* projected, const uint32_t* val
                                      const int32_t* sizes, int32_t V, const gs_config* cfg, float* image,
                                      float* final_T, uint32_t* last, const float* target, int64_t n_values, float w_l1,
                                      float w_l2, int32_t accumulate, float* dL_dimage, double* loss_dev,
-                                     gs_stream_t stream_) {
+                                     uint16_t* cull_masks, gs_stream_t stream_) {
   using namespace gs;
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   if (!target || !dL_dimage || !loss_dev || n_values <= 0) return GS_ERR_ARG;
@@ -178,26 +182,28 @@ extern "C" int gs_rasterize_fwd_l1l2(const float* projected, const uint32_t* val
   IL.w2 = w_l2;
   IL.inv_n = 1.0f / static_cast<float>(n_values);
   IL.inv_n_d = 1.0 / static_cast<double>(n_values);
-  return rasterize_fwd_impl(projected, vals, tile_ranges, sizes, V, cfg, image, final_T, last, IL, nullptr, stream);
+  return rasterize_fwd_impl(projected, vals, tile_ranges, sizes, V, cfg, image, final_T, last, IL, nullptr,
+                            cull_masks, stream);
 }
 
 extern "C" int gs_rasterize_bwd_pixels(const float* projected, const uint32_t* vals, const uint32_t* tile_ranges,
                                        const int32_t* sizes, int32_t V, const gs_config* cfg, int64_t N,
                                        const float* final_T, const uint32_t* last, const float* dL_dimage,
-                                       float* d_projected, gs_stream_t stream) {
+                                       float* d_projected, const uint16_t* cull_masks, gs_stream_t stream) {
   return gs::rasterize_bwd_pixels_impl(projected, vals, tile_ranges, sizes, V, cfg, N, final_T, last, dL_dimage,
-                                       d_projected, nullptr, reinterpret_cast<cudaStream_t>(stream));
+                                       d_projected, nullptr, cull_masks, reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" int gs_rasterize_bwd_pixels_counted(const float* projected, const uint32_t* vals,
                                                const uint32_t* tile_ranges, const int32_t* sizes, int32_t V,
                                                const gs_config* cfg, int64_t N, const float* final_T,
                                                const uint32_t* last, const float* dL_dimage, float* d_projected,
-                                               uint64_t* pair_counts_dev, gs_stream_t stream) {
+                                               uint64_t* pair_counts_dev, const uint16_t* cull_masks,
+                                               gs_stream_t stream) {
   if (!pair_counts_dev) return GS_ERR_ARG;
   return gs::rasterize_bwd_pixels_impl(projected, vals, tile_ranges, sizes, V, cfg, N, final_T, last, dL_dimage,
                                        d_projected, reinterpret_cast<unsigned long long*>(pair_counts_dev),
-                                       reinterpret_cast<cudaStream_t>(stream));
+                                       cull_masks, reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" int gs_rasterize_bwd(const float* means, const float* log_scales, const float* quats,
@@ -206,9 +212,10 @@ extern "C" int gs_rasterize_bwd(const float* means, const float* log_scales, con
                                 const uint32_t* counts, const uint32_t* vals, const uint32_t* tile_ranges,
                                 const float* final_T, const uint32_t* last, const float* dL_dimage,
                                 float* d_projected, float* d_means, float* d_log_scales, float* d_quats,
-                                float* d_opacity_logits, float* d_sh, int32_t* status_dev, gs_stream_t stream) {
+                                float* d_opacity_logits, float* d_sh, const uint16_t* cull_masks, int32_t* status_dev,
+                                gs_stream_t stream) {
   const int rc = gs_rasterize_bwd_pixels(projected, vals, tile_ranges, sizes, V, cfg, N, final_T, last, dL_dimage,
-                                         d_projected, stream);
+                                         d_projected, cull_masks, stream);
   if (rc != GS_OK) return rc;
   return gs_project_bwd(means, log_scales, quats, opacity_logits, sh, N, cams_dev, sizes, V, cfg, counts, d_projected,
                         d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, status_dev, stream);

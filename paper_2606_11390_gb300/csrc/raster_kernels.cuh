@@ -122,11 +122,31 @@ struct Geo {
   }
 };
 
+// Per-entry cull masks handed from the forward to the backward: 16 bits per
+// sorted-list entry, the warps whose block the splat can reach (low byte)
+// and a tag naming the tile shape and pixels per thread (high byte), so that
+// the backward uses a mask only when it was made for the same warp layout
+// and computes the cull itself otherwise. Layouts with more than 8 warps
+// (32x32 tiles at 2 pixels per thread) do not hand masks over (tag 0).
+template <int TW, int TH, int PPT>
+constexpr uint32_t cull_tag() {
+  return (TW == 8 && TH == 8 && PPT == 2)     ? 0x81u
+         : (TW == 16 && TH == 16 && PPT == 2) ? 0x82u
+         : (TW == 16 && TH == 16 && PPT == 4) ? 0x83u
+         : (TW == 32 && TH == 16 && PPT == 2) ? 0x84u
+         : (TW == 32 && TH == 16 && PPT == 4) ? 0x85u
+         : (TW == 32 && TH == 32 && PPT == 4) ? 0x86u
+                                              : 0u;
+}
+
 // Minimum over y in [y0, y1] of q(x, y) = m00 x^2 + 2 m01 x y + m11 y^2 for
-// fixed x (the quadratic in y is minimised at y = -m01 x / m11, clamped).
-__device__ __forceinline__ float edge_min_y(float x, float y0, float y1, float m00, float m01, float m11) {
-  const float y = fminf(fmaxf(-m01 * x / m11, y0), y1);
-  return m00 * x * x + 2.0f * m01 * x * y + m11 * y * y;
+// fixed x: the quadratic in y is minimised at y = k x with k = -m01 / m11
+// (one division per splat, not per edge), clamped to the edge. A y a rounding
+// away from the true minimiser raises q only by m11 dy^2, far inside the
+// cull's margins.
+__device__ __forceinline__ float edge_min_y(float x, float y0, float y1, float m00, float m01, float m11, float k) {
+  const float y = fminf(fmaxf(k * x, y0), y1);
+  return (m00 * x + 2.0f * m01 * y) * x + m11 * y * y;
 }
 
 // Bitmask of the warps of the tile at (tx0, ty0) whose pixel block can hold a
@@ -149,9 +169,13 @@ __device__ __forceinline__ uint32_t warp_cull_mask(const float4& a, const float4
   if (!(det > 0.0f) || !(m00 > 0.0f) || !(m11 > 0.0f)) return kAll;
   const float ts = (__log2f(o) - __log2f(amin)) * 1.001f + 0.01f;
   const float lim = 2.0f * ts;
-  const float hx = sqrtf(lim * m11 / det) * 1.001f + 0.05f;
-  const float hy = sqrtf(lim * m00 / det) * 1.001f + 0.05f;
+  const float idet = 1.0f / det;
+  const float hx = sqrtf(lim * m11 * idet) * 1.001f + 0.05f;
+  const float hy = sqrtf(lim * m00 * idet) * 1.001f + 0.05f;
   if (!(hx < 1e30f) || !(hy < 1e30f)) return kAll;
+  // minimisers of the quadratic along vertical (y = kx x) and horizontal
+  // (x = ky y) edges
+  const float kx = -m01 / m11, ky = -m01 / m00;
   uint32_t mask = 0;
 #pragma unroll
   for (int w = 0; w < G::NW; ++w) {
@@ -165,9 +189,9 @@ __device__ __forceinline__ uint32_t warp_cull_mask(const float4& a, const float4
       mask |= 1u << w;  // the centre lies in the block
       continue;
     }
-    float qmin = fminf(edge_min_y(x0, y0, y1, m00, m01, m11), edge_min_y(x1, y0, y1, m00, m01, m11));
-    qmin = fminf(qmin, edge_min_y(y0, x0, x1, m11, m01, m00));
-    qmin = fminf(qmin, edge_min_y(y1, x0, x1, m11, m01, m00));
+    float qmin = fminf(edge_min_y(x0, y0, y1, m00, m01, m11, kx), edge_min_y(x1, y0, y1, m00, m01, m11, kx));
+    qmin = fminf(qmin, edge_min_y(y0, x0, x1, m11, m01, m00, ky));
+    qmin = fminf(qmin, edge_min_y(y1, x0, x1, m11, m01, m00, ky));
     if (qmin <= lim * 1.001f + 0.01f) mask |= 1u << w;
   }
   return mask;
@@ -249,7 +273,8 @@ __global__ void __launch_bounds__(TW* TH / PPT, 1024 / (TW * TH / PPT)) raster_f
                                                                    const Consts K, float* __restrict__ image,
                                                                    float* __restrict__ final_T,
                                                                    uint32_t* __restrict__ last, const ImageLoss IL,
-                                                                   unsigned long long* __restrict__ counts) {
+                                                                   unsigned long long* __restrict__ counts,
+                                                                   uint16_t* __restrict__ cull_out) {
   using G = Geo<TW, TH, PPT>;
   constexpr int NT = G::NT;
   static_assert(B >= 32 && B <= 512 && (B & (B - 1)) == 0, "splats per batch: a power of two in [32, 512]");
@@ -296,7 +321,10 @@ __global__ void __launch_bounds__(TW* TH / PPT, 1024 / (TW * TH / PPT)) raster_f
       s_a[k] = a;
       s_b[k] = b;
       s_c[k] = c;
-      s_m[k] = warp_cull_mask<G>(a, b, tx0, ty0, amin);
+      const uint32_t mk = warp_cull_mask<G>(a, b, tx0, ty0, amin);
+      s_m[k] = mk;
+      constexpr uint32_t kTag = cull_tag<TW, TH, PPT>();
+      if (kTag && cull_out) cull_out[range.x + b0 + k] = static_cast<uint16_t>(mk | (kTag << 8));
     }
     __syncthreads();
     const int cnt = min(B, n - b0);
@@ -545,7 +573,7 @@ __global__ void GS_RBWD_BOUNDS(TW* TH / PPT) raster_bwd_kernel(
     const float4* __restrict__ projected, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
     const uint32_t* __restrict__ order, const Layout L, const Consts K, const float* __restrict__ final_T,
     const uint32_t* __restrict__ last, const float* __restrict__ dL_dimage, float* __restrict__ d_proj,
-    unsigned long long* __restrict__ counts) {
+    unsigned long long* __restrict__ counts, const uint16_t* __restrict__ cull_in) {
   using Gm = Geo<TW, TH, PPT>;
   constexpr int NT = Gm::NT, NW = Gm::NW;
   static_assert(B >= 32 && B <= 512 && (B & (B - 1)) == 0, "splats per batch: a power of two in [32, 512]");
@@ -637,7 +665,10 @@ __global__ void GS_RBWD_BOUNDS(TW* TH / PPT) raster_bwd_kernel(
       s_b[k] = b;
       s_c[k] = c;
       s_vg[k] = vg;
-      s_m[k] = warp_cull_mask<Gm>(a, b, tx0, ty0, amin);
+      // the forward's mask for this entry when it made one for this layout
+      constexpr uint32_t kTag = cull_tag<TW, TH, PPT>();
+      const uint32_t handed = (kTag && cull_in) ? cull_in[range.x + b_end - 1 - k] : 0u;
+      s_m[k] = (handed >> 8) == kTag && kTag ? (handed & 0xffu) : warp_cull_mask<Gm>(a, b, tx0, ty0, amin);
     }
     __syncthreads();
     // entries j hold relative position b_end-1-j; this warp needs rel < wmax.
@@ -740,14 +771,14 @@ __global__ void GS_RBWD_BOUNDS(TW* TH / PPT) raster_bwd_kernel(
 template <int TW, int TH, int PPT, int B, bool COUNT>
 int launch_fwd(const FwdArgs& a, cudaStream_t stream) {
   raster_fwd_kernel<TW, TH, PPT, B, COUNT><<<static_cast<unsigned>(a.L.n_tiles), TW * TH / PPT, 0, stream>>>(
-      a.projected, a.vals, a.ranges, a.order, a.L, a.K, a.image, a.final_T, a.last, a.IL, a.counts);
+      a.projected, a.vals, a.ranges, a.order, a.L, a.K, a.image, a.final_T, a.last, a.IL, a.counts, a.cull);
   return cuda_status(cudaGetLastError());
 }
 
 template <int TW, int TH, int PPT, int B, bool BG, bool COUNT>
 int launch_bwd(const BwdArgs& a, cudaStream_t stream) {
   raster_bwd_kernel<TW, TH, PPT, B, BG, COUNT><<<static_cast<unsigned>(a.L.n_tiles), TW * TH / PPT, 0, stream>>>(
-      a.projected, a.vals, a.ranges, a.order, a.L, a.K, a.final_T, a.last, a.dL_dimage, a.d_proj, a.counts);
+      a.projected, a.vals, a.ranges, a.order, a.L, a.K, a.final_T, a.last, a.dL_dimage, a.d_proj, a.counts, a.cull);
   return cuda_status(cudaGetLastError());
 }
 

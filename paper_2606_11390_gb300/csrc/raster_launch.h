@@ -54,6 +54,7 @@ struct FwdArgs {
   uint32_t* last;
   ImageLoss IL;
   unsigned long long* counts;
+  uint16_t* cull;  // optional: per-entry cull masks written for the backward
 };
 
 struct BwdArgs {
@@ -68,6 +69,7 @@ struct BwdArgs {
   const float* dL_dimage;
   float* d_proj;
   unsigned long long* counts;
+  const uint16_t* cull;  // optional: the forward's per-entry cull masks
 };
 
 template <int TW, int TH, int PPT, int B, bool COUNT>

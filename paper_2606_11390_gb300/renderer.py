@@ -123,6 +123,8 @@ class Frame:
         self.keys = (torch.zeros(max(capacity, 1), dtype=torch.int64, device=self.device) if self.keep_keys
                      else None)
         self.vals = torch.zeros(max(capacity, 1), dtype=torch.int32, device=self.device)
+        # per list entry: the forward's cull mask for the backward (uint16 bits)
+        self.cull = torch.zeros(max(capacity, 1), dtype=torch.int16, device=self.device)
         if self.partitions == 1:
             ws = gs.gs_bin_sort_workspace_bytes(self.N, self.cams.V, capacity, self.n_tiles)
         else:
@@ -142,14 +144,16 @@ class Frame:
         """Moves what a backward of the last render reads out of this frame
         into a FrameState (no copy) and gives the frame fresh buffers in their
         place, so that a later render on this frame cannot overwrite them:
-        the projected records, tile counts, sorted list and tile ranges, and
-        per pixel the image, final transmittance and last-contributor count.
+        the projected records, tile counts, sorted list, its cull masks and
+        tile ranges, and per pixel the image, final transmittance and
+        last-contributor count.
         The camera records are copied (V x 80 bytes), since the caller may
         refill them."""
         st = FrameState(self)
         self.projected = torch.zeros_like(self.projected)
         self.counts = torch.zeros_like(self.counts)
         self.vals = torch.zeros_like(self.vals)
+        self.cull = torch.zeros_like(self.cull)
         self.tile_ranges = torch.zeros_like(self.tile_ranges)
         self.ranges = self.tile_ranges[:2 * self.n_tiles]
         self.image = torch.zeros_like(self.image)
@@ -170,7 +174,7 @@ class FrameState:
         self.cams.dev = c.dev.clone()
         self.cams.n_pixels, self.cams.pix_base = c.n_pixels, c.pix_base.copy()
         self.N, self.cfg, self.n_tiles = frame.N, dict(frame.cfg), frame.n_tiles
-        self.projected, self.counts, self.vals = frame.projected, frame.counts, frame.vals
+        self.projected, self.counts, self.vals, self.cull = frame.projected, frame.counts, frame.vals, frame.cull
         self.tile_ranges, self.image = frame.tile_ranges, frame.image
         self.final_T, self.last = frame.final_T, frame.last
         self.d_projected = None
@@ -207,7 +211,7 @@ def bin_sort(frame: Frame, stream=None):
 
 def rasterize_fwd(frame: Frame, stream=None):
     gs.gs_rasterize_fwd(frame.projected, frame.vals, frame.tile_ranges, frame.cams.sizes, frame.cfg, frame.image,
-                        frame.final_T, frame.last, stream)
+                        frame.final_T, frame.last, stream, cull_masks=frame.cull)
 
 
 def rasterize_fwd_l1l2(frame: Frame, target, n_values, w_l1, w_l2, accumulate, dL_dimage, loss, stream=None):
@@ -215,7 +219,7 @@ def rasterize_fwd_l1l2(frame: Frame, target, n_values, w_l1, w_l2, accumulate, d
     (target and dL_dimage laid out like frame.image)."""
     gs.gs_rasterize_fwd_l1l2(frame.projected, frame.vals, frame.tile_ranges, frame.cams.sizes, frame.cfg,
                              frame.image, frame.final_T, frame.last, target, n_values, w_l1, w_l2, accumulate,
-                             dL_dimage, loss, stream)
+                             dL_dimage, loss, stream, cull_masks=frame.cull)
 
 
 def rasterize_bwd(params: FlatParams, cams: Cameras, frame: Frame, dL_dimage, grads: FlatParams, stream=None,
@@ -226,7 +230,7 @@ def rasterize_bwd(params: FlatParams, cams: Cameras, frame: Frame, dL_dimage, gr
                         params["sh"], cams.dev, cams.sizes, cfg, frame.projected, frame.counts, frame.vals,
                         frame.tile_ranges, frame.final_T, frame.last, dL_dimage, frame.d_projected, grads["means"],
                         grads["log_scales"], grads["quats"], grads["opacity_logits"], grads["sh"], frame.status,
-                        stream)
+                        stream, cull_masks=frame.cull)
 
 
 def render(params: FlatParams, cams: Cameras, frame: Frame, max_retries: int = 3):

@@ -183,3 +183,45 @@ def test_bad_batch_size_is_rejected():
             gs.gs_rasterize_bwd_pixels(fr.projected, fr.vals, fr.tile_ranges, cams.sizes,
                                        dict(fr.cfg, raster_batch_bwd=val), fr.N, fr.final_T, fr.last,
                                        torch.zeros_like(fr.image), fr.d_projected)
+
+
+@pytest.mark.parametrize("tw,th,flags", [(32, 16, 0), (16, 16, 2), (8, 8, 0), (32, 32, 2)],
+                         ids=["32x16", "16x16_2px", "8x8", "32x32_2px_no_masks"])
+def test_backward_with_the_forwards_cull_masks(oracle, tw, th, flags):
+    """The backward reusing the forward's per-entry cull masks takes the same
+    decisions as computing them itself: the same pair counts, and the same
+    gradients up to the order of the FP32 atomics; a backward with another
+    warp layout (pixels per thread) than the forward's ignores the masks."""
+    import torch
+
+    from paper_2606_11390_gb300 import _native as gs
+
+    s = TUNE_SCENE()
+    s["cfg"] = scenes.make_cfg(tile_w=tw, tile_h=th, flags=flags)
+    params, cams, fr = _render(s, dict(s["cfg"]))  # the forward writes fr.cull
+    o_proj, o_bins, o_ras = oracle.forward(s, "f32")
+    dl_np = _upstream(s, o_ras)
+    o_dproj, _ = oracle.backward(s, o_proj, o_bins, dl_np.astype(np.float64), "f32")
+    dl = torch.from_numpy(dl_np.reshape(-1)).cuda()
+    out = {}
+    for name, cfg, masks in (("own", fr.cfg, None), ("handed", fr.cfg, fr.cull),
+                             ("other_layout", dict(fr.cfg, flags=int(fr.cfg["flags"]) ^ gs.GS_FLAG_RASTER_2PX)
+                              if tw != 8 else fr.cfg, fr.cull)):
+        dp = torch.zeros_like(fr.d_projected)
+        cnt = torch.zeros(3, dtype=torch.int64, device="cuda")
+        gs.gs_rasterize_bwd_pixels_counted(fr.projected, fr.vals, fr.tile_ranges, cams.sizes, cfg, fr.N, fr.final_T,
+                                           fr.last, dl, dp, cnt, cull_masks=masks)
+        torch.cuda.synchronize()
+        out[name] = (to_np(dp).reshape(-1, 9), [int(x) for x in cnt.cpu()])
+        grad_close(out[name][0], o_dproj, name=f"d_projected ({name})")
+    assert out["handed"][1] == out["own"][1]
+    if tw == 32 and th == 32 and flags:
+        assert not fr.cull.any()  # layouts of more than 8 warps hand no masks over
+    else:
+        # entries the forward staged carry its layout's tag (the forward stops
+        # staging a tile once all its pixels are done)
+        n = int(fr.n_isect.item())
+        tags = to_np(fr.cull[:n]).view(np.uint16) >> 8
+        want = {(32, 16, 0): 0x85, (16, 16, 2): 0x82, (8, 8, 0): 0x81}[(tw, th, flags)]
+        assert set(np.unique(tags).tolist()) <= {0, want}
+        assert (tags == want).mean() > 0.5
