@@ -232,8 +232,9 @@ struct PassArgs {
   const uint32_t* vals_in;
   uint32_t* keys_out;  // may be null: the keys are not written
   uint32_t* vals_out;
-  uint2* ranges;             // last tile-id pass: per-key (~first, last + 1) bounds, else null
+  uint2* ranges;             // last pass: per-key (~first, last + 1) bounds, else null
   uint32_t n_keys;           // ranges has n_keys entries
+  uint32_t key_mask;         // the bits of a key that name its range (others ride along unsorted)
   const int64_t* n_total;   // items = min(*n_total, cap)
   int64_t cap;
   int shift;
@@ -425,9 +426,10 @@ __global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) sort_pass_ke
         // first and last items bound the key's range: the start kept as
         // ~position under atomicMax (zero-initialised), the end as
         // position + 1.
-        if (k < a.n_keys) {
-          if (idx == 0 || sm.keys[idx - 1] != k) atomicMax(&a.ranges[k].x, ~p);
-          if (idx == n_valid - 1 || sm.keys[idx + 1] != k) atomicMax(&a.ranges[k].y, p + 1);
+        const uint32_t kk = k & a.key_mask;
+        if (kk < a.n_keys) {
+          if (idx == 0 || (sm.keys[idx - 1] & a.key_mask) != kk) atomicMax(&a.ranges[kk].x, ~p);
+          if (idx == n_valid - 1 || (sm.keys[idx + 1] & a.key_mask) != kk) atomicMax(&a.ranges[kk].y, p + 1);
         } else {
           set_status(status, GS_STATUS_BOUNDS);
         }
@@ -674,7 +676,12 @@ __device__ __forceinline__ int view_of_record(uint32_t vg, int64_t N, int V, flo
 //     and lane l produces entries l, l + 32, ... of the warp's concatenated
 //     output. It also adds the records' tile counts into *n_isect (the exact
 //     intersection count) and gathers the digit histograms of the super-tile
-//     passes.
+//     passes. With `packed`, each key also carries, above the 16-bit
+//     super-tile id, the record's rectangle clipped to that super-tile in its
+//     local tile coordinates (3 bits each for x0, y0, x1 - 1, y1 - 1): the
+//     sort passes use only the id's bits as digits and carry the rest, so the
+//     chunk kernels read a record's coverage from its sorted key instead of
+//     gathering its rectangle.
 constexpr int kEmitThreads = 256;
 static_assert(kEmitThreads == kScanThreads, "the emission scans its records with the block scan");
 constexpr int kEmitItems = 4;                         // records per thread in the count scan
@@ -689,11 +696,12 @@ __device__ __forceinline__ uint32_t super_count(short4 rc) {
 
 __global__ void __launch_bounds__(kEmitThreads) emit_super_kernel(
     const uint32_t* __restrict__ order, const int64_t* n_visible, const short4* __restrict__ rects, int64_t N,
-    const Layout L, const SuperLayout S, uint64_t capacity, int passes, ScanState st, uint32_t* __restrict__ skeys,
-    uint32_t* __restrict__ svals, uint32_t* __restrict__ hist, int64_t* n_super_total,
-    unsigned long long* __restrict__ n_isect, int32_t* status) {
+    const Layout L, const SuperLayout S, uint64_t capacity, int passes, int packed, ScanState st,
+    uint32_t* __restrict__ skeys, uint32_t* __restrict__ svals, uint32_t* __restrict__ hist,
+    int64_t* n_super_total, unsigned long long* __restrict__ n_isect, int32_t* status) {
   __shared__ uint32_t s_hist[kMaxSuperPasses][kRadix];
   __shared__ uint32_t s_vg[kEmitTile], s_cnt[kEmitTile], s_off[kEmitTile];
+  __shared__ short4 s_rect[kEmitTile];  // the records' rectangles, gathered once
   __shared__ uint32_t s_tile;
   __shared__ uint64_t s_warp[kScanThreads / 32];
   __shared__ uint64_t s_prefix;
@@ -717,11 +725,13 @@ __global__ void __launch_bounds__(kEmitThreads) emit_super_kernel(
     const bool ok = base + i < n;
     const uint32_t vg = ok ? order[base + i] : 0u;
     c[i] = 0u;
+    short4 rc = make_short4(0, 0, 1, 1);
     if (ok) {
-      const short4 rc = rects[vg];
+      rc = rects[vg];
       c[i] = super_count(rc);
       tiles += static_cast<uint64_t>(rc.z - rc.x) * static_cast<uint64_t>(rc.w - rc.y);
     }
+    s_rect[tid * kEmitItems + i] = rc;
     s_vg[tid * kEmitItems + i] = vg;
     s_cnt[tid * kEmitItems + i] = c[i];
     local += c[i];
@@ -749,7 +759,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_super_kernel(
     if (j < n) {
       vg = s_vg[r];
       cnt = s_cnt[r];
-      const short4 rc = rects[vg];
+      const short4 rc = s_rect[r];
       const int v = view_of_record(vg, N, L.V, invN);
       sb = S.sbase[v];
       const int sx0 = rc.x >> kSuperLog, sx1 = ((rc.z - 1) >> kSuperLog) + 1, sy0 = rc.y >> kSuperLog;
@@ -786,8 +796,18 @@ __global__ void __launch_bounds__(kEmitThreads) emit_super_kernel(
       if (e < total && pos < capacity) {
         const uint32_t r_w = r_wn & 0xffffu, r_stx = r_wn >> 16;
         const uint32_t row = k / r_w, col = k - row * r_w;
-        const uint32_t s = r_sb + ((r_xy >> 16) + row) * r_stx + (r_xy & 0xffffu) + col;
-        skeys[pos] = s;
+        const uint32_t sxa = (r_xy & 0xffffu) + col, sya = (r_xy >> 16) + row;
+        const uint32_t s = r_sb + sya * r_stx + sxa;
+        uint32_t key = s;
+        if (packed) {
+          // the record's rectangle in the super-tile's local tile coordinates
+          const short4 rc = s_rect[g * 32 + (src & 31)];
+          const int ox = static_cast<int>(sxa) << kSuperLog, oy = static_cast<int>(sya) << kSuperLog;
+          const int lx0 = max(rc.x - ox, 0), lx1 = min(rc.z - ox, kSuperDim);
+          const int ly0 = max(rc.y - oy, 0), ly1 = min(rc.w - oy, kSuperDim);
+          key |= static_cast<uint32_t>(lx0 | (ly0 << 3) | ((lx1 - 1) << 6) | ((ly1 - 1) << 9)) << 16;
+        }
+        skeys[pos] = key;
         svals[pos] = r_vg;
         for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p][(s >> (8 * p)) & 0xffu], 1u);
       }
@@ -862,6 +882,7 @@ __global__ void __launch_bounds__(kChunkTableThreads) super_chunks_kernel(
 // thread, and each record's coverage of the super-tile's 64 tiles.
 struct ChunkArgs {
   const uint32_t* svals;        // super-tile lists (records), depth order within each
+  const uint32_t* skeys;        // their keys with the local rectangles (or null: gather the rectangles)
   const uint2* sranges;         // [n_super] [start, end) in svals
   const uint32_t* chunk_base;   // [n_super + 1]
   const uint4* chunk_info;      // [chunks] first record, length, super-tile
@@ -902,6 +923,20 @@ __device__ __forceinline__ uint64_t coverage_mask(short4 rc, const ChunkView& cv
   // one byte per covered row: the multiplication places copies without carries
   const uint64_t rows = (0x0101010101010101ull >> (8 * (kSuperDim - (ly1 - ly0)))) << (8 * ly0);
   return row * rows;
+}
+
+// The same mask from a record's rectangle in the super-tile's local
+// coordinates, packed as the emission stores it above the key's id.
+__device__ __forceinline__ uint64_t packed_mask(uint32_t pack) {
+  const int lx0 = pack & 7, ly0 = (pack >> 3) & 7, lx1 = ((pack >> 6) & 7) + 1, ly1 = ((pack >> 9) & 7) + 1;
+  const uint64_t row = ((1ull << (lx1 - lx0)) - 1ull) << lx0;
+  const uint64_t rows = (0x0101010101010101ull >> (8 * (kSuperDim - (ly1 - ly0)))) << (8 * ly0);
+  return row * rows;
+}
+
+// Coverage mask of the chunk's record `e` (a position in the super-tile lists).
+__device__ __forceinline__ uint64_t record_mask(const ChunkArgs& a, const ChunkView& cv, uint32_t e, uint32_t vg) {
+  return a.skeys ? packed_mask(a.skeys[e] >> 16) : coverage_mask(a.rects[vg], cv);
 }
 
 // Global tile id of local tile t of the chunk's super-tile, or -1 if it lies
@@ -946,7 +981,10 @@ __global__ void __launch_bounds__(kChunkThreads) chunk_count_kernel(const ChunkA
   for (uint32_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
     const ChunkView cv = chunk_view(a, L, S, c);
     uint64_t m = 0;
-    if (static_cast<uint32_t>(tid) < cv.len) m = coverage_mask(a.rects[a.svals[cv.first + tid]], cv);
+    if (static_cast<uint32_t>(tid) < cv.len) {
+      const uint32_t e = cv.first + tid;
+      m = record_mask(a, cv, e, a.skeys ? 0u : a.svals[e]);
+    }
     uint32_t lo, hi;
     warp_tile_lanes(m, lo, hi);
     s_cnt[warp][lane] = __popc(lo);
@@ -1076,8 +1114,9 @@ __global__ void __launch_bounds__(kChunkThreads) scatter_kernel(const ChunkArgs 
     uint64_t m = 0;
     uint32_t vg = 0;
     if (static_cast<uint32_t>(tid) < cv.len) {
-      vg = a.svals[cv.first + tid];
-      m = coverage_mask(a.rects[vg], cv);
+      const uint32_t e = cv.first + tid;
+      vg = a.svals[e];
+      m = record_mask(a, cv, e, vg);
     }
     uint32_t lo, hi;
     warp_tile_lanes(m, lo, hi);
@@ -1335,7 +1374,7 @@ int run_u32_sort_passes(uint32_t* const keys[2], uint32_t* const vals[2], const 
     a.keys_in = keys[p & 1]; a.vals_in = vals[p & 1]; a.keys_out = keys[(p + 1) & 1]; a.vals_out = vals[(p + 1) & 1];
     a.n_total = n_dev; a.cap = cap; a.shift = 8 * p; a.digit_offsets = hist + p * kRadix; a.scan_digits = 0;
     a.ticket = tickets + p;
-    a.ranges = nullptr; a.n_keys = 0;
+    a.ranges = nullptr; a.n_keys = 0; a.key_mask = 0xffffffffu;
     a.stall_tile = -1;
     a.spin_limit = kSpinLimit;
     a.lookback = lookback + static_cast<size_t>(p) * (tiles + 1) * kRadix;
@@ -1408,7 +1447,7 @@ int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* 
       a.n_total = n_visible; a.cap = VN; a.shift = 8 * p; a.digit_offsets = hist_d + p * kRadix;
       a.scan_digits = 1;  // the counts gathered by the compaction
       a.ticket = tickets + 2 + p;
-      a.ranges = nullptr; a.n_keys = 0;
+      a.ranges = nullptr; a.n_keys = 0; a.key_mask = 0xffffffffu;
       a.stall_tile = (p == 0 && (cfg->flags & GS_FLAG_TEST_STALL_LOOKBACK)) ? 0 : -1;
       a.spin_limit = (cfg->flags & GS_FLAG_TEST_STALL_LOOKBACK) ? kTestSpinLimit : kSpinLimit;
       a.lookback = reinterpret_cast<uint64_t*>(ws + w.lb_depth) + static_cast<size_t>(p) * (w.n_depth_tiles + 1) * kRadix;
@@ -1465,6 +1504,8 @@ int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* 
   // 2a. super-tile emission in depth order (and the exact intersection count)
   const SuperLayout S = make_super_layout(L);
   const int SP = passes_for(S.n_super);
+  // super-tile ids of at most 16 bits leave the key's high half for the local rectangles
+  const bool packed = S.n_super <= (1 << 16);
   uint32_t* sk[2] = {u32(w.skeys0), u32(w.skeys1)};
   uint32_t* sv[2] = {u32(w.svals0), u32(w.svals1)};
   uint32_t* hist_s = u32(w.hist_s);
@@ -1473,17 +1514,20 @@ int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* 
   uint2* ranges = reinterpret_cast<uint2*>(tile_ranges);
   ScanState st2{reinterpret_cast<uint64_t*>(ws + w.scan_s), tickets + 1};
   emit_super_kernel<<<static_cast<unsigned>(w.n_emit_tiles), kEmitThreads, 0, stream>>>(
-      order, n_visible, reinterpret_cast<const short4*>(rects), N, L, S, static_cast<uint64_t>(capacity), SP, st2,
-      sk[0], sv[0], hist_s, n_super_total, reinterpret_cast<unsigned long long*>(n_isect_dev), status_dev);
+      order, n_visible, reinterpret_cast<const short4*>(rects), N, L, S, static_cast<uint64_t>(capacity), SP,
+      packed ? 1 : 0, st2, sk[0], sv[0], hist_s, n_super_total, reinterpret_cast<unsigned long long*>(n_isect_dev),
+      status_dev);
   // 2b. stable super-tile passes; the last one bounds the super-tile ranges
   for (int p = 0; p < SP; ++p) {
     PassArgs a;
     a.keys_in = sk[p & 1]; a.vals_in = sv[p & 1]; a.keys_out = sk[(p + 1) & 1]; a.vals_out = sv[(p + 1) & 1];
-    a.ranges = nullptr; a.n_keys = 0;
+    a.ranges = nullptr; a.n_keys = 0; a.key_mask = packed ? 0xffffu : 0xffffffffu;
     if (p == SP - 1) {
+      // the last pass bounds the super-tile ranges; it writes the keys too
+      // when they carry the records' local rectangles
       a.ranges = sranges;
       a.n_keys = static_cast<uint32_t>(S.n_super);
-      a.keys_out = nullptr;
+      if (!packed) a.keys_out = nullptr;
     }
     a.n_total = n_super_total; a.cap = capacity; a.shift = 8 * p; a.digit_offsets = hist_s + p * kRadix;
     a.scan_digits = 1;  // the counts gathered by the emission
@@ -1518,6 +1562,7 @@ int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* 
                                                            chunk_info);
   ChunkArgs ca;
   ca.svals = sv[SP & 1];
+  ca.skeys = packed ? sk[SP & 1] : nullptr;
   ca.sranges = sranges;
   ca.chunk_base = chunk_base;
   ca.chunk_info = chunk_info;
