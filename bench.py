@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the per-view comparison leg")
     ap.add_argument("--tile", default=None, help="WxH tile override, e.g. 16x16 (skips the autotuner)")
+    ap.add_argument("--raster", default=None,
+                    help="explicit rasteriser configuration TWxTH/Ppx/fB/bB as the autotuner names them, e.g. "
+                         "32x16/4px/f128/b256 (skips the autotuner)")
     ap.add_argument("--no-tune", action="store_true",
                     help="use the workload's tile shape and the default rasteriser configuration instead of the "
                          "autotuner's choice")
@@ -466,7 +469,14 @@ def main():
     tile = tuple(int(x) for x in args.tile.split("x")) if args.tile else (scene["cfg"]["tile_w"], scene["cfg"]["tile_h"])
     raster_kw = {"tile": tile}
     tune = None
-    if not args.no_tune and not args.tile and args.raster_px == 4:
+    if args.raster:
+        from paper_2606_11390_gb300 import autotune
+
+        c = autotune.parse_name(args.raster)
+        raster_kw = autotune.step_kwargs(c)
+        tile = raster_kw["tile"]
+        tune = {"choice": autotune.name(c), "ms": {}}
+    elif not args.no_tune and not args.tile and args.raster_px == 4:
         # the rasteriser configuration (tile shape, pixels per thread, splats
         # per batch) from the autotuner, timed on this GPU for this workload
         from paper_2606_11390_gb300 import autotune

@@ -74,6 +74,15 @@ def name(c: dict) -> str:
     return f"{c['tile'][0]}x{c['tile'][1]}/{c['ppt']}px/f{c['batch_fwd']}/b{c['batch_bwd']}"
 
 
+def parse_name(label: str) -> dict:
+    """The configuration a name() label describes, e.g. 32x16/4px/f128/b256."""
+    t, px, f, b = label.split("/")
+    tw, th = (int(x) for x in t.split("x"))
+    if not px.endswith("px") or not f.startswith("f") or not b.startswith("b"):
+        raise ValueError(f"bad rasteriser configuration {label!r}")
+    return {"tile": (tw, th), "ppt": int(px[:-2]), "batch_fwd": int(f[1:]), "batch_bwd": int(b[1:])}
+
+
 def tile_candidates(tiles=TILES):
     """(tile, pixels per thread) pairs at the default batch sizes."""
     out = []

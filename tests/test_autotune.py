@@ -62,3 +62,11 @@ def test_step_kwargs():
 def test_library_digest_is_stable():
     pytest.importorskip("hashlib")
     assert autotune.library_digest() == autotune.library_digest()
+
+
+def test_names_round_trip():
+    for c in autotune.tile_candidates():
+        c = dict(c, batch_fwd=128, batch_bwd=256)
+        assert autotune.parse_name(autotune.name(c)) == c
+    with pytest.raises(ValueError):
+        autotune.parse_name("32x16/4/f128/b256")
