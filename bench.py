@@ -606,9 +606,26 @@ def kernel_digest(kernel):
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel, workload):
+def raster_variant(stage, cfg):
+    """Template instance the rasteriser stage launches under a step
+    configuration, e.g. raster_bwd<32,16,4,256> (tile, pixels per thread,
+    splats per batch; a batch of 0 resolves to the kernel's default)."""
+    from paper_2606_11390_gb300 import _native as gs
+
+    tw, th = int(cfg["tile_w"]), int(cfg["tile_h"])
+    ppt = 2 if (tw, th) == (8, 8) or int(cfg.get("flags", 0)) & gs.GS_FLAG_RASTER_2PX else 4
+    nt = tw * th // ppt
+    if stage == "raster_fwd":
+        batch = int(cfg.get("raster_batch_fwd", 0)) or (nt if nt > 128 else 128)
+    else:
+        batch = int(cfg.get("raster_batch_bwd", 0)) or min(max(nt, 64), 256)
+    return f"{stage}<{tw},{th},{ppt},{batch}>"
+
+
+def recorded_traffic(kernel, workload, variant=None):
     """DRAM bytes per launch of `kernel` on `workload` from profiles/dram_traffic.json,
-    if they were captured from the kernel's current sources; else None."""
+    if they were captured from the kernel's current sources (and, where the
+    entry names one, the same template instance); else None."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(p) as f:
@@ -617,6 +634,8 @@ def recorded_traffic(kernel, workload):
         return None
     e = d.get(f"{kernel}|{workload}")
     if not e or kernel not in KERNEL_SOURCES or e.get("digest") != kernel_digest(kernel):
+        return None
+    if variant is not None and e.get("variant") not in (None, variant):
         return None
     return e.get("bytes_per_launch")
 
@@ -644,7 +663,8 @@ def roofline_for(stage, ms, step, peaks, src, workload, pc=None):
     import torch
 
     N, V, I, P = step.N, step.cams.V, step.n_isect(), step.cams.n_pixels
-    traffic = recorded_traffic(stage, workload)
+    variant = raster_variant(stage, step.cfg) if stage in FLOP_PER_PAIR else None
+    traffic = recorded_traffic(stage, workload, variant)
     if stage in FLOP_PER_PAIR:
         pc = pc if pc is not None else pair_counts(step)
         flops, work = raster_work(stage, pc)
@@ -652,7 +672,7 @@ def roofline_for(stage, ms, step, peaks, src, workload, pc=None):
         n_sm = torch.cuda.get_device_properties(0).multi_processor_count
         peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
         achieved = flops / (ms * 1e-3) / 1e12
-        return {"kernel": stage, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+        return {"kernel": stage, "variant": variant, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz ({src} max SM clock; no measured FP32 peak)",
                 "work": work, "flop": flops, "ms": ms}
