@@ -98,10 +98,11 @@ typedef struct gs_camera {
  * raster_batch_fwd / raster_batch_bwd: splats the rasteriser stages per
  * shared-memory batch in the forward / backward, 0 for the default
  * (forward: max(threads per tile, 128); backward: threads per tile, clamped
- * to [64, 256]) or one of 64, 128, 256 (GS_ERR_UNSUPPORTED otherwise); a
- * performance choice only, results are the same (with a non-zero bg the
- * backward keeps its default). Threads per tile = tile_w * tile_h / pixels
- * per thread (see GS_FLAG_RASTER_2PX). */
+ * to [64, 256]) or one of 64, 128, 256, 512 (GS_ERR_UNSUPPORTED otherwise;
+ * the backward takes 512 only for tiles of at most 128 threads, whose shared
+ * memory it fits); a performance choice only, results are the same (with a
+ * non-zero bg the backward keeps its default). Threads per tile = tile_w *
+ * tile_h / pixels per thread (see GS_FLAG_RASTER_2PX). */
 typedef struct gs_config {
   int32_t tile_w, tile_h, sh_degree, flags;
   float near_plane, far_plane, eps2d, alpha_cap, alpha_min, t_stop;

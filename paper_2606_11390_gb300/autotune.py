@@ -5,12 +5,13 @@ rasteriser's launch configuration:
 - tile shape (8x8, 16x16, 32x16, 32x32) together with the pixels each thread
   owns (2 or 4, so threads per tile = tile area / pixels per thread; 8x8 tiles
   take 2 only);
-- splats staged per shared-memory batch in the forward (64, 128, 256);
-- splats staged per shared-memory batch in the backward (64, 128, 256).
+- splats staged per shared-memory batch in the forward (64, 128, 256, 512);
+- splats staged per shared-memory batch in the backward (64, 128, 256, and
+  512 for tiles of at most 128 threads).
 The search is coordinate descent: every tile shape and pixels per thread at
 the default batch sizes, then the forward batch at the best of those, then
-the backward batch; 13 timed configurations instead of the 63 of the full
-product. Each is timed as the whole captured training step. Every
+the backward batch; at most 15 timed configurations instead of the 150 of
+the full product. Each is timed as the whole captured training step. Every
 configuration produces the same image (tests/test_gpu_raster_variants.py),
 so the choice is about time only.
 
@@ -28,7 +29,7 @@ import os
 import numpy as np
 
 TILES = ((16, 16), (8, 8), (32, 16), (32, 32))
-BATCHES = (64, 128, 256)
+BATCHES = (64, 128, 256, 512)
 
 
 def _cache_path():
@@ -92,6 +93,16 @@ def tile_candidates(tiles=TILES):
     return out
 
 
+def threads_per_tile(c: dict) -> int:
+    return c["tile"][0] * c["tile"][1] // c["ppt"]
+
+
+def batch_supported(c: dict, dim: str, b: int) -> bool:
+    """Whether the library has the variant: a 512-splat backward batch only
+    fits the shared memory of tiles of at most 128 threads."""
+    return not (dim == "batch_bwd" and b == 512 and threads_per_tile(c) > 128)
+
+
 def search(measure, tiles=TILES, batches=BATCHES):
     """Coordinate descent over the configuration space with measure(config) ->
     ms; returns (best config, {label: ms} of every configuration timed)."""
@@ -105,7 +116,7 @@ def search(measure, tiles=TILES, batches=BATCHES):
 
     best = min(tile_candidates(tiles), key=timed)
     for dim in ("batch_fwd", "batch_bwd"):
-        cands = [best] + [dict(best, **{dim: b}) for b in batches]
+        cands = [best] + [dict(best, **{dim: b}) for b in batches if batch_supported(best, dim, b)]
         best = min(cands, key=timed)
     return best, times
 

@@ -138,50 +138,100 @@ __device__ __forceinline__ uint64_t block_scan_lookback(uint64_t local, uint32_t
 // With depth_keys (float bits of each record's depth, 0 for a culled record,
 // as gs_project writes them) the kernel reads 4 coalesced bytes per record;
 // without, the tile counts and a gather of the depth from each 48-byte
-// projected record.
+// projected record. Items are striped (item i of thread (warp, lane) is
+// record i * 256 + warp * 32 + lane of the tile), so a warp reads 32
+// consecutive records and writes its visible ones to consecutive positions:
+// the position is the tile's prefix, plus the visible counts of the (item,
+// warp) groups before it in record order, plus the lane's rank in its
+// group's ballot. The two high depth digits take few distinct values (the
+// exponent byte of a positive float is nearly constant over a scene), so
+// their histogram updates are aggregated per warp (one atomic per distinct
+// digit); the two low digits are spread and take one atomic per record.
 __global__ void __launch_bounds__(kScanThreads) compact_visible_kernel(
     const uint32_t* __restrict__ counts, const float* __restrict__ projected, const uint32_t* __restrict__ depth_keys,
     int64_t n, uint32_t index_base, ScanState st, uint32_t* __restrict__ dkeys, uint32_t* __restrict__ dvals,
     uint32_t* __restrict__ hist, int64_t* n_visible, int32_t* status) {
+  constexpr int kWarps = kScanThreads / 32;
+  static_assert(kScanItems <= 32 && (kScanItems * kWarps) % 32 == 0, "item bits in one word; offsets split over a warp");
   __shared__ uint32_t s_tile;
-  __shared__ uint64_t s_warp[kScanThreads / 32];
+  __shared__ uint64_t s_warp[kWarps];
   __shared__ uint64_t s_prefix;
+  __shared__ uint32_t s_off[kScanItems * kWarps];  // visible count, then exclusive offset, of each (item, warp)
+  __shared__ uint32_t s_total;
   __shared__ uint32_t s_hist[kDepthPasses][kRadix];
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < kDepthPasses * kRadix; i += kScanThreads) (&s_hist[0][0])[i] = 0;
   if (tid == 0) s_tile = atomicAdd(st.ticket, 1u);
   __syncthreads();
   const uint32_t t = s_tile;
-  const int64_t base = static_cast<int64_t>(t) * kScanTile + static_cast<int64_t>(tid) * kScanItems;
+  const int64_t base = static_cast<int64_t>(t) * kScanTile + warp * 32 + lane;  // item i: base + i * kScanThreads
   uint32_t vis = 0;  // bit i: item i visible
   uint32_t dkey[kScanItems];
-  if (depth_keys) {
-#pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-      dkey[i] = base + i < n ? depth_keys[base + i] : 0u;
-      if (dkey[i] != 0u) vis |= 1u << i;
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-      dkey[i] = 0u;
-      if (base + i < n && counts[base + i] > 0) vis |= 1u << i;
-    }
-  }
-  const uint64_t pos0 = block_scan_lookback(__popc(vis), t, st, s_warp, &s_prefix, status);
-  uint64_t pos = pos0;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
-    if (vis & (1u << i)) {
-      const uint32_t d = depth_keys ? dkey[i] : __float_as_uint(projected[(base + i) * kRecordFloats + 6]);
-      dkeys[pos] = d;
-      dvals[pos] = index_base + static_cast<uint32_t>(base + i);
+    const int64_t r = base + static_cast<int64_t>(i) * kScanThreads;
+    bool v;
+    if (depth_keys) {
+      dkey[i] = r < n ? depth_keys[r] : 0u;
+      v = dkey[i] != 0u;
+    } else {
+      dkey[i] = 0u;
+      v = r < n && counts[r] > 0;
+    }
+    const uint32_t bal = __ballot_sync(0xffffffffu, v);
+    if (v) vis |= 1u << i;
+    if (lane == 0) s_off[i * kWarps + warp] = __popc(bal);
+  }
+  // the tile's global prefix (in s_prefix; the thread-order offset is unused)
+  (void)block_scan_lookback(__popc(vis), t, st, s_warp, &s_prefix, status);
+  if (warp == 0) {
+    // exclusive scan of the (item, warp) counts in record order
+    constexpr int kPer = kScanItems * kWarps / 32;
+    uint32_t c[kPer], sum = 0;
 #pragma unroll
-      for (int p = 0; p < kDepthPasses; ++p) atomicAdd(&s_hist[p][(d >> (8 * p)) & 0xffu], 1u);
-      ++pos;
+    for (int k = 0; k < kPer; ++k) {
+      c[k] = s_off[lane * kPer + k];
+      sum += c[k];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t nb = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += nb;
+    }
+    uint32_t run = incl - sum;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      s_off[lane * kPer + k] = run;
+      run += c[k];
+    }
+    if (lane == 31) s_total = incl;
+  }
+  __syncthreads();
+  const uint64_t tile_prefix = s_prefix;
+  const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const uint32_t bal = __ballot_sync(0xffffffffu, (vis >> i) & 1u);
+    if ((vis >> i) & 1u) {
+      const int64_t r = base + static_cast<int64_t>(i) * kScanThreads;
+      const uint32_t d = depth_keys ? dkey[i] : __float_as_uint(projected[r * kRecordFloats + 6]);
+      const uint64_t pos = tile_prefix + s_off[i * kWarps + warp] + __popc(bal & lt);
+      dkeys[pos] = d;
+      dvals[pos] = index_base + static_cast<uint32_t>(r);
+      atomicAdd(&s_hist[0][d & 0xffu], 1u);
+      atomicAdd(&s_hist[1][(d >> 8) & 0xffu], 1u);
+#pragma unroll
+      for (int p = 2; p < kDepthPasses; ++p) {
+        const uint32_t dp = (d >> (8 * p)) & 0xffu;
+        const uint32_t peers = __match_any_sync(bal, dp);
+        if (lane == __ffs(peers) - 1) atomicAdd(&s_hist[p][dp], static_cast<uint32_t>(__popc(peers)));
+      }
     }
   }
-  if (n > 0 && base <= n - 1 && n - 1 < base + kScanItems) *n_visible = static_cast<int64_t>(pos);
+  const int64_t tile_start = static_cast<int64_t>(t) * kScanTile;
+  if (tid == 0 && n > 0 && tile_start <= n - 1 && n - 1 < tile_start + kScanTile)
+    *n_visible = static_cast<int64_t>(tile_prefix + s_total);
   __syncthreads();
   for (int i = tid; i < kDepthPasses * kRadix; i += kScanThreads) {
     const uint32_t c = (&s_hist[0][0])[i];

@@ -27,7 +27,13 @@ inline int pixels_per_thread(const Layout& L, const Consts& K) {
 }
 
 // 0 (the default) or a batch size the kernels are instantiated for.
-inline bool valid_batch(int32_t b) { return b == 0 || b == 64 || b == 128 || b == 256; }
+inline bool valid_batch(int32_t b) { return b == 0 || b == 64 || b == 128 || b == 256 || b == 512; }
+
+// The backward's 512-splat batch exists only for layouts whose shared memory
+// it fits (at most 4 warps per tile).
+inline bool bwd_batch_fits(const Layout& L, int ppt, int32_t b) {
+  return b != 512 || rast::bwd_smem_bytes(512, L.tile_w * L.tile_h / ppt / 32) <= rast::kStaticSmem;
+}
 
 template <int TW, int TH, int PPT>
 int fwd_variant(int32_t batch, bool count, const FwdArgs& a, cudaStream_t s) {
@@ -38,6 +44,7 @@ int fwd_variant(int32_t batch, bool count, const FwdArgs& a, cudaStream_t s) {
   if (b == 64) return rast::launch_fwd<TW, TH, PPT, 64, false>(a, s);
   if (b == 128) return rast::launch_fwd<TW, TH, PPT, 128, false>(a, s);
   if (b == 256) return rast::launch_fwd<TW, TH, PPT, 256, false>(a, s);
+  if (b == 512) return rast::launch_fwd<TW, TH, PPT, 512, false>(a, s);
   return GS_ERR_UNSUPPORTED;
 }
 
@@ -52,6 +59,9 @@ int bwd_variant(int32_t batch, bool bg, bool count, const BwdArgs& a, cudaStream
   if (b == 64) return rast::launch_bwd<TW, TH, PPT, 64, false, false>(a, s);
   if (b == 128) return rast::launch_bwd<TW, TH, PPT, 128, false, false>(a, s);
   if (b == 256) return rast::launch_bwd<TW, TH, PPT, 256, false, false>(a, s);
+  if constexpr (rast::bwd_smem_bytes(512, TW * TH / PPT / 32) <= rast::kStaticSmem) {
+    if (b == 512) return rast::launch_bwd<TW, TH, PPT, 512, false, false>(a, s);
+  }
   return GS_ERR_UNSUPPORTED;
 }
 
@@ -118,8 +128,9 @@ int rasterize_bwd_pixels_impl(const float* projected, const uint32_t* vals, cons
   if (!aligned16(projected) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7u)) return GS_ERR_ARG;
   if (counts && (reinterpret_cast<uintptr_t>(counts) & 7u)) return GS_ERR_ARG;
   if (cull && (reinterpret_cast<uintptr_t>(cull) & 1u)) return GS_ERR_ARG;
-  if (!valid_batch(cfg->raster_batch_bwd)) return GS_ERR_UNSUPPORTED;
   a.K = make_consts(*cfg);
+  if (!valid_batch(cfg->raster_batch_bwd) || !bwd_batch_fits(a.L, pixels_per_thread(a.L, a.K), cfg->raster_batch_bwd))
+    return GS_ERR_UNSUPPORTED;
   if (cudaMemsetAsync(d_projected, 0, sizeof(float) * kDRecordFloats * static_cast<size_t>(N) * V, stream) !=
       cudaSuccess)
     return GS_ERR_CUDA;

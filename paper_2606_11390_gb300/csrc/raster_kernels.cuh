@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(TW* TH / PPT, 1024 / (TW * TH / PPT)) raster_f
   using G = Geo<TW, TH, PPT>;
   constexpr int NT = G::NT;
   static_assert(B >= 32 && B <= 512 && (B & (B - 1)) == 0, "splats per batch: a power of two in [32, 512]");
-  static_assert(B * (40 + 2 * G::NW) <= 48 * 1024, "forward shared memory over 48 KB");
+  static_assert(fwd_smem_bytes(B, G::NW) <= kStaticSmem, "forward shared memory over 48 KB");
   __shared__ float4 s_a[B];
   __shared__ float4 s_b[B];
   __shared__ float s_c[B];
@@ -577,7 +577,7 @@ __global__ void GS_RBWD_BOUNDS(TW* TH / PPT) raster_bwd_kernel(
   using Gm = Geo<TW, TH, PPT>;
   constexpr int NT = Gm::NT, NW = Gm::NW;
   static_assert(B >= 32 && B <= 512 && (B & (B - 1)) == 0, "splats per batch: a power of two in [32, 512]");
-  static_assert(B * (80 + 2 * NW) + 4 * NW <= 48 * 1024, "backward shared memory over 48 KB");
+  static_assert(bwd_smem_bytes(B, NW) <= kStaticSmem, "backward shared memory over 48 KB");
   __shared__ float4 s_a[B];
   __shared__ float4 s_b[B];
   __shared__ float s_c[B];

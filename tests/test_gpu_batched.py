@@ -108,14 +108,17 @@ def test_tuned_step_equals_default(R, px, batch):
 
 
 def test_autotuner_on_the_gpu(R, tmp_path, monkeypatch):
-    """best_config times its 13 configurations, returns one of them and
-    caches it under the library digest; a second call reads the cache."""
+    """best_config times its configurations (7 tile / pixel choices, 4
+    forward batches, the backward batches the chosen tile has), returns one
+    of them and caches it under the library digest; a second call reads the
+    cache."""
     from paper_2606_11390_gb300 import autotune
 
     monkeypatch.setenv("GS_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
     s = _scene()
     best, times = autotune.best_config(s, steps=1)
-    assert len(times) == 13 and autotune.name(best) in times
+    n_bwd = sum(autotune.batch_supported(best, "batch_bwd", b) for b in autotune.BATCHES)
+    assert len(times) == 7 + len(autotune.BATCHES) + n_bwd and autotune.name(best) in times
     assert times[autotune.name(best)] == min(times.values())
     again, times2 = autotune.best_config(s, steps=1)
     assert again == best and times2 == times
