@@ -19,9 +19,11 @@
 // cannot touch its pixels. Skipped pairs are pairs the compositing rule would
 // skip anyway, so the result is unchanged. The per-pixel step has no
 // branches: every lane evaluates the splat and the decisions select, so a
-// thread's pixels interleave. The per-pair arithmetic is written with
-// explicitly rounded operations and a fixed ex2.approx so that the backward
-// recomputes bit-identical alphas and takes exactly the forward's skip / stop
+// thread's pixels interleave; the forward steps them two at a time in packed
+// f32x2 operations (one issue slot for two pixels' adds, multiplies and
+// FMAs). The per-pair arithmetic is written with explicitly rounded
+// operations and a fixed ex2.approx so that the backward recomputes
+// bit-identical alphas and takes exactly the forward's skip / stop
 // decisions. The backward walks the list in reverse, each warp from the
 // largest `last` among its pixels, recovers T_k = T_{k+1} / (1 - alpha_k) from
 // the stored final T, sums a splat's 9 gradient values over the thread's
@@ -197,50 +199,59 @@ __device__ __forceinline__ uint32_t warp_cull_mask(const float4& a, const float4
   return mask;
 }
 
-struct PixelFwd {
-  float T, c0, c1, c2;
-  float thr;      // alpha threshold: alpha_min while compositing, +inf once stopped or outside the image
-  uint32_t last;
-};
-
-// One compositing step of one pixel (forward rule), without branches: every
-// lane evaluates the splat and the decisions select what changes, so the
+// One compositing step (forward rule) for two pixels of a thread, rows r and
+// r + 1 of its column, in f32x2 operations: the .x lanes carry the first
+// pixel, the .y lanes the second. The step has no branches: every lane
+// evaluates the splat and the decisions select what changes, so the
 // compiler can interleave the independent pixels of a thread (a branch only
 // saves issue slots when all 32 lanes agree, which a partly covered block
 // rarely does). Adding w = 0 leaves the colour unchanged bit for bit. A pixel
 // that has stopped (or lies outside the image) carries an infinite alpha
-// threshold, so no later splat passes its test.
-// The splat's exponent and alpha at one pixel (independent of the pixel state).
-__device__ __forceinline__ void splat_alpha(const SplatCol& col, float py, const float4& a, const float4& b, float cap,
-                                            float& e, float& alpha) {
-  float dy;
-  e = splat_exponent(col, py, a, b.x, dy);
-  alpha = fminf(cap, __fmul_rn(b.y, ex2_approx(e)));
+// threshold, so no later splat passes its test. A packed add, multiply or
+// FMA rounds each lane as __fadd_rn / __fmul_rn / __fmaf_rn does, and a
+// subtraction x - y is formed as fma(y, -1, x), which rounds the exact
+// difference once as __fsub_rn does: each lane's exponent and alpha are the
+// bits splat_exponent and the backward's scalar steps compute, so the
+// backward recomputes the forward's decisions exactly. The splat's constants
+// enter as broadcast pairs (no extra instructions), and a packed operation
+// takes one issue slot for two lanes' work.
+struct PixelFwd2 {
+  float2 T, c0, c1, c2;
+  float2 thr;  // alpha threshold: alpha_min while compositing, +inf once stopped or outside the image
+  uint32_t last0, last1;
+};
+
+__device__ __forceinline__ float2 bc2(float x) { return make_float2(x, x); }
+
+// The splat's exponent and alpha at both pixels (independent of the pixel state).
+__device__ __forceinline__ void splat_alpha2(const SplatCol& col, float2 py, const float4& a, const float4& b,
+                                             float cap, float2& e, float2& alpha) {
+  const float2 dy = __ffma2_rn(bc2(a.y), bc2(-1.0f), py);
+  e = __ffma2_rn(dy, __ffma2_rn(bc2(b.x), dy, bc2(col.bdx)), bc2(col.adx2));
+  const float2 oG = __fmul2_rn(bc2(b.y), make_float2(ex2_approx(e.x), ex2_approx(e.y)));
+  alpha = make_float2(fminf(cap, oG.x), fminf(cap, oG.y));
 }
 
-// The compositing decisions and update of one pixel for a splat with
-// exponent e and alpha.
-__device__ __forceinline__ bool composite_apply(PixelFwd& P, float e, float alpha, const float4& b, float cb,
+// The compositing decisions and update of both pixels for a splat with
+// exponents e and alphas alpha; returns how many of the two took it.
+__device__ __forceinline__ int composite_apply2(PixelFwd2& P, float2 e, float2 alpha, const float4& b, float cb,
                                                 uint32_t rel, float tstop) {
-  const float Tn = __fmul_rn(P.T, __fsub_rn(1.0f, alpha));
-  const bool ok = !(e > 0.0f) && !(alpha < P.thr);
-  const bool stop = ok && Tn < tstop;
-  const bool take = ok && !stop;
-  const float w = take ? __fmul_rn(alpha, P.T) : 0.0f;
-  P.c0 = __fmaf_rn(b.z, w, P.c0);
-  P.c1 = __fmaf_rn(b.w, w, P.c1);
-  P.c2 = __fmaf_rn(cb, w, P.c2);
-  P.T = take ? Tn : P.T;
-  P.last = take ? rel + 1 : P.last;
-  P.thr = stop ? __int_as_float(0x7f800000) : P.thr;
-  return take;
-}
-
-__device__ __forceinline__ bool composite_step(PixelFwd& P, const SplatCol& col, float py, const float4& a,
-                                               const float4& b, float cb, uint32_t rel, float cap, float tstop) {
-  float e, alpha;
-  splat_alpha(col, py, a, b, cap, e, alpha);
-  return composite_apply(P, e, alpha, b, cb, rel, tstop);
+  const float2 Tn = __fmul2_rn(P.T, __ffma2_rn(alpha, bc2(-1.0f), bc2(1.0f)));
+  const float2 w = __fmul2_rn(alpha, P.T);
+  const bool ok0 = !(e.x > 0.0f) && !(alpha.x < P.thr.x);
+  const bool ok1 = !(e.y > 0.0f) && !(alpha.y < P.thr.y);
+  const bool stop0 = ok0 && Tn.x < tstop, stop1 = ok1 && Tn.y < tstop;
+  const bool take0 = ok0 && !stop0, take1 = ok1 && !stop1;
+  const float2 ws = make_float2(take0 ? w.x : 0.0f, take1 ? w.y : 0.0f);
+  P.c0 = __ffma2_rn(bc2(b.z), ws, P.c0);
+  P.c1 = __ffma2_rn(bc2(b.w), ws, P.c1);
+  P.c2 = __ffma2_rn(bc2(cb), ws, P.c2);
+  P.T = make_float2(take0 ? Tn.x : P.T.x, take1 ? Tn.y : P.T.y);
+  P.last0 = take0 ? rel + 1 : P.last0;
+  P.last1 = take1 ? rel + 1 : P.last1;
+  const float kInf = __int_as_float(0x7f800000);
+  P.thr = make_float2(stop0 ? kInf : P.thr.x, stop1 ? kInf : P.thr.y);
+  return static_cast<int>(take0) + static_cast<int>(take1);
 }
 
 // Pair counters of the COUNT variants, per thread, added once per warp to
@@ -303,14 +314,19 @@ __global__ void __launch_bounds__(TW* TH / PPT, 1024 / (TW * TH / PPT)) raster_f
   const float cap = K.alpha_cap, amin = K.alpha_min, tstop = K.t_stop;
   const float tx0 = static_cast<float>(tx * TW), ty0 = static_cast<float>(ty * TH);
   const float kInf = __int_as_float(0x7f800000);
-  PixelFwd P[PPT];
+  static_assert(PPT % 2 == 0, "pixels are stepped in pairs");
+  constexpr int NP = PPT / 2;
+  PixelFwd2 P[NP];
+  float2 py2[NP];  // pixel centres of each pair's rows
   PairCount pc;
   bool all_done = true;
 #pragma unroll
-  for (int r = 0; r < PPT; ++r) {
-    const bool inside = x < W && y0 + r * G::RS < H;
-    P[r] = PixelFwd{1.0f, 0.0f, 0.0f, 0.0f, inside ? amin : kInf, 0u};
-    all_done = all_done && !inside;
+  for (int k = 0; k < NP; ++k) {
+    const bool in0 = x < W && y0 + 2 * k * G::RS < H, in1 = x < W && y0 + (2 * k + 1) * G::RS < H;
+    P[k] = PixelFwd2{bc2(1.0f), bc2(0.0f), bc2(0.0f), bc2(0.0f), make_float2(in0 ? amin : kInf, in1 ? amin : kInf),
+                     0u, 0u};
+    py2[k] = make_float2(py0 + static_cast<float>(2 * k * G::RS), py0 + static_cast<float>((2 * k + 1) * G::RS));
+    all_done = all_done && !in0 && !in1;
   }
   for (int b0 = 0; b0 < n; b0 += B) {
     if (__syncthreads_count(all_done) == NT) break;
@@ -340,14 +356,14 @@ __global__ void __launch_bounds__(TW* TH / PPT, 1024 / (TW * TH / PPT)) raster_f
     __syncwarp();
     int q = 0;
 #ifndef GS_FWD_GROUP
-#define GS_FWD_GROUP 3
+#define GS_FWD_GROUP 4
 #endif
     // GS_FWD_GROUP splats per iteration: their exponents / alphas are
     // independent of the pixel state and are issued first; the compositing
     // then applies them in list order
     constexpr int GR = GS_FWD_GROUP;
     for (; q + GR - 1 < nl && !all_done; q += GR) {
-      float e[GR][PPT], al[GR][PPT];
+      float2 e[GR][NP], al[GR][NP];
       int js[GR];
 #pragma unroll
       for (int u = 0; u < GR; ++u) {
@@ -355,20 +371,20 @@ __global__ void __launch_bounds__(TW* TH / PPT, 1024 / (TW * TH / PPT)) raster_f
         const float4 a = s_a[js[u]], b = s_b[js[u]];
         const SplatCol col = splat_column(px, a);
 #pragma unroll
-        for (int r = 0; r < PPT; ++r) splat_alpha(col, py0 + static_cast<float>(r * G::RS), a, b, cap, e[u][r], al[u][r]);
+        for (int k = 0; k < NP; ++k) splat_alpha2(col, py2[k], a, b, cap, e[u][k], al[u][k]);
       }
       all_done = true;
 #pragma unroll
-      for (int r = 0; r < PPT; ++r) {
+      for (int k = 0; k < NP; ++k) {
 #pragma unroll
         for (int u = 0; u < GR; ++u) {
           const float4 b = s_b[js[u]];
-          if constexpr (COUNT) pc.ev += P[r].thr != kInf;
-          const bool took =
-              composite_apply(P[r], e[u][r], al[u][r], b, s_c[js[u]], static_cast<uint32_t>(b0 + js[u]), tstop);
+          if constexpr (COUNT) pc.ev += (P[k].thr.x != kInf) + (P[k].thr.y != kInf);
+          const int took =
+              composite_apply2(P[k], e[u][k], al[u][k], b, s_c[js[u]], static_cast<uint32_t>(b0 + js[u]), tstop);
           if constexpr (COUNT) pc.co += took;
         }
-        all_done = all_done && P[r].thr == kInf;
+        all_done = all_done && P[k].thr.x == kInf && P[k].thr.y == kInf;
       }
       if constexpr (COUNT) pc.ex += GR * PPT;
     }
@@ -381,11 +397,13 @@ __global__ void __launch_bounds__(TW* TH / PPT, 1024 / (TW * TH / PPT)) raster_f
       const SplatCol col = splat_column(px, a);
       all_done = true;
 #pragma unroll
-      for (int r = 0; r < PPT; ++r) {
-        if constexpr (COUNT) pc.ev += P[r].thr != kInf;
-        const bool took = composite_step(P[r], col, py0 + static_cast<float>(r * G::RS), a, b, cb, rel, cap, tstop);
+      for (int k = 0; k < NP; ++k) {
+        if constexpr (COUNT) pc.ev += (P[k].thr.x != kInf) + (P[k].thr.y != kInf);
+        float2 e, al;
+        splat_alpha2(col, py2[k], a, b, cap, e, al);
+        const int took = composite_apply2(P[k], e, al, b, cb, rel, tstop);
         if constexpr (COUNT) pc.co += took;
-        all_done = all_done && P[r].thr == kInf;
+        all_done = all_done && P[k].thr.x == kInf && P[k].thr.y == kInf;
       }
       if constexpr (COUNT) pc.ex += PPT;
     }
@@ -399,11 +417,15 @@ __global__ void __launch_bounds__(TW* TH / PPT, 1024 / (TW * TH / PPT)) raster_f
     const int yy = y0 + r * G::RS;
     if (x < W && yy < H) {
       const size_t p = pb + static_cast<size_t>(yy) * W + x;
-      const float c[3] = {P[r].c0 + P[r].T * K.bg[0], P[r].c1 + P[r].T * K.bg[1], P[r].c2 + P[r].T * K.bg[2]};
+      const PixelFwd2& Q = P[r / 2];
+      const bool hi = r & 1;
+      const float T = hi ? Q.T.y : Q.T.x;
+      const float c[3] = {(hi ? Q.c0.y : Q.c0.x) + T * K.bg[0], (hi ? Q.c1.y : Q.c1.x) + T * K.bg[1],
+                          (hi ? Q.c2.y : Q.c2.x) + T * K.bg[2]};
 #pragma unroll
       for (int k = 0; k < 3; ++k) image[3 * p + k] = c[k];
-      final_T[p] = P[r].T;
-      last[p] = P[r].last;
+      final_T[p] = T;
+      last[p] = hi ? Q.last1 : Q.last0;
       if (with_loss) {
         // the L1 + L2 image loss of these values (same arithmetic as gs_image_loss)
 #pragma unroll
@@ -505,12 +527,15 @@ __device__ __forceinline__ int slot18_of_lane(int lane) {
   return h0 ? w[1] : w[0];
 }
 
-struct PixelBwd {
+// Two pixels of a thread (rows r and r + 1 of its column) in the backward,
+// stepped together in f32x2 operations as in the forward (.x: the first
+// pixel, .y: the second).
+struct PixelBwd2 {
   // S = (colour accumulated behind the current entry, normalised) . dL/dC:
   // the alpha gradient needs the accumulated colour only through this dot
   // product, so one scalar replaces the three channels
-  float T, g0, g1, g2, gbg, S;
-  uint32_t last;
+  float2 T, g0, g1, g2, gbg, S;
+  uint32_t last0, last1;
 };
 
 // Backward contribution of splat (a, b, cb) at relative position `rel` to one
@@ -532,40 +557,74 @@ __device__ __forceinline__ void finish_geometry(float gv[9], const SplatCol& col
   gv[4] = m2;
 }
 
-template <bool BG>
-__device__ __forceinline__ bool pixel_grad(PixelBwd& P, const SplatCol& col, float py, const float4& a,
-                                           const float4& b, float cb, uint32_t rel, float cap, float amin,
-                                           float gv[9]) {
+// The backward step of both pixels of a PixelBwd2 for one splat, adding
+// into gv[9] (per pixel, in .x / .y); returns whether either took part.
+// Exponent and alpha are the forward's bits (same packed operations), so
+// the skip / stop decisions are the forward's.
+template <bool BG, bool COUNT>
+__device__ __forceinline__ bool pixel_grad2(PixelBwd2& P, const SplatCol& col, float2 py, const float4& a,
+                                            const float4& b, float cb, uint32_t rel, float cap, float amin,
+                                            float2 gv[9], PairCount& pc) {
   // branch-free, like the forward step: decisions select, zeros add nothing
-  float dy;
-  const float e = splat_exponent(col, py, a, b.x, dy);
-  const float G = ex2_approx(e);
-  const float oG = __fmul_rn(b.y, G);
-  const float alpha = fminf(cap, oG);
-  const bool ok = rel < P.last && !(e > 0.0f) && !(alpha < amin);
-  const float inv = rcp_approx(__fsub_rn(1.0f, alpha));
-  P.T = ok ? P.T * inv : P.T;  // transmittance in front of this entry
-  const float aok = ok ? alpha : 0.0f;
-  const float w = aok * P.T;
-  gv[5] += w * P.g0;
-  gv[6] += w * P.g1;
-  gv[7] += w * P.g2;
+  const float2 dy = __ffma2_rn(bc2(a.y), bc2(-1.0f), py);
+  const float2 e = __ffma2_rn(dy, __ffma2_rn(bc2(b.x), dy, bc2(col.bdx)), bc2(col.adx2));
+  const float2 G = make_float2(ex2_approx(e.x), ex2_approx(e.y));
+  const float2 oG = __fmul2_rn(bc2(b.y), G);
+  const float2 al = make_float2(fminf(cap, oG.x), fminf(cap, oG.y));
+  const bool in0 = rel < P.last0, in1 = rel < P.last1;
+  const bool ok0 = in0 && !(e.x > 0.0f) && !(al.x < amin);
+  const bool ok1 = in1 && !(e.y > 0.0f) && !(al.y < amin);
+  if constexpr (COUNT) {
+    pc.ev += static_cast<uint32_t>(in0) + static_cast<uint32_t>(in1);
+    pc.co += static_cast<uint32_t>(ok0) + static_cast<uint32_t>(ok1);
+  }
+  const float2 om = __ffma2_rn(al, bc2(-1.0f), bc2(1.0f));
+  const float2 inv = make_float2(rcp_approx(om.x), rcp_approx(om.y));
+  const float2 Ti = __fmul2_rn(P.T, inv);
+  P.T = make_float2(ok0 ? Ti.x : P.T.x, ok1 ? Ti.y : P.T.y);  // transmittance in front of this entry
+  const float2 aok = make_float2(ok0 ? al.x : 0.0f, ok1 ? al.y : 0.0f);
+  const float2 w = __fmul2_rn(aok, P.T);
+  gv[5] = __ffma2_rn(w, P.g0, gv[5]);
+  gv[6] = __ffma2_rn(w, P.g1, gv[6]);
+  gv[7] = __ffma2_rn(w, P.g2, gv[7]);
   // (c - accumulated) . dL/dC = c . dL/dC - S
-  const float dcs = fmaf(cb, P.g2, fmaf(b.w, P.g1, b.z * P.g0)) - P.S;
+  const float2 cd = __ffma2_rn(bc2(cb), P.g2, __ffma2_rn(bc2(b.w), P.g1, __fmul2_rn(bc2(b.z), P.g0)));
+  const float2 dcs = __ffma2_rn(P.S, bc2(-1.0f), cd);
   // with a zero background (the default) the background term vanishes
-  const float dalpha = BG ? P.T * dcs - P.gbg * inv : P.T * dcs;
-  P.S = fmaf(aok, dcs, P.S);
-  const float da = (ok && !(oG > cap)) ? dalpha : 0.0f;
-  gv[8] += da * G;
+  float2 dal = __fmul2_rn(P.T, dcs);
+  if constexpr (BG) dal = __ffma2_rn(__fmul2_rn(P.gbg, bc2(-1.0f)), inv, dal);
+  P.S = __ffma2_rn(aok, dcs, P.S);
+  const float2 da = make_float2((ok0 && !(oG.x > cap)) ? dal.x : 0.0f, (ok1 && !(oG.y > cap)) ? dal.y : 0.0f);
+  gv[8] = __ffma2_rn(da, G, gv[8]);
   // The geometric sums need dpw = dalpha * alpha only through its moments in
   // dy (the thread's pixels share dx): gv[0..2] collect sum dpw, sum dpw dy,
   // sum dpw dy^2 here and finish_geometry turns them into the five sums.
-  const float dpw = da * alpha;
-  const float dpy = dpw * dy;
-  gv[0] += dpw;
-  gv[1] += dpy;
-  gv[2] += dpy * dy;
-  return ok;
+  const float2 dpw = __fmul2_rn(da, al);
+  const float2 dpy = __fmul2_rn(dpw, dy);
+  gv[0] = __fadd2_rn(gv[0], dpw);
+  gv[1] = __fadd2_rn(gv[1], dpy);
+  gv[2] = __ffma2_rn(dpy, dy, gv[2]);
+  return ok0 || ok1;
+}
+
+// The nine gradient sums of one splat over a thread's pixels (NP pairs),
+// collapsed to one value each and finished (finish_geometry); returns
+// whether any of the pixels took part.
+template <bool BG, bool COUNT, int NP>
+__device__ __forceinline__ bool splat_grads(PixelBwd2 (&P)[NP], const float2 (&py2)[NP], float px, const float4& a,
+                                            const float4& b, float cb, uint32_t rel, float cap, float amin,
+                                            float g[9], PairCount& pc) {
+  const SplatCol col = splat_column(px, a);
+  float2 acc[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) acc[i] = bc2(0.0f);
+  bool any = false;
+#pragma unroll
+  for (int k = 0; k < NP; ++k) any |= pixel_grad2<BG, COUNT>(P[k], col, py2[k], a, b, cb, rel, cap, amin, acc, pc);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) g[i] = acc[i].x + acc[i].y;
+  finish_geometry(g, col, a, b);
+  return any;
 }
 
 template <int TW, int TH, int PPT, int B, bool BG, bool COUNT>
@@ -603,23 +662,33 @@ __global__ void GS_RBWD_BOUNDS(TW* TH / PPT) raster_bwd_kernel(
   const uint2 range = ranges[tile];
   const float cap = K.alpha_cap, amin = K.alpha_min;
   const float tx0 = static_cast<float>(tx * TW), ty0 = static_cast<float>(ty * TH);
-  PixelBwd P[PPT];
+  static_assert(PPT % 2 == 0, "pixels are stepped in pairs");
+  constexpr int NP = PPT / 2;
+  PixelBwd2 P[NP];
+  float2 py2[NP];  // pixel centres of each pair's rows
   PairCount pc;
   uint32_t lmax = 0;
 #pragma unroll
-  for (int r = 0; r < PPT; ++r) {
-    P[r] = PixelBwd{1.0f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u};
-    const int yy = y0 + r * Gm::RS;
-    if (x < W && yy < H) {
-      const size_t p = static_cast<size_t>(L.pix_base[v]) + static_cast<size_t>(yy) * W + x;
-      P[r].T = final_T[p];
-      P[r].last = last[p];
-      P[r].g0 = dL_dimage[3 * p];
-      P[r].g1 = dL_dimage[3 * p + 1];
-      P[r].g2 = dL_dimage[3 * p + 2];
-      P[r].gbg = P[r].T * (P[r].g0 * K.bg[0] + P[r].g1 * K.bg[1] + P[r].g2 * K.bg[2]);
+  for (int k = 0; k < NP; ++k) {
+    float T[2] = {1.0f, 1.0f}, g0[2] = {0.f, 0.f}, g1[2] = {0.f, 0.f}, g2[2] = {0.f, 0.f}, gbg[2] = {0.f, 0.f};
+    uint32_t ls[2] = {0u, 0u};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int yy = y0 + (2 * k + h) * Gm::RS;
+      if (x < W && yy < H) {
+        const size_t p = static_cast<size_t>(L.pix_base[v]) + static_cast<size_t>(yy) * W + x;
+        T[h] = final_T[p];
+        ls[h] = last[p];
+        g0[h] = dL_dimage[3 * p];
+        g1[h] = dL_dimage[3 * p + 1];
+        g2[h] = dL_dimage[3 * p + 2];
+        gbg[h] = T[h] * (g0[h] * K.bg[0] + g1[h] * K.bg[1] + g2[h] * K.bg[2]);
+      }
+      lmax = max(lmax, ls[h]);
     }
-    lmax = max(lmax, P[r].last);
+    P[k] = PixelBwd2{make_float2(T[0], T[1]),     make_float2(g0[0], g0[1]), make_float2(g1[0], g1[1]),
+                     make_float2(g2[0], g2[1]),   make_float2(gbg[0], gbg[1]), bc2(0.0f), ls[0], ls[1]};
+    py2[k] = make_float2(py0 + static_cast<float>(2 * k * Gm::RS), py0 + static_cast<float>((2 * k + 1) * Gm::RS));
   }
   const int my_slot = slot_of_lane(lane);
   // the pair reduction: which splat of the pair and which of its 9 values
@@ -690,69 +759,22 @@ __global__ void GS_RBWD_BOUNDS(TW* TH / PPT) raster_bwd_kernel(
     for (; q + 1 < nl; q += 2) {
       const int jA = s_list[warp][q], jB = s_list[warp][q + 1];
       float gA[9], gB[9];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) gA[i] = gB[i] = 0.0f;
-      bool cA = false, cB = false;
-      {
-        const float4 a = s_a[jA];
-        const float4 b = s_b[jA];
-        const float cb = s_c[jA];
-        const uint32_t rel = static_cast<uint32_t>(b_end - 1 - jA);
-        const SplatCol col = splat_column(px, a);
-#pragma unroll
-        for (int r = 0; r < PPT; ++r) {
-          if constexpr (COUNT) pc.ev += rel < P[r].last;
-          const bool ok =
-              pixel_grad<BG>(P[r], col, py0 + static_cast<float>(r * Gm::RS), a, b, cb, rel, cap, amin, gA);
-          cA |= ok;
-          if constexpr (COUNT) pc.co += ok;
-        }
-        finish_geometry(gA, col, a, b);
-      }
-      {
-        const float4 a = s_a[jB];
-        const float4 b = s_b[jB];
-        const float cb = s_c[jB];
-        const uint32_t rel = static_cast<uint32_t>(b_end - 1 - jB);
-        const SplatCol col = splat_column(px, a);
-#pragma unroll
-        for (int r = 0; r < PPT; ++r) {
-          if constexpr (COUNT) pc.ev += rel < P[r].last;
-          const bool ok =
-              pixel_grad<BG>(P[r], col, py0 + static_cast<float>(r * Gm::RS), a, b, cb, rel, cap, amin, gB);
-          cB |= ok;
-          if constexpr (COUNT) pc.co += ok;
-        }
-        finish_geometry(gB, col, a, b);
-      }
+      splat_grads<BG, COUNT>(P, py2, px, s_a[jA], s_b[jA], s_c[jA], static_cast<uint32_t>(b_end - 1 - jA), cap, amin,
+                             gA, pc);
+      splat_grads<BG, COUNT>(P, py2, px, s_a[jB], s_b[jB], s_c[jB], static_cast<uint32_t>(b_end - 1 - jB), cap, amin,
+                             gB, pc);
       // listed splats nearly always contribute: reduce without a branch, so
       // the two reductions and the pixel work form one block to schedule
-      (void)cA;
-      (void)cB;
       if constexpr (COUNT) pc.ex += 2 * PPT;
       const float red = warp_reduce18(gA, gB, lane);
       if (slot18 >= 0 && red != 0.0f) atomicAdd(&s_grad[(pair_b ? jB : jA) * 9 + pair_slot], red);
     }
     if (q < nl) {
       const int j = s_list[warp][q];
-      const float4 a = s_a[j];
-      const float4 b = s_b[j];
-      const float cb = s_c[j];
-      const uint32_t rel = static_cast<uint32_t>(b_end - 1 - j);
       float gv[9];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) gv[i] = 0.0f;
-      bool contrib = false;
-      const SplatCol col = splat_column(px, a);
-#pragma unroll
-      for (int r = 0; r < PPT; ++r) {
-        if constexpr (COUNT) pc.ev += rel < P[r].last;
-        const bool ok = pixel_grad<BG>(P[r], col, py0 + static_cast<float>(r * Gm::RS), a, b, cb, rel, cap, amin, gv);
-        contrib |= ok;
-        if constexpr (COUNT) pc.co += ok;
-      }
+      const bool contrib = splat_grads<BG, COUNT>(P, py2, px, s_a[j], s_b[j], s_c[j],
+                                                  static_cast<uint32_t>(b_end - 1 - j), cap, amin, gv, pc);
       if constexpr (COUNT) pc.ex += PPT;
-      finish_geometry(gv, col, a, b);
       if (__any_sync(0xffffffffu, contrib)) {
         const float red = warp_reduce9(gv, lane);
         if (!(lane & 1) && my_slot >= 0 && red != 0.0f) atomicAdd(&s_grad[j * 9 + my_slot], red);
