@@ -623,16 +623,18 @@ def raster_variant(stage, cfg):
 
 
 def recorded_traffic(kernel, workload, variant=None):
-    """DRAM bytes per launch of `kernel` on `workload` from profiles/dram_traffic.json,
-    if they were captured from the kernel's current sources (and, where the
-    entry names one, the same template instance); else None."""
+    """DRAM bytes per launch of `kernel` on `workload` from profiles/dram_traffic.json
+    (entries keyed kernel|workload, or kernel|workload|instance for the
+    rasteriser's template instances), if they were captured from the kernel's
+    current sources and, where the entry names one, the same instance; else None."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
     except (OSError, ValueError):
         return None
-    e = d.get(f"{kernel}|{workload}")
+    e = d.get(f"{kernel}|{workload}|{variant}") if variant is not None else None
+    e = e or d.get(f"{kernel}|{workload}")
     if not e or kernel not in KERNEL_SOURCES or e.get("digest") != kernel_digest(kernel):
         return None
     if variant is not None and e.get("variant") not in (None, variant):
