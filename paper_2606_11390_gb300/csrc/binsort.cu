@@ -880,7 +880,7 @@ constexpr int kChunkTableThreads = 1024;
 
 __global__ void __launch_bounds__(kChunkTableThreads) super_chunks_kernel(
     uint2* __restrict__ sranges, int32_t n_super, int passes, const int64_t* n_super_total, int64_t capacity,
-    uint32_t* __restrict__ chunk_base, uint4* __restrict__ chunk_info) {
+    uint32_t* __restrict__ chunk_base, uint4* __restrict__ chunk_info, const SuperLayout S, int V) {
   __shared__ uint32_t s_w[kChunkTableThreads / 32];
   __shared__ uint32_t s_run;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -921,9 +921,15 @@ __global__ void __launch_bounds__(kChunkTableThreads) super_chunks_kernel(
   for (int s = warp; s < n_super; s += kChunkTableThreads / 32) {
     const uint2 r = sranges[s];
     const uint32_t c0 = chunk_base[s], nc = chunk_base[s + 1] - c0;
+    // the super-tile's view and position in its view's super grid, packed
+    // once here for the chunk kernels (view < 64, coordinates < 4096)
+    const int v = view_of_super(S, V, static_cast<uint32_t>(s));
+    const uint32_t local = static_cast<uint32_t>(s) - S.sbase[v], stx = static_cast<uint32_t>(S.stx[v]);
+    const uint32_t sy = local / stx, sx = local - sy * stx;
+    const uint32_t pos = static_cast<uint32_t>(v) | (sx << 6) | (sy << 18);
     for (uint32_t j = lane; j < nc; j += 32) {
       const uint32_t first = r.x + j * kChunk;
-      chunk_info[c0 + j] = make_uint4(first, min(static_cast<uint32_t>(kChunk), r.y - first), static_cast<uint32_t>(s), 0u);
+      chunk_info[c0 + j] = make_uint4(first, min(static_cast<uint32_t>(kChunk), r.y - first), static_cast<uint32_t>(s), pos);
     }
   }
 }
@@ -935,7 +941,7 @@ struct ChunkArgs {
   const uint32_t* skeys;        // their keys with the local rectangles (or null: gather the rectangles)
   const uint2* sranges;         // [n_super] [start, end) in svals
   const uint32_t* chunk_base;   // [n_super + 1]
-  const uint4* chunk_info;      // [chunks] first record, length, super-tile
+  const uint4* chunk_info;      // [chunks] first record, length, super-tile, packed (view, sx, sy)
   const short4* rects;
   uint32_t* chunk_cnt;          // [chunks][64]: tile counts, then their exclusive prefix within the super-tile
   const uint2* ranges;          // [n_tiles] tile ranges (scatter)
@@ -949,17 +955,15 @@ struct ChunkView {
   uint32_t first, len;  // records [first, first + len) of svals
 };
 
-__device__ __forceinline__ ChunkView chunk_view(const ChunkArgs& a, const Layout& L, const SuperLayout& S, uint32_t c) {
+__device__ __forceinline__ ChunkView chunk_view(const ChunkArgs& a, uint32_t c) {
   ChunkView cv;
   const uint4 info = a.chunk_info[c];
   cv.first = info.x;
   cv.len = info.y;
   cv.s = info.z;
-  cv.v = view_of_super(S, L.V, cv.s);
-  const uint32_t local = cv.s - S.sbase[cv.v];
-  const uint32_t stx = static_cast<uint32_t>(S.stx[cv.v]);
-  cv.sy = local / stx;
-  cv.sx = local - cv.sy * stx;
+  cv.v = static_cast<int>(info.w & 63u);
+  cv.sx = (info.w >> 6) & 0xfffu;
+  cv.sy = info.w >> 18;
   return cv;
 }
 
@@ -1029,7 +1033,7 @@ __global__ void __launch_bounds__(kChunkThreads) chunk_count_kernel(const ChunkA
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t n_chunks = a.chunk_base[S.n_super];
   for (uint32_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
-    const ChunkView cv = chunk_view(a, L, S, c);
+    const ChunkView cv = chunk_view(a, c);
     uint64_t m = 0;
     if (static_cast<uint32_t>(tid) < cv.len) {
       const uint32_t e = cv.first + tid;
@@ -1052,7 +1056,10 @@ __global__ void __launch_bounds__(kChunkThreads) chunk_count_kernel(const ChunkA
 
 // 2e. Per super-tile (one CTA each): the exclusive prefix of every tile's
 //     counts over the super-tile's chunks (in place) and the tile totals.
-constexpr int kSuperScanThreads = 256;
+// 16 groups of 64 threads, each walking a 16th of the super-tile's chunks
+// with 4 loads in flight: the largest super-tiles (about a thousand chunks at
+// the centre of a 4K view) set the kernel's time.
+constexpr int kSuperScanThreads = 1024;
 constexpr int kSuperScanGroups = kSuperScanThreads / kSuperTiles;
 
 __global__ void __launch_bounds__(kSuperScanThreads) super_scan_kernel(uint32_t* __restrict__ chunk_cnt,
@@ -1067,6 +1074,7 @@ __global__ void __launch_bounds__(kSuperScanThreads) super_scan_kernel(uint32_t*
   const uint32_t j0 = min(nc, g * per), j1 = min(nc, j0 + per);
   uint32_t* col = chunk_cnt + static_cast<size_t>(c0) * kSuperTiles + t;
   uint32_t sum = 0;
+#pragma unroll 4
   for (uint32_t j = j0; j < j1; ++j) sum += col[static_cast<size_t>(j) * kSuperTiles];
   s_part[g][t] = sum;
   __syncthreads();
@@ -1077,7 +1085,18 @@ __global__ void __launch_bounds__(kSuperScanThreads) super_scan_kernel(uint32_t*
     if (h < g) run += p;
     total += p;
   }
-  for (uint32_t j = j0; j < j1; ++j) {
+  uint32_t j = j0;
+  for (; j + 4 <= j1; j += 4) {
+    uint32_t x[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) x[k] = col[static_cast<size_t>(j + k) * kSuperTiles];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      col[static_cast<size_t>(j + k) * kSuperTiles] = run;
+      run += x[k];
+    }
+  }
+  for (; j < j1; ++j) {
     const uint32_t x = col[static_cast<size_t>(j) * kSuperTiles];
     col[static_cast<size_t>(j) * kSuperTiles] = run;
     run += x;
@@ -1154,12 +1173,16 @@ __global__ void __launch_bounds__(kChunkThreads) scatter_kernel(const ChunkArgs 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t n_chunks = a.chunk_base[S.n_super];
   for (uint32_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
-    const ChunkView cv = chunk_view(a, L, S, c);
+    const ChunkView cv = chunk_view(a, c);
     // the tile bases do not depend on the records: their loads go out first
-    uint32_t gb = 0;
-    if (tid < kSuperTiles) {
-      const int64_t tile = tile_of(L, cv, tid);
-      if (tile >= 0) gb = a.ranges[tile].x + a.chunk_cnt[static_cast<size_t>(c) * kSuperTiles + tid];
+    // (warp 0, tiles lane and lane + 32)
+    uint32_t gb[2] = {0u, 0u};
+    if (warp == 0) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t tile = tile_of(L, cv, lane + 32 * h);
+        if (tile >= 0) gb[h] = a.ranges[tile].x + a.chunk_cnt[static_cast<size_t>(c) * kSuperTiles + lane + 32 * h];
+      }
     }
     uint64_t m = 0;
     uint32_t vg = 0;
@@ -1174,27 +1197,36 @@ __global__ void __launch_bounds__(kChunkThreads) scatter_kernel(const ChunkArgs 
     s_pre[warp][lane] = __popc(lo);
     s_pre[warp][lane + 32] = __popc(hi);
     __syncthreads();
-    if (tid < kSuperTiles) {
-      s_gbase[tid] = gb;
-      uint32_t tot = 0;
+    if (warp == 0) {
+      // per tile (lane, lane + 32): the warps' exclusive prefix and the total,
+      // then the staging layout, an exclusive scan of the 64 totals
+      uint32_t tot[2];
 #pragma unroll
-      for (int w = 0; w < kChunkWarps; ++w) {
-        const uint32_t x = s_pre[w][tid];
-        s_pre[w][tid] = tot;
-        tot += x;
+      for (int h = 0; h < 2; ++h) {
+        const int t = lane + 32 * h;
+        s_gbase[t] = gb[h];
+        tot[h] = 0;
+#pragma unroll
+        for (int w = 0; w < kChunkWarps; ++w) {
+          const uint32_t x = s_pre[w][t];
+          s_pre[w][t] = tot[h];
+          tot[h] += x;
+        }
       }
-      // staging layout: exclusive scan of the 64 tile totals (warps 0 and 1)
-      uint32_t v = tot;
+      uint32_t v0 = tot[0], v1 = tot[1];
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t nb = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += nb;
+        const uint32_t n0 = __shfl_up_sync(0xffffffffu, v0, o), n1 = __shfl_up_sync(0xffffffffu, v1, o);
+        if (lane >= o) {
+          v0 += n0;
+          v1 += n1;
+        }
       }
-      s_tloc[tid + 1] = v;  // inclusive within the warp; the second warp adds the first's total below
+      const uint32_t first_half = __shfl_sync(0xffffffffu, v0, 31);
+      s_tloc[lane + 1] = v0;
+      s_tloc[lane + 33] = v1 + first_half;
+      if (lane == 0) s_tloc[0] = 0;
     }
-    __syncthreads();
-    if (tid >= 32 && tid < kSuperTiles) s_tloc[tid + 1] += s_tloc[32];
-    if (tid == 0) s_tloc[0] = 0;
     __syncthreads();
     const uint32_t total = s_tloc[kSuperTiles];
     const bool staged = total <= static_cast<uint32_t>(kStage);
@@ -1609,7 +1641,7 @@ int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* 
   uint32_t* chunk_base = u32(w.chunk_base);
   uint4* chunk_info = reinterpret_cast<uint4*>(ws + w.chunk_info);
   super_chunks_kernel<<<1, kChunkTableThreads, 0, stream>>>(sranges, S.n_super, SP, n_super_total, capacity, chunk_base,
-                                                           chunk_info);
+                                                           chunk_info, S, L.V);
   ChunkArgs ca;
   ca.svals = sv[SP & 1];
   ca.skeys = packed ? sk[SP & 1] : nullptr;
