@@ -874,13 +874,13 @@ __global__ void __launch_bounds__(kEmitThreads) emit_super_kernel(
 //     the last super-tile pass left complemented (with no pass, the one
 //     super-tile holds the whole list), turns each super-tile's length into
 //     chunks of kChunk records (chunk_base: exclusive offsets, chunk_base
-//     [n_super] the total) and describes every chunk (first record, length,
-//     super-tile), one warp per super-tile.
+//     [n_super] the total); chunk_info_kernel then describes every chunk
+//     (first record, length, super-tile, packed view and grid position).
 constexpr int kChunkTableThreads = 1024;
 
 __global__ void __launch_bounds__(kChunkTableThreads) super_chunks_kernel(
     uint2* __restrict__ sranges, int32_t n_super, int passes, const int64_t* n_super_total, int64_t capacity,
-    uint32_t* __restrict__ chunk_base, uint4* __restrict__ chunk_info, const SuperLayout S, int V) {
+    uint32_t* __restrict__ chunk_base) {
   __shared__ uint32_t s_w[kChunkTableThreads / 32];
   __shared__ uint32_t s_run;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -917,8 +917,21 @@ __global__ void __launch_bounds__(kChunkTableThreads) super_chunks_kernel(
     __syncthreads();
   }
   if (tid == 0) chunk_base[n_super] = s_run;
-  __syncthreads();
-  for (int s = warp; s < n_super; s += kChunkTableThreads / 32) {
+}
+
+// The chunk table, one warp per super-tile (many CTAs: the table has a
+// 16-byte entry per chunk, 328K on the 16-view workload).
+constexpr int kChunkInfoThreads = 256;
+
+__global__ void __launch_bounds__(kChunkInfoThreads) chunk_info_kernel(const uint2* __restrict__ sranges,
+                                                                       int32_t n_super,
+                                                                       const uint32_t* __restrict__ chunk_base,
+                                                                       uint4* __restrict__ chunk_info,
+                                                                       const SuperLayout S, int V) {
+  const int lane = threadIdx.x & 31;
+  constexpr int kWarps = kChunkInfoThreads / 32;
+  const int nw = static_cast<int>(gridDim.x) * kWarps;
+  for (int s = static_cast<int>(blockIdx.x) * kWarps + (threadIdx.x >> 5); s < n_super; s += nw) {
     const uint2 r = sranges[s];
     const uint32_t c0 = chunk_base[s], nc = chunk_base[s + 1] - c0;
     // the super-tile's view and position in its view's super grid, packed
@@ -1640,8 +1653,14 @@ int bin_sort_impl(const float* projected, const int16_t* rects, const uint32_t* 
   //        ranges, scatter into `vals`
   uint32_t* chunk_base = u32(w.chunk_base);
   uint4* chunk_info = reinterpret_cast<uint4*>(ws + w.chunk_info);
-  super_chunks_kernel<<<1, kChunkTableThreads, 0, stream>>>(sranges, S.n_super, SP, n_super_total, capacity, chunk_base,
-                                                           chunk_info, S, L.V);
+  super_chunks_kernel<<<1, kChunkTableThreads, 0, stream>>>(sranges, S.n_super, SP, n_super_total, capacity,
+                                                           chunk_base);
+  {
+    const int64_t want = (S.n_super + kChunkInfoThreads / 32 - 1) / (kChunkInfoThreads / 32);
+    const unsigned grid = static_cast<unsigned>(want < 4 * static_cast<int64_t>(sm_count()) ? (want > 0 ? want : 1)
+                                                                                             : 4 * sm_count());
+    chunk_info_kernel<<<grid, kChunkInfoThreads, 0, stream>>>(sranges, S.n_super, chunk_base, chunk_info, S, L.V);
+  }
   ChunkArgs ca;
   ca.svals = sv[SP & 1];
   ca.skeys = packed ? sk[SP & 1] : nullptr;

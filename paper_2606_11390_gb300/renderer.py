@@ -447,9 +447,9 @@ class TrainStep:
     def _sort_launches(fr: Frame) -> int:
         """Kernels gs_bin_sort launches: compaction, 4 depth passes, the
         super-tile emission, the super-tile passes (each scans its digit counts
-        itself), the chunk table, the chunk counts, the per-super-tile scan,
-        the tile scan and the scatter, then the optional 64-bit keys and tile
-        order."""
+        itself), the chunk offsets and the chunk table, the chunk counts, the
+        per-super-tile scan, the tile scan and the scatter, then the optional
+        64-bit keys and tile order."""
         tw, th = int(fr.cfg["tile_w"]), int(fr.cfg["tile_h"])
         n_super = 0
         for W, H in fr.cams.sizes:
@@ -460,7 +460,7 @@ class TrainStep:
             bits += 1
         super_passes = (bits + 7) // 8
         order = 1 if fr.cfg.get("flags", 0) & gs.GS_FLAG_TILE_ORDER else 0
-        return 1 + 4 + 1 + super_passes + 4 + 1 + (1 if fr.keep_keys else 0) + order
+        return 1 + 4 + 1 + super_passes + 5 + 1 + (1 if fr.keep_keys else 0) + order
 
     def prepare(self, warmup_checks=2):
         """Sizes the key capacity from an eager run, then (batched mode)
