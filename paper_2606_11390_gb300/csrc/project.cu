@@ -396,6 +396,53 @@ __device__ __forceinline__ void stage_params(ParamSmem& sm, const float* means, 
   __syncthreads();
 }
 
+// Per-thread pipeline of the backward's per-view inputs where they are not
+// staged in bulk (several views, or a partial slice): the count of view
+// v + 2 is loaded into a register and the gradient-record fields of view
+// v + 1 (F floats from field `first`; records are 36 bytes, so the copies
+// are 4-byte cp.async pieces, and only for a view whose count is non-zero)
+// go into the thread's own slot of a shared ring while view v is processed,
+// so each view's load latency overlaps the previous view's arithmetic. A
+// thread reads only its own slots: the waits are per thread
+// (cp.async.wait_group) and need no barrier.
+constexpr int kRingFields = 5;
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+template <int F, class Body>
+__device__ __forceinline__ void pipelined_views(bool active, int V, int64_t N, int64_t g, const uint32_t* counts,
+                                                const float* d_proj, int first,
+                                                float (&ring)[2][kRingFields][kProjBlock], Body body) {
+  static_assert(F <= kRingFields, "ring slot too small");
+  const int tid = threadIdx.x;
+  auto count_of = [&](int v) -> uint32_t { return (active && v < V) ? counts[static_cast<int64_t>(v) * N + g] : 0u; };
+  auto fetch = [&](int v, int slot) {
+    const float* src = d_proj + (static_cast<int64_t>(v) * N + g) * kDRecordFloats + first;
+#pragma unroll
+    for (int k = 0; k < F; ++k) cp_async4(&ring[slot][k][tid], src + k);
+  };
+  uint32_t c_cur = count_of(0), c_next = count_of(1);
+  if (c_cur) fetch(0, 0);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  for (int v = 0; v < V; ++v) {
+    const uint32_t c_after = count_of(v + 2);
+    if (c_next) fetch(v + 1, (v + 1) & 1);  // non-zero only for v + 1 < V
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 1;" ::: "memory");  // all but view v + 1's copies have landed
+    if (c_cur) {
+      float f[F];
+#pragma unroll
+      for (int k = 0; k < F; ++k) f[k] = ring[v & 1][k][tid];
+      body(v, f);
+    }
+    c_cur = c_next;
+    c_next = c_after;
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 struct __align__(16) ProjFwdSmem {
   ParamSmem p;
   float4 out[kProjBlock * 3];  // 6 KB staging of projected records
@@ -472,7 +519,11 @@ __global__ void __launch_bounds__(kProjBlock, 5) project_fwd_kernel(
 // gradient accumulates in registers and leaves through the thread's own slot
 // of the shared-memory staging area, then as coalesced stores.
 // ---------------------------------------------------------------------------
-template <int DEG>
+// MULTI: the instance for several views, whose per-view inputs go through
+// the per-thread pipeline; the single-view instance stages them with the
+// parameters (full slices) or reads them directly (the last, partial slice),
+// and keeps the registers the pipeline would take.
+template <int DEG, bool MULTI>
 __global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ opac, const float* __restrict__ sh, int64_t N, const gs_camera* __restrict__ cams,
@@ -488,9 +539,11 @@ __global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_ke
   const int64_t g0 = static_cast<int64_t>(blockIdx.x) * kProjBlock;
   const int n = static_cast<int>(N - g0 < kProjBlock ? N - g0 : kProjBlock);
   // one view: the CTA's gradient records and tile counts join the staging
-  __shared__ __align__(16) float s_dp[kProjBlock * kDRecordFloats];
-  __shared__ __align__(16) uint32_t s_cnt[kProjBlock];
-  const bool staged = use_bulk == 2 && L.V == 1 && n == kProjBlock;
+  __shared__ __align__(16) float s_dp[MULTI ? 4 : kProjBlock * kDRecordFloats];
+  __shared__ __align__(16) uint32_t s_cnt[MULTI ? 4 : kProjBlock];
+  // several views: the per-thread view pipeline's ring
+  __shared__ __align__(16) float s_ring[MULTI ? 2 : 1][kRingFields][MULTI ? kProjBlock : 1];
+  const bool staged = !MULTI && use_bulk == 2 && L.V == 1 && n == kProjBlock;
   ExtraCopies ex;
   if (staged) {
     ex.n = 2;
@@ -522,12 +575,10 @@ __global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_ke
     const float* shc = reinterpret_cast<const float*>(my_sh4);
     const float* mean = &sm.p.means[3 * tid];
     const float o = active ? 1.0f / (1.0f + __expf(-sm.p.opac[tid])) : 0.0f;
-    for (int v = 0; active && v < L.V; ++v) {
-      const int64_t vg = static_cast<int64_t>(v) * N + g0 + tid;
-      if ((staged ? s_cnt[tid] : counts[vg]) == 0) continue;
-      const float* dp = staged ? &s_dp[kDRecordFloats * tid] : d_proj + vg * kDRecordFloats;
-      const float gc0 = dp[5], gc1 = dp[6], gc2 = dp[7];
-      go += dp[8] * o * (1.0f - o);
+    // one view's colour gradients (dL/dc, and dL/dopacity through the
+    // record's field 8)
+    auto colour_view = [&](int v, float gc0, float gc1, float gc2, float gop) {
+      go += gop * o * (1.0f - o);
       const gs_camera& cam = sm.p.cams[v];
       float dvec[3], dnorm;
       view_dir(cam, mean, dvec, dnorm);
@@ -554,6 +605,17 @@ __global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_ke
       sh_basis_grad_acc<DEG>(d, coef, gdir);
       const float dd = d[0] * gdir[0] + d[1] * gdir[1] + d[2] * gdir[2];
       for (int k = 0; k < 3; ++k) gm[k] += (gdir[k] - d[k] * dd) * inv;
+    };
+    if constexpr (MULTI) {
+      pipelined_views<4>(active, L.V, N, g0 + tid, counts, d_proj, 5, s_ring,
+                         [&](int v, const float (&f)[4]) { colour_view(v, f[0], f[1], f[2], f[3]); });
+    } else {
+      for (int v = 0; active && v < L.V; ++v) {
+        const int64_t vg = static_cast<int64_t>(v) * N + g0 + tid;
+        if ((staged ? s_cnt[tid] : counts[vg]) == 0) continue;
+        const float* dp = staged ? &s_dp[kDRecordFloats * tid] : d_proj + vg * kDRecordFloats;
+        colour_view(v, dp[5], dp[6], dp[7], dp[8]);
+      }
     }
     // SH gradients into the thread's own slot (coefficients past the degree
     // get 0); stored to global memory, coalesced, at the end
@@ -568,13 +630,9 @@ __global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_ke
   // Pass 2: geometry (2D mean and conic -> mean, scales, rotation), over all views.
   GaussLocal G;
   if (active) gauss_local(&sm.p.means[3 * tid], &sm.p.log_scales[3 * tid], sm.p.quats[tid], sm.p.opac[tid], G);
-  for (int v = 0; active && v < L.V; ++v) {
-    const int64_t vg = static_cast<int64_t>(v) * N + g0 + tid;
-    if ((staged ? s_cnt[tid] : counts[vg]) == 0) continue;
-    const float* dp = staged ? &s_dp[kDRecordFloats * tid] : d_proj + vg * kDRecordFloats;
-    float g9[5];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) g9[i] = dp[i];
+  // one view's geometric gradients (dL/dmean2d, dL/dconic: the record's
+  // fields 0..4)
+  auto geometry_view = [&](int v, const float (&g9)[5]) {
     const gs_camera& cam = sm.p.cams[v];
     ViewProj P;
     project_view_bwd(G, cam, L.width[v], L.height[v], K, P);
@@ -636,6 +694,17 @@ __global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_ke
     gqn[3] = 2.f * (-2.f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.f * z * gR[4] + y * gR[5] + x * gR[6] +
                     y * gR[7]);
     for (int k = 0; k < 4; ++k) gq[k] += gqn[k];
+  };
+  if constexpr (MULTI) {
+    pipelined_views<5>(active, L.V, N, g0 + tid, counts, d_proj, 0, s_ring, geometry_view);
+  } else {
+    for (int v = 0; active && v < L.V; ++v) {
+      const int64_t vg = static_cast<int64_t>(v) * N + g0 + tid;
+      if ((staged ? s_cnt[tid] : counts[vg]) == 0) continue;
+      const float* dp = staged ? &s_dp[kDRecordFloats * tid] : d_proj + vg * kDRecordFloats;
+      const float g9[5] = {dp[0], dp[1], dp[2], dp[3], dp[4]};
+      geometry_view(v, g9);
+    }
   }
   const bool acc = (K.flags & GS_FLAG_ACCUMULATE_GRADS) != 0;
   if (active) {
@@ -694,11 +763,18 @@ int launch_project_bwd(const float* means, const float* log_scales, const float*
   // 2: the gradient records and counts can join the bulk staging too
   const int bulk_mode = !bulk ? 0 : (aligned16(d_projected) && aligned16(counts) ? 2 : 1);
   const unsigned blocks = static_cast<unsigned>((N + kProjBlock - 1) / kProjBlock);
-#define GS_PBWD(D)                                                                                              \
-  project_bwd_kernel<D><<<blocks, kProjBlock, 0, stream>>>(means, log_scales, quats, opacity_logits, sh, N, cams, L, \
-                                                           K, counts, d_projected, d_means, d_log_scales, d_quats,      \
-                                                           d_opacity_logits, d_sh, bulk_mode,                     \
-                                                           resident_ctas<10 + D>(project_bwd_kernel<D>), status)
+#define GS_PBWD_M(D, M)                                                                                         \
+  project_bwd_kernel<D, M><<<blocks, kProjBlock, 0, stream>>>(means, log_scales, quats, opacity_logits, sh, N, cams, \
+                                                              L, K, counts, d_projected, d_means, d_log_scales,   \
+                                                              d_quats, d_opacity_logits, d_sh, bulk_mode,         \
+                                                              resident_ctas<10 + D + (M ? 4 : 0)>(                \
+                                                                  project_bwd_kernel<D, M>),                      \
+                                                              status)
+#define GS_PBWD(D)          \
+  if (L.V > 1)              \
+    GS_PBWD_M(D, true);     \
+  else                      \
+    GS_PBWD_M(D, false)
   switch (K.sh_degree) {
     case 0: GS_PBWD(0); break;
     case 1: GS_PBWD(1); break;
@@ -706,6 +782,7 @@ int launch_project_bwd(const float* means, const float* log_scales, const float*
     default: GS_PBWD(3); break;
   }
 #undef GS_PBWD
+#undef GS_PBWD_M
   return cuda_status(cudaGetLastError());
 }
 
