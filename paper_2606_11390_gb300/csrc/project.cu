@@ -11,7 +11,9 @@
 // views. A CTA of 128 Gaussians stages its contiguous parameter slices
 // (means, log-scales, quaternions, opacities, SH) into shared memory with TMA
 // bulk copies (cp.async.bulk + mbarrier), and writes its projected records
-// back through shared memory as coalesced 16-byte stores. With its own copies
+// with three 16-byte stores per thread (a warp's stores cover its records'
+// contiguous bytes; staging them through shared memory cost two barriers per
+// view: 3.35 -> 2.92 ms for 16 views). With its own copies
 // it asks L2 to prefetch (cp.async.bulk.prefetch.L2) the slices of the CTA
 // one resident wave later, which then stages from L2 instead of DRAM.
 //
@@ -445,7 +447,6 @@ __device__ __forceinline__ void pipelined_views(bool active, int V, int64_t N, i
 
 struct __align__(16) ProjFwdSmem {
   ParamSmem p;
-  float4 out[kProjBlock * 3];  // 6 KB staging of projected records
 };
 
 // Compiled for 5 resident CTAs per SM (at most 102 registers): 0.234 -> 0.225
@@ -504,13 +505,13 @@ __global__ void __launch_bounds__(kProjBlock, 5) project_fwd_kernel(
         r2 = make_float4(rgb[0], rgb[1], rgb[2], 0.0f);
       }
     }
-    sm.out[3 * tid] = r0;
-    sm.out[3 * tid + 1] = r1;
-    sm.out[3 * tid + 2] = r2;
-    __syncthreads();
-    float4* dst = projected + (static_cast<int64_t>(v) * N + g0) * 3;
-    for (int i = tid; i < n * 3; i += kProjBlock) dst[i] = sm.out[i];
-    __syncthreads();
+    if (active) {
+      // a warp's three stores cover its 32 records' 1536 contiguous bytes
+      float4* dst = projected + (static_cast<int64_t>(v) * N + g0 + tid) * 3;
+      dst[0] = r0;
+      dst[1] = r1;
+      dst[2] = r2;
+    }
   }
 }
 
