@@ -157,27 +157,33 @@ __device__ __forceinline__ float edge_min_y(float x, float y0, float y1, float m
 // ellipse d^T M d <= 2 ts, ts = log2(o / alpha_min). A block is kept if its
 // rectangle of pixel centres meets the ellipse: the minimum of d^T M d over
 // the rectangle is 0 when the centre lies inside, else the smallest of the
-// four edge minima. ts and the rectangle are widened (x1.001 + margins), far
-// beyond the rounding of the per-pixel evaluation, so no pixel of a dropped
-// block can pass the alpha test.
+// edge minima over the edges that face the centre (from the minimising
+// point the direction to the centre lowers the quadratic, so it must leave
+// the rectangle there: at most one vertical and one horizontal edge). ts and
+// the rectangle are widened (x1.001 + margins), far beyond the rounding of
+// the per-pixel evaluation and of the approximate divisions and square roots
+// here (a few ulp), so no pixel of a dropped block can pass the alpha test.
 template <class G>
 __device__ __forceinline__ uint32_t warp_cull_mask(const float4& a, const float4& b, float tx0, float ty0,
-                                                    float amin) {
+                                                    float amin, float log2_amin) {
   constexpr uint32_t kAll = (G::NW >= 32) ? 0xffffffffu : ((1u << G::NW) - 1u);
   const float o = b.y;
   if (!(o > amin)) return 0u;
   const float m00 = -2.0f * a.z, m01 = -a.w, m11 = -2.0f * b.x;
   const float det = m00 * m11 - m01 * m01;
   if (!(det > 0.0f) || !(m00 > 0.0f) || !(m11 > 0.0f)) return kAll;
-  const float ts = (__log2f(o) - __log2f(amin)) * 1.001f + 0.01f;
+  const float ts = (__log2f(o) - log2_amin) * 1.001f + 0.01f;
   const float lim = 2.0f * ts;
-  const float idet = 1.0f / det;
-  const float hx = sqrtf(lim * m11 * idet) * 1.001f + 0.05f;
-  const float hy = sqrtf(lim * m00 * idet) * 1.001f + 0.05f;
+  const float idet = __fdividef(1.0f, det);
+  const float sx = lim * m11 * idet, sy = lim * m00 * idet;
+  const float hx = sx * rsqrtf(sx) * 1.001f + 0.05f;
+  const float hy = sy * rsqrtf(sy) * 1.001f + 0.05f;
   if (!(hx < 1e30f) || !(hy < 1e30f)) return kAll;
   // minimisers of the quadratic along vertical (y = kx x) and horizontal
   // (x = ky y) edges
-  const float kx = -m01 / m11, ky = -m01 / m00;
+  const float kx = __fdividef(-m01, m11), ky = __fdividef(-m01, m00);
+  const float lim_kept = lim * 1.001f + 0.01f;
+  const float kInf = __int_as_float(0x7f800000);
   uint32_t mask = 0;
 #pragma unroll
   for (int w = 0; w < G::NW; ++w) {
@@ -187,14 +193,14 @@ __device__ __forceinline__ uint32_t warp_cull_mask(const float4& a, const float4
     const float y0 = ty0 + static_cast<float>(8 * (w / G::WXN)) + 0.45f - a.y;
     const float y1 = y0 + 7.1f;
     if (x1 < -hx || x0 > hx || y1 < -hy || y0 > hy) continue;  // outside the bounding box
-    if (x0 <= 0.0f && x1 >= 0.0f && y0 <= 0.0f && y1 >= 0.0f) {
+    const bool left = x0 > 0.0f, right = x1 < 0.0f, below = y0 > 0.0f, above = y1 < 0.0f;
+    if (!left && !right && !below && !above) {
       mask |= 1u << w;  // the centre lies in the block
       continue;
     }
-    float qmin = fminf(edge_min_y(x0, y0, y1, m00, m01, m11, kx), edge_min_y(x1, y0, y1, m00, m01, m11, kx));
-    qmin = fminf(qmin, edge_min_y(y0, x0, x1, m11, m01, m00, ky));
-    qmin = fminf(qmin, edge_min_y(y1, x0, x1, m11, m01, m00, ky));
-    if (qmin <= lim * 1.001f + 0.01f) mask |= 1u << w;
+    const float qv = (left || right) ? edge_min_y(left ? x0 : x1, y0, y1, m00, m01, m11, kx) : kInf;
+    const float qh = (below || above) ? edge_min_y(below ? y0 : y1, x0, x1, m11, m01, m00, ky) : kInf;
+    if (fminf(qv, qh) <= lim_kept) mask |= 1u << w;
   }
   return mask;
 }
@@ -311,7 +317,7 @@ __global__ void __launch_bounds__(TW* TH / PPT, 1024 / (TW * TH / PPT)) raster_f
   const float px = static_cast<float>(x) + 0.5f, py0 = static_cast<float>(y0) + 0.5f;
   const uint2 range = ranges[tile];
   const int n = static_cast<int>(range.y - range.x);
-  const float cap = K.alpha_cap, amin = K.alpha_min, tstop = K.t_stop;
+  const float cap = K.alpha_cap, amin = K.alpha_min, tstop = K.t_stop, log2_amin = __log2f(amin);
   const float tx0 = static_cast<float>(tx * TW), ty0 = static_cast<float>(ty * TH);
   const float kInf = __int_as_float(0x7f800000);
   static_assert(PPT % 2 == 0, "pixels are stepped in pairs");
@@ -337,7 +343,7 @@ __global__ void __launch_bounds__(TW* TH / PPT, 1024 / (TW * TH / PPT)) raster_f
       s_a[k] = a;
       s_b[k] = b;
       s_c[k] = c;
-      const uint32_t mk = warp_cull_mask<G>(a, b, tx0, ty0, amin);
+      const uint32_t mk = warp_cull_mask<G>(a, b, tx0, ty0, amin, log2_amin);
       s_m[k] = mk;
       constexpr uint32_t kTag = cull_tag<TW, TH, PPT>();
       if (kTag && cull_out) cull_out[range.x + b0 + k] = static_cast<uint16_t>(mk | (kTag << 8));
@@ -660,7 +666,7 @@ __global__ void GS_RBWD_BOUNDS(TW* TH / PPT) raster_bwd_kernel(
   const int x = tx * TW + lx, y0 = ty * TH + ly;
   const float px = static_cast<float>(x) + 0.5f, py0 = static_cast<float>(y0) + 0.5f;
   const uint2 range = ranges[tile];
-  const float cap = K.alpha_cap, amin = K.alpha_min;
+  const float cap = K.alpha_cap, amin = K.alpha_min, log2_amin = __log2f(amin);
   const float tx0 = static_cast<float>(tx * TW), ty0 = static_cast<float>(ty * TH);
   static_assert(PPT % 2 == 0, "pixels are stepped in pairs");
   constexpr int NP = PPT / 2;
@@ -737,7 +743,7 @@ __global__ void GS_RBWD_BOUNDS(TW* TH / PPT) raster_bwd_kernel(
       // the forward's mask for this entry when it made one for this layout
       constexpr uint32_t kTag = cull_tag<TW, TH, PPT>();
       const uint32_t handed = (kTag && cull_in) ? cull_in[range.x + b_end - 1 - k] : 0u;
-      s_m[k] = (handed >> 8) == kTag && kTag ? (handed & 0xffu) : warp_cull_mask<Gm>(a, b, tx0, ty0, amin);
+      s_m[k] = (handed >> 8) == kTag && kTag ? (handed & 0xffu) : warp_cull_mask<Gm>(a, b, tx0, ty0, amin, log2_amin);
     }
     __syncthreads();
     // entries j hold relative position b_end-1-j; this warp needs rel < wmax.
