@@ -88,11 +88,6 @@ __device__ __forceinline__ SplatCol splat_column(float px, const float4& a) {
   return c;
 }
 
-__device__ __forceinline__ float splat_exponent(const SplatCol& c, float py, const float4& a, float Cp, float& dy) {
-  dy = __fsub_rn(py, a.y);
-  return __fmaf_rn(dy, __fmaf_rn(Cp, dy, c.bdx), c.adx2);
-}
-
 // Resident warps per SM the backward kernel is compiled for (0: no register
 // cap); the cap trades registers for latency hiding.
 #ifndef GS_RBWD_TARGET_WARPS
@@ -216,9 +211,9 @@ __device__ __forceinline__ uint32_t warp_cull_mask(const float4& a, const float4
 // threshold, so no later splat passes its test. A packed add, multiply or
 // FMA rounds each lane as __fadd_rn / __fmul_rn / __fmaf_rn does, and a
 // subtraction x - y is formed as fma(y, -1, x), which rounds the exact
-// difference once as __fsub_rn does: each lane's exponent and alpha are the
-// bits splat_exponent and the backward's scalar steps compute, so the
-// backward recomputes the forward's decisions exactly. The splat's constants
+// difference once as __fsub_rn does. The backward (pixel_grad2) forms each
+// exponent and alpha with the same packed operations, so it recomputes the
+// forward's decisions exactly. The splat's constants
 // enter as broadcast pairs (no extra instructions), and a packed operation
 // takes one issue slot for two lanes' work.
 struct PixelFwd2 {
