@@ -5,8 +5,8 @@ backward) on the 4M-Gaussian 3840x2160 workload, on N GPUs of one node.
 
 Prints ONE JSON line on rank 0. `value` is Mpix/s of the whole job (rendered
 and back-propagated pixels of all ranks / max-over-ranks time). With
---impl reference, the CPU oracle (the reference implementation of this build)
-is timed instead on bounded window samples of the same workload.
+--impl reference, the CPU oracle (the plain reference implementation of the
+method) is timed instead on bounded window samples of the same workload.
 
 Multi-GPU: the path needs no exchange on one GPU per scene, so --gpus N runs N
 independent replicas (weak scaling, no collective on the data path; a
