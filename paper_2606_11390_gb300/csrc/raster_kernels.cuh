@@ -88,16 +88,20 @@ __device__ __forceinline__ SplatCol splat_column(float px, const float4& a) {
   return c;
 }
 
-// Resident warps per SM the backward kernel is compiled for (0: no register
-// cap); the cap trades registers for latency hiding.
-#ifndef GS_RBWD_TARGET_WARPS
-#define GS_RBWD_TARGET_WARPS 0
+// Resident warps per SM the 4-pixel backward is compiled for (0: no register
+// cap). Uncapped it takes 96 registers at 32x16 tiles (5 CTAs of 128
+// threads); capped for 24 warps it takes 80 (6 CTAs, 4-8 bytes of spills)
+// and runs 1.322 -> 1.287 ms at 4K. At 2 pixels a thread the same cap
+// raises the count the compiler picks (70 -> 77 registers at 16x16 tiles,
+// 7 -> 6 CTAs, 10.57 -> 10.73 ms on 16 views), so those stay uncapped: a
+// minimum of 0 CTAs leaves the count to the compiler as if none were given
+// (a minimum of 1 would let it grow to 87-93 registers there).
+#ifndef GS_RBWD_WARPS_4PX
+#define GS_RBWD_WARPS_4PX 24
 #endif
-#if GS_RBWD_TARGET_WARPS > 0
-#define GS_RBWD_BOUNDS(NT) __launch_bounds__(NT, GS_RBWD_TARGET_WARPS / ((NT) / 32))
-#else
-#define GS_RBWD_BOUNDS(NT) __launch_bounds__(NT)
-#endif
+constexpr int bwd_min_ctas(int threads, int ppt) {
+  return ppt == 4 && GS_RBWD_WARPS_4PX > 0 ? GS_RBWD_WARPS_4PX / (threads / 32) : 0;
+}
 
 // Thread / pixel geometry. With PPT pixels per thread a warp covers a block
 // of WB = 4 PPT columns by 8 rows: lane l owns column l % WB and rows
@@ -629,7 +633,7 @@ __device__ __forceinline__ bool splat_grads(PixelBwd2 (&P)[NP], const float2 (&p
 }
 
 template <int TW, int TH, int PPT, int B, bool BG, bool COUNT>
-__global__ void GS_RBWD_BOUNDS(TW* TH / PPT) raster_bwd_kernel(
+__global__ void __launch_bounds__(TW* TH / PPT, bwd_min_ctas(TW* TH / PPT, PPT)) raster_bwd_kernel(
     const float4* __restrict__ projected, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
     const uint32_t* __restrict__ order, const Layout L, const Consts K, const float* __restrict__ final_T,
     const uint32_t* __restrict__ last, const float* __restrict__ dL_dimage, float* __restrict__ d_proj,
