@@ -279,10 +279,23 @@ struct PairCount {
 };
 
 
-// Compiled for 1024 resident threads per SM (8 CTAs of 128 at 32x16 tiles,
-// 64 registers, no spills): 0.5 % faster than 7 CTAs at 72 registers.
+// Resident threads per SM the forward is compiled for. At 4 pixels a thread
+// 1024 (8 CTAs of 128 at 32x16 tiles, 64 registers, no spills): 0.5 %
+// faster than 7 CTAs at 72 registers; 1280 would leave 48 registers and
+// spill 90-116 bytes. At 2 pixels and at most 256 splats a batch 1280: 48
+// registers without spills at 16x16 and 32x16 tiles (1024 gives 64 and
+// spills 4-8 bytes at 16x16), 4.73 -> 4.63 ms on the 16-view workload. The
+// 512-splat batch keeps 1024: at 48 registers it spills 8 bytes at 32x16 and
+// the 64M-Gaussian street forward ran 5.02 -> 5.11 ms. A minimum above the
+// SM's 32 resident CTAs (32-thread 8x8 tiles) would be ignored, so it is
+// clamped there.
+constexpr int fwd_min_ctas(int threads, int ppt, int batch) {
+  const int per_sm = ppt == 2 && batch <= 256 ? 1280 : 1024;
+  return per_sm / threads < 32 ? per_sm / threads : 32;
+}
+
 template <int TW, int TH, int PPT, int B, bool COUNT>
-__global__ void __launch_bounds__(TW* TH / PPT, 1024 / (TW * TH / PPT)) raster_fwd_kernel(const float4* __restrict__ projected,
+__global__ void __launch_bounds__(TW* TH / PPT, fwd_min_ctas(TW* TH / PPT, PPT, B)) raster_fwd_kernel(const float4* __restrict__ projected,
                                                                    const uint32_t* __restrict__ vals,
                                                                    const uint2* __restrict__ ranges,
                                                                    const uint32_t* __restrict__ order, const Layout L,
