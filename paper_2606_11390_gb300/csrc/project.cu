@@ -524,7 +524,7 @@ __global__ void __launch_bounds__(kProjBlock, 5) project_fwd_kernel(
 // the per-thread pipeline; the single-view instance stages them with the
 // parameters (full slices) or reads them directly (the last, partial slice),
 // and keeps the registers the pipeline would take.
-template <int DEG, bool MULTI>
+template <int DEG, bool MULTI, bool SHT>
 __global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ opac, const float* __restrict__ sh, int64_t N, const gs_camera* __restrict__ cams,
@@ -562,9 +562,33 @@ __global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_ke
     ex.pf_src[1] = counts + (pf ? g_pf : g0);
   }
   stage_params(sm.p, means, log_scales, quats, opac, sh, g0, n, cams, L.V, use_bulk != 0, status, pf ? g_pf : -1, ex);
+  // The SH slice arrives Gaussian-major (12 float4 per Gaussian, as in
+  // global memory), so a thread's 16-byte loads of its own coefficients have
+  // a 192-byte stride: 8 threads of a phase meet only 2 of the 8 16-byte
+  // bank groups (4-way conflicts). The colour pass re-reads them in every
+  // view that sees the Gaussian (on 16 views 77M of the 118M shared-load
+  // wavefronts were conflicts). With many views (SHT) the slice is
+  // transposed once to chunk-major order (float4 j of Gaussian t at
+  // j * kProjBlock + t), where those loads are conflict-free: 16 views
+  // 5.48 -> 4.64 ms. With few views most Gaussians are seen in few of them
+  // and the transpose costs more than it saves (the 4-view street workload
+  // 11.9 -> 13.8 ms), so those instances keep the staged layout.
+  static_assert(MULTI || !SHT, "the transposed layout is for several views");
+  if constexpr (SHT) {
+    float4 q[12];
+#pragma unroll
+    for (int j = 0; j < 12; ++j) q[j] = sm.p.sh[12 * tid + j];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 12; ++j) sm.p.sh[j * kProjBlock + tid] = q[j];
+    __syncthreads();
+  }
   const bool active = tid < n;
   float gm[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, go = 0.f;
   float4* my_sh4 = &sm.p.sh[12 * tid];
+  // coefficient f (0..47) of this thread's Gaussian in either layout
+  const float* shb = SHT ? reinterpret_cast<const float*>(sm.p.sh) + 4 * tid : reinterpret_cast<const float*>(my_sh4);
+  auto shc = [&](int f) -> float { return SHT ? shb[(f >> 2) * (4 * kProjBlock) + (f & 3)] : shb[f]; };
   // Pass 1: colour -> SH coefficients and view direction, over all views.
   // The coefficients are read from this thread's staging slot when needed
   // rather than held in registers, and the slot then takes the SH gradients;
@@ -573,7 +597,6 @@ __global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_ke
     float gsh[3 * NB];
 #pragma unroll
     for (int i = 0; i < 3 * NB; ++i) gsh[i] = 0.0f;
-    const float* shc = reinterpret_cast<const float*>(my_sh4);
     const float* mean = &sm.p.means[3 * tid];
     const float o = active ? 1.0f / (1.0f + __expf(-sm.p.opac[tid])) : 0.0f;
     // one view's colour gradients (dL/dc, and dL/dopacity through the
@@ -590,15 +613,15 @@ __global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_ke
       float acc0 = 0.5f, acc1 = 0.5f, acc2 = 0.5f;
 #pragma unroll
       for (int i = 0; i < NB; ++i) {
-        acc0 += Y[i] * shc[3 * i];
-        acc1 += Y[i] * shc[3 * i + 1];
-        acc2 += Y[i] * shc[3 * i + 2];
+        acc0 += Y[i] * shc(3 * i);
+        acc1 += Y[i] * shc(3 * i + 1);
+        acc2 += Y[i] * shc(3 * i + 2);
       }
       const float graw[3] = {acc0 > 0.0f ? gc0 : 0.0f, acc1 > 0.0f ? gc1 : 0.0f, acc2 > 0.0f ? gc2 : 0.0f};
       float coef[16];
 #pragma unroll
       for (int i = 0; i < NB; ++i) {
-        coef[i] = shc[3 * i] * graw[0] + shc[3 * i + 1] * graw[1] + shc[3 * i + 2] * graw[2];
+        coef[i] = shc(3 * i) * graw[0] + shc(3 * i + 1) * graw[1] + shc(3 * i + 2) * graw[2];
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) gsh[3 * i + ch] += Y[i] * graw[ch];
       }
@@ -618,8 +641,13 @@ __global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_ke
         colour_view(v, dp[5], dp[6], dp[7], dp[8]);
       }
     }
-    // SH gradients into the thread's own slot (coefficients past the degree
-    // get 0); stored to global memory, coalesced, at the end
+    // SH gradients into the thread's own slot, Gaussian-major (coefficients
+    // past the degree get 0); stored to global memory, coalesced, at the end.
+    // After a transpose the slot belongs to other threads' coefficients,
+    // read until every thread has left the view loop. (Keeping the gradients
+    // chunk-major instead, with no barrier here and the final store reading
+    // through the index map, ran 4.72 ms on 16 views.)
+    if constexpr (SHT) __syncthreads();
 #pragma unroll
     for (int i = 0; i < 12; ++i) {
       float q[4];
@@ -754,6 +782,10 @@ int64_t resident_ctas(F kernel) {
   return n;
 }
 
+// Views from which the projection backward takes the SH-transposed instance
+// (measured: faster on 16 views, slower on 4).
+constexpr int kShTransposeViews = 8;
+
 int launch_project_bwd(const float* means, const float* log_scales, const float* quats, const float* opacity_logits,
                        const float* sh, int64_t N, const gs_camera* cams, const Layout& L, const Consts& K,
                        const uint32_t* counts, const float* d_projected, float* d_means, float* d_log_scales,
@@ -764,18 +796,18 @@ int launch_project_bwd(const float* means, const float* log_scales, const float*
   // 2: the gradient records and counts can join the bulk staging too
   const int bulk_mode = !bulk ? 0 : (aligned16(d_projected) && aligned16(counts) ? 2 : 1);
   const unsigned blocks = static_cast<unsigned>((N + kProjBlock - 1) / kProjBlock);
-#define GS_PBWD_M(D, M)                                                                                         \
-  project_bwd_kernel<D, M><<<blocks, kProjBlock, 0, stream>>>(means, log_scales, quats, opacity_logits, sh, N, cams, \
-                                                              L, K, counts, d_projected, d_means, d_log_scales,   \
-                                                              d_quats, d_opacity_logits, d_sh, bulk_mode,         \
-                                                              resident_ctas<10 + D + (M ? 4 : 0)>(                \
-                                                                  project_bwd_kernel<D, M>),                      \
-                                                              status)
-#define GS_PBWD(D)          \
-  if (L.V > 1)              \
-    GS_PBWD_M(D, true);     \
-  else                      \
-    GS_PBWD_M(D, false)
+#define GS_PBWD_M(D, M, T)                                                                                         \
+  project_bwd_kernel<D, M, T><<<blocks, kProjBlock, 0, stream>>>(                                                   \
+      means, log_scales, quats, opacity_logits, sh, N, cams, L, K, counts, d_projected, d_means, d_log_scales,      \
+      d_quats, d_opacity_logits, d_sh, bulk_mode,                                                                  \
+      resident_ctas<10 + D + (M ? 4 : 0) + (T ? 4 : 0)>(project_bwd_kernel<D, M, T>), status)
+#define GS_PBWD(D)                      \
+  if (L.V >= kShTransposeViews)         \
+    GS_PBWD_M(D, true, true);           \
+  else if (L.V > 1)                     \
+    GS_PBWD_M(D, true, false);          \
+  else                                  \
+    GS_PBWD_M(D, false, false)
   switch (K.sh_degree) {
     case 0: GS_PBWD(0); break;
     case 1: GS_PBWD(1); break;

@@ -37,6 +37,9 @@ def _scenes():
     s["cfg"] = scenes.make_cfg(tile_w=32, tile_h=16, bg=(0.2, 0.5, 0.9))
     yield "tile32x16_bg", s
     yield "sh_deg1", scenes.random_small(104, N=300, width=64, height=64, sh_degree=1)
+    # 9 views take the projection backward whose SH slice is transposed in
+    # shared memory; 1000 Gaussians leave a partial last slice
+    yield "nine_views", scenes.random_small(105, N=1000, width=64, height=48, n_views=9, spread=1.5)
     s = scenes.random_small(110, N=900, width=150, height=100, n_views=2, spread=1.5)
     s["cfg"] = scenes.make_cfg(flags=2)  # two pixels per rasteriser thread
     yield "two_px_per_thread", s
