@@ -15,7 +15,11 @@
 // contiguous bytes; staging them through shared memory cost two barriers per
 // view: 3.35 -> 2.92 ms for 16 views). With its own copies
 // it asks L2 to prefetch (cp.async.bulk.prefetch.L2) the slices of the CTA
-// one resident wave later, which then stages from L2 instead of DRAM.
+// one resident wave later, which then stages from L2 instead of DRAM. With
+// several views the SH slice is staged chunk-major by TMA tensor copies
+// (cp.async.bulk.tensor), so that the per-view re-reads of the coefficients
+// are free of bank conflicts, and the backward's SH gradients leave by
+// tensor stores.
 //
 // Bit-exact tile rectangles. Steps 1-8 of the projection (scale activation
 // through the tile rectangle) decide integers, so they are evaluated with
@@ -25,6 +29,8 @@
 // reduction, degree-7 Taylor polynomial) instead of expf, whose last bit is
 // not specified. Any float implementation that follows the same order gets
 // the same rectangles.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -37,6 +43,60 @@ namespace gs {
 namespace {
 
 constexpr int kProjBlock = 128;
+
+// ---- SH slices as 2-D tensors for TMA ----
+// An [N][48] float array (the SH coefficients, or their gradients) viewed as
+// a 2-D tensor with boxes of 4 floats x kProjBlock rows: box (4j, g0) is the
+// float4 chunk j of the CTA's Gaussians, which a tensor copy lays down in
+// shared memory as kProjBlock consecutive float4. A CTA's slice thus arrives
+// chunk-major (float4 j of Gaussian t at j * kProjBlock + t), where each
+// thread's 16-byte loads of its own coefficients are conflict-free; in the
+// Gaussian-major order of a plain copy (a 192-byte stride per thread) 8
+// threads of a phase meet only 2 of the 8 16-byte bank groups.
+//
+// Host: encodes the map, or returns false where the array is not 16-byte
+// aligned or the driver entry point is unavailable (the kernels then take
+// plain loads and stores).
+bool encode_sh_map(CUtensorMap* m, const float* base, int64_t N) {
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  if (!encode || !aligned16(base) || N <= 0) return false;
+  const cuuint64_t dims[2] = {48, static_cast<cuuint64_t>(N)};
+  const cuuint64_t strides[1] = {48 * sizeof(float)};
+  const cuuint32_t box[2] = {4, kProjBlock};
+  const cuuint32_t elem[2] = {1, 1};
+  return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, elem,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Box (x, y) of `map` into shared `dst`, completing on `bar` (rows past the
+// tensor's end are filled with zeros). x is a multiple of 4 floats.
+__device__ __forceinline__ void tma_load_box(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+// Shared `src` into box (x, y) of `map` (stored, or added to what is there);
+// rows past the tensor's end are not written.
+__device__ __forceinline__ void tma_store_box(const CUtensorMap* map, int x, int y, const void* src, bool add) {
+  if (add)
+    asm volatile("cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map),
+                 "r"(x), "r"(y), "r"(smem_u32(src))
+                 : "memory");
+  else
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map), "r"(x),
+                 "r"(y), "r"(smem_u32(src))
+                 : "memory");
+}
 // CTAs per SM the backward is compiled for (register cap 65536 / (128 x this)).
 #ifndef GS_PBWD_MIN_BLOCKS
 #define GS_PBWD_MIN_BLOCKS 4
@@ -310,9 +370,10 @@ __device__ __forceinline__ void view_dir(const gs_camera& cam, const float* mean
   dnorm = sqrtf(dvec[0] * dvec[0] + dvec[1] * dvec[1] + dvec[2] * dvec[2]);
 }
 
-// Shared-memory staging of one CTA's parameter slices.
-struct __align__(16) ParamSmem {
-  float4 sh[kProjBlock * 12];       // 24 KB
+// Shared-memory staging of one CTA's parameter slices (128-byte aligned for
+// the tensor copies into `sh`).
+struct __align__(128) ParamSmem {
+  float4 sh[kProjBlock * 12];       // 24 KB: Gaussian-major, or chunk-major (float4 j of Gaussian t at j * kProjBlock + t)
   float4 quats[kProjBlock];         // 2 KB
   float means[kProjBlock * 3];      // 1.5 KB
   float log_scales[kProjBlock * 3]; // 1.5 KB
@@ -322,7 +383,13 @@ struct __align__(16) ParamSmem {
 };
 
 // Loads the CTA's slice [g0, g0+n) of all parameter arrays and the cameras.
-// Full, aligned slices go through TMA bulk copies; others through plain loads.
+// Full, aligned slices go through TMA bulk copies; others through plain
+// loads. CM: the SH slice chunk-major, by the tensor copies of `tm_sh` (or
+// plain loads in that order), for kernels that re-read the coefficients in
+// every view. With one view they are read once, and the contiguous 24 KB
+// bulk copy of the Gaussian-major slice is the faster staging: the tensor
+// boxes' 16-byte rows at a 192-byte stride took the 4K projection 0.216 ->
+// 0.261 ms and its backward 0.452 -> 0.514 ms.
 // Optional extra bulk copies that join the parameter staging transaction.
 struct ExtraCopies {
   int n = 0;
@@ -337,10 +404,11 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
+template <bool CM>
 __device__ __forceinline__ void stage_params(ParamSmem& sm, const float* means, const float* log_scales,
                                              const float* quats, const float* opac, const float* sh, int64_t g0, int n,
-                                             const gs_camera* cams, int V, bool use_bulk, int32_t* status,
-                                             int64_t g_pf, const ExtraCopies& extra = ExtraCopies()) {
+                                             const gs_camera* cams, int V, bool use_bulk, const CUtensorMap* tm_sh,
+                                             int32_t* status, int64_t g_pf, const ExtraCopies& extra = ExtraCopies()) {
   const int tid = threadIdx.x;
   {
     const float* src = reinterpret_cast<const float*>(cams);
@@ -365,7 +433,11 @@ __device__ __forceinline__ void stage_params(ParamSmem& sm, const float* means, 
       bulk_g2s(sm.log_scales, log_scales + g0 * 3, b_means, &sm.bar);
       bulk_g2s(sm.quats, quats + g0 * 4, b_quat, &sm.bar);
       bulk_g2s(sm.opac, opac + g0, b_op, &sm.bar);
-      bulk_g2s(sm.sh, sh + g0 * 48, b_sh, &sm.bar);
+      if constexpr (CM) {
+        for (int j = 0; j < 12; ++j) tma_load_box(&sm.sh[j * kProjBlock], tm_sh, 4 * j, static_cast<int>(g0), &sm.bar);
+      } else {
+        bulk_g2s(sm.sh, sh + g0 * 48, b_sh, &sm.bar);
+      }
       // the slice of the CTA that will take this one's place: into L2 now,
       // so that its staging copies find it there
       if (g_pf >= 0) {
@@ -393,7 +465,10 @@ __device__ __forceinline__ void stage_params(ParamSmem& sm, const float* means, 
     }
     const float* shs = sh + g0 * 48;
     float* shd = reinterpret_cast<float*>(sm.sh);
-    for (int i = tid; i < n * 48; i += blockDim.x) shd[i] = shs[i];
+    for (int i = tid; i < n * 48; i += blockDim.x) {
+      const int g = i / 48, f = i - 48 * g;  // value f of Gaussian g
+      shd[CM ? ((f >> 2) * kProjBlock + g) * 4 + (f & 3) : i] = shs[i];
+    }
   }
   __syncthreads();
 }
@@ -445,34 +520,35 @@ __device__ __forceinline__ void pipelined_views(bool active, int V, int64_t N, i
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-struct __align__(16) ProjFwdSmem {
+struct __align__(128) ProjFwdSmem {
   ParamSmem p;
 };
 
 // Compiled for 5 resident CTAs per SM (at most 102 registers): 0.234 -> 0.225
 // ms at 4K against the unconstrained 124 registers (4 CTAs).
-template <int DEG>
+template <int DEG, bool CM>
 __global__ void __launch_bounds__(kProjBlock, 5) project_fwd_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ opac, const float* __restrict__ sh, int64_t N, const gs_camera* __restrict__ cams,
     const Layout L, const Consts K, float4* __restrict__ projected, short4* __restrict__ rects,
-    uint32_t* __restrict__ counts, uint32_t* __restrict__ depth_keys, int use_bulk, int64_t ahead, int32_t* status) {
+    uint32_t* __restrict__ counts, uint32_t* __restrict__ depth_keys, int use_bulk, int64_t ahead, int32_t* status,
+    const __grid_constant__ CUtensorMap tm_sh) {
   __shared__ ProjFwdSmem sm;
   const int tid = threadIdx.x;
   const int64_t g0 = static_cast<int64_t>(blockIdx.x) * kProjBlock;
   const int n = static_cast<int>(N - g0 < kProjBlock ? N - g0 : kProjBlock);
   const int64_t g_pf = (static_cast<int64_t>(blockIdx.x) + ahead) * kProjBlock;
-  stage_params(sm.p, means, log_scales, quats, opac, sh, g0, n, cams, L.V, use_bulk != 0, status,
-               ahead > 0 && g_pf + kProjBlock <= N ? g_pf : -1);
+  stage_params<CM>(sm.p, means, log_scales, quats, opac, sh, g0, n, cams, L.V, use_bulk != 0, &tm_sh, status,
+                   ahead > 0 && g_pf + kProjBlock <= N ? g_pf : -1);
   const bool active = tid < n;
   constexpr int NB = (DEG + 1) * (DEG + 1);
   GaussLocal G;
   float shc[3 * NB];
   if (active) {
     gauss_local(&sm.p.means[3 * tid], &sm.p.log_scales[3 * tid], sm.p.quats[tid], sm.p.opac[tid], G);
-    const float* s1 = reinterpret_cast<const float*>(&sm.p.sh[12 * tid]);
+    const float* s1 = reinterpret_cast<const float*>(sm.p.sh) + (CM ? 4 : 48) * tid;
 #pragma unroll
-    for (int i = 0; i < 3 * NB; ++i) shc[i] = s1[i];
+    for (int i = 0; i < 3 * NB; ++i) shc[i] = s1[CM ? (i >> 2) * (4 * kProjBlock) + (i & 3) : i];
   }
   for (int v = 0; v < L.V; ++v) {
     float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
@@ -524,13 +600,14 @@ __global__ void __launch_bounds__(kProjBlock, 5) project_fwd_kernel(
 // the per-thread pipeline; the single-view instance stages them with the
 // parameters (full slices) or reads them directly (the last, partial slice),
 // and keeps the registers the pipeline would take.
-template <int DEG, bool MULTI, bool SHT>
+template <int DEG, bool MULTI>
 __global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_kernel(
     const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ opac, const float* __restrict__ sh, int64_t N, const gs_camera* __restrict__ cams,
     const Layout L, const Consts K, const uint32_t* __restrict__ counts, const float* __restrict__ d_proj,
     float* __restrict__ d_means, float* __restrict__ d_log_scales, float* __restrict__ d_quats,
-    float* __restrict__ d_opac, float* __restrict__ d_sh, int use_bulk, int64_t ahead, int32_t* status) {
+    float* __restrict__ d_opac, float* __restrict__ d_sh, int use_bulk, int64_t ahead, int32_t* status,
+    const __grid_constant__ CUtensorMap tm_sh, const __grid_constant__ CUtensorMap tm_dsh, int store_tma) {
   constexpr int NB = (DEG + 1) * (DEG + 1);
   __shared__ ParamSmem sm_p;
   struct {
@@ -561,34 +638,17 @@ __global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_ke
     ex.pf_src[0] = d_proj + (pf ? g_pf : g0) * kDRecordFloats;
     ex.pf_src[1] = counts + (pf ? g_pf : g0);
   }
-  stage_params(sm.p, means, log_scales, quats, opac, sh, g0, n, cams, L.V, use_bulk != 0, status, pf ? g_pf : -1, ex);
-  // The SH slice arrives Gaussian-major (12 float4 per Gaussian, as in
-  // global memory), so a thread's 16-byte loads of its own coefficients have
-  // a 192-byte stride: 8 threads of a phase meet only 2 of the 8 16-byte
-  // bank groups (4-way conflicts). The colour pass re-reads them in every
-  // view that sees the Gaussian (on 16 views 77M of the 118M shared-load
-  // wavefronts were conflicts). With many views (SHT) the slice is
-  // transposed once to chunk-major order (float4 j of Gaussian t at
-  // j * kProjBlock + t), where those loads are conflict-free: 16 views
-  // 5.48 -> 4.64 ms. With few views most Gaussians are seen in few of them
-  // and the transpose costs more than it saves (the 4-view street workload
-  // 11.9 -> 13.8 ms), so those instances keep the staged layout.
-  static_assert(MULTI || !SHT, "the transposed layout is for several views");
-  if constexpr (SHT) {
-    float4 q[12];
-#pragma unroll
-    for (int j = 0; j < 12; ++j) q[j] = sm.p.sh[12 * tid + j];
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < 12; ++j) sm.p.sh[j * kProjBlock + tid] = q[j];
-    __syncthreads();
-  }
+  // the SH slice chunk-major with several views, Gaussian-major with one
+  stage_params<MULTI>(sm.p, means, log_scales, quats, opac, sh, g0, n, cams, L.V, use_bulk != 0, &tm_sh, status,
+                      pf ? g_pf : -1, ex);
   const bool active = tid < n;
   float gm[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, go = 0.f;
-  float4* my_sh4 = &sm.p.sh[12 * tid];
-  // coefficient f (0..47) of this thread's Gaussian in either layout
-  const float* shb = SHT ? reinterpret_cast<const float*>(sm.p.sh) + 4 * tid : reinterpret_cast<const float*>(my_sh4);
-  auto shc = [&](int f) -> float { return SHT ? shb[(f >> 2) * (4 * kProjBlock) + (f & 3)] : shb[f]; };
+  // coefficient f (0..47) of this thread's Gaussian: the colour pass
+  // re-reads them in every view that sees the Gaussian, and in the
+  // chunk-major slice a warp's 16-byte loads of one chunk cover 512
+  // contiguous bytes
+  const float* shb = reinterpret_cast<const float*>(sm.p.sh) + (MULTI ? 4 : 48) * tid;
+  auto shc = [&](int f) -> float { return shb[MULTI ? (f >> 2) * (4 * kProjBlock) + (f & 3) : f]; };
   // Pass 1: colour -> SH coefficients and view direction, over all views.
   // The coefficients are read from this thread's staging slot when needed
   // rather than held in registers, and the slot then takes the SH gradients;
@@ -641,19 +701,15 @@ __global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_ke
         colour_view(v, dp[5], dp[6], dp[7], dp[8]);
       }
     }
-    // SH gradients into the thread's own slot, Gaussian-major (coefficients
-    // past the degree get 0); stored to global memory, coalesced, at the end.
-    // After a transpose the slot belongs to other threads' coefficients,
-    // read until every thread has left the view loop. (Keeping the gradients
-    // chunk-major instead, with no barrier here and the final store reading
-    // through the index map, ran 4.72 ms on 16 views.)
-    if constexpr (SHT) __syncthreads();
+    // SH gradients into the thread's own slots of the slice (coefficients
+    // past the degree get 0), which only this thread reads; they leave at
+    // the end by tensor stores (or plain ones)
 #pragma unroll
     for (int i = 0; i < 12; ++i) {
       float q[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) q[k] = (4 * i + k < 3 * NB) ? gsh[(4 * i + k < 3 * NB) ? 4 * i + k : 0] : 0.0f;
-      my_sh4[i] = make_float4(q[0], q[1], q[2], q[3]);
+      sm.p.sh[MULTI ? i * kProjBlock + tid : 12 * tid + i] = make_float4(q[0], q[1], q[2], q[3]);
     }
   }
   // Pass 2: geometry (2D mean and conic -> mean, scales, rotation), over all views.
@@ -750,10 +806,27 @@ __global__ void __launch_bounds__(kProjBlock, GS_PBWD_MIN_BLOCKS) project_bwd_ke
       d_quats[4 * g + k] = (gq[k] - G.qn[k] * dotp) / qnorm + (acc ? d_quats[4 * g + k] : 0.0f);
     d_opac[g] = go + (acc ? d_opac[g] : 0.0f);
   }
-  __syncthreads();
-  float* dst = d_sh + g0 * 48;
-  const float* src = reinterpret_cast<const float*>(sm.p.sh);
-  for (int i = tid; i < n * 48; i += kProjBlock) dst[i] = src[i] + (acc ? dst[i] : 0.0f);
+  if (MULTI && store_tma) {
+    // the slice's 12 boxes by tensor stores (added to the gradients there
+    // when accumulating; rows past N are not written), issued once every
+    // thread's shared writes are visible to the copy engine; the issuing
+    // thread waits until they have been read out before the CTA exits
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      for (int j = 0; j < 12; ++j) tma_store_box(&tm_dsh, 4 * j, static_cast<int>(g0), &sm.p.sh[j * kProjBlock], acc);
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    }
+  } else {
+    __syncthreads();
+    float* dst = d_sh + g0 * 48;
+    const float* src = reinterpret_cast<const float*>(sm.p.sh);
+    for (int i = tid; i < n * 48; i += kProjBlock) {
+      const int g = i / 48, f = i - 48 * g;  // value f of Gaussian g
+      dst[i] = src[MULTI ? ((f >> 2) * kProjBlock + g) * 4 + (f & 3) : i] + (acc ? dst[i] : 0.0f);
+    }
+  }
 }
 
 }  // namespace
@@ -782,32 +855,31 @@ int64_t resident_ctas(F kernel) {
   return n;
 }
 
-// Views from which the projection backward takes the SH-transposed instance
-// (measured: faster on 16 views, slower on 4).
-constexpr int kShTransposeViews = 8;
-
 int launch_project_bwd(const float* means, const float* log_scales, const float* quats, const float* opacity_logits,
                        const float* sh, int64_t N, const gs_camera* cams, const Layout& L, const Consts& K,
                        const uint32_t* counts, const float* d_projected, float* d_means, float* d_log_scales,
                        float* d_quats, float* d_opacity_logits, float* d_sh, int32_t* status, cudaStream_t stream) {
   if (N == 0) return GS_OK;
+  // several views: the SH slice chunk-major, staged and stored by tensor
+  // copies where the arrays allow (tensor coordinates are 32-bit)
+  const bool cm = L.V > 1, small = N < (int64_t(1) << 31);
+  CUtensorMap tm_sh{}, tm_dsh{};
   const bool bulk = aligned16(means) && aligned16(log_scales) && aligned16(quats) && aligned16(opacity_logits) &&
-                    aligned16(sh);
+                    aligned16(sh) && (!cm || (small && encode_sh_map(&tm_sh, sh, N)));
+  const int store_tma = cm && small && encode_sh_map(&tm_dsh, d_sh, N) ? 1 : 0;
   // 2: the gradient records and counts can join the bulk staging too
   const int bulk_mode = !bulk ? 0 : (aligned16(d_projected) && aligned16(counts) ? 2 : 1);
   const unsigned blocks = static_cast<unsigned>((N + kProjBlock - 1) / kProjBlock);
-#define GS_PBWD_M(D, M, T)                                                                                         \
-  project_bwd_kernel<D, M, T><<<blocks, kProjBlock, 0, stream>>>(                                                   \
-      means, log_scales, quats, opacity_logits, sh, N, cams, L, K, counts, d_projected, d_means, d_log_scales,      \
-      d_quats, d_opacity_logits, d_sh, bulk_mode,                                                                  \
-      resident_ctas<10 + D + (M ? 4 : 0) + (T ? 4 : 0)>(project_bwd_kernel<D, M, T>), status)
-#define GS_PBWD(D)                      \
-  if (L.V >= kShTransposeViews)         \
-    GS_PBWD_M(D, true, true);           \
-  else if (L.V > 1)                     \
-    GS_PBWD_M(D, true, false);          \
-  else                                  \
-    GS_PBWD_M(D, false, false)
+#define GS_PBWD_M(D, M)                                                                                           \
+  project_bwd_kernel<D, M><<<blocks, kProjBlock, 0, stream>>>(                                                     \
+      means, log_scales, quats, opacity_logits, sh, N, cams, L, K, counts, d_projected, d_means, d_log_scales,     \
+      d_quats, d_opacity_logits, d_sh, bulk_mode, resident_ctas<10 + D + (M ? 4 : 0)>(project_bwd_kernel<D, M>),   \
+      status, tm_sh, tm_dsh, store_tma)
+#define GS_PBWD(D)          \
+  if (L.V > 1)              \
+    GS_PBWD_M(D, true);     \
+  else                      \
+    GS_PBWD_M(D, false)
   switch (K.sh_degree) {
     case 0: GS_PBWD(0); break;
     case 1: GS_PBWD(1); break;
@@ -835,22 +907,32 @@ extern "C" int gs_project(const float* means, const float* log_scales, const flo
   if (!means || !log_scales || !quats || !opacity_logits || !sh || !cams_dev || !projected || !rects || !counts)
     return GS_ERR_ARG;
   if (!aligned16(projected) || (reinterpret_cast<uintptr_t>(rects) & 7u)) return GS_ERR_ARG;
+  // several views: the SH slice chunk-major, staged by tensor copies where
+  // the array allows (tensor coordinates are 32-bit)
+  const bool cm = L.V > 1;
+  CUtensorMap tm_sh{};
   const bool bulk = aligned16(means) && aligned16(log_scales) && aligned16(quats) && aligned16(opacity_logits) &&
-                    aligned16(sh);
+                    aligned16(sh) && (!cm || (N < (int64_t(1) << 31) && encode_sh_map(&tm_sh, sh, N)));
   const unsigned blocks = static_cast<unsigned>((N + kProjBlock - 1) / kProjBlock);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const Consts K = make_consts(*cfg);
-#define GS_PFWD(D)                                                                                               \
-  project_fwd_kernel<D><<<blocks, kProjBlock, 0, st>>>(means, log_scales, quats, opacity_logits, sh, N, cams_dev, L, K, \
-                                                       reinterpret_cast<float4*>(projected),                           \
-                                                       reinterpret_cast<short4*>(rects), counts, depth_keys,            \
-                                                       bulk ? 1 : 0, resident_ctas<D>(project_fwd_kernel<D>), status_dev)
+#define GS_PFWD_C(D, C)                                                                                     \
+  project_fwd_kernel<D, C><<<blocks, kProjBlock, 0, st>>>(                                                        \
+      means, log_scales, quats, opacity_logits, sh, N, cams_dev, L, K, reinterpret_cast<float4*>(projected),      \
+      reinterpret_cast<short4*>(rects), counts, depth_keys, bulk ? 1 : 0,                                         \
+      resident_ctas<D + (C ? 4 : 0)>(project_fwd_kernel<D, C>), status_dev, tm_sh)
+#define GS_PFWD(D)         \
+  if (cm)                  \
+    GS_PFWD_C(D, true);    \
+  else                     \
+    GS_PFWD_C(D, false)
   switch (cfg->sh_degree) {
     case 0: GS_PFWD(0); break;
     case 1: GS_PFWD(1); break;
     case 2: GS_PFWD(2); break;
     default: GS_PFWD(3); break;
   }
+#undef GS_PFWD_C
 #undef GS_PFWD
   return cuda_status(cudaGetLastError());
 }

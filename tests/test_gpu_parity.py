@@ -354,3 +354,35 @@ def test_forward_with_l1l2_loss(oracle, idx):
     # the mean must cover at least this call's values
     with pytest.raises(_native.GSError):
         R.rasterize_fwd_l1l2(fb, tgt, P * 3 - 1, w1, w2, False, dlb, lb)
+
+
+@pytest.mark.parametrize("N", [1000, 777])
+def test_accumulated_backward_adds(N):
+    """A backward with GS_FLAG_ACCUMULATE_GRADS adds its gradients to those in
+    the output arrays. With N = 1000 the SH gradient array is 16-byte aligned
+    and leaves the projection backward by tensor reduce-adds; with N = 777 it
+    is not and takes plain loads and stores."""
+    import torch
+
+    from paper_2606_11390_gb300 import renderer as R
+
+    s = scenes.random_small(106, N=N, width=96, height=64, n_views=2, spread=1.5)
+    params = R.FlatParams(N).load_from(s)
+    cams = R.Cameras(s["cams"], s["sizes"])
+    frame = R.Frame(N, cams, dict(s["cfg"]))
+    R.render(params, cams, frame)
+    rng = np.random.default_rng(3)
+    dl = torch.from_numpy(rng.standard_normal(frame.image.numel()).astype(np.float32) / 1e3).cuda()
+    fresh = params.like()
+    R.rasterize_bwd(params, cams, frame, dl, fresh)
+    summed = params.like()
+    base = torch.from_numpy(rng.standard_normal(summed.flat.numel()).astype(np.float32)).cuda()
+    summed.flat.copy_(base)
+    R.rasterize_bwd(params, cams, frame, dl, summed, accumulate=True)
+    torch.cuda.synchronize()
+    assert frame.read_status() == 0
+    want = base.cpu().numpy().astype(np.float64) + to_np(fresh.flat).astype(np.float64)
+    got = to_np(summed.flat).astype(np.float64)
+    # the two backward calls may sum their atomics in another order
+    np.testing.assert_allclose(got, want, rtol=1e-5, atol=1e-6)
+    assert np.abs(to_np(fresh["sh"])).max() > 0
