@@ -827,7 +827,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_super_kernel(
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
     const uint64_t out_base = s_off[g * 32];
     const uint32_t le_mask = 0xffffffffu >> (31 - lane);  // bits 0..lane
-    uint32_t started = 0;  // records (lanes) whose entries start before this round
+    uint32_t started = 0;  // records (lanes) whose entries start before this group of 32 entries
     for (uint32_t eb = 0; eb < total; eb += 32) {
       // bit i: a record's first entry is entry eb + i (counts are >= 1, so
       // the starts are distinct); the record of entry eb + lane is the last
