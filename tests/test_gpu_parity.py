@@ -40,6 +40,9 @@ def _scenes():
     # 9 views take the projection backward whose SH slice is transposed in
     # shared memory; 1000 Gaussians leave a partial last slice
     yield "nine_views", scenes.random_small(105, N=1000, width=64, height=48, n_views=9, spread=1.5)
+    # several views at SH degree 2: the tensor copies move all 48 coefficients
+    # and the backward writes zeros past the degree (640: full slices only)
+    yield "sh_deg2_3view", scenes.random_small(107, N=640, width=80, height=60, n_views=3, spread=1.5, sh_degree=2)
     s = scenes.random_small(110, N=900, width=150, height=100, n_views=2, spread=1.5)
     s["cfg"] = scenes.make_cfg(flags=2)  # two pixels per rasteriser thread
     yield "two_px_per_thread", s
