@@ -99,8 +99,9 @@ typedef struct gs_camera {
  * shared-memory batch in the forward / backward, 0 for the default
  * (forward: max(threads per tile, 128); backward: threads per tile, clamped
  * to [64, 256]) or one of 64, 128, 256, 512 (GS_ERR_UNSUPPORTED otherwise;
- * the backward takes 512 only for tiles of at most 128 threads, whose shared
- * memory it fits); a performance choice only, results are the same (with a
+ * a backward batch whose staging exceeds 48 KB of shared memory, as 512 on
+ * tiles of more than 4 warps, is launched with the opt-in for more); a
+ * performance choice only, results are the same (with a
  * non-zero bg the backward keeps its default). Threads per tile = tile_w *
  * tile_h / pixels per thread (see GS_FLAG_RASTER_2PX). */
 typedef struct gs_config {

@@ -6,8 +6,7 @@ rasteriser's launch configuration:
   owns (2 or 4, so threads per tile = tile area / pixels per thread; 8x8 tiles
   take 2 only);
 - splats staged per shared-memory batch in the forward (64, 128, 256, 512);
-- splats staged per shared-memory batch in the backward (64, 128, 256, and
-  512 for tiles of at most 128 threads).
+- splats staged per shared-memory batch in the backward (64, 128, 256, 512).
 The search is coordinate descent: every tile shape and pixels per thread at
 the default batch sizes, then the forward batch at the best of those, then
 the backward batch; at most 15 timed configurations instead of the 150 of
@@ -98,9 +97,12 @@ def threads_per_tile(c: dict) -> int:
 
 
 def batch_supported(c: dict, dim: str, b: int) -> bool:
-    """Whether the library has the variant: a 512-splat backward batch only
-    fits the shared memory of tiles of at most 128 threads."""
-    return not (dim == "batch_bwd" and b == 512 and threads_per_tile(c) > 128)
+    """Whether the library has the variant: the backward's batch must fit a
+    CTA's shared memory (b x (80 + 2 x warps) + 4 x warps bytes, with an
+    opt-in above 48 KB up to 227 KB), which every batch size does on every
+    tile; the forward's always does."""
+    warps = threads_per_tile(c) // 32
+    return dim != "batch_bwd" or b * (80 + 2 * warps) + 4 * warps <= 227 * 1024
 
 
 def search(measure, tiles=TILES, batches=BATCHES):

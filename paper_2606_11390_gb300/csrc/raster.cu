@@ -29,10 +29,10 @@ inline int pixels_per_thread(const Layout& L, const Consts& K) {
 // 0 (the default) or a batch size the kernels are instantiated for.
 inline bool valid_batch(int32_t b) { return b == 0 || b == 64 || b == 128 || b == 256 || b == 512; }
 
-// The backward's 512-splat batch exists only for layouts whose shared memory
-// it fits (at most 4 warps per tile).
+// The backward's batch must fit a CTA's shared memory (opted in above
+// 48 KB); every batch size does on every layout.
 inline bool bwd_batch_fits(const Layout& L, int ppt, int32_t b) {
-  return b != 512 || rast::bwd_smem_bytes(512, L.tile_w * L.tile_h / ppt / 32) <= rast::kStaticSmem;
+  return b == 0 || rast::bwd_smem_bytes(b, L.tile_w * L.tile_h / ppt / 32) <= rast::kMaxSmem;
 }
 
 template <int TW, int TH, int PPT>
@@ -59,9 +59,7 @@ int bwd_variant(int32_t batch, bool bg, bool count, const BwdArgs& a, cudaStream
   if (b == 64) return rast::launch_bwd<TW, TH, PPT, 64, false, false>(a, s);
   if (b == 128) return rast::launch_bwd<TW, TH, PPT, 128, false, false>(a, s);
   if (b == 256) return rast::launch_bwd<TW, TH, PPT, 256, false, false>(a, s);
-  if constexpr (rast::bwd_smem_bytes(512, TW * TH / PPT / 32) <= rast::kStaticSmem) {
-    if (b == 512) return rast::launch_bwd<TW, TH, PPT, 512, false, false>(a, s);
-  }
+  if (b == 512) return rast::launch_bwd<TW, TH, PPT, 512, false, false>(a, s);
   return GS_ERR_UNSUPPORTED;
 }
 

@@ -654,15 +654,24 @@ __global__ void __launch_bounds__(TW* TH / PPT, bwd_min_ctas(TW* TH / PPT, PPT))
   using Gm = Geo<TW, TH, PPT>;
   constexpr int NT = Gm::NT, NW = Gm::NW;
   static_assert(B >= 32 && B <= 512 && (B & (B - 1)) == 0, "splats per batch: a power of two in [32, 512]");
-  static_assert(bwd_smem_bytes(B, NW) <= kStaticSmem, "backward shared memory over 48 KB");
-  __shared__ float4 s_a[B];
-  __shared__ float4 s_b[B];
-  __shared__ float s_c[B];
-  __shared__ uint32_t s_m[B];
-  __shared__ uint32_t s_vg[B];
-  __shared__ float s_grad[B * 9];
-  __shared__ uint32_t s_wmax[NW];
-  __shared__ uint16_t s_list[NW][B];  // per warp: the staged splats that can touch its block
+  static_assert(bwd_smem_bytes(B, NW) <= kMaxSmem, "backward shared memory over the opt-in limit");
+  // the staged batch, its gradient slots, the warps' bounds and lists:
+  // static shared memory up to 48 KB, above it dynamic (opted in by
+  // launch_bwd). The static size also steers the compiler's register choice
+  // (as dynamic memory the 16x16 2-pixel instance took 64 registers and
+  // spilled instead of 70).
+  constexpr bool kDyn = bwd_smem_bytes(B, NW) > kStaticSmem;
+  __shared__ __align__(16) unsigned char bwd_smem_st[kDyn ? 16 : bwd_smem_bytes(B, NW)];
+  extern __shared__ __align__(16) unsigned char bwd_smem_dyn[];
+  unsigned char* bwd_smem = kDyn ? bwd_smem_dyn : bwd_smem_st;
+  float4* s_a = reinterpret_cast<float4*>(bwd_smem);
+  float4* s_b = s_a + B;
+  float* s_c = reinterpret_cast<float*>(s_b + B);
+  uint32_t* s_m = reinterpret_cast<uint32_t*>(s_c + B);
+  uint32_t* s_vg = s_m + B;
+  float* s_grad = reinterpret_cast<float*>(s_vg + B);
+  uint32_t* s_wmax = reinterpret_cast<uint32_t*>(s_grad + 9 * B);
+  uint16_t(*s_list)[B] = reinterpret_cast<uint16_t(*)[B]>(s_wmax + NW);  // per warp: the staged splats that can touch its block
   // CTA i takes tile order[i] (longest lists first) when an order is given
   const uint32_t tile = order ? order[blockIdx.x] : blockIdx.x;
   if (tile >= L.n_tiles) return;
@@ -817,7 +826,14 @@ int launch_fwd(const FwdArgs& a, cudaStream_t stream) {
 
 template <int TW, int TH, int PPT, int B, bool BG, bool COUNT>
 int launch_bwd(const BwdArgs& a, cudaStream_t stream) {
-  raster_bwd_kernel<TW, TH, PPT, B, BG, COUNT><<<static_cast<unsigned>(a.L.n_tiles), TW * TH / PPT, 0, stream>>>(
+  // above 48 KB the shared memory is dynamic and the kernel opted in (set
+  // on every call: the attribute belongs to the current device)
+  constexpr int bytes = bwd_smem_bytes(B, TW * TH / PPT / 32);
+  constexpr int dyn = bytes > kStaticSmem ? bytes : 0;
+  if (dyn && cudaFuncSetAttribute(raster_bwd_kernel<TW, TH, PPT, B, BG, COUNT>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) != cudaSuccess)
+    return GS_ERR_CUDA;
+  raster_bwd_kernel<TW, TH, PPT, B, BG, COUNT><<<static_cast<unsigned>(a.L.n_tiles), TW * TH / PPT, dyn, stream>>>(
       a.projected, a.vals, a.ranges, a.order, a.L, a.K, a.final_T, a.last, a.dL_dimage, a.d_proj, a.counts, a.cull);
   return cuda_status(cudaGetLastError());
 }

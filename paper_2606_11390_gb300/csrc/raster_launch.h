@@ -40,12 +40,14 @@ constexpr int default_batch_bwd() {
   return NT < 64 ? 64 : (NT > 256 ? 256 : NT);
 }
 
-// Static shared memory of one CTA with B splats per batch and NW warps; the
-// kernels keep it within the 48 KB a CTA gets without an opt-in, so a batch
-// of 512 exists for every forward and for backwards of at most 4 warps.
+// Shared memory of one CTA with B splats per batch and NW warps. The forward
+// keeps it within the 48 KB a CTA gets without an opt-in; the backward's is
+// static up to that and dynamic above it (512 splats on tiles of more than 4
+// warps: 49 KB at 32x32 tiles and 4 pixels a thread), up to kMaxSmem.
 constexpr int fwd_smem_bytes(int B, int NW) { return B * (40 + 2 * NW); }
 constexpr int bwd_smem_bytes(int B, int NW) { return B * (80 + 2 * NW) + 4 * NW; }
 constexpr int kStaticSmem = 48 * 1024;
+constexpr int kMaxSmem = 227 * 1024;  // a CTA's opt-in limit
 
 // Arguments of one forward / backward launch (unpacked into the kernels'
 // parameters, so the kernels read them from parameter space as before).

@@ -20,28 +20,30 @@ def test_search_walks_each_dimension_once():
     calls = []
     best, times = autotune.search(_fake_measure({("f", 256): -0.3, ("b", 64): -0.2, ("b", 128): -0.1}, calls))
     assert best == {"tile": (32, 16), "ppt": 4, "batch_fwd": 256, "batch_bwd": 64}
-    # 7 tile / pixel choices + 4 forward + 4 backward batches (32x16 at 4 px
-    # has 128 threads, so its backward takes 512)
+    # 7 tile / pixel choices + 4 forward + 4 backward batches
     assert len(calls) == len(set(calls)) == 15
     assert set(times) == set(calls)
     assert min(times, key=times.get) == autotune.name(best)
 
 
-def test_no_512_backward_batch_on_large_tiles():
-    """A 512-splat backward batch is only tried where the library has it:
-    tiles of at most 128 threads."""
+def test_512_backward_batch_on_large_tiles():
+    """A 512-splat backward batch is tried on 256-thread tiles too (its 49 KB
+    of staging is opted in) and can win there; the shared-memory rule admits
+    every batch size on every tile."""
     calls = []
 
     def measure(c):
         calls.append(c)
-        return (1.0 if c["tile"] == (32, 32) and c["ppt"] == 4 else 9.0) - (0.5 if c["batch_fwd"] == 512 else 0.0)
+        return (1.0 if c["tile"] == (32, 32) and c["ppt"] == 4 else 9.0) - (0.5 if c["batch_bwd"] == 512 else 0.0)
 
     best, _ = autotune.search(measure)
-    assert best["tile"] == (32, 32) and best["ppt"] == 4 and best["batch_fwd"] == 512
-    assert not any(c["batch_bwd"] == 512 for c in calls)
-    assert autotune.batch_supported({"tile": (32, 16), "ppt": 4}, "batch_bwd", 512)
-    assert not autotune.batch_supported({"tile": (32, 16), "ppt": 2}, "batch_bwd", 512)
-    assert autotune.batch_supported({"tile": (32, 32), "ppt": 2}, "batch_fwd", 512)
+    assert best == {"tile": (32, 32), "ppt": 4, "batch_fwd": 0, "batch_bwd": 512}
+    assert any(c["batch_bwd"] == 512 for c in calls)
+    for tile in autotune.TILES:
+        for ppt in (2, 4):
+            for b in autotune.BATCHES:
+                for dim in ("batch_fwd", "batch_bwd"):
+                    assert autotune.batch_supported({"tile": tile, "ppt": ppt}, dim, b)
 
 
 def test_defaults_win_when_nothing_is_faster():
